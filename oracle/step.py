@@ -1,0 +1,188 @@
+"""One full ADER-DG + a-posteriori subcell-limiter time step (oracle).
+
+Sec. 4.4, the five acts, plus the neighbour flux correction that follows them:
+  1. unlimited ADER-DG candidate u* (dg.predictor, dg.corrector);
+  2. scatter v* = P(u*);
+  3. detection (PAD + relaxed DMP) against bounds from v^n over V_i, where
+     v^n = P(u^n) if beta^n = 0 and the stored A(v^{n-1}) if beta^n = 1
+     (Eq. ader.icbc) -> beta^{n+1};
+  4. troubled cells (beta^{n+1} = 1) are recomputed from v^n on the subgrid by
+     the ADER-WENO3 operator A, with ghost data from V_i built the same way;
+  5. gather u^{n+1} = R(v^{n+1}) for troubled cells; v^{n+1} is kept for the
+     next step.
+Each zone is decremented at most once (no MOOD cascade).  Unlimited cells that
+share a face with a troubled cell have their DG face flux on that face
+replaced by the sub-face ADER-WENO fluxes (flux correction of Sec. 4.4): with
+the sub-face flux constant on each sub-face, the exact integral against the
+test function gives, at tangential node b,
+    Fsub_b = (1 / W_b) sum_e Fbar_e prod_j P1[e_j, b_j] / N_s^{d-1}
+and the correction  -(dt/dx)(phi_a(1)/w_a)(Fsub_b - Gbar_b)  on a high face,
++(dt/dx)(phi_a(0)/w_a)(Fsub_b - Gbar_b) on a low face.  Corrected neighbours
+are not detected again.
+
+Subgrid ghost data at a transmissive boundary: the global subcell index is
+clamped into the domain (constant extrapolation of the boundary subcell).
+"""
+import numpy as np
+
+from . import detect as det
+from . import dg
+from .basis import Basis
+from .subcell import projection_matrix, project, reconstruct, reconstruction_matrix
+from .weno import ader_weno
+
+
+class Scheme:
+    """Fixed operators of one (grid, N, gamma) configuration."""
+
+    def __init__(self, grid, N, gamma, eps=det.EPS, floor=det.FLOOR, n_iter=None):
+        self.grid = grid
+        self.N = N
+        self.gamma = gamma
+        self.basis = Basis(N)
+        self.Ns = 2 * N + 1
+        self.P1 = projection_matrix(self.basis, self.Ns)
+        self.R1 = reconstruction_matrix(self.P1)
+        self.eps = eps
+        self.floor = floor
+        self.n_iter = N + 1 if n_iter is None else n_iter
+
+    @property
+    def dim(self):
+        return self.grid.dim
+
+    def P(self, U):
+        return project(U, self.P1, self.dim)
+
+    def R(self, V):
+        return reconstruct(V, self.R1, self.dim)
+
+
+class State:
+    """u (nvar, cells..., n^d nodes), beta (cells...), Vs (nvar, cells..., N_s^d)
+    holding v^n for cells with beta = 1 (NaN elsewhere)."""
+
+    def __init__(self, U, beta, Vs):
+        self.U = U
+        self.beta = beta
+        self.Vs = Vs
+
+    def copy(self):
+        return State(self.U.copy(), self.beta.copy(), self.Vs.copy())
+
+
+def subcell_data(sch, st):
+    """v^n for every cell (Eq. ader.icbc)."""
+    Vp = sch.P(st.U)
+    sel = (slice(None),) + (st.beta == 1,)
+    Vp[sel] = st.Vs[sel]
+    return Vp
+
+
+def stable_dt(sch, st, cfl):
+    """Eq. (cfl) evaluated on the subcell data v^n of every cell."""
+    return dg.max_dt(subcell_data(sch, st), sch.grid, sch.gamma, cfl)
+
+
+def global_subgrid(V, dim):
+    """(nvar, cells..., Ns...) -> (nvar, n_1*Ns, ..., n_d*Ns)."""
+    nv = V.shape[0]
+    cells = V.shape[1:1 + dim]
+    Ns = V.shape[-1]
+    order = [0]
+    for k in range(dim):
+        order += [1 + k, 1 + dim + k]
+    G = np.transpose(V, order)
+    return G.reshape((nv,) + tuple(c * Ns for c in cells))
+
+
+def patch(sch, G, cell):
+    """(nvar, L, .., L) subgrid patch around `cell` (local -3..N_s+2)."""
+    Ns = sch.Ns
+    idx = []
+    for k in range(sch.dim):
+        nk = sch.grid.ncell[k] * Ns
+        g = cell[k] * Ns - 3 + np.arange(Ns + 6)
+        g = np.mod(g, nk) if sch.grid.periodic(k) else np.clip(g, 0, nk - 1)
+        idx.append(g)
+    return G[(slice(None),) + np.ix_(*idx)]
+
+
+def neighbour(sch, cell, k, side):
+    """Face neighbour of `cell` along axis k (side -1 low, +1 high), or None."""
+    c = list(cell)
+    c[k] += side
+    nk = sch.grid.ncell[k]
+    if c[k] < 0 or c[k] >= nk:
+        if not sch.grid.periodic(k):
+            return None
+        c[k] %= nk
+    return tuple(c)
+
+
+def step(sch, st, dt, force_all=False):
+    """Advance `st` by dt; returns (new state, info dict)."""
+    g, gam, b, d = sch.grid, sch.gamma, sch.basis, sch.dim
+    U = st.U
+    # act 1: unlimited candidate
+    q = dg.predictor(U, [dt / g.dx[k] for k in range(d)], b, dg.euler_flux_fn(gam), sch.n_iter)
+    Ustar, Gbar = dg.corrector(U, q, dt, b, g, gam)
+    # act 2 + 3: scatter and detect against bounds from v^n over V_i
+    Vn = subcell_data(sch, st)
+    cmin, cmax = det.cell_minmax(Vn, d)
+    m, M = det.neighbourhood_bounds(cmin, cmax, g)
+    vstar = sch.P(Ustar)
+    beta = det.detect(vstar, m, M, gam, d, sch.eps, sch.floor)
+    if force_all:
+        beta[...] = 1
+    Unew = Ustar.copy()
+    Vs_new = np.full((U.shape[0],) + g.ncell + (sch.Ns,) * d, np.nan)
+    troubled = [tuple(int(x) for x in c) for c in np.argwhere(beta == 1)]
+    info = {"troubled": len(troubled), "beta": beta.copy(), "m": m, "M": M,
+            "vstar": vstar, "Ustar": Ustar.copy(), "fixed": 0}
+    if not troubled:
+        return State(Unew, beta, Vs_new), info
+    # act 4: subcell ADER-WENO3 from v^n
+    G = global_subgrid(Vn, d)
+    patches = np.stack([patch(sch, G, c) for c in troubled], axis=1)
+    h = [g.dx[k] / sch.Ns for k in range(d)]
+    vnew, faces = ader_weno(patches, dt, h, gam, d)
+    # act 5: gather, keep v^{n+1}
+    for t, c in enumerate(troubled):
+        sel = (slice(None),) + c
+        Vs_new[sel] = vnew[:, t]
+        Unew[sel] = sch.R(vnew[:, t])
+    # flux correction of unlimited face neighbours
+    Mt = (sch.P1.T / sch.Ns) / b.w[:, None]            # Mt[b, e] = P1[e, b] / (N_s w_b)
+    fixed = 0
+    for t, c in enumerate(troubled):
+        for k in range(d):
+            for side in (-1, 1):
+                nb = neighbour(sch, c, k, side)
+                if nb is None or beta[nb] == 1:
+                    continue
+                # faces[k] = (low, high) of the troubled cell; the neighbour on
+                # the troubled cell's low side sees it through its own high face
+                Fsub = faces[k][0 if side == -1 else 1][:, t]
+                for j in range(d - 1):
+                    Fsub = dg.along(Mt, Fsub, 1 + j)
+                # DG face flux on the same face (faces indexed 0..n_k along axis k)
+                fidx = c[k] if side == -1 else c[k] + 1
+                gsel = [slice(None)] + list(c)
+                gsel[1 + k] = fidx
+                Gdg = Gbar[k][tuple(gsel)]                 # (nvar, tangential nodes)
+                diff = Fsub - Gdg
+                node_axis = 1 + k                           # node axis k in (nvar, nodes...)
+                shape = [1] * (1 + d)
+                shape[node_axis] = b.n
+                diff = np.expand_dims(diff, node_axis)
+                cdt = dt / g.dx[k]
+                if side == -1:   # neighbour below: its high face
+                    corr = -cdt * (b.phi1 / b.w).reshape(shape) * diff
+                else:            # neighbour above: its low face
+                    corr = cdt * (b.phi0 / b.w).reshape(shape) * diff
+                Unew[(slice(None),) + nb] += corr
+                fixed += 1
+    info["faces"] = faces
+    info["fixed"] = fixed
+    return State(Unew, beta, Vs_new), info
