@@ -1,0 +1,190 @@
+/*
+ * adg.h -- C ABI of libadg: one ADER-DG time step with a-posteriori subcell
+ * (MOOD) limiting for the compressible Euler equations on 2D/3D Cartesian
+ * grids, after Dumbser, Zanotti, Loubere, Diot, "A posteriori subcell limiting
+ * of the discontinuous Galerkin finite element method for hyperbolic
+ * conservation laws" (arXiv 1406.7416).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns int: 0 = ADG_OK, < 0 an error, > 0 a warning.  No C++
+ *     exception crosses this boundary.  adg_last_error() gives the message of
+ *     the last failed call on a state.
+ *   - The library owns all device memory of a state; the caller owns every
+ *     host buffer it passes (read during the call only, never retained).
+ *   - Work is enqueued on the state's CUDA stream (adg_set_stream; default:
+ *     the legacy default stream).  Calls that copy to the host synchronize that
+ *     stream before returning; adg_step does not synchronize.
+ *   - Host array layouts (double unless stated):
+ *       cell index   c = i + n0 * (j + n1 * k)          (x fastest)
+ *       node index   l = a + n * (b + n * c3)           (x fastest), n = N + 1
+ *       subcell idx  s = sx + Ns * (sy + Ns * sz)       (x fastest), Ns = 2N + 1
+ *       DOFs         dofs[c][v][l],  v = 0..nvar-1, nvar = dim + 2
+ *                    (rho, rho*u, rho*v, [rho*w], rho*E), nodal values at the
+ *                    tensor Gauss-Legendre points of each cell (Sec. 2.1
+ *                    Eq. ansatz.uh)
+ *       subcells     sub[c][v][s]: subcell averages (Sec. 4.2 Eq. subcell.p)
+ *       flags        beta[c]: uint8, 1 = troubled cell (Sec. 4.3)
+ *
+ * Precision modes (adg_create `prec`)
+ *   ADG_PREC_FP64        every step of the path in FP64.
+ *   ADG_PREC_MIXED_FP32  predictor Picard sweeps in FP32 except the last one,
+ *                        which runs in FP64; corrector, detector, projections
+ *                        and the subcell limiter stay FP64.
+ */
+#ifndef ADG_H
+#define ADG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADG_OK 0
+#define ADG_ERR_ARG (-1)          /* invalid argument or call order          */
+#define ADG_ERR_OOM (-2)          /* device allocation failed                */
+#define ADG_ERR_CUDA (-3)         /* a CUDA runtime call failed              */
+#define ADG_ERR_TIMEOUT (-4)      /* a bounded device wait gave up           */
+#define ADG_ERR_CAPACITY (-5)     /* more troubled cells than subcell slots  */
+#define ADG_ERR_STATE (-6)        /* no admissible wave speed (dt undefined) */
+#define ADG_WARN_SUBCELL_INADMISSIBLE 1 /* a subcell average left the
+                                           admissible set after the limiter */
+
+#define ADG_BC_PERIODIC 0
+#define ADG_BC_TRANSMISSIVE 1
+
+#define ADG_PREC_FP64 0
+#define ADG_PREC_MIXED_FP32 1
+
+/* adg_set_option keys */
+#define ADG_OPT_DMP_EPS 1         /* eps of Eq. (relax), default 1e-3                 */
+#define ADG_OPT_DMP_FLOOR 2       /* floor of delta, default 1e-4 (relative to
+                                     max(1,|M|,|m|)); 0 gives the literal Eq. (relax) */
+#define ADG_OPT_FORCE_LIMITER 3   /* 1: flag every cell every step (testing)          */
+#define ADG_OPT_PICARD_ITERS 4    /* Picard sweeps of Eq. (pde.nc.dg2), default N+1   */
+#define ADG_OPT_SLOT_CAPACITY 5   /* max troubled cells per step (before first load)  */
+#define ADG_OPT_PROFILE 6         /* 1: time the phases of every step with CUDA events */
+
+/* Cartesian grid (Sec. 2.1): cells n[k] of size dx[k] from corner x0[k]. */
+typedef struct {
+  int dim;        /* 2 or 3 */
+  int n[3];       /* cells per axis; n[2] ignored for dim == 2 */
+  double x0[3];   /* lower corner */
+  double dx[3];   /* cell size per axis */
+} adg_grid;
+
+/* Test-problem initial data (Sec. 5.2, 5.6, 5.8), projected on the device by
+ * adg_init_problem.  States are primitive: (rho, u, v, [w], p). */
+#define ADG_IC_RADIAL 0   /* inner state for |x - center| <= radius, else outer */
+#define ADG_IC_QUADRANT 1 /* 2D: state 1 x>xc,y>yc; 2 x<=xc,y>yc; 3 x<=xc,y<=yc; 4 x>xc,y<=yc */
+typedef struct {
+  int kind;
+  double center[3];
+  double radius;
+  double inner[5];
+  double outer[5];
+  double quad[4][4];              /* (rho, u, v, p) of quadrants 1..4            */
+  int vortex;                     /* 1: superpose the isentropic vortex          */
+  double vortex_center[2];
+  double vortex_strength;         /* beta of Sec. 5.2                            */
+  const double* cell_rho_factor;  /* host [cells] density factor, or NULL        */
+} adg_problem;
+
+typedef struct adg_state adg_state;
+
+/* Create a solver state for `grid`, polynomial degree N (1..9 in 2D, 1..3 in
+ * 3D), ideal-gas gamma > 1, boundary kind per face bc[2*k] (low side of axis
+ * k), bc[2*k+1] (high side): periodic faces must come in pairs.  No device
+ * memory is touched until the first load.  Errors: ADG_ERR_ARG. */
+int adg_create(const adg_grid* grid, int N, double gamma, const int* bc, int prec,
+               adg_state** out);
+
+/* Device allocator used for every buffer of this state (call before the first
+ * load).  alloc(bytes, ctx) returns a device pointer or NULL; free(ptr, ctx).
+ * Default: cudaMalloc / cudaFree. */
+int adg_set_allocator(adg_state* st, void* (*alloc)(size_t, void*),
+                      void (*free_fn)(void*, void*), void* ctx);
+
+/* CUDA stream (a cudaStream_t passed as void*) for all work of this state. */
+int adg_set_stream(adg_state* st, void* stream);
+
+/* Numerical options, keys ADG_OPT_*.  Errors: ADG_ERR_ARG. */
+int adg_set_option(adg_state* st, int key, double value);
+
+/* Load the DG DOFs (host dofs[cells][nvar][n^dim]) as u^n.  With
+ * exact_subcell_avgs (host sub[cells][nvar][Ns^dim]) the detector of Sec. 4.3
+ * is applied to P(u^0) against bounds from the exact averages (Sec. 4.4, last
+ * paragraph); flagged cells keep the exact averages as subcell data and their
+ * DOFs become R(exact averages).  With NULL every cell starts unflagged.
+ * Errors: ADG_ERR_ARG, ADG_ERR_OOM, ADG_ERR_CUDA, ADG_ERR_CAPACITY. */
+int adg_load(adg_state* st, const double* dofs, const double* exact_subcell_avgs);
+
+/* Project a test problem on the device: composite Gauss-Legendre rule of
+ * Ns subintervals x (N+2) points per axis and cell for the L2 projection and
+ * the exact subcell averages, then the same initial detection as adg_load. */
+int adg_init_problem(adg_state* st, const adg_problem* problem);
+
+/* Load / read a complete state (checkpoint-resume and testing): DOFs, flags
+ * and the subcell data of flagged cells (host sub[cells][nvar][Ns^dim]; rows
+ * of unflagged cells are ignored on load and written as NaN on read). */
+int adg_load_full(adg_state* st, const double* dofs, const uint8_t* beta,
+                  const double* subcells);
+int adg_read_full(adg_state* st, double* dofs, uint8_t* beta, double* subcells);
+
+/* One full time step of size dt > 0 (Sec. 4.4): predictor (Eq. pde.nc.dg2),
+ * corrector (Eq. pde.nc.gw2), detection (Eqs. positivity, dmp, relax),
+ * subcell ADER-WENO3 recomputation of troubled cells (Eq. aderweno with the
+ * data of Eq. ader.icbc), reconstruction R, and the flux correction of their
+ * unlimited face neighbours.  Asynchronous.  Errors: ADG_ERR_ARG (dt <= 0,
+ * nothing loaded), ADG_ERR_CUDA.  Device-side conditions (capacity overflow,
+ * inadmissible subcells) surface on the next synchronizing call. */
+int adg_step(adg_state* st, double dt);
+
+/* Same step with dt = min(cfl * min_k dx_k / lambda_max, dt_max) computed on
+ * the device from the current state (Eq. cfl); nothing returns to the host. */
+int adg_step_cfl(adg_state* st, double cfl, double dt_max);
+
+/* Eq. (cfl): dt = cfl * min_k dx_k / lambda_max with lambda_max over the
+ * subcell averages v^n of every cell; cfl includes 1/(d (2N+1)).
+ * Synchronizes.  Errors: ADG_ERR_STATE when no admissible wave speed exists. */
+int adg_max_dt(adg_state* st, double cfl, double* dt_out);
+
+/* Flags beta^{n+1} of the last step (or beta^0 after a load), host uint8[cells]. */
+int adg_flags(adg_state* st, uint8_t* beta);
+
+/* Current DOFs, host dofs[cells][nvar][n^dim]. */
+int adg_read(adg_state* st, double* dofs);
+
+/* Number of troubled cells of the last step. */
+int adg_troubled_count(adg_state* st, int64_t* out);
+
+/* Synchronize and report pending device-side conditions of earlier steps
+ * (ADG_ERR_CAPACITY, ADG_WARN_SUBCELL_INADMISSIBLE); clears them. */
+int adg_status(adg_state* st);
+
+/* Counts of the per-state scalars: cells, nvar, nodes per cell (n^dim),
+ * subcells per cell (Ns^dim). */
+int adg_sizes(const adg_state* st, int64_t* cells, int* nvar, int* nodes, int* subcells);
+
+/* Launch layout after the first load: out[0] = subcell slot capacity,
+ * out[1] = troubled cells per limiter chunk, out[2] = kernels launched by one
+ * adg_step, out[3] = device bytes held by the state.  Needs cap >= 4. */
+int adg_info(const adg_state* st, int64_t* out, int cap);
+
+/* Phase timing (ADG_OPT_PROFILE = 1): accumulated milliseconds of the steps
+ * since the last call, measured with CUDA events on the state's stream, in
+ * the order predictor, face fluxes, corrector + detector, subcell limiter,
+ * neighbour flux correction; ms[5] = number of steps timed.  Synchronizes and
+ * resets the sums.  Needs cap >= 6. */
+int adg_phase_times(adg_state* st, double* ms, int cap);
+
+const char* adg_last_error(const adg_state* st);
+
+/* Free every device buffer of the state and the state itself. */
+void adg_destroy(adg_state* st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ADG_H */

@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libadg (include/adg.h): argument marshalling only.
+
+Every step of the time step runs in the library's CUDA kernels; this module
+converts numpy arrays and Python scalars into the C ABI's pointers and sizes.
+It raises when libadg.so is missing -- there is no fallback path.
+
+Host array layouts follow include/adg.h: dofs[cell][var][node],
+sub[cell][var][subcell], beta[cell], with x fastest in every index.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libadg.so")
+
+OK = 0
+ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_CAPACITY, ERR_STATE = -1, -2, -3, -4, -5, -6
+WARN_SUBCELL_INADMISSIBLE = 1
+BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
+PREC_FP64, PREC_MIXED_FP32 = 0, 1
+OPT_DMP_EPS, OPT_DMP_FLOOR, OPT_FORCE_LIMITER, OPT_PICARD_ITERS, OPT_SLOT_CAPACITY = 1, 2, 3, 4, 5
+OPT_PROFILE = 6
+PHASES = ("predictor", "faceflux", "correct_detect", "limiter", "fix")
+IC_RADIAL, IC_QUADRANT = 0, 1
+
+# every entry point declared in include/adg.h
+SYMBOLS = ("adg_create", "adg_set_allocator", "adg_set_stream", "adg_set_option", "adg_load",
+           "adg_init_problem", "adg_load_full", "adg_read_full", "adg_step", "adg_step_cfl",
+           "adg_max_dt", "adg_flags", "adg_read", "adg_troubled_count", "adg_status",
+           "adg_sizes", "adg_info", "adg_phase_times", "adg_last_error", "adg_destroy")
+
+
+class AdgGrid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("x0", ctypes.c_double * 3),
+                ("dx", ctypes.c_double * 3)]
+
+
+class AdgProblem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("center", ctypes.c_double * 3),
+                ("radius", ctypes.c_double), ("inner", ctypes.c_double * 5),
+                ("outer", ctypes.c_double * 5), ("quad", (ctypes.c_double * 4) * 4),
+                ("vortex", ctypes.c_int), ("vortex_center", ctypes.c_double * 2),
+                ("vortex_strength", ctypes.c_double),
+                ("cell_rho_factor", ctypes.POINTER(ctypes.c_double))]
+
+
+class AdgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libadg error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path=None):
+    """Load libadg.so (built in-tree by build_lib.py); raises if it is missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"libadg.so not found at {p}: run paper_1406_7416_gb300.build_lib.build()")
+    lib = ctypes.CDLL(p)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    lib.adg_create.argtypes = [ctypes.POINTER(AdgGrid), ip, ctypes.c_double,
+                               ctypes.POINTER(ctypes.c_int), ip, ctypes.POINTER(vp)]
+    lib.adg_set_allocator.argtypes = [vp, vp, vp, vp]
+    lib.adg_set_stream.argtypes = [vp, vp]
+    lib.adg_set_option.argtypes = [vp, ip, ctypes.c_double]
+    lib.adg_load.argtypes = [vp, dp, dp]
+    lib.adg_init_problem.argtypes = [vp, ctypes.POINTER(AdgProblem)]
+    lib.adg_load_full.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_uint8), dp]
+    lib.adg_read_full.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_uint8), dp]
+    lib.adg_step.argtypes = [vp, ctypes.c_double]
+    lib.adg_step_cfl.argtypes = [vp, ctypes.c_double, ctypes.c_double]
+    lib.adg_max_dt.argtypes = [vp, ctypes.c_double, dp]
+    lib.adg_flags.argtypes = [vp, ctypes.POINTER(ctypes.c_uint8)]
+    lib.adg_read.argtypes = [vp, dp]
+    lib.adg_troubled_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.adg_status.argtypes = [vp]
+    lib.adg_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.adg_phase_times.argtypes = [vp, dp, ip]
+    lib.adg_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ip]
+    lib.adg_last_error.argtypes = [vp]
+    lib.adg_last_error.restype = ctypes.c_char_p
+    lib.adg_destroy.argtypes = [vp]
+    lib.adg_destroy.restype = None
+    for name in SYMBOLS:
+        if name not in ("adg_last_error", "adg_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _u8ptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+
+
+def _contig(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Solver:
+    """One libadg state: grid, degree, gamma, boundary kinds, precision."""
+
+    def __init__(self, dim, ncell, x0, dx, bc, N, gamma=1.4, prec=PREC_FP64):
+        self.lib = load_library()
+        g = AdgGrid()
+        g.dim = dim
+        for k in range(3):
+            g.n[k] = int(ncell[k]) if k < dim else 1
+            g.x0[k] = float(x0[k]) if k < dim else 0.0
+            g.dx[k] = float(dx[k]) if k < dim else 1.0
+        bcs = (ctypes.c_int * 6)(*([int(b) for b in bc] + [0] * (6 - len(bc))))
+        h = ctypes.c_void_p()
+        rc = self.lib.adg_create(ctypes.byref(g), int(N), float(gamma), bcs, int(prec), ctypes.byref(h))
+        if rc != OK:
+            raise AdgError(rc, "adg_create rejected its arguments")
+        self.h = h
+        self.dim, self.N, self.gamma, self.prec = dim, N, gamma, prec
+        self.ncell = tuple(int(c) for c in ncell[:dim])
+        c, nv, nd, ns = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self.lib.adg_sizes(h, ctypes.byref(c), ctypes.byref(nv), ctypes.byref(nd), ctypes.byref(ns))
+        self.cells, self.nvar, self.nodes, self.subcells = c.value, nv.value, nd.value, ns.value
+        self._keep = []
+
+    @classmethod
+    def from_workload(cls, w, prec=PREC_FP64):
+        return cls(w["dim"], w["ncell"], w["x0"], w["dx"], w["bc"], w["N"], w["gamma"], prec)
+
+    # -- helpers ------------------------------------------------------------
+    def _check(self, rc, what):
+        if rc < 0:
+            raise AdgError(rc, f"{what}: {self.lib.adg_last_error(self.h).decode()}")
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.adg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- configuration ------------------------------------------------------
+    def set_option(self, key, value):
+        self._check(self.lib.adg_set_option(self.h, int(key), float(value)), "adg_set_option")
+
+    def set_stream(self, stream_handle):
+        self._check(self.lib.adg_set_stream(self.h, ctypes.c_void_p(int(stream_handle))),
+                    "adg_set_stream")
+
+    def use_torch_allocator(self):
+        """Route the state's device allocations through torch's caching allocator."""
+        import torch
+        AllocT = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+        FreeT = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+        dev = torch.cuda.current_device()
+
+        def _alloc(nbytes, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev)
+            except RuntimeError:
+                return None
+
+        def _free(ptr, ctx):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        a, f = AllocT(_alloc), FreeT(_free)
+        self._keep += [a, f]
+        self._check(self.lib.adg_set_allocator(self.h, ctypes.cast(a, ctypes.c_void_p),
+                                               ctypes.cast(f, ctypes.c_void_p), None),
+                    "adg_set_allocator")
+
+    # -- data in / out ------------------------------------------------------
+    def load(self, dofs, exact=None):
+        d = _contig(dofs, np.float64)
+        assert d.size == self.cells * self.nvar * self.nodes
+        e = None if exact is None else _contig(exact, np.float64)
+        self._check(self.lib.adg_load(self.h, _dptr(d), None if e is None else _dptr(e)),
+                    "adg_load")
+
+    def init_problem(self, problem):
+        pr = AdgProblem()
+        fac = None
+        if problem["kind"] == "radial":
+            pr.kind = IC_RADIAL
+            for k, c in enumerate(problem["center"]):
+                pr.center[k] = c
+            pr.radius = problem["radius"]
+            for k, v in enumerate(problem["inner"]):
+                pr.inner[k] = v
+            for k, v in enumerate(problem["outer"]):
+                pr.outer[k] = v
+            if problem.get("cell_rho_factor") is not None:
+                # per-cell factors in the ABI's cell order (x fastest)
+                fac = _contig(np.asarray(problem["cell_rho_factor"]).transpose().ravel(), np.float64)
+                pr.cell_rho_factor = _dptr(fac)
+        else:
+            pr.kind = IC_QUADRANT
+            pr.center[0], pr.center[1] = problem["center"]
+            for q in range(4):
+                for k in range(4):
+                    pr.quad[q][k] = problem["states"][q][k]
+            vx = problem.get("vortex")
+            if vx is not None:
+                pr.vortex = 1
+                pr.vortex_center[0], pr.vortex_center[1] = vx["center"]
+                pr.vortex_strength = vx["strength"]
+        self._check(self.lib.adg_init_problem(self.h, ctypes.byref(pr)), "adg_init_problem")
+
+    def load_full(self, dofs, beta, sub):
+        d = _contig(dofs, np.float64)
+        b = _contig(beta, np.uint8)
+        s = _contig(sub, np.float64)
+        self._check(self.lib.adg_load_full(self.h, _dptr(d), _u8ptr(b), _dptr(s)), "adg_load_full")
+
+    def read(self, out=None):
+        out = np.empty((self.cells, self.nvar, self.nodes)) if out is None else out
+        self._check(self.lib.adg_read(self.h, _dptr(out)), "adg_read")
+        return out
+
+    def read_full(self):
+        d = np.empty((self.cells, self.nvar, self.nodes))
+        b = np.empty(self.cells, dtype=np.uint8)
+        s = np.empty((self.cells, self.nvar, self.subcells))
+        self._check(self.lib.adg_read_full(self.h, _dptr(d), _u8ptr(b), _dptr(s)), "adg_read_full")
+        return d, b, s
+
+    def flags(self):
+        b = np.empty(self.cells, dtype=np.uint8)
+        self._check(self.lib.adg_flags(self.h, _u8ptr(b)), "adg_flags")
+        return b
+
+    def troubled_count(self):
+        c = ctypes.c_int64()
+        self._check(self.lib.adg_troubled_count(self.h, ctypes.byref(c)), "adg_troubled_count")
+        return c.value
+
+    def status(self):
+        return self._check(self.lib.adg_status(self.h), "adg_status")
+
+    # -- time stepping ------------------------------------------------------
+    def step(self, dt):
+        self._check(self.lib.adg_step(self.h, float(dt)), "adg_step")
+
+    def step_cfl(self, cfl, dt_max=-1.0):
+        self._check(self.lib.adg_step_cfl(self.h, float(cfl), float(dt_max)), "adg_step_cfl")
+
+    def phase_times(self):
+        """{phase: accumulated ms} and the number of steps timed (profiling on)."""
+        ms = np.zeros(8)
+        self._check(self.lib.adg_phase_times(self.h, _dptr(ms), 8), "adg_phase_times")
+        return dict(zip(PHASES, ms[:5].tolist())), int(ms[5])
+
+    def info(self):
+        """Slot capacity, limiter chunk, kernels per adg_step, device bytes held."""
+        out = (ctypes.c_int64 * 4)()
+        self._check(self.lib.adg_info(self.h, out, 4), "adg_info")
+        return dict(capacity=out[0], chunk=out[1], launches_per_step=out[2], bytes=out[3])
+
+    def max_dt(self, cfl):
+        dt = ctypes.c_double()
+        self._check(self.lib.adg_max_dt(self.h, float(cfl), ctypes.byref(dt)), "adg_max_dt")
+        return dt.value
+
+
+__all__ = ["Solver", "AdgError", "load_library", "SYMBOLS", "inputs"]

@@ -1,0 +1,293 @@
+// Internal declarations of libadg: operator tables, grid geometry, device
+// buffers, Euler physics and the kernel launch interface.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/adg.h"
+
+namespace adg {
+
+constexpr int MAXN = 10;              // nodes per axis, n = N + 1 <= 10
+constexpr int MAXNS = 19;             // subcells per axis, Ns = 2N + 1 <= 19
+constexpr double WENO_EPS = 1e-14;    // WENO3 weights: lambda_k / (sigma_k + eps)^8
+constexpr double WENO_LAMBDA_C = 1e5; // central stencil; side stencils use 1
+
+// 1D operators of the degree-N nodal Gauss-Legendre basis on [0, 1] and of the
+// degree-2 subcell basis, generated on the host (ops_host.cpp) and copied to
+// the device once per state.
+struct Ops {
+  int N, n, Ns;
+  double xi[MAXN], w[MAXN];
+  double D[MAXN * MAXN];      // D[a*n+b]  = phi_b'(xi_a)
+  double Kt[MAXN * MAXN];     // Ktau[m*n+j] = (K1^{-1} diag(w))[m][j]
+  double phi0[MAXN], phi1[MAXN];
+  double phi0w[MAXN], phi1w[MAXN];   // phi(0)/w, phi(1)/w
+  double Mvol[MAXN * MAXN];   // Mvol[a*n+j] = w_j D[j][a] / w_a
+  double P1[MAXNS * MAXN];    // P1[s*n+a]   subcell averages of phi_a
+  double R1[MAXN * MAXNS];    // R1[a*Ns+s]  (P1^T P1)^{-1} P1^T
+  double Mt[MAXN * MAXNS];    // Mt[b*Ns+e]  = P1[e][b] / (Ns w_b)
+  // composite rule for the initial data: Ns subintervals x (N+2) points
+  double cq_x[MAXNS * (MAXN + 1)], cq_w[MAXNS * (MAXN + 1)];
+  double cq_phi[MAXNS * (MAXN + 1) * MAXN];   // phi_a(cq_x[p]) at [p*n+a]
+  // degree-2 subcell basis (3 GL nodes)
+  double w3[3], xi3[3], D3[9], Kt3[9], phi03[3], phi13[3];
+  // WENO3: coefficient matrices C[k][p*3+r] (stencil k, monomial p, cell r),
+  // nodal evaluation E[j*3+p] = xi3_j^p
+  double C[3][9];
+  double E[9];
+  // float copies for the reduced-precision Picard sweeps
+  float Df[MAXN * MAXN], Ktf[MAXN * MAXN];
+};
+
+// Builds the operator table of degree N (host, long double arithmetic).
+void build_ops(int N, Ops* ops);
+
+struct Geo {
+  int dim;
+  int n[3];
+  int periodic[3];
+  double x0[3];
+  double dx[3];
+  long long cells;
+};
+
+// Per-state device buffers.  Index [cur] holds time level n, [1-cur] level n+1.
+struct Bufs {
+  double* U[2];          // [cells][nv][n^d]
+  uint8_t* beta[2];      // [cells]
+  double* cmm[2];        // [cells][nv][2]  per-cell min / max of the subcell data
+  int* slot[2];          // [cells] slot of a troubled cell, -1 otherwise
+  int* list[2];          // [cap]   cell of each slot
+  double* store[2];      // [cap][nv][Ns^d] subcell data v of troubled cells
+  double* trace;         // [cells][d][2][nv][n^(d-1) * n]
+  double* G[3];          // per axis [faces][nv][n^(d-1)], time-averaged DG face flux
+  double* lam;           // [cells] max wave speed over the cell's subcell data
+  int* counters;         // see CNT_*
+  int* fixlist;          // [cells]
+  int* fixstamp;         // [cells]
+  double* edge;          // [cap][d][2][nv][Ns^(d-1)] sub-face fluxes on the cell faces
+  double* dt;            // [1] time step of the current step
+  double* lamred;        // [1] reduced lambda
+  // limiter scratch, sized for one chunk of `chunk` troubled cells
+  double* patch;         // [chunk][nv][L^d]
+  double* sweep[3];      // [chunk][nv][...] after the x, y, z reconstructions
+  double* qsub;          // [chunk][(Ns+2)^d][nv][3^(d+1)]
+  double* fsub[3];       // [chunk][nv][faces along axis k]
+  double* tmp_sub;       // load-time scratch [cells][nv][Ns^d]
+};
+
+enum {
+  CNT_TROUBLED0 = 0,     // troubled count of buffer 0
+  CNT_TROUBLED1 = 1,     // troubled count of buffer 1
+  CNT_FIX = 2,           // neighbour-fix list length
+  CNT_STATUS = 3,        // bit 0: slot capacity exceeded, bit 1: bad dt
+  CNT_INADM = 4,         // subcells left inadmissible after the limiter
+  CNT_COUNT = 8
+};
+
+struct Params {
+  Geo geo;
+  int N, dim, nv, prec, iters, force, cap, chunk;
+  double gamma, eps, floor;
+  const Ops* ops;        // device copy
+  Bufs b;
+  int cur;               // buffer index of time level n
+  int stamp;             // step counter (fix-list stamps)
+};
+
+// Kernel launch interface: one dispatcher per translation unit (2D low N,
+// 2D high N, 3D), selected by dimension and degree.
+enum LaunchOp {
+  OP_STEP_DG = 0,      // predictor, face fluxes, corrector + detector
+  OP_STEP_LIMITER,     // subcell limiter over the troubled list + flux correction
+  OP_LOAD_DETECT,      // initial detection (exact may be null)
+  OP_LOAD_FULL,        // full-state load
+  OP_READ_FULL,        // subcell rows of flagged cells
+  OP_PROJECT,          // initial data projection
+  OP_SUB_MINMAX        // per-cell min/max of subcell rows
+};
+
+struct LaunchArgs {
+  int op;
+  const Params* p;
+  cudaStream_t stream;
+  const double* exact;     // OP_LOAD_DETECT: exact averages (device) or null
+  const double* cmm_ex;    // OP_LOAD_DETECT: their per-cell min/max
+  const uint8_t* beta;     // OP_LOAD_FULL
+  const double* sub;       // OP_LOAD_FULL input, OP_SUB_MINMAX input
+  double* out;             // OP_READ_FULL rows, OP_PROJECT exact averages, OP_SUB_MINMAX result
+  const adg_problem* prob; // OP_PROJECT
+  const double* fac;       // OP_PROJECT per-cell density factor (device) or null
+  cudaEvent_t* ev;         // OP_STEP_*: phase events (null: none), see PHASE_*
+};
+
+// Phase boundaries recorded when profiling is on: ev[PHASE_x] before phase x,
+// ev[PHASE_END] after the last one.
+enum { PHASE_PREDICTOR = 0, PHASE_FACEFLUX, PHASE_CORRECT, PHASE_LIMITER, PHASE_FIX, PHASE_END,
+       PHASE_COUNT };
+
+cudaError_t dispatch_2d_lo(int N, const LaunchArgs& a);   // N = 1..5
+cudaError_t dispatch_2d_hi(int N, const LaunchArgs& a);   // N = 6..9
+cudaError_t dispatch_3d(int N, const LaunchArgs& a);      // N = 1..3
+cudaError_t launch_dt(const Params& p, double cfl, double dt_max, cudaStream_t s);
+cudaError_t launch_set_scalar(double* dst, double v, cudaStream_t s);
+
+// Scratch doubles per troubled cell of the limiter chunk buffers.
+size_t limiter_scratch_doubles(int dim, int N, size_t* patch, size_t* sw0, size_t* sw1,
+                               size_t* sw2, size_t* qsub, size_t* fsub);
+
+// ---------------------------------------------------------------------------
+// Euler physics (Sec. 5): conserved (rho, rho v, rho E), ideal gas.
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__device__ __forceinline__ void euler_fluxes(const T* Q, T gm1, T (*F)[D + 2]) {
+  const T r = T(1) / Q[0];
+  T v[D];
+  T kin = T(0);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    v[k] = Q[1 + k] * r;
+    kin += Q[1 + k] * v[k];
+  }
+  const T p = gm1 * (Q[D + 1] - T(0.5) * kin);
+  const T Ep = Q[D + 1] + p;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    F[k][0] = Q[1 + k];
+#pragma unroll
+    for (int j = 0; j < D; ++j) F[k][1 + j] = Q[1 + j] * v[k];
+    F[k][1 + k] += p;
+    F[k][D + 1] = v[k] * Ep;
+  }
+}
+
+__device__ __forceinline__ double nanmax(double a, double b) {
+  // max that propagates NaN from either argument
+  return (a > b || a != a) ? a : b;
+}
+
+template <int D>
+__device__ __forceinline__ double euler_pressure(const double* Q, double gm1) {
+  double kin = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) kin += Q[1 + k] * Q[1 + k];
+  return gm1 * (Q[D + 1] - 0.5 * kin / Q[0]);
+}
+
+// Rusanov flux through a face with normal +e_k, pointwise (Sec. 2.3).
+template <int D>
+__device__ __forceinline__ void rusanov(const double* QL, const double* QR, int k, double gamma,
+                                        double* G) {
+  const double gm1 = gamma - 1.0;
+  double sL, sR, FL[D + 2], FR[D + 2];
+  {
+    const double r = 1.0 / QL[0];
+    double kin = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) kin += QL[1 + j] * QL[1 + j];
+    const double p = gm1 * (QL[D + 1] - 0.5 * kin * r);
+    const double vk = QL[1 + k] * r;
+    sL = fabs(vk) + sqrt(gamma * p * r);
+    FL[0] = QL[1 + k];
+#pragma unroll
+    for (int j = 0; j < D; ++j) FL[1 + j] = QL[1 + j] * vk;
+    FL[1 + k] += p;
+    FL[D + 1] = vk * (QL[D + 1] + p);
+  }
+  {
+    const double r = 1.0 / QR[0];
+    double kin = 0.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) kin += QR[1 + j] * QR[1 + j];
+    const double p = gm1 * (QR[D + 1] - 0.5 * kin * r);
+    const double vk = QR[1 + k] * r;
+    sR = fabs(vk) + sqrt(gamma * p * r);
+    FR[0] = QR[1 + k];
+#pragma unroll
+    for (int j = 0; j < D; ++j) FR[1 + j] = QR[1 + j] * vk;
+    FR[1 + k] += p;
+    FR[D + 1] = vk * (QR[D + 1] + p);
+  }
+  const double s = nanmax(sL, sR);
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) G[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * s * (QR[v] - QL[v]);
+}
+
+// max_k |v_k| + c of one state (wave speed for Eq. cfl)
+template <int D>
+__device__ __forceinline__ double wave_speed(const double* Q, double gamma) {
+  const double r = 1.0 / Q[0];
+  double kin = 0.0, vm = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    kin += Q[1 + k] * Q[1 + k];
+    vm = nanmax(vm, fabs(Q[1 + k] * r));
+  }
+  const double p = (gamma - 1.0) * (Q[D + 1] - 0.5 * kin * r);
+  return vm + sqrt(gamma * p * r);
+}
+
+// ---------------------------------------------------------------------------
+// Grid helpers
+// ---------------------------------------------------------------------------
+template <int D>
+__device__ __forceinline__ void cell_coords(long long c, const Geo& g, int* ijk) {
+  ijk[0] = (int)(c % g.n[0]);
+  long long r = c / g.n[0];
+  if (D == 3) {
+    ijk[1] = (int)(r % g.n[1]);
+    ijk[2] = (int)(r / g.n[1]);
+  } else {
+    ijk[1] = (int)r;
+  }
+}
+
+template <int D>
+__device__ __forceinline__ long long cell_index(const int* ijk, const Geo& g) {
+  long long c = ijk[0] + (long long)g.n[0] * ijk[1];
+  if (D == 3) c += (long long)g.n[0] * g.n[1] * ijk[2];
+  return c;
+}
+
+// Neighbour across the low (side = -1) or high (side = +1) face of axis k.
+// Returns false outside a transmissive boundary.
+template <int D>
+__device__ __forceinline__ bool face_neighbour(const Geo& g, const int* ijk, int k, int side,
+                                               int* out) {
+#pragma unroll
+  for (int j = 0; j < D; ++j) out[j] = ijk[j];
+  int c = ijk[k] + side;
+  if (c < 0 || c >= g.n[k]) {
+    if (!g.periodic[k]) return false;
+    c = (c + g.n[k]) % g.n[k];
+  }
+  out[k] = c;
+  return true;
+}
+
+// Face index along axis k: faces (n_k + 1) along k, cells along the others.
+template <int D>
+__device__ __forceinline__ long long face_index(const Geo& g, const int* ijk, int k, int f) {
+  long long idx = 0, stride = 1;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const int e = (j == k) ? g.n[j] + 1 : g.n[j];
+    const int c = (j == k) ? f : ijk[j];
+    idx += stride * c;
+    stride *= e;
+  }
+  return idx;
+}
+
+template <int D>
+__host__ __device__ __forceinline__ long long face_count(const Geo& g, int k) {
+  long long c = 1;
+  for (int j = 0; j < D; ++j) c *= (j == k) ? g.n[j] + 1 : g.n[j];
+  return c;
+}
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+}  // namespace adg

@@ -1,0 +1,565 @@
+// ADER-DG kernels: space-time predictor (Sec. 2.2 Eq. pde.nc.dg2), DG face
+// fluxes and corrector (Sec. 2.3 Eq. pde.nc.gw2) fused with the a-posteriori
+// detector (Sec. 4.3 Eqs. positivity, dmp, relax).
+#pragma once
+
+#include "adg_internal.h"
+
+namespace adg {
+
+template <int D, int N>
+struct Dims {
+  static constexpr int n = N + 1;
+  static constexpr int NV = D + 2;
+  static constexpr int ND = ipow(n, D);          // spatial nodes per cell
+  static constexpr int NST = ipow(n, D + 1);     // space-time nodes per cell
+  static constexpr int NF = ipow(n, D - 1);      // tangential nodes per face
+  static constexpr int NT = NF * n;              // tangential x time nodes per face
+  static constexpr int Ns = 2 * N + 1;
+  static constexpr int NSD = ipow(Ns, D);        // subcells per cell
+  static constexpr int NSF = ipow(Ns, D - 1);    // sub-faces per cell face
+  static constexpr int L = Ns + 6;               // limiter patch width (3 ghost layers)
+  static constexpr int LD = ipow(L, D);
+  static constexpr int NE = Ns + 2;              // reconstructed block -1..Ns
+  static constexpr int NED = ipow(NE, D);
+  static constexpr int NST3 = ipow(3, D + 1);    // subcell space-time nodes
+  static constexpr int ND3 = ipow(3, D);
+};
+
+// ---------------------------------------------------------------------------
+// Picard phases on one space-time block of n^(D+1) nodes (Eq. pde.nc.dg2):
+//   q <- u (x) 1 - Ktau x_tau sum_k c_k D x_k f_k(q),  c_k = dt / dx_k.
+// Work items are spread over threads tid .. (step nth).
+// ---------------------------------------------------------------------------
+template <int D, int n, typename T>
+__device__ __forceinline__ void picard_flux(const T* __restrict__ q, T* __restrict__ F, T gm1,
+                                            int tid, int nth) {
+  constexpr int NV = D + 2, NST = ipow(n, D + 1);
+  for (int l = tid; l < NST; l += nth) {
+    T Q[NV];
+    T Fl[D][D + 2];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Q[v] = q[v * NST + l];
+    euler_fluxes<D, T>(Q, gm1, Fl);
+#pragma unroll
+    for (int k = 0; k < D; ++k)
+#pragma unroll
+      for (int v = 0; v < NV; ++v) F[(k * NV + v) * NST + l] = Fl[k][v];
+  }
+}
+
+template <int D, int n, typename T>
+__device__ __forceinline__ void picard_deriv(const T* __restrict__ F, T* __restrict__ S,
+                                             const T* __restrict__ Dm, const T* c, int tid,
+                                             int nth) {
+  constexpr int NV = D + 2, NST = ipow(n, D + 1);
+  for (int e = tid; e < NV * NST; e += nth) {
+    const int v = e / NST, l = e - v * NST;
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int st = (k == 0) ? 1 : (k == 1 ? n : n * n);
+      const int ak = (l / st) % n;
+      const T* f = F + (k * NV + v) * NST + (l - ak * st);
+      const T* dr = Dm + ak * n;
+      T acc = T(0);
+#pragma unroll
+      for (int j = 0; j < n; ++j) acc += dr[j] * f[j * st];
+      s += c[k] * acc;
+    }
+    S[e] = s;
+  }
+}
+
+template <int D, int n, typename T>
+__device__ __forceinline__ void picard_time(T* __restrict__ q, const double* __restrict__ u,
+                                            const T* __restrict__ Kt, int tid, int nth) {
+  constexpr int NV = D + 2, ND = ipow(n, D), NST = ipow(n, D + 1);
+  for (int e = tid; e < NV * ND; e += nth) {
+    const int v = e / ND, i = e - v * ND;
+    T Sl[n];
+#pragma unroll
+    for (int m = 0; m < n; ++m) Sl[m] = q[v * NST + i + m * ND];
+    const T u0 = (T)u[v * ND + i];
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      T acc = T(0);
+#pragma unroll
+      for (int j = 0; j < n; ++j) acc += Kt[m * n + j] * Sl[j];
+      q[v * NST + i + m * ND] = u0 - acc;
+    }
+  }
+}
+
+// Apply a matrix along axis k of a (nv, e0, e1, e2) tensor (x fastest):
+// out[v][.., r, ..] = sum_c M[r * cols + c] in[v][.., c, ..].
+// ein: extents of `in`; out has extent `rows` along k.
+template <int D>
+__device__ __forceinline__ void apply_axis(const double* __restrict__ in, double* __restrict__ out,
+                                           const double* __restrict__ M, int rows, int cols, int k,
+                                           const int* ein, int nv, int tid, int nth) {
+  int eout[3] = {1, 1, 1};
+  int insz = 1, outsz = 1;
+  for (int j = 0; j < D; ++j) {
+    eout[j] = (j == k) ? rows : ein[j];
+    insz *= ein[j];
+    outsz *= eout[j];
+  }
+  int stride = 1;
+  for (int j = 0; j < k; ++j) stride *= ein[j];
+  for (int e = tid; e < nv * outsz; e += nth) {
+    const int v = e / outsz;
+    int r = e - v * outsz;
+    int idx[3] = {0, 0, 0};
+    for (int j = 0; j < D; ++j) {
+      idx[j] = r % eout[j];
+      r /= eout[j];
+    }
+    int off = 0, s = 1;
+    for (int j = 0; j < D; ++j) {
+      off += (j == k ? 0 : idx[j]) * s;
+      s *= ein[j];
+    }
+    const double* src = in + v * insz + off;
+    const double* mr = M + idx[k] * cols;
+    double acc = 0.0;
+    for (int c = 0; c < cols; ++c) acc += mr[c] * src[c * stride];
+    out[e] = acc;
+  }
+}
+
+// Tensor projection / reconstruction of all variables of one cell, in place
+// through two buffers (a, b).  `from` extent per axis -> `to` extent, matrix
+// M[to][from].  Result ends in the buffer returned.
+template <int D>
+__device__ __forceinline__ double* apply_all_axes(double* a, double* b, const double* M, int to,
+                                                  int from, int nv, int tid, int nth) {
+  int ext[3] = {from, from, from};
+  double* src = a;
+  double* dst = b;
+  for (int k = 0; k < D; ++k) {
+    apply_axis<D>(src, dst, M, to, from, k, ext, nv, tid, nth);
+    ext[k] = to;
+    __syncthreads();
+    double* t = src;
+    src = dst;
+    dst = t;
+  }
+  return src;
+}
+
+// Block-wide reductions of per-thread values (blockDim a multiple of 32).
+__device__ __forceinline__ double block_reduce_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[w] = v;
+  __syncthreads();
+  double r = red[0];
+  for (int i = 1; i < nw; ++i) r = nanmax(r, red[i]);
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double block_reduce_min(double v, double* red) {
+  return -block_reduce_max(-v, red);
+}
+
+// ---------------------------------------------------------------------------
+// K1 predictor: one cell per block.  Writes the candidate's volume part
+// u + sum_k c_k Mvol x_k fbar_k into Unext and the space-time face traces.
+// ---------------------------------------------------------------------------
+template <int D, int N, bool MIXED>
+__host__ __device__ constexpr size_t predictor_smem_bytes() {
+  using DM = Dims<D, N>;
+  size_t d = (size_t)DM::NV * DM::ND + (size_t)DM::NV * DM::NST + (size_t)D * DM::NV * DM::NST +
+             (size_t)D * DM::NV * DM::ND + 3 * DM::n * DM::n + 3 * DM::n;
+  size_t f = MIXED ? ((size_t)DM::NV * DM::NST + (size_t)D * DM::NV * DM::NST + 2 * DM::n * DM::n)
+                   : 0;
+  return d * sizeof(double) + f * sizeof(float);
+}
+
+template <int D, int N, bool MIXED>
+__global__ void __launch_bounds__(256) k_predictor(Params p) {
+  using DM = Dims<D, N>;
+  constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, NST = DM::NST, NF = DM::NF, NT = DM::NT;
+  extern __shared__ double sm[];
+  double* u = sm;
+  double* q = u + NV * ND;
+  double* F = q + NV * NST;
+  double* fbar = F + D * NV * NST;
+  double* Dm = fbar + D * NV * ND;
+  double* Kt = Dm + n * n;
+  double* Mv = Kt + n * n;
+  double* w = Mv + n * n;
+  double* ph0 = w + n;
+  double* ph1 = ph0 + n;
+  float* qf = reinterpret_cast<float*>(ph1 + n);
+  float* Ff = qf + NV * NST;
+  float* Dmf = Ff + D * NV * NST;
+  float* Ktf = Dmf + n * n;
+
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const Ops* o = p.ops;
+  for (int i = tid; i < n * n; i += nth) {
+    Dm[i] = o->D[i];
+    Kt[i] = o->Kt[i];
+    Mv[i] = o->Mvol[i];
+    if (MIXED) {
+      Dmf[i] = o->Df[i];
+      Ktf[i] = o->Ktf[i];
+    }
+  }
+  for (int i = tid; i < n; i += nth) {
+    w[i] = o->w[i];
+    ph0[i] = o->phi0[i];
+    ph1[i] = o->phi1[i];
+  }
+  const double dt = *p.b.dt;
+  double c[3];
+#pragma unroll
+  for (int k = 0; k < D; ++k) c[k] = dt / p.geo.dx[k];
+  const double gm1 = p.gamma - 1.0;
+
+  for (long long cell = blockIdx.x; cell < p.geo.cells; cell += gridDim.x) {
+    const double* Uc = p.b.U[p.cur] + cell * (NV * ND);
+    for (int i = tid; i < NV * ND; i += nth) u[i] = Uc[i];
+    __syncthreads();
+    int it0 = 0;
+    if (MIXED && p.iters > 1) {
+      float cf[3];
+#pragma unroll
+      for (int k = 0; k < D; ++k) cf[k] = (float)c[k];
+      for (int e = tid; e < NV * NST; e += nth) {
+        const int v = e / NST, l = e - v * NST;
+        qf[e] = (float)u[v * ND + (l % ND)];
+      }
+      __syncthreads();
+      for (int it = 0; it < p.iters - 1; ++it) {
+        picard_flux<D, n, float>(qf, Ff, (float)gm1, tid, nth);
+        __syncthreads();
+        picard_deriv<D, n, float>(Ff, qf, Dmf, cf, tid, nth);
+        __syncthreads();
+        picard_time<D, n, float>(qf, u, Ktf, tid, nth);
+        __syncthreads();
+      }
+      for (int e = tid; e < NV * NST; e += nth) q[e] = (double)qf[e];
+      it0 = p.iters - 1;
+    } else {
+      for (int e = tid; e < NV * NST; e += nth) {
+        const int v = e / NST, l = e - v * NST;
+        q[e] = u[v * ND + (l % ND)];
+      }
+    }
+    __syncthreads();
+    for (int it = it0; it < p.iters; ++it) {
+      picard_flux<D, n, double>(q, F, gm1, tid, nth);
+      __syncthreads();
+      picard_deriv<D, n, double>(F, q, Dm, c, tid, nth);
+      __syncthreads();
+      picard_time<D, n, double>(q, u, Kt, tid, nth);
+      __syncthreads();
+    }
+    // corrector volume term from the time-averaged nodal fluxes
+    picard_flux<D, n, double>(q, F, gm1, tid, nth);
+    __syncthreads();
+    for (int e = tid; e < D * NV * ND; e += nth) {
+      const int kv = e / ND, i = e - kv * ND;
+      double acc = 0.0;
+#pragma unroll
+      for (int m = 0; m < n; ++m) acc += w[m] * F[kv * NST + i + m * ND];
+      fbar[e] = acc;
+    }
+    __syncthreads();
+    double* Uo = p.b.U[1 - p.cur] + cell * (NV * ND);
+    for (int e = tid; e < NV * ND; e += nth) {
+      const int v = e / ND, i = e - v * ND;
+      double acc = u[e];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const int st = (k == 0) ? 1 : (k == 1 ? n : n * n);
+        const int ak = (i / st) % n;
+        const double* f = fbar + (k * NV + v) * ND + (i - ak * st);
+        double t = 0.0;
+#pragma unroll
+        for (int j = 0; j < n; ++j) t += Mv[ak * n + j] * f[j * st];
+        acc += c[k] * t;
+      }
+      Uo[e] = acc;
+    }
+    // space-time traces on the 2D faces: trace[cell][k][side][v][ts + NF * m]
+    double* tr = p.b.trace + cell * (size_t)(D * 2 * NV * NT);
+    for (int e = tid; e < D * 2 * NV * NT; e += nth) {
+      const int k = e / (2 * NV * NT);
+      int r = e - k * (2 * NV * NT);
+      const int s = r / (NV * NT);
+      r -= s * (NV * NT);
+      const int v = r / NT, tt = r - v * NT;
+      const int m = tt / NF;
+      int ts = tt - m * NF;
+      int base = m * ND, st = 1, stk = 1;
+#pragma unroll
+      for (int j = 0; j < D; ++j) {
+        if (j == k) {
+          stk = st;
+        } else {
+          base += (ts % n) * st;
+          ts /= n;
+        }
+        st *= n;
+      }
+      const double* ph = s ? ph1 : ph0;
+      const double* qq = q + v * NST + base;
+      double acc = 0.0;
+#pragma unroll
+      for (int a = 0; a < n; ++a) acc += ph[a] * qq[a * stk];
+      tr[e] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2 face flux: time-averaged Rusanov flux at every tangential node of every
+// face normal to axis k.  Transmissive boundary: the missing side copies the
+// interior trace (G = F(q^-)).
+// ---------------------------------------------------------------------------
+template <int D, int N>
+__global__ void __launch_bounds__(256) k_faceflux(Params p, int k) {
+  using DM = Dims<D, N>;
+  constexpr int n = DM::n, NV = DM::NV, NF = DM::NF, NT = DM::NT;
+  const Geo& g = p.geo;
+  const long long nf = face_count<D>(g, k);
+  const double* w = p.ops->w;
+  double* G = p.b.G[k];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nf * NF;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long face = e / NF;
+    const int ts = (int)(e - face * NF);
+    int ijk[3] = {0, 0, 0};
+    long long r = face;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      const int ext = (j == k) ? g.n[j] + 1 : g.n[j];
+      ijk[j] = (int)(r % ext);
+      r /= ext;
+    }
+    const int f = ijk[k];
+    int L[3], R[3];
+#pragma unroll
+    for (int j = 0; j < D; ++j) L[j] = R[j] = ijk[j];
+    bool hasL = true, hasR = true;
+    if (f == 0) {
+      if (g.periodic[k]) L[k] = g.n[k] - 1; else hasL = false;
+    } else {
+      L[k] = f - 1;
+    }
+    if (f == g.n[k]) {
+      if (g.periodic[k]) R[k] = 0; else hasR = false;
+    }
+    const size_t csz = (size_t)D * 2 * NV * NT;
+    const double* trL = hasL ? p.b.trace + cell_index<D>(L, g) * csz + ((size_t)k * 2 + 1) * NV * NT
+                             : nullptr;
+    const double* trR = hasR ? p.b.trace + cell_index<D>(R, g) * csz + ((size_t)k * 2 + 0) * NV * NT
+                             : nullptr;
+    if (!hasL) trL = trR;
+    if (!hasR) trR = trL;
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+    for (int m = 0; m < n; ++m) {
+      double QL[NV], QR[NV], Gm[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        QL[v] = trL[v * NT + ts + NF * m];
+        QR[v] = trR[v * NT + ts + NF * m];
+      }
+      rusanov<D>(QL, QR, k, p.gamma, Gm);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += w[m] * Gm[v];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) G[(face * NV + v) * NF + ts] = acc[v];
+  }
+}
+
+// Tangential node index of spatial node i for the faces normal to axis k.
+template <int D, int n>
+__device__ __forceinline__ int tangential(int i, int k) {
+  int ts = 0, mul = 1;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    const int a = i % n;
+    i /= n;
+    if (j != k) {
+      ts += a * mul;
+      mul *= n;
+    }
+  }
+  return ts;
+}
+
+// Detector bounds over the Voronoi neighbourhood (3^d block) from per-cell
+// min/max, then the relaxed DMP interval [m - delta, M + delta] (Eq. relax
+// with a relative floor).  Threads v < nvar write lohi[2v], lohi[2v+1].
+template <int D>
+__device__ __forceinline__ void dmp_interval(const Params& p, const double* __restrict__ cmm,
+                                             const int* ijk, double* lohi) {
+  const int NV = D + 2;
+  const int v = threadIdx.x;
+  if (v >= NV) return;
+  const Geo& g = p.geo;
+  double mn = INFINITY, mx = -INFINITY;
+  const int nb3 = ipow(3, D);
+  for (int o = 0; o < nb3; ++o) {
+    int c[3] = {0, 0, 0}, oo = o;
+    bool in = true;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+      int cj = ijk[j] + (oo % 3) - 1;
+      oo /= 3;
+      if (cj < 0 || cj >= g.n[j]) {
+        if (!g.periodic[j]) in = false;
+        cj = (cj + g.n[j]) % g.n[j];
+      }
+      c[j] = cj;
+    }
+    if (!in) continue;
+    const long long nb = cell_index<D>(c, g);
+    mn = fmin(mn, cmm[(nb * NV + v) * 2 + 0]);
+    mx = fmax(mx, cmm[(nb * NV + v) * 2 + 1]);
+  }
+  const double scale = fmax(1.0, fmax(fabs(mx), fabs(mn)));
+  const double delta = fmax(p.eps * (mx - mn), p.floor * scale);
+  lohi[2 * v] = mn - delta;
+  lohi[2 * v + 1] = mx + delta;
+}
+
+// Checks the subcell data vs[v][s] of one cell (PAD + DMP when lohi != null),
+// reduces per-variable min / max into mm[2v], mm[2v+1] and the wave speed.
+// Returns (block-uniform) whether any check failed.
+template <int D>
+__device__ __forceinline__ bool check_subcells(const double* __restrict__ vs, int nsub,
+                                               const double* lohi, double gamma, double* mm,
+                                               double* lam, double* red) {
+  const int NV = D + 2;
+  bool bad = false;
+  double lmin[NV], lmax[NV], lw = 0.0;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    lmin[v] = INFINITY;
+    lmax[v] = -INFINITY;
+  }
+  for (int s = threadIdx.x; s < nsub; s += blockDim.x) {
+    double Q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Q[v] = vs[v * nsub + s];
+      lmin[v] = fmin(lmin[v], Q[v]);
+      lmax[v] = fmax(lmax[v], Q[v]);
+    }
+    const double pr = euler_pressure<D>(Q, gamma - 1.0);
+    bool ok = (Q[0] > 0.0) && (pr > 0.0);
+    if (lohi) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) ok = ok && (Q[v] >= lohi[2 * v]) && (Q[v] <= lohi[2 * v + 1]);
+    }
+    bad = bad || !ok;
+    lw = nanmax(lw, wave_speed<D>(Q, gamma));
+  }
+  const bool any_bad = __syncthreads_or(bad);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double a = block_reduce_min(lmin[v], red);
+    const double b = block_reduce_max(lmax[v], red);
+    if (threadIdx.x == 0) {
+      mm[2 * v] = a;
+      mm[2 * v + 1] = b;
+    }
+  }
+  const double l = block_reduce_max(lw, red);
+  if (threadIdx.x == 0) *lam = l;
+  return any_bad;
+}
+
+// ---------------------------------------------------------------------------
+// K3 + K4 corrector and detector: one cell per block.
+// ---------------------------------------------------------------------------
+template <int D, int N>
+__host__ __device__ constexpr size_t correct_smem_bytes() {
+  using DM = Dims<D, N>;
+  const int big = DM::NSD > DM::ND * 4 ? DM::NSD : DM::ND * 4;
+  return (size_t)(2 * DM::NV * (DM::NSD > big ? DM::NSD : big) + DM::Ns * DM::n + 4 * DM::NV + 64) *
+         sizeof(double);
+}
+
+template <int D, int N>
+__global__ void __launch_bounds__(128) k_correct_detect(Params p) {
+  using DM = Dims<D, N>;
+  constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, NF = DM::NF, Ns = DM::Ns, NSD = DM::NSD;
+  constexpr int BUF = (DM::NSD > DM::ND * 4 ? DM::NSD : DM::ND * 4);
+  extern __shared__ double sm[];
+  double* A = sm;                     // NV * BUF
+  double* B = A + NV * BUF;           // NV * BUF
+  double* P1 = B + NV * BUF;          // Ns * n
+  double* lohi = P1 + Ns * n;         // 2 NV
+  double* mm = lohi + 2 * NV;         // 2 NV
+  double* red = mm + 2 * NV;          // 32 (+ lam)
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const Ops* o = p.ops;
+  for (int i = tid; i < Ns * n; i += nth) P1[i] = o->P1[i];
+  const double dt = *p.b.dt;
+  double c[3];
+#pragma unroll
+  for (int k = 0; k < D; ++k) c[k] = dt / p.geo.dx[k];
+  const int nxt = 1 - p.cur;
+  for (long long cell = blockIdx.x; cell < p.geo.cells; cell += gridDim.x) {
+    int ijk[3];
+    cell_coords<D>(cell, p.geo, ijk);
+    double* Uo = p.b.U[nxt] + cell * (NV * ND);
+    for (int e = tid; e < NV * ND; e += nth) {
+      const int v = e / ND, i = e - v * ND;
+      double acc = Uo[e];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const int st = (k == 0) ? 1 : (k == 1 ? n : n * n);
+        const int ak = (i / st) % n;
+        const int ts = tangential<D, n>(i, k);
+        const long long flo = face_index<D>(p.geo, ijk, k, ijk[k]);
+        const long long fhi = face_index<D>(p.geo, ijk, k, ijk[k] + 1);
+        const double Glo = p.b.G[k][(flo * NV + v) * NF + ts];
+        const double Ghi = p.b.G[k][(fhi * NV + v) * NF + ts];
+        acc -= c[k] * (o->phi1w[ak] * Ghi - o->phi0w[ak] * Glo);
+      }
+      A[e] = acc;
+      Uo[e] = acc;
+    }
+    __syncthreads();
+    double* vs = apply_all_axes<D>(A, B, P1, Ns, n, NV, tid, nth);
+    dmp_interval<D>(p, p.b.cmm[p.cur], ijk, lohi);
+    __syncthreads();
+    double lam;
+    const bool bad = check_subcells<D>(vs, NSD, lohi, p.gamma, mm, &lam, red);
+    if (tid == 0) {
+      int slot = -1;
+      if (bad || p.force) {
+        slot = atomicAdd(&p.b.counters[CNT_TROUBLED0 + nxt], 1);
+        if (slot < p.cap) {
+          p.b.list[nxt][slot] = (int)cell;
+        } else {
+          // no subcell slot left: the cell keeps its candidate, the step is
+          // reported as failed (ADG_ERR_CAPACITY) by the next status query
+          atomicOr(&p.b.counters[CNT_STATUS], 1);
+          slot = -1;
+        }
+      }
+      p.b.beta[nxt][cell] = (uint8_t)(slot >= 0);
+      p.b.slot[nxt][cell] = slot;
+      p.b.lam[cell] = lam;
+    }
+    if (tid < 2 * NV) p.b.cmm[nxt][cell * 2 * NV + tid] = mm[tid];
+    __syncthreads();
+  }
+}
+
+}  // namespace adg

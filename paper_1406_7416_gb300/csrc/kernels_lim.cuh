@@ -1,0 +1,515 @@
+// Subcell limiter kernels (Sec. 4.3-4.4): gather of the subcell patch from
+// Eq. (ader.icbc), dimension-by-dimension WENO3 reconstruction, degree-2
+// space-time predictor per subcell, sub-face Rusanov fluxes, finite volume
+// update A (Eq. aderweno), reconstruction R (Eq. subcell.r) and the flux
+// correction of unlimited face neighbours.  All work runs over the compacted
+// troubled-cell list, in chunks of `chunk` cells that share the scratch.
+#pragma once
+
+#include "kernels_dg.cuh"
+
+namespace adg {
+
+__host__ __device__ __forceinline__ int ipow3(int k) { return k == 0 ? 1 : (k == 1 ? 3 : (k == 2 ? 9 : 27)); }
+
+// number of troubled cells handled by chunk `chunk0` (0 when past the end)
+__device__ __forceinline__ int chunk_len(const Params& p, int chunk0) {
+  int nT = p.b.counters[CNT_TROUBLED0 + (1 - p.cur)];
+  if (nT > p.cap) nT = p.cap;
+  const int len = nT - chunk0;
+  return len < 0 ? 0 : (len > p.chunk ? p.chunk : len);
+}
+
+// v^n at one subcell of cell `o` (Eq. ader.icbc): the stored subgrid data of a
+// troubled cell, else the projection P(u^n) evaluated at that subcell.
+template <int D, int N>
+__device__ __forceinline__ void subcell_value(const Params& p, long long o, const int* s,
+                                              const double* __restrict__ P1, double* out) {
+  using DM = Dims<D, N>;
+  constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, Ns = DM::Ns, NSD = DM::NSD;
+  if (p.b.beta[p.cur][o]) {
+    const int slot = p.b.slot[p.cur][o];
+    const int sidx = s[0] + Ns * (s[1] + (D == 3 ? Ns * s[2] : 0));
+    const double* st = p.b.store[p.cur] + (size_t)slot * NV * NSD;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) out[v] = st[v * NSD + sidx];
+    return;
+  }
+  const double* U = p.b.U[p.cur] + o * (NV * ND);
+  const double* px = P1 + s[0] * n;
+  const double* py = P1 + s[1] * n;
+  const double* pz = P1 + (D == 3 ? s[2] : 0) * n;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double* Uv = U + v * ND;
+    double acc = 0.0;
+    for (int c = 0; c < (D == 3 ? n : 1); ++c) {
+      double accb = 0.0;
+      for (int b = 0; b < n; ++b) {
+        double acca = 0.0;
+#pragma unroll
+        for (int a = 0; a < n; ++a) acca += px[a] * Uv[a + n * (b + n * c)];
+        accb += py[b] * acca;
+      }
+      acc += (D == 3 ? pz[c] : 1.0) * accb;
+    }
+    out[v] = acc;
+  }
+}
+
+// L0: patch[j][v][L^d], local subcell -3..Ns+2 per axis around troubled cell
+// list[chunk0 + j].  Periodic: wrap; transmissive: clamp the global subcell
+// index into the domain.
+template <int D, int N>
+__global__ void __launch_bounds__(256) k_lim_patch(Params p, int chunk0) {
+  using DM = Dims<D, N>;
+  constexpr int n = DM::n, NV = DM::NV, Ns = DM::Ns, L = DM::L, LD = DM::LD;
+  __shared__ double P1[DM::Ns * DM::n];
+  for (int i = threadIdx.x; i < Ns * n; i += blockDim.x) P1[i] = p.ops->P1[i];
+  __syncthreads();
+  const int len = chunk_len(p, chunk0);
+  const Geo& g = p.geo;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)len * LD;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e / LD);
+    int r = (int)(e - (long long)j * LD);
+    const long long cell = p.b.list[1 - p.cur][chunk0 + j];
+    int ijk[3];
+    cell_coords<D>(cell, g, ijk);
+    int own[3] = {0, 0, 0}, sub[3] = {0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int loc = r % L - 3;
+      r /= L;
+      const int ng = g.n[k] * Ns;
+      int gi = ijk[k] * Ns + loc;
+      if (g.periodic[k]) gi = (gi % ng + ng) % ng;
+      else gi = gi < 0 ? 0 : (gi >= ng ? ng - 1 : gi);
+      own[k] = gi / Ns;
+      sub[k] = gi - own[k] * Ns;
+    }
+    double val[NV];
+    subcell_value<D, N>(p, cell_index<D>(own, g), sub, P1, val);
+    double* dst = p.b.patch + (size_t)j * NV * LD + (e - (long long)j * LD);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dst[v * LD] = val[v];
+  }
+}
+
+// 1D WENO3 on five consecutive subcell averages u[0..4] (target subcell u[2]):
+// values of the reconstruction at the 3 GL nodes of the target subcell.
+__device__ __forceinline__ void weno3(const double* u, const Ops* __restrict__ o, double* out) {
+  double num0 = 0.0, num1 = 0.0, num2 = 0.0, den = 0.0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double* C = o->C[k];
+    const double c0 = C[0] * u[k] + C[1] * u[k + 1] + C[2] * u[k + 2];
+    const double c1 = C[3] * u[k] + C[4] * u[k + 1] + C[5] * u[k + 2];
+    const double c2 = C[6] * u[k] + C[7] * u[k + 1] + C[8] * u[k + 2];
+    // sigma = int_0^1 (p')^2 + (p'')^2 = c1^2 + 2 c1 c2 + 16/3 c2^2
+    const double sigma = c1 * (c1 + 2.0 * c2) + (16.0 / 3.0) * c2 * c2;
+    double t = sigma + WENO_EPS;
+    t = t * t;
+    t = t * t;
+    t = t * t;
+    const double wt = (k == 1 ? WENO_LAMBDA_C : 1.0) / t;
+    num0 += wt * (c0 + c1 * o->E[1] + c2 * o->E[2]);
+    num1 += wt * (c0 + c1 * o->E[4] + c2 * o->E[5]);
+    num2 += wt * (c0 + c1 * o->E[7] + c2 * o->E[8]);
+    den += wt;
+  }
+  out[0] = num0 / den;
+  out[1] = num1 / den;
+  out[2] = num2 / den;
+}
+
+// L1..L3: sweep along axis k.  Input extents (Ex, Ey, Ez) with NNin nodal
+// values per element; the output has extent Ns+2 along k and 3*NNin nodes
+// (the new nodal index is the slowest digit).
+template <int D, int N>
+__global__ void __launch_bounds__(256) k_lim_sweep(Params p, int chunk0, int k) {
+  using DM = Dims<D, N>;
+  constexpr int NV = DM::NV, L = DM::L, NE = DM::NE;
+  const int len = chunk_len(p, chunk0);
+  int ein[3], eout[3];
+  for (int j = 0; j < 3; ++j) {
+    const bool done = j < k, active = j < D;
+    ein[j] = active ? (done ? NE : L) : 1;
+    eout[j] = active ? (j <= k ? NE : L) : 1;
+  }
+  const int NNin = ipow3(k);
+  const int insz = ein[0] * ein[1] * ein[2] * NNin;
+  const int outsz = eout[0] * eout[1] * eout[2] * NNin;   // elements producing 3 values
+  const double* in = (k == 0) ? p.b.patch : p.b.sweep[k - 1];
+  double* out = p.b.sweep[k];
+  const int stride = (k == 0) ? 1 : (k == 1 ? ein[0] : ein[0] * ein[1]);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       e < (long long)len * NV * outsz; e += (long long)gridDim.x * blockDim.x) {
+    const long long jv = e / outsz;
+    int r = (int)(e - jv * outsz);
+    const int node = r % NNin;
+    r /= NNin;
+    int idx[3];
+    idx[0] = r % eout[0];
+    r /= eout[0];
+    idx[1] = r % eout[1];
+    idx[2] = r / eout[1];
+    // input element whose axis-k index is idx[k] (stencil idx[k] .. idx[k]+4)
+    int off = 0;
+    {
+      int s = 1;
+      for (int j = 0; j < 3; ++j) {
+        off += idx[j] * s;
+        s *= ein[j];
+      }
+    }
+    const double* src = in + jv * insz + (size_t)off * NNin + node;
+    double u[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) u[q] = src[(size_t)q * stride * NNin];
+    double res[3];
+    weno3(u, p.ops, res);
+    int ooff = idx[0] + eout[0] * (idx[1] + eout[1] * idx[2]);
+    double* dst = out + jv * (size_t)outsz * 3 + (size_t)ooff * NNin * 3 + node;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) dst[a * NNin] = res[a];
+  }
+}
+
+// L4: degree-2 space-time predictor on every subcell of the block -1..Ns
+// (Eq. pde.nc.dg2 with 3 GL nodes per axis, 3 Picard sweeps).
+constexpr int SUBS_PER_BLOCK_2D = 4;
+constexpr int SUBS_PER_BLOCK_3D = 2;
+
+template <int D, int N>
+__global__ void __launch_bounds__(256) k_lim_predict(Params p, int chunk0) {
+  using DM = Dims<D, N>;
+  constexpr int NV = DM::NV, NST3 = DM::NST3, ND3 = DM::ND3, NED = DM::NED, Ns = DM::Ns;
+  constexpr int SPB = (D == 2) ? SUBS_PER_BLOCK_2D : SUBS_PER_BLOCK_3D;
+  __shared__ double su[SPB][NV * ND3];
+  __shared__ double sq[SPB][NV * NST3];
+  __shared__ double sF[SPB][D * NV * NST3];
+  __shared__ double D3[9], K3[9];
+  if (threadIdx.x < 9) {
+    D3[threadIdx.x] = p.ops->D3[threadIdx.x];
+    K3[threadIdx.x] = p.ops->Kt3[threadIdx.x];
+  }
+  const int len = chunk_len(p, chunk0);
+  const int grp = threadIdx.x / NST3, lt = threadIdx.x - grp * NST3;
+  const bool active_thread = grp < SPB;
+  const double dt = *p.b.dt;
+  double c[3];
+#pragma unroll
+  for (int k = 0; k < D; ++k) c[k] = dt * Ns / p.geo.dx[k];
+  const double gm1 = p.gamma - 1.0;
+  const double* W = p.b.sweep[D - 1];          // [j][v][NED][ND3]
+  const long long total = (long long)len * NED;
+  for (long long base = (long long)blockIdx.x * SPB; base < total;
+       base += (long long)gridDim.x * SPB) {
+    const long long item = base + grp;
+    const bool live = active_thread && item < total;
+    __syncthreads();
+    if (live) {
+      const long long j = item / NED;
+      const int sc = (int)(item - j * NED);
+      for (int e = lt; e < NV * ND3; e += NST3) {
+        const int v = e / ND3, i = e - v * ND3;
+        su[grp][e] = W[((j * NV + v) * NED + sc) * ND3 + i];
+      }
+    }
+    __syncthreads();
+    if (live)
+      for (int e = lt; e < NV * NST3; e += NST3) {
+        const int v = e / NST3, l = e - v * NST3;
+        sq[grp][e] = su[grp][v * ND3 + (l % ND3)];
+      }
+    __syncthreads();
+    for (int it = 0; it < 3; ++it) {
+      if (live) picard_flux<D, 3, double>(sq[grp], sF[grp], gm1, lt, NST3);
+      __syncthreads();
+      if (live) picard_deriv<D, 3, double>(sF[grp], sq[grp], D3, c, lt, NST3);
+      __syncthreads();
+      if (live) picard_time<D, 3, double>(sq[grp], su[grp], K3, lt, NST3);
+      __syncthreads();
+    }
+    if (live) {
+      double* dst = p.b.qsub + item * (size_t)(NV * NST3);
+      for (int e = lt; e < NV * NST3; e += NST3) dst[e] = sq[grp][e];
+    }
+  }
+}
+
+// L5: sub-face fluxes normal to axis k: Rusanov at the 3^(d-1) x 3
+// tangential x time GL points, averaged with the GL weights.  Faces f = 0..Ns
+// along k (between local subcells f-1 and f), tangential subcells 0..Ns-1.
+template <int D, int N>
+__global__ void __launch_bounds__(256) k_lim_flux(Params p, int chunk0, int k) {
+  using DM = Dims<D, N>;
+  constexpr int NV = DM::NV, NST3 = DM::NST3, ND3 = DM::ND3, NE = DM::NE, NED = DM::NED,
+                Ns = DM::Ns;
+  constexpr int NFK = (Ns + 1) * DM::NSF;
+  const int len = chunk_len(p, chunk0);
+  const Ops* o = p.ops;
+  const int stk = (k == 0) ? 1 : (k == 1 ? 3 : 9);       // node stride of axis k
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)len * NFK;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long j = e / NFK;
+    int r = (int)(e - j * NFK);
+    int fc[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const int ext = (a == k) ? Ns + 1 : Ns;
+      fc[a] = r % ext;
+      r /= ext;
+    }
+    // left / right subcells in the (Ns+2)^d block (array index = local + 1)
+    int sl = 0, sr = 0, mul = 1;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const int il = (a == k) ? fc[a] : fc[a] + 1;
+      const int ir = (a == k) ? fc[a] + 1 : fc[a] + 1;
+      sl += il * mul;
+      sr += ir * mul;
+      mul *= NE;
+    }
+    const double* qL = p.b.qsub + ((size_t)j * NED + sl) * NV * NST3;
+    const double* qR = p.b.qsub + ((size_t)j * NED + sr) * NV * NST3;
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+    // tangential x time nodes: digits over axes != k, then time
+    for (int t = 0; t < ND3; ++t) {
+      int base = 0, tt = t, wmul = 1;
+      double wt = 1.0;
+      int st = 1;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        if (a != k) {
+          const int dg = tt % 3;
+          tt /= 3;
+          base += dg * st;
+          wt *= o->w3[dg];
+        }
+        st *= 3;
+      }
+      const int m = tt;                 // remaining digit: time node
+      wt *= o->w3[m];
+      base += m * ND3;
+      (void)wmul;
+      double QL[NV], QR[NV], G[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const double* a = qL + v * NST3 + base;
+        const double* b = qR + v * NST3 + base;
+        QL[v] = o->phi13[0] * a[0] + o->phi13[1] * a[stk] + o->phi13[2] * a[2 * stk];
+        QR[v] = o->phi03[0] * b[0] + o->phi03[1] * b[stk] + o->phi03[2] * b[2 * stk];
+      }
+      rusanov<D>(QL, QR, k, p.gamma, G);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] += wt * G[v];
+    }
+    double* dst = p.b.fsub[k] + (size_t)j * NV * NFK + (e - j * NFK);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) dst[v * NFK] = acc[v];
+  }
+}
+
+// L6: finite volume update, storage of v^{n+1}, reconstruction R, per-cell
+// min/max and wave speed, sub-face fluxes of the cell faces, and marking of
+// unlimited face neighbours for the flux correction.  One block per cell.
+template <int D, int N>
+__global__ void __launch_bounds__(128) k_lim_update(Params p, int chunk0) {
+  using DM = Dims<D, N>;
+  constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, Ns = DM::Ns, NSD = DM::NSD, L = DM::L,
+                LD = DM::LD, NSF = DM::NSF;
+  constexpr int NFK = (Ns + 1) * NSF;
+  extern __shared__ double sm[];
+  double* A = sm;                 // NV * NSD
+  double* B = A + NV * NSD;       // NV * NSD
+  double* R1 = B + NV * NSD;      // n * Ns
+  double* mm = R1 + n * Ns;       // 2 NV
+  double* red = mm + 2 * NV;      // 32
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = tid; i < n * Ns; i += nth) R1[i] = p.ops->R1[i];
+  const int len = chunk_len(p, chunk0);
+  const int nxt = 1 - p.cur;
+  const double dt = *p.b.dt;
+  double c[3];
+#pragma unroll
+  for (int k = 0; k < D; ++k) c[k] = dt * Ns / p.geo.dx[k];
+  for (int j = blockIdx.x; j < len; j += gridDim.x) {
+    const int t = chunk0 + j;
+    const long long cell = p.b.list[nxt][t];
+    const double* pt = p.b.patch + (size_t)j * NV * LD;
+    double* st = p.b.store[nxt] + (size_t)t * NV * NSD;
+    __syncthreads();
+    for (int e = tid; e < NV * NSD; e += nth) {
+      const int v = e / NSD;
+      int s = e - v * NSD;
+      int sc[3] = {0, 0, 0};
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        sc[a] = s % Ns;
+        s /= Ns;
+      }
+      int poff = 0, pm = 1;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        poff += (sc[a] + 3) * pm;
+        pm *= L;
+      }
+      double val = pt[v * LD + poff];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        int flo = 0, mul = 1;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          flo += sc[a] * mul;
+          mul *= (a == k) ? Ns + 1 : Ns;
+        }
+        const int kst = (k == 0) ? 1 : (k == 1 ? Ns : Ns * Ns);   // stride of axis k
+        const double* F = p.b.fsub[k] + ((size_t)j * NV + v) * NFK;
+        val -= c[k] * (F[flo + kst] - F[flo]);
+      }
+      A[e] = val;
+      st[e] = val;
+    }
+    __syncthreads();
+    double lam;
+    const bool bad = check_subcells<D>(A, NSD, nullptr, p.gamma, mm, &lam, red);
+    if (tid == 0) {
+      p.b.lam[cell] = lam;
+      if (bad) atomicAdd(&p.b.counters[CNT_INADM], 1);
+    }
+    if (tid < 2 * NV) p.b.cmm[nxt][cell * 2 * NV + tid] = mm[tid];
+    // sub-face fluxes on the faces of the cell: edge[t][k][side][v][NSF]
+    for (int e = tid; e < D * 2 * NV * NSF; e += nth) {
+      const int k = e / (2 * NV * NSF);
+      int r = e - k * (2 * NV * NSF);
+      const int side = r / (NV * NSF);
+      r -= side * NV * NSF;
+      const int v = r / NSF, ts = r - v * NSF;
+      int tc[2] = {ts % Ns, ts / Ns};
+      int fidx = 0, mul = 1, q = 0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        const int cc = (a == k) ? (side ? Ns : 0) : tc[q++];
+        fidx += cc * mul;
+        mul *= (a == k) ? Ns + 1 : Ns;
+      }
+      p.b.edge[(size_t)t * D * 2 * NV * NSF + e] = p.b.fsub[k][((size_t)j * NV + v) * NFK + fidx];
+    }
+    // reconstruction R of the new subcell data
+    __syncthreads();
+    double* u = apply_all_axes<D>(A, B, R1, n, Ns, NV, tid, nth);
+    double* Uo = p.b.U[nxt] + cell * (NV * ND);
+    for (int e = tid; e < NV * ND; e += nth) Uo[e] = u[e];
+    // unlimited face neighbours get the flux correction
+    if (tid < 2 * D) {
+      const int k = tid >> 1, side = (tid & 1) ? 1 : -1;
+      int ijk[3], nb[3];
+      cell_coords<D>(cell, p.geo, ijk);
+      if (face_neighbour<D>(p.geo, ijk, k, side, nb)) {
+        const long long nc = cell_index<D>(nb, p.geo);
+        if (!p.b.beta[nxt][nc]) {
+          const int old = atomicExch(&p.b.fixstamp[nc], p.stamp);
+          if (old != p.stamp) {
+            const int idx = atomicAdd(&p.b.counters[CNT_FIX], 1);
+            p.b.fixlist[idx] = (int)nc;
+          }
+        }
+      }
+    }
+  }
+}
+
+// L7: flux correction of unlimited cells with troubled face neighbours
+// (Sec. 4.4): on each such face the DG flux Gbar is replaced by the sub-face
+// fluxes integrated against the test functions,
+//   Fsub_b = (1/W_b) sum_e Fbar_e prod P1[e][b] / Ns^(d-1).
+template <int D, int N>
+__global__ void __launch_bounds__(128) k_lim_fix(Params p) {
+  using DM = Dims<D, N>;
+  constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, NF = DM::NF, Ns = DM::Ns, NSD = DM::NSD,
+                NSF = DM::NSF;
+  extern __shared__ double sm[];
+  double* U = sm;                      // NV * ND
+  double* A = U + NV * ND;             // NV * max(NSD, ...)
+  double* B = A + NV * NSD;
+  double* Mt = B + NV * NSD;           // n * Ns
+  double* P1 = Mt + n * Ns;            // Ns * n
+  double* mm = P1 + Ns * n;
+  double* red = mm + 2 * NV;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = tid; i < n * Ns; i += nth) {
+    Mt[i] = p.ops->Mt[i];
+    P1[i] = p.ops->P1[i];
+  }
+  const int nfix = p.b.counters[CNT_FIX];
+  const int nxt = 1 - p.cur;
+  const double dt = *p.b.dt;
+  for (int f = blockIdx.x; f < nfix; f += gridDim.x) {
+    const long long cell = p.b.fixlist[f];
+    int ijk[3];
+    cell_coords<D>(cell, p.geo, ijk);
+    double* Uo = p.b.U[nxt] + cell * (NV * ND);
+    __syncthreads();
+    for (int e = tid; e < NV * ND; e += nth) U[e] = Uo[e];
+    for (int k = 0; k < D; ++k) {
+      const double ck = dt / p.geo.dx[k];
+      for (int side = -1; side <= 1; side += 2) {
+        int nb[3];
+        if (!face_neighbour<D>(p.geo, ijk, k, side, nb)) continue;
+        const long long nc = cell_index<D>(nb, p.geo);
+        if (!p.b.beta[nxt][nc]) continue;
+        const int slot = p.b.slot[nxt][nc];
+        if (slot < 0) continue;
+        // the neighbour's face that touches this cell
+        const int eside = (side > 0) ? 0 : 1;
+        const double* Fs = p.b.edge + (size_t)slot * D * 2 * NV * NSF + ((size_t)k * 2 + eside) * NV * NSF;
+        __syncthreads();
+        // project the Ns^(d-1) sub-face fluxes on the n^(d-1) tangential nodes
+        for (int e = tid; e < NV * NSF; e += nth) A[e] = Fs[e];
+        __syncthreads();
+        double* Fp = A;
+        if (D == 2) {
+          int ext[3] = {Ns, 1, 1};
+          apply_axis<1>(A, B, Mt, n, Ns, 0, ext, NV, tid, nth);
+          Fp = B;
+        } else {
+          int ext[3] = {Ns, Ns, 1};
+          apply_axis<2>(A, B, Mt, n, Ns, 0, ext, NV, tid, nth);
+          __syncthreads();
+          ext[0] = n;
+          apply_axis<2>(B, A, Mt, n, Ns, 1, ext, NV, tid, nth);
+          Fp = A;
+        }
+        __syncthreads();
+        const long long face = face_index<D>(p.geo, ijk, k, side > 0 ? ijk[k] + 1 : ijk[k]);
+        const double* Gd = p.b.G[k] + face * NV * NF;
+        for (int e = tid; e < NV * ND; e += nth) {
+          const int v = e / ND, i = e - v * ND;
+          const int st = (k == 0) ? 1 : (k == 1 ? n : n * n);
+          const int ak = (i / st) % n;
+          const int ts = tangential<D, n>(i, k);
+          const double diff = Fp[v * NF + ts] - Gd[v * NF + ts];
+          if (side > 0) U[e] -= ck * p.ops->phi1w[ak] * diff;
+          else U[e] += ck * p.ops->phi0w[ak] * diff;
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < NV * ND; e += nth) {
+      Uo[e] = U[e];
+      A[e] = U[e];
+    }
+    __syncthreads();
+    double* vs = apply_all_axes<D>(A, B, P1, Ns, n, NV, tid, nth);
+    double lam;
+    check_subcells<D>(vs, NSD, nullptr, p.gamma, mm, &lam, red);
+    if (tid == 0) p.b.lam[cell] = lam;
+    if (tid < 2 * NV) p.b.cmm[nxt][cell * 2 * NV + tid] = mm[tid];
+  }
+}
+
+}  // namespace adg

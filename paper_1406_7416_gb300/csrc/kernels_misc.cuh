@@ -1,0 +1,315 @@
+// Load-time kernels (initial detection, full-state load / read), the device
+// projection of the test problems' initial data, and the time-step reduction.
+#pragma once
+
+#include "kernels_lim.cuh"
+
+namespace adg {
+
+// Initial detection (Sec. 4.4, last paragraph) or plain load.  One cell per
+// block.  `exact` (device [cells][nv][Ns^d]) may be null: no detection.
+// cmm_ex: per-cell min/max of the exact averages (used when exact != null).
+template <int D, int N>
+__global__ void __launch_bounds__(128) k_load_detect(Params p, const double* __restrict__ exact,
+                                                     const double* __restrict__ cmm_ex) {
+  using DM = Dims<D, N>;
+  constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, Ns = DM::Ns, NSD = DM::NSD;
+  extern __shared__ double sm[];
+  double* A = sm;
+  double* B = A + NV * NSD;
+  double* P1 = B + NV * NSD;
+  double* R1 = P1 + Ns * n;
+  double* lohi = R1 + n * Ns;
+  double* mm = lohi + 2 * NV;
+  double* red = mm + 2 * NV;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = tid; i < Ns * n; i += nth) {
+    P1[i] = p.ops->P1[i];
+    R1[i] = p.ops->R1[i];
+  }
+  __shared__ int s_slot;
+  const int cur = p.cur;
+  for (long long cell = blockIdx.x; cell < p.geo.cells; cell += gridDim.x) {
+    int ijk[3];
+    cell_coords<D>(cell, p.geo, ijk);
+    double* U = p.b.U[cur] + cell * (NV * ND);
+    __syncthreads();
+    for (int e = tid; e < NV * ND; e += nth) A[e] = U[e];
+    __syncthreads();
+    double* vs = apply_all_axes<D>(A, B, P1, Ns, n, NV, tid, nth);
+    if (exact) dmp_interval<D>(p, cmm_ex, ijk, lohi);
+    __syncthreads();
+    double lam;
+    const bool troubled = check_subcells<D>(vs, NSD, exact ? lohi : nullptr, p.gamma, mm, &lam, red)
+                          && exact != nullptr;
+    if (!troubled) {
+      if (tid == 0) {
+        p.b.beta[cur][cell] = 0;
+        p.b.slot[cur][cell] = -1;
+        p.b.lam[cell] = lam;
+      }
+      if (tid < 2 * NV) p.b.cmm[cur][cell * 2 * NV + tid] = mm[tid];
+      continue;
+    }
+    // flagged at t = 0: keep the exact averages, DOFs become R(exact)
+    if (tid == 0) {
+      int slot = atomicAdd(&p.b.counters[CNT_TROUBLED0 + cur], 1);
+      if (slot < p.cap) {
+        p.b.list[cur][slot] = (int)cell;
+      } else {
+        atomicOr(&p.b.counters[CNT_STATUS], 1);
+        slot = -1;
+      }
+      s_slot = slot;
+    }
+    __syncthreads();
+    const int slot = s_slot;
+    const double* ex = exact + cell * (size_t)(NV * NSD);
+    if (slot < 0) {
+      if (tid == 0) p.b.beta[cur][cell] = 0;
+      continue;
+    }
+    double* st = p.b.store[cur] + (size_t)slot * NV * NSD;
+    __syncthreads();
+    for (int e = tid; e < NV * NSD; e += nth) {
+      st[e] = ex[e];
+      A[e] = ex[e];
+    }
+    __syncthreads();
+    check_subcells<D>(A, NSD, nullptr, p.gamma, mm, &lam, red);
+    double* u = apply_all_axes<D>(A, B, R1, n, Ns, NV, tid, nth);
+    for (int e = tid; e < NV * ND; e += nth) U[e] = u[e];
+    if (tid == 0) {
+      p.b.beta[cur][cell] = 1;
+      p.b.slot[cur][cell] = slot;
+      p.b.lam[cell] = lam;
+    }
+    if (tid < 2 * NV) p.b.cmm[cur][cell * 2 * NV + tid] = mm[tid];
+  }
+}
+
+// Per-cell min / max of subcell data sub[cells][nv][Ns^d] -> out[cells][nv][2]
+template <int D, int N>
+__global__ void k_sub_minmax(const double* __restrict__ sub, double* __restrict__ out,
+                             long long cells) {
+  using DM = Dims<D, N>;
+  constexpr int NV = DM::NV, NSD = DM::NSD;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < cells * NV;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double* s = sub + e * NSD;
+    double mn = s[0], mx = s[0];
+    for (int i = 1; i < NSD; ++i) {
+      mn = fmin(mn, s[i]);
+      mx = fmax(mx, s[i]);
+    }
+    out[2 * e] = mn;
+    out[2 * e + 1] = mx;
+  }
+}
+
+// Full-state load: flags given; flagged cells take their subcell rows.
+template <int D, int N>
+__global__ void __launch_bounds__(128) k_load_full(Params p, const uint8_t* __restrict__ beta,
+                                                   const double* __restrict__ sub) {
+  using DM = Dims<D, N>;
+  constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, Ns = DM::Ns, NSD = DM::NSD;
+  extern __shared__ double sm[];
+  double* A = sm;
+  double* B = A + NV * NSD;
+  double* P1 = B + NV * NSD;
+  double* mm = P1 + Ns * n;
+  double* red = mm + 2 * NV;
+  __shared__ int s_slot;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = tid; i < Ns * n; i += nth) P1[i] = p.ops->P1[i];
+  const int cur = p.cur;
+  for (long long cell = blockIdx.x; cell < p.geo.cells; cell += gridDim.x) {
+    __syncthreads();
+    const bool flagged = beta[cell] != 0;
+    double* vs;
+    if (flagged) {
+      if (tid == 0) {
+        int slot = atomicAdd(&p.b.counters[CNT_TROUBLED0 + cur], 1);
+        if (slot < p.cap) {
+          p.b.list[cur][slot] = (int)cell;
+        } else {
+          atomicOr(&p.b.counters[CNT_STATUS], 1);
+          slot = -1;
+        }
+        s_slot = slot;
+      }
+      __syncthreads();
+      const int slot = s_slot;
+      const double* src = sub + cell * (size_t)(NV * NSD);
+      for (int e = tid; e < NV * NSD; e += nth) {
+        A[e] = src[e];
+        if (slot >= 0) p.b.store[cur][(size_t)slot * NV * NSD + e] = src[e];
+      }
+      if (tid == 0) {
+        p.b.beta[cur][cell] = slot >= 0 ? 1 : 0;
+        p.b.slot[cur][cell] = slot;
+      }
+      __syncthreads();
+      vs = A;
+    } else {
+      const double* U = p.b.U[cur] + cell * (NV * ND);
+      for (int e = tid; e < NV * ND; e += nth) A[e] = U[e];
+      if (tid == 0) {
+        p.b.beta[cur][cell] = 0;
+        p.b.slot[cur][cell] = -1;
+      }
+      __syncthreads();
+      vs = apply_all_axes<D>(A, B, P1, Ns, n, NV, tid, nth);
+    }
+    double lam;
+    check_subcells<D>(vs, NSD, nullptr, p.gamma, mm, &lam, red);
+    if (tid == 0) p.b.lam[cell] = lam;
+    if (tid < 2 * NV) p.b.cmm[cur][cell * 2 * NV + tid] = mm[tid];
+  }
+}
+
+// Subcell data of flagged cells -> sub[cells][nv][Ns^d] (NaN rows elsewhere)
+template <int D, int N>
+__global__ void k_read_full(Params p, double* __restrict__ sub) {
+  using DM = Dims<D, N>;
+  constexpr int NV = DM::NV, NSD = DM::NSD;
+  const long long total = p.geo.cells * NV * NSD;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long cell = e / (NV * NSD);
+    const int r = (int)(e - cell * (NV * NSD));
+    double v = __longlong_as_double(0x7ff8000000000000LL);
+    if (p.b.beta[p.cur][cell]) {
+      const int slot = p.b.slot[p.cur][cell];
+      if (slot >= 0) v = p.b.store[p.cur][(size_t)slot * NV * NSD + r];
+    }
+    sub[e] = v;
+  }
+}
+
+// Primitive initial state at one point of a test problem (Sec. 5.2, 5.6, 5.8).
+template <int D>
+__device__ __forceinline__ void problem_state(const adg_problem& pr, const double* x, double fac,
+                                              double gamma, double* Q) {
+  double rho, vel[3] = {0.0, 0.0, 0.0}, p;
+  if (pr.kind == ADG_IC_RADIAL) {
+    double r2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) r2 += (x[k] - pr.center[k]) * (x[k] - pr.center[k]);
+    const double* s = (r2 <= pr.radius * pr.radius) ? pr.inner : pr.outer;
+    rho = s[0] * fac;
+#pragma unroll
+    for (int k = 0; k < D; ++k) vel[k] = s[1 + k];
+    p = s[1 + D];
+  } else {
+    const bool right = x[0] > pr.center[0], up = x[1] > pr.center[1];
+    const int q = right ? (up ? 0 : 3) : (up ? 1 : 2);
+    rho = pr.quad[q][0];
+    vel[0] = pr.quad[q][1];
+    vel[1] = pr.quad[q][2];
+    p = pr.quad[q][3];
+    if (pr.vortex) {
+      const double xp = x[0] - pr.vortex_center[0], yp = x[1] - pr.vortex_center[1];
+      const double r2 = xp * xp + yp * yp;
+      const double b = pr.vortex_strength;
+      const double e = exp(0.5 * (1.0 - r2));
+      const double pi = 3.14159265358979323846;
+      // temperature perturbation with beta^2 (radial equilibrium of the vortex)
+      const double dT = -(gamma - 1.0) * b * b / (8.0 * gamma * pi * pi) * e * e;
+      const double T0 = p / rho;
+      const double T = T0 + dT;
+      rho = rho * pow(T / T0, 1.0 / (gamma - 1.0));
+      p = rho * T;
+      vel[0] += -yp * b / (2.0 * pi) * e;
+      vel[1] += xp * b / (2.0 * pi) * e;
+    }
+  }
+  Q[0] = rho;
+  double kin = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    Q[1 + k] = rho * vel[k];
+    kin += vel[k] * vel[k];
+  }
+  Q[1 + D] = p / (gamma - 1.0) + 0.5 * rho * kin;
+}
+
+// L2 projection of the initial data (composite rule: Ns subintervals x
+// (N+2) GL points per axis) and exact subcell averages.  One cell per block;
+// rows of points along x are reduced first, then accumulated.
+template <int D, int N>
+__global__ void __launch_bounds__(128) k_project(Params p, adg_problem pr,
+                                                 const double* __restrict__ fac,
+                                                 double* __restrict__ exact) {
+  using DM = Dims<D, N>;
+  constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, Ns = DM::Ns, NSD = DM::NSD;
+  constexpr int Q1 = N + 2, NQ = Ns * Q1;
+  __shared__ double row[NV][NQ];
+  __shared__ double tx[NV][n];
+  __shared__ double sx[NV][Ns];
+  __shared__ double Ua[NV * ND];
+  __shared__ double Va[NV * NSD];
+  const Ops* o = p.ops;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int nrows = (D == 3) ? NQ * NQ : NQ;
+  for (long long cell = blockIdx.x; cell < p.geo.cells; cell += gridDim.x) {
+    int ijk[3];
+    cell_coords<D>(cell, p.geo, ijk);
+    const double f = fac ? fac[cell] : 1.0;
+    __syncthreads();
+    for (int e = tid; e < NV * ND; e += nth) Ua[e] = 0.0;
+    for (int e = tid; e < NV * NSD; e += nth) Va[e] = 0.0;
+    for (int rw = 0; rw < nrows; ++rw) {
+      const int qy = rw % NQ, qz = rw / NQ;
+      __syncthreads();
+      for (int px = tid; px < NQ; px += nth) {
+        double x[3];
+        x[0] = p.geo.x0[0] + (ijk[0] + o->cq_x[px]) * p.geo.dx[0];
+        x[1] = p.geo.x0[1] + (ijk[1] + o->cq_x[qy]) * p.geo.dx[1];
+        x[2] = (D == 3) ? p.geo.x0[2] + (ijk[2] + o->cq_x[qz]) * p.geo.dx[2] : 0.0;
+        double Q[NV];
+        problem_state<D>(pr, x, f, p.gamma, Q);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) row[v][px] = Q[v];
+      }
+      __syncthreads();
+      // reduce the row along x: DOF weights and subcell averages
+      for (int e = tid; e < NV * (n + Ns); e += nth) {
+        const int v = e / (n + Ns), r = e - v * (n + Ns);
+        double acc = 0.0;
+        if (r < n) {
+          for (int q = 0; q < NQ; ++q) acc += o->cq_w[q] * o->cq_phi[q * n + r] * row[v][q];
+          tx[v][r] = acc / o->w[r];
+        } else {
+          const int s = r - n;
+          for (int q = s * Q1; q < (s + 1) * Q1; ++q) acc += o->cq_w[q] * Ns * row[v][q];
+          sx[v][s] = acc;
+        }
+      }
+      __syncthreads();
+      const double wy = o->cq_w[qy], wz = (D == 3) ? o->cq_w[qz] : 1.0;
+      for (int e = tid; e < NV * ND; e += nth) {
+        const int v = e / ND;
+        int i = e - v * ND;
+        const int a = i % n, b = (i / n) % n, c = (D == 3) ? i / (n * n) : 0;
+        double wgt = wy * o->cq_phi[qy * n + b] / o->w[b];
+        if (D == 3) wgt *= wz * o->cq_phi[qz * n + c] / o->w[c];
+        Ua[e] += wgt * tx[v][a];
+      }
+      const int sy = qy / Q1, sz = (D == 3) ? qz / Q1 : 0;
+      for (int e = tid; e < NV * Ns; e += nth) {
+        const int v = e / Ns, s = e - v * Ns;
+        double wgt = wy * Ns;
+        if (D == 3) wgt *= wz * Ns;
+        Va[v * NSD + s + Ns * (sy + Ns * sz)] += wgt * sx[v][s];
+      }
+    }
+    __syncthreads();
+    double* U = p.b.U[p.cur] + cell * (NV * ND);
+    for (int e = tid; e < NV * ND; e += nth) U[e] = Ua[e];
+    double* ex = exact + cell * (size_t)(NV * NSD);
+    for (int e = tid; e < NV * NSD; e += nth) ex[e] = Va[e];
+  }
+}
+
+}  // namespace adg

@@ -1,0 +1,150 @@
+// Launch configuration of every kernel for one (dimension, degree).
+#pragma once
+
+#include "kernels_misc.cuh"
+
+namespace adg {
+
+constexpr int kBlocksPerSM = 8;
+constexpr int kNumSM = 152;
+
+inline int grid_for(long long work, int threads, int cap_blocks = kNumSM * kBlocksPerSM * 4) {
+  long long b = (work + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap_blocks) b = cap_blocks;
+  return (int)b;
+}
+
+inline int cells_grid(long long cells) {
+  return (int)(cells < (1LL << 30) ? cells : (1LL << 30));
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int D, int N>
+struct Launch {
+  using DM = Dims<D, N>;
+  static constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, NSD = DM::NSD, Ns = DM::Ns;
+
+  static int pred_threads() {
+    int t = ((NV * DM::NST + 31) / 32) * 32;
+    return t > 256 ? 256 : t;
+  }
+  static size_t cell_smem() { return (size_t)(2 * NV * NSD + 2 * Ns * n + 4 * NV + 64) * sizeof(double); }
+  static size_t fix_smem() {
+    return (size_t)(NV * ND + 2 * NV * NSD + 2 * Ns * n + 4 * NV + 64) * sizeof(double);
+  }
+
+  static void mark(cudaEvent_t* ev, int phase, cudaStream_t s) {
+    if (ev) cudaEventRecord(ev[phase], s);
+  }
+
+  static cudaError_t step_dg(const Params& p, cudaStream_t s, cudaEvent_t* ev) {
+    cudaError_t e;
+    const int grid = cells_grid(p.geo.cells);
+    mark(ev, PHASE_PREDICTOR, s);
+    if (p.prec == ADG_PREC_MIXED_FP32) {
+      const size_t sm = predictor_smem_bytes<D, N, true>();
+      if ((e = set_smem(k_predictor<D, N, true>, sm)) != cudaSuccess) return e;
+      k_predictor<D, N, true><<<grid, pred_threads(), sm, s>>>(p);
+    } else {
+      const size_t sm = predictor_smem_bytes<D, N, false>();
+      if ((e = set_smem(k_predictor<D, N, false>, sm)) != cudaSuccess) return e;
+      k_predictor<D, N, false><<<grid, pred_threads(), sm, s>>>(p);
+    }
+    mark(ev, PHASE_FACEFLUX, s);
+    for (int k = 0; k < D; ++k) {
+      const long long work = face_count<D>(p.geo, k) * DM::NF;
+      k_faceflux<D, N><<<grid_for(work, 256), 256, 0, s>>>(p, k);
+    }
+    mark(ev, PHASE_CORRECT, s);
+    const size_t sc = correct_smem_bytes<D, N>();
+    if ((e = set_smem(k_correct_detect<D, N>, sc)) != cudaSuccess) return e;
+    k_correct_detect<D, N><<<grid, 128, sc, s>>>(p);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t step_limiter(const Params& p, cudaStream_t s, cudaEvent_t* ev) {
+    cudaError_t e;
+    mark(ev, PHASE_LIMITER, s);
+    const int nchunks = (p.cap + p.chunk - 1) / p.chunk;
+    const size_t su = cell_smem();
+    if ((e = set_smem(k_lim_update<D, N>, su)) != cudaSuccess) return e;
+    constexpr int SPB = (D == 2) ? SUBS_PER_BLOCK_2D : SUBS_PER_BLOCK_3D;
+    for (int c = 0; c < nchunks; ++c) {
+      const int chunk0 = c * p.chunk;
+      const long long ch = p.chunk;
+      k_lim_patch<D, N><<<grid_for(ch * DM::LD, 256), 256, 0, s>>>(p, chunk0);
+      for (int k = 0; k < D; ++k)
+        k_lim_sweep<D, N><<<grid_for(ch * NV * DM::LD, 256), 256, 0, s>>>(p, chunk0, k);
+      k_lim_predict<D, N><<<grid_for(ch * DM::NED, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(
+          p, chunk0);
+      for (int k = 0; k < D; ++k)
+        k_lim_flux<D, N><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(p, chunk0, k);
+      k_lim_update<D, N><<<(int)(ch < kNumSM * 8 ? ch : kNumSM * 8), 128, su, s>>>(p, chunk0);
+    }
+    mark(ev, PHASE_FIX, s);
+    const size_t sf = fix_smem();
+    if ((e = set_smem(k_lim_fix<D, N>, sf)) != cudaSuccess) return e;
+    k_lim_fix<D, N><<<kNumSM * 8, 128, sf, s>>>(p);
+    mark(ev, PHASE_END, s);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t run(const LaunchArgs& a) {
+    const Params& p = *a.p;
+    cudaStream_t s = a.stream;
+    cudaError_t e;
+    const int grid = cells_grid(p.geo.cells);
+    switch (a.op) {
+      case OP_STEP_DG:
+        return step_dg(p, s, a.ev);
+      case OP_STEP_LIMITER:
+        return step_limiter(p, s, a.ev);
+      case OP_LOAD_DETECT: {
+        const size_t sm = cell_smem();
+        if ((e = set_smem(k_load_detect<D, N>, sm)) != cudaSuccess) return e;
+        k_load_detect<D, N><<<grid, 128, sm, s>>>(p, a.exact, a.cmm_ex);
+        return cudaGetLastError();
+      }
+      case OP_LOAD_FULL: {
+        const size_t sm = cell_smem();
+        if ((e = set_smem(k_load_full<D, N>, sm)) != cudaSuccess) return e;
+        k_load_full<D, N><<<grid, 128, sm, s>>>(p, a.beta, a.sub);
+        return cudaGetLastError();
+      }
+      case OP_READ_FULL:
+        k_read_full<D, N><<<grid_for(p.geo.cells * NV * NSD, 256), 256, 0, s>>>(p, a.out);
+        return cudaGetLastError();
+      case OP_PROJECT:
+        k_project<D, N><<<grid, 128, 0, s>>>(p, *a.prob, a.fac, a.out);
+        return cudaGetLastError();
+      case OP_SUB_MINMAX:
+        k_sub_minmax<D, N><<<grid_for(p.geo.cells * NV, 256), 256, 0, s>>>(a.sub, a.out,
+                                                                            p.geo.cells);
+        return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+  }
+};
+
+// Scratch of the limiter per troubled cell, in doubles.
+template <int D, int N>
+size_t scratch_of(size_t* patch, size_t* sw0, size_t* sw1, size_t* sw2, size_t* qsub,
+                  size_t* fsub) {
+  using DM = Dims<D, N>;
+  const size_t NV = DM::NV, L = DM::L, NE = DM::NE;
+  *patch = NV * DM::LD;
+  *sw0 = NV * NE * (D == 3 ? L * L : L) * 3;
+  *sw1 = NV * NE * NE * (D == 3 ? L : 1) * 9;
+  *sw2 = (D == 3) ? NV * NE * NE * NE * 27 : 0;
+  *qsub = (size_t)DM::NED * NV * DM::NST3;
+  *fsub = NV * (DM::Ns + 1) * DM::NSF;
+  return *patch + *sw0 + *sw1 + *sw2 + *qsub + D * *fsub;
+}
+
+}  // namespace adg

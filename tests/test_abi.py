@@ -1,0 +1,62 @@
+"""CPU checks of the C ABI: the library builds, loads, and exports every entry
+point that include/adg.h declares; argument validation needs no GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1406_7416_gb300 import adg, build_lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "adg.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(adg_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib.build()
+    return adg.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(adg.SYMBOLS)
+
+
+@pytest.mark.parametrize("dim,N,gamma,bc,prec", [
+    (1, 3, 1.4, [0, 0], 0),            # bad dimension
+    (2, 0, 1.4, [0, 0, 0, 0], 0),      # N out of range
+    (2, 10, 1.4, [0, 0, 0, 0], 0),
+    (3, 4, 1.4, [0] * 6, 0),           # 3D limited to N <= 3
+    (2, 3, 1.0, [0, 0, 0, 0], 0),      # gamma <= 1
+    (2, 3, 1.4, [0, 1, 0, 0], 0),      # unpaired periodic face
+    (2, 3, 1.4, [0, 0, 0, 0], 7),      # unknown precision
+])
+def test_create_rejects_bad_arguments(lib, dim, N, gamma, bc, prec):
+    g = adg.AdgGrid()
+    g.dim = dim
+    for k in range(3):
+        g.n[k] = 4
+        g.dx[k] = 0.1
+    bcs = (ctypes.c_int * 6)(*(bc + [0] * (6 - len(bc))))
+    h = ctypes.c_void_p()
+    assert lib.adg_create(ctypes.byref(g), N, gamma, bcs, prec, ctypes.byref(h)) == adg.ERR_ARG
+    assert not h.value
+
+
+def test_create_and_destroy_without_device_work(lib):
+    s = adg.Solver(2, (5, 3), (0, 0), (0.2, 0.3), (1, 1, 0, 0), 3)
+    assert (s.cells, s.nvar, s.nodes, s.subcells) == (15, 4, 16, 49)
+    with pytest.raises(adg.AdgError):
+        s.step(0.1)            # nothing loaded
+    with pytest.raises(adg.AdgError):
+        s.set_option(99, 1.0)
+    s.close()
