@@ -65,6 +65,8 @@ extern "C" {
 #define ADG_OPT_PICARD_ITERS 4    /* Picard sweeps of Eq. (pde.nc.dg2), default N+1   */
 #define ADG_OPT_SLOT_CAPACITY 5   /* max troubled cells per step (before first load)  */
 #define ADG_OPT_PROFILE 6         /* 1: time the phases of every step with CUDA events */
+#define ADG_OPT_FP64_SWEEPS 7     /* mixed precision: final Picard sweeps run in FP64
+                                     (default 1; the others run in FP32)              */
 
 /* Cartesian grid (Sec. 2.1): cells n[k] of size dx[k] from corner x0[k]. */
 typedef struct {

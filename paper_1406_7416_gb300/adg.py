@@ -24,6 +24,7 @@ BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
 PREC_FP64, PREC_MIXED_FP32 = 0, 1
 OPT_DMP_EPS, OPT_DMP_FLOOR, OPT_FORCE_LIMITER, OPT_PICARD_ITERS, OPT_SLOT_CAPACITY = 1, 2, 3, 4, 5
 OPT_PROFILE = 6
+OPT_FP64_SWEEPS = 7
 PHASES = ("predictor", "faceflux", "correct_detect", "limiter", "fix")
 IC_RADIAL, IC_QUADRANT = 0, 1
 

@@ -16,7 +16,7 @@ struct adg_state {
   Geo geo;
   int N = 0, dim = 0, nv = 0, prec = 0;
   double gamma = 1.4, eps = 1e-3, floor = 1e-4;
-  int force = 0, iters = 0;
+  int force = 0, iters = 0, fp64_sweeps = 1;
   long long cap_req = -1;
   int cap = 0, chunk = 0;
   void* (*alloc)(size_t, void*) = nullptr;
@@ -33,6 +33,8 @@ struct adg_state {
   size_t bytes_held = 0;
   std::string err;
   bool profile = false;
+  bool lam_mode = false;    // steps keep the per-cell wave speeds current
+  bool lam_valid = false;   // b.lam describes the current level
   cudaEvent_t ev[PHASE_COUNT] = {};
   double phase_ms[PHASE_COUNT] = {};
   int timed_steps = 0;
@@ -114,6 +116,8 @@ Params make_params(const adg_state* st) {
   p.b = st->b;
   p.cur = st->cur;
   p.stamp = st->stamp;
+  p.lam_mode = st->lam_mode ? 1 : 0;
+  p.fp64_sweeps = st->fp64_sweeps < st->iters ? st->fp64_sweeps : st->iters;
   return p;
 }
 
@@ -267,6 +271,7 @@ int load_detect(adg_state* st, const double* exact_dev) {
   CUDA_TRY(st, cudaMemcpy(&status, st->b.counters + CNT_STATUS, sizeof(int), cudaMemcpyDeviceToHost));
   if (status & 1) return fail(st, ADG_ERR_CAPACITY, "more flagged cells than subcell slots");
   st->loaded = true;
+  st->lam_valid = true;
   return ADG_OK;
 }
 
@@ -303,6 +308,19 @@ int common_step(adg_state* st) {
   if (rc) return rc;
   st->cur = nxt;
   st->pending = st->profile;
+  st->lam_valid = st->lam_mode;
+  return ADG_OK;
+}
+
+// Make b.lam describe the current level; later steps keep it current.
+int ensure_lambda(adg_state* st) {
+  st->lam_mode = true;
+  if (st->lam_valid) return ADG_OK;
+  LaunchArgs a{};
+  a.op = OP_LAMBDA;
+  int rc = launch(st, a, "wave speeds");
+  if (rc) return rc;
+  st->lam_valid = true;
   return ADG_OK;
 }
 
@@ -387,6 +405,10 @@ int adg_set_option(adg_state* st, int key, double value) {
       if (!(value >= 1.0 && value <= 64.0)) return fail(st, ADG_ERR_ARG, "iterations in 1..64");
       st->iters = (int)value;
       return ADG_OK;
+    case ADG_OPT_FP64_SWEEPS:
+      if (!(value >= 1.0 && value <= 64.0)) return fail(st, ADG_ERR_ARG, "FP64 sweeps in 1..64");
+      st->fp64_sweeps = (int)value;
+      return ADG_OK;
     case ADG_OPT_PROFILE:
       if (value != 0.0 && !st->ev[0])
         for (int i = 0; i < PHASE_COUNT; ++i) CUDA_TRY(st, cudaEventCreate(&st->ev[i]));
@@ -467,6 +489,7 @@ int adg_load_full(adg_state* st, const double* dofs, const uint8_t* beta, const 
   CUDA_TRY(st, cudaMemcpy(&status, st->b.counters + CNT_STATUS, sizeof(int), cudaMemcpyDeviceToHost));
   if (status & 1) return fail(st, ADG_ERR_CAPACITY, "more flagged cells than subcell slots");
   st->loaded = true;
+  st->lam_valid = true;
   return ADG_OK;
 }
 
@@ -502,6 +525,8 @@ int adg_step_cfl(adg_state* st, double cfl, double dt_max) {
   if (!st) return ADG_ERR_ARG;
   if (!st->loaded) return fail(st, ADG_ERR_ARG, "nothing loaded");
   if (!(cfl > 0.0)) return fail(st, ADG_ERR_ARG, "cfl must be positive");
+  int rc = ensure_lambda(st);
+  if (rc) return rc;
   Params p = make_params(st);
   CUDA_TRY(st, launch_dt(p, cfl, dt_max, st->stream));
   return common_step(st);
@@ -511,6 +536,8 @@ int adg_max_dt(adg_state* st, double cfl, double* dt_out) {
   if (!st || !dt_out) return ADG_ERR_ARG;
   if (!st->loaded) return fail(st, ADG_ERR_ARG, "nothing loaded");
   if (!(cfl > 0.0)) return fail(st, ADG_ERR_ARG, "cfl must be positive");
+  int rc0 = ensure_lambda(st);
+  if (rc0) return rc0;
   Params p = make_params(st);
   CUDA_TRY(st, launch_dt(p, cfl, -1.0, st->stream));
   double dt = 0.0;

@@ -95,6 +95,8 @@ struct Params {
   Bufs b;
   int cur;               // buffer index of time level n
   int stamp;             // step counter (fix-list stamps)
+  int lam_mode;          // 1: kernels keep the per-cell wave speeds current
+  int fp64_sweeps;       // mixed precision: number of final FP64 Picard sweeps
 };
 
 // Kernel launch interface: one dispatcher per translation unit (2D low N,
@@ -106,7 +108,8 @@ enum LaunchOp {
   OP_LOAD_FULL,        // full-state load
   OP_READ_FULL,        // subcell rows of flagged cells
   OP_PROJECT,          // initial data projection
-  OP_SUB_MINMAX        // per-cell min/max of subcell rows
+  OP_SUB_MINMAX,       // per-cell min/max of subcell rows
+  OP_LAMBDA            // per-cell wave speeds of the current level
 };
 
 struct LaunchArgs {

@@ -3,6 +3,8 @@
 // detector (Sec. 4.3 Eqs. positivity, dmp, relax).
 #pragma once
 
+#include <climits>
+
 #include "adg_internal.h"
 
 namespace adg {
@@ -71,8 +73,8 @@ __device__ __forceinline__ void picard_deriv(const T* __restrict__ F, T* __restr
   }
 }
 
-template <int D, int n, typename T>
-__device__ __forceinline__ void picard_time(T* __restrict__ q, const double* __restrict__ u,
+template <int D, int n, typename T, typename UT>
+__device__ __forceinline__ void picard_time(T* __restrict__ q, const UT* __restrict__ u,
                                             const T* __restrict__ Kt, int tid, int nth) {
   constexpr int NV = D + 2, ND = ipow(n, D), NST = ipow(n, D + 1);
   for (int e = tid; e < NV * ND; e += nth) {
@@ -148,6 +150,48 @@ __device__ __forceinline__ double* apply_all_axes(double* a, double* b, const do
   return src;
 }
 
+// Compile-time variant of apply_all_axes: NV variables, NI -> NO points per
+// axis, matrix M[NO][NI]; every index division is by a constant.
+template <int D, int NV, int NI, int NO, int K>
+__device__ __forceinline__ void apply_pass_ct(const double* __restrict__ in, double* __restrict__ out,
+                                              const double* __restrict__ M, int tid, int nth) {
+  constexpr int I0 = (0 < K) ? NO : NI, I1 = (1 < K) ? NO : NI, I2 = (2 < K) ? NO : NI;
+  constexpr int O0 = (0 <= K) ? NO : NI, O1 = (1 <= K) ? NO : NI, O2 = (2 <= K) ? NO : NI;
+  constexpr int E1 = (D > 1) ? 1 : 0, E2 = (D > 2) ? 1 : 0;
+  constexpr int ISZ = I0 * (E1 ? I1 : 1) * (E2 ? I2 : 1);
+  constexpr int OSZ = O0 * (E1 ? O1 : 1) * (E2 ? O2 : 1);
+  constexpr int STRIDE = (K == 0) ? 1 : (K == 1 ? I0 : I0 * I1);
+  for (int e = tid; e < NV * OSZ; e += nth) {
+    const int v = e / OSZ;
+    int r = e - v * OSZ;
+    const int x0 = r % O0;
+    r /= O0;
+    const int x1 = E1 ? r % O1 : 0;
+    const int x2 = E2 ? r / O1 : 0;
+    const int xk = (K == 0) ? x0 : (K == 1 ? x1 : x2);
+    const int off = (K == 0 ? 0 : x0) + I0 * ((K == 1 ? 0 : x1) + I1 * (K == 2 ? 0 : x2));
+    const double* src = in + v * ISZ + off;
+    const double* mr = M + xk * NI;
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < NI; ++c) acc += mr[c] * src[c * STRIDE];
+    out[e] = acc;
+  }
+}
+
+template <int D, int NV, int NI, int NO>
+__device__ __forceinline__ double* apply_ct(double* a, double* b, const double* M, int tid, int nth) {
+  apply_pass_ct<D, NV, NI, NO, 0>(a, b, M, tid, nth);
+  __syncthreads();
+  if (D == 1) return b;
+  apply_pass_ct<D, NV, NI, NO, 1>(b, a, M, tid, nth);
+  __syncthreads();
+  if (D == 2) return a;
+  apply_pass_ct<D, NV, NI, NO, 2>(a, b, M, tid, nth);
+  __syncthreads();
+  return b;
+}
+
 // Block-wide reductions of per-thread values (blockDim a multiple of 32).
 __device__ __forceinline__ double block_reduce_max(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -174,7 +218,8 @@ __host__ __device__ constexpr size_t predictor_smem_bytes() {
   using DM = Dims<D, N>;
   size_t d = (size_t)DM::NV * DM::ND + (size_t)DM::NV * DM::NST + (size_t)D * DM::NV * DM::NST +
              (size_t)D * DM::NV * DM::ND + 3 * DM::n * DM::n + 3 * DM::n;
-  size_t f = MIXED ? ((size_t)DM::NV * DM::NST + (size_t)D * DM::NV * DM::NST + 2 * DM::n * DM::n)
+  size_t f = MIXED ? ((size_t)DM::NV * DM::NST + (size_t)D * DM::NV * DM::NST + 2 * DM::n * DM::n +
+                      (size_t)DM::NV * DM::ND)
                    : 0;
   return d * sizeof(double) + f * sizeof(float);
 }
@@ -198,6 +243,7 @@ __global__ void __launch_bounds__(256) k_predictor(Params p) {
   float* Ff = qf + NV * NST;
   float* Dmf = Ff + D * NV * NST;
   float* Ktf = Dmf + n * n;
+  float* uf = Ktf + n * n;
 
   const int tid = threadIdx.x, nth = blockDim.x;
   const Ops* o = p.ops;
@@ -226,25 +272,28 @@ __global__ void __launch_bounds__(256) k_predictor(Params p) {
     for (int i = tid; i < NV * ND; i += nth) u[i] = Uc[i];
     __syncthreads();
     int it0 = 0;
-    if (MIXED && p.iters > 1) {
+    const int n32 = p.iters - p.fp64_sweeps;    // sweeps in FP32
+    if (MIXED && n32 > 0) {
       float cf[3];
 #pragma unroll
       for (int k = 0; k < D; ++k) cf[k] = (float)c[k];
+      for (int e = tid; e < NV * ND; e += nth) uf[e] = (float)u[e];
+      __syncthreads();
       for (int e = tid; e < NV * NST; e += nth) {
         const int v = e / NST, l = e - v * NST;
-        qf[e] = (float)u[v * ND + (l % ND)];
+        qf[e] = uf[v * ND + (l % ND)];
       }
       __syncthreads();
-      for (int it = 0; it < p.iters - 1; ++it) {
+      for (int it = 0; it < n32; ++it) {
         picard_flux<D, n, float>(qf, Ff, (float)gm1, tid, nth);
         __syncthreads();
         picard_deriv<D, n, float>(Ff, qf, Dmf, cf, tid, nth);
         __syncthreads();
-        picard_time<D, n, float>(qf, u, Ktf, tid, nth);
+        picard_time<D, n, float>(qf, uf, Ktf, tid, nth);
         __syncthreads();
       }
       for (int e = tid; e < NV * NST; e += nth) q[e] = (double)qf[e];
-      it0 = p.iters - 1;
+      it0 = n32;
     } else {
       for (int e = tid; e < NV * NST; e += nth) {
         const int v = e / NST, l = e - v * NST;
@@ -435,51 +484,93 @@ __device__ __forceinline__ void dmp_interval(const Params& p, const double* __re
   lohi[2 * v + 1] = mx + delta;
 }
 
-// Checks the subcell data vs[v][s] of one cell (PAD + DMP when lohi != null),
-// reduces per-variable min / max into mm[2v], mm[2v+1] and the wave speed.
-// Returns (block-uniform) whether any check failed.
+// Order-preserving map of a double onto a signed 64-bit key (x < y <=> key(x)
+// < key(y) for non-NaN x, y; +NaN above +inf), so that min / max reductions
+// run on the integer pipe instead of the FP64 pipe.
+__device__ __forceinline__ long long ord_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double ord_val(long long k) {
+  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
+}
+
+// Max-reduces K integer keys per thread over the block (blockDim a multiple of
+// 32, at most 256 threads); the results land in red[nw * K + j].
+template <int K>
+__device__ __forceinline__ const long long* block_max_keys(long long* r, long long* red) {
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+    for (int o = 16; o > 0; o >>= 1) r[j] = max(r[j], __shfl_xor_sync(0xffffffffu, r[j], o));
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int j = 0; j < K; ++j) red[w * K + j] = r[j];
+  __syncthreads();
+  if (threadIdx.x < K) {
+    long long x = red[threadIdx.x];
+    for (int i = 1; i < nw; ++i) x = max(x, red[i * K + threadIdx.x]);
+    red[nw * K + threadIdx.x] = x;
+  }
+  __syncthreads();
+  return red + nw * K;
+}
+
+// Checks the subcell data vs[v][s] of one cell.
+//   PAD: rho > 0 and rho E - |m|^2 / 2 > 0 on every subcell (for rho > 0 the
+//        second test is p > 0 without a division; NaN in any component fails);
+//   DMP (lohi != null): every subcell inside [lo_v, hi_v], tested exactly on
+//        the per-variable extremes (min >= lo and max <= hi).
+// Writes the per-variable min / max to mm[2v], mm[2v+1] and, when lam != null,
+// the largest wave speed max_k |v_k| + c.  Returns (block-uniform) whether
+// any check failed.  `red` needs (blockDim/32 + 1) * (2 nvar + 1) doubles.
 template <int D>
 __device__ __forceinline__ bool check_subcells(const double* __restrict__ vs, int nsub,
                                                const double* lohi, double gamma, double* mm,
                                                double* lam, double* red) {
-  const int NV = D + 2;
+  constexpr int NV = D + 2, K = 2 * NV + 1;
   bool bad = false;
-  double lmin[NV], lmax[NV], lw = 0.0;
+  long long r[K];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    lmin[v] = INFINITY;
-    lmax[v] = -INFINITY;
-  }
+  for (int j = 0; j < K; ++j) r[j] = LLONG_MIN;
   for (int s = threadIdx.x; s < nsub; s += blockDim.x) {
     double Q[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       Q[v] = vs[v * nsub + s];
-      lmin[v] = fmin(lmin[v], Q[v]);
-      lmax[v] = fmax(lmax[v], Q[v]);
+      const long long k = ord_key(Q[v]);
+      r[2 * v] = max(r[2 * v], ~k);          // ~k reverses the order: max of ~k = ~min k
+      r[2 * v + 1] = max(r[2 * v + 1], k);
     }
-    const double pr = euler_pressure<D>(Q, gamma - 1.0);
-    bool ok = (Q[0] > 0.0) && (pr > 0.0);
-    if (lohi) {
+    double kin = 0.0;
 #pragma unroll
-      for (int v = 0; v < NV; ++v) ok = ok && (Q[v] >= lohi[2 * v]) && (Q[v] <= lohi[2 * v + 1]);
-    }
-    bad = bad || !ok;
-    lw = nanmax(lw, wave_speed<D>(Q, gamma));
+    for (int k = 0; k < D; ++k) kin += Q[1 + k] * Q[1 + k];
+    bad = bad || !((Q[0] > 0.0) && (Q[D + 1] * Q[0] - 0.5 * kin > 0.0));
+    if (lam) r[2 * NV] = max(r[2 * NV], ord_key(wave_speed<D>(Q, gamma)));
   }
-  const bool any_bad = __syncthreads_or(bad);
+  bad = __syncthreads_or(bad);
+  const long long* res = block_max_keys<K>(r, reinterpret_cast<long long*>(red));
+  double mn[NV], mx[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const double a = block_reduce_min(lmin[v], red);
-    const double b = block_reduce_max(lmax[v], red);
-    if (threadIdx.x == 0) {
-      mm[2 * v] = a;
-      mm[2 * v + 1] = b;
-    }
+    mn[v] = ord_val(~res[2 * v]);
+    mx[v] = ord_val(res[2 * v + 1]);
   }
-  const double l = block_reduce_max(lw, red);
-  if (threadIdx.x == 0) *lam = l;
-  return any_bad;
+  if (lohi) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      bad = bad || !((mn[v] >= lohi[2 * v]) && (mx[v] <= lohi[2 * v + 1]));
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      mm[2 * v] = mn[v];
+      mm[2 * v + 1] = mx[v];
+    }
+    if (lam) *lam = ord_val(res[2 * NV]);
+  }
+  return bad;
 }
 
 // ---------------------------------------------------------------------------
@@ -489,7 +580,7 @@ template <int D, int N>
 __host__ __device__ constexpr size_t correct_smem_bytes() {
   using DM = Dims<D, N>;
   const int big = DM::NSD > DM::ND * 4 ? DM::NSD : DM::ND * 4;
-  return (size_t)(2 * DM::NV * (DM::NSD > big ? DM::NSD : big) + DM::Ns * DM::n + 4 * DM::NV + 64) *
+  return (size_t)(2 * DM::NV * (DM::NSD > big ? DM::NSD : big) + DM::Ns * DM::n + 4 * DM::NV + 128) *
          sizeof(double);
 }
 
@@ -504,7 +595,7 @@ __global__ void __launch_bounds__(128) k_correct_detect(Params p) {
   double* P1 = B + NV * BUF;          // Ns * n
   double* lohi = P1 + Ns * n;         // 2 NV
   double* mm = lohi + 2 * NV;         // 2 NV
-  double* red = mm + 2 * NV;          // 32 (+ lam)
+  double* red = mm + 2 * NV;          // 128
   const int tid = threadIdx.x, nth = blockDim.x;
   const Ops* o = p.ops;
   for (int i = tid; i < Ns * n; i += nth) P1[i] = o->P1[i];
@@ -535,11 +626,11 @@ __global__ void __launch_bounds__(128) k_correct_detect(Params p) {
       Uo[e] = acc;
     }
     __syncthreads();
-    double* vs = apply_all_axes<D>(A, B, P1, Ns, n, NV, tid, nth);
+    double* vs = apply_ct<D, NV, n, Ns>(A, B, P1, tid, nth);
     dmp_interval<D>(p, p.b.cmm[p.cur], ijk, lohi);
     __syncthreads();
-    double lam;
-    const bool bad = check_subcells<D>(vs, NSD, lohi, p.gamma, mm, &lam, red);
+    double lam = 0.0;
+    const bool bad = check_subcells<D>(vs, NSD, lohi, p.gamma, mm, p.lam_mode ? &lam : nullptr, red);
     if (tid == 0) {
       int slot = -1;
       if (bad || p.force) {
@@ -555,7 +646,7 @@ __global__ void __launch_bounds__(128) k_correct_detect(Params p) {
       }
       p.b.beta[nxt][cell] = (uint8_t)(slot >= 0);
       p.b.slot[nxt][cell] = slot;
-      p.b.lam[cell] = lam;
+      if (p.lam_mode) p.b.lam[cell] = lam;
     }
     if (tid < 2 * NV) p.b.cmm[nxt][cell * 2 * NV + tid] = mm[tid];
     __syncthreads();

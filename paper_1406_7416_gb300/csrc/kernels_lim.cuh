@@ -98,8 +98,12 @@ __global__ void __launch_bounds__(256) k_lim_patch(Params p, int chunk0) {
 
 // 1D WENO3 on five consecutive subcell averages u[0..4] (target subcell u[2]):
 // values of the reconstruction at the 3 GL nodes of the target subcell.
+// Weights w_k = lambda_k / t_k, t_k = (sigma_k + eps)^8, normalised; with
+// a_k = lambda_k prod_{j != k} t_j the normalised weights are a_k / sum a, so
+// one division serves all outputs (the plain form is used if a product of
+// two t_j could overflow).
 __device__ __forceinline__ void weno3(const double* u, const Ops* __restrict__ o, double* out) {
-  double num0 = 0.0, num1 = 0.0, num2 = 0.0, den = 0.0;
+  double t[3], p0[3], p1[3], p2[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const double* C = o->C[k];
@@ -108,123 +112,188 @@ __device__ __forceinline__ void weno3(const double* u, const Ops* __restrict__ o
     const double c2 = C[6] * u[k] + C[7] * u[k + 1] + C[8] * u[k + 2];
     // sigma = int_0^1 (p')^2 + (p'')^2 = c1^2 + 2 c1 c2 + 16/3 c2^2
     const double sigma = c1 * (c1 + 2.0 * c2) + (16.0 / 3.0) * c2 * c2;
-    double t = sigma + WENO_EPS;
-    t = t * t;
-    t = t * t;
-    t = t * t;
-    const double wt = (k == 1 ? WENO_LAMBDA_C : 1.0) / t;
-    num0 += wt * (c0 + c1 * o->E[1] + c2 * o->E[2]);
-    num1 += wt * (c0 + c1 * o->E[4] + c2 * o->E[5]);
-    num2 += wt * (c0 + c1 * o->E[7] + c2 * o->E[8]);
-    den += wt;
+    double tk = sigma + WENO_EPS;
+    tk = tk * tk;
+    tk = tk * tk;
+    t[k] = tk * tk;
+    p0[k] = c0 + c1 * o->E[1] + c2 * o->E[2];
+    p1[k] = c0 + c1 * o->E[4] + c2 * o->E[5];
+    p2[k] = c0 + c1 * o->E[7] + c2 * o->E[8];
   }
-  out[0] = num0 / den;
-  out[1] = num1 / den;
-  out[2] = num2 / den;
+  double a0, a1, a2;
+  if (t[0] < 1e150 && t[1] < 1e150 && t[2] < 1e150) {
+    a0 = t[1] * t[2];
+    a1 = WENO_LAMBDA_C * (t[0] * t[2]);
+    a2 = t[0] * t[1];
+  } else {
+    a0 = 1.0 / t[0];
+    a1 = WENO_LAMBDA_C / t[1];
+    a2 = 1.0 / t[2];
+  }
+  const double inv = 1.0 / (a0 + a1 + a2);
+  out[0] = (a0 * p0[0] + a1 * p0[1] + a2 * p0[2]) * inv;
+  out[1] = (a0 * p1[0] + a1 * p1[1] + a2 * p1[2]) * inv;
+  out[2] = (a0 * p2[0] + a1 * p2[1] + a2 * p2[2]) * inv;
 }
 
-// L1..L3: sweep along axis k.  Input extents (Ex, Ey, Ez) with NNin nodal
-// values per element; the output has extent Ns+2 along k and 3*NNin nodes
-// (the new nodal index is the slowest digit).
-template <int D, int N>
-__global__ void __launch_bounds__(256) k_lim_sweep(Params p, int chunk0, int k) {
+// L1..L3: sweep along axis K.  Input extents (L or Ns+2 per axis) with NNIN
+// nodal values per element; the output has extent Ns+2 along K and 3 NNIN
+// nodes (the new nodal index is the slowest digit).
+template <int D, int N, int K>
+__global__ void __launch_bounds__(256) k_lim_sweep(Params p, int chunk0) {
   using DM = Dims<D, N>;
   constexpr int NV = DM::NV, L = DM::L, NE = DM::NE;
+  constexpr int I0 = (0 < K) ? NE : L, I1 = (1 < K) ? NE : L, I2 = (D < 3) ? 1 : ((2 < K) ? NE : L);
+  constexpr int O0 = (0 <= K) ? NE : L, O1 = (1 <= K) ? NE : L, O2 = (D < 3) ? 1 : ((2 <= K) ? NE : L);
+  constexpr int NNIN = ipow(3, K);
+  constexpr int INSZ = I0 * I1 * I2 * NNIN;
+  constexpr int OUTSZ = O0 * O1 * O2 * NNIN;          // elements, each producing 3 values
+  constexpr int STRIDE = ((K == 0) ? 1 : (K == 1 ? I0 : I0 * I1)) * NNIN;
   const int len = chunk_len(p, chunk0);
-  int ein[3], eout[3];
-  for (int j = 0; j < 3; ++j) {
-    const bool done = j < k, active = j < D;
-    ein[j] = active ? (done ? NE : L) : 1;
-    eout[j] = active ? (j <= k ? NE : L) : 1;
-  }
-  const int NNin = ipow3(k);
-  const int insz = ein[0] * ein[1] * ein[2] * NNin;
-  const int outsz = eout[0] * eout[1] * eout[2] * NNin;   // elements producing 3 values
-  const double* in = (k == 0) ? p.b.patch : p.b.sweep[k - 1];
-  double* out = p.b.sweep[k];
-  const int stride = (k == 0) ? 1 : (k == 1 ? ein[0] : ein[0] * ein[1]);
+  const double* in = (K == 0) ? p.b.patch : p.b.sweep[K > 0 ? K - 1 : 0];
+  double* out = p.b.sweep[K];
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-       e < (long long)len * NV * outsz; e += (long long)gridDim.x * blockDim.x) {
-    const long long jv = e / outsz;
-    int r = (int)(e - jv * outsz);
-    const int node = r % NNin;
-    r /= NNin;
-    int idx[3];
-    idx[0] = r % eout[0];
-    r /= eout[0];
-    idx[1] = r % eout[1];
-    idx[2] = r / eout[1];
-    // input element whose axis-k index is idx[k] (stencil idx[k] .. idx[k]+4)
-    int off = 0;
-    {
-      int s = 1;
-      for (int j = 0; j < 3; ++j) {
-        off += idx[j] * s;
-        s *= ein[j];
-      }
-    }
-    const double* src = in + jv * insz + (size_t)off * NNin + node;
+       e < (long long)len * NV * OUTSZ; e += (long long)gridDim.x * blockDim.x) {
+    const long long jv = e / OUTSZ;
+    int r = (int)(e - jv * OUTSZ);
+    const int node = r % NNIN;
+    r /= NNIN;
+    const int x0 = r % O0;
+    r /= O0;
+    const int x1 = r % O1;
+    const int x2 = r / O1;
+    // input element whose axis-K index equals the output's (stencil x_K .. x_K + 4)
+    const int off = x0 + I0 * (x1 + I1 * x2);
+    const double* src = in + jv * INSZ + (size_t)off * NNIN + node;
     double u[5];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) u[q] = src[(size_t)q * stride * NNin];
+    for (int q = 0; q < 5; ++q) u[q] = src[q * STRIDE];
     double res[3];
     weno3(u, p.ops, res);
-    int ooff = idx[0] + eout[0] * (idx[1] + eout[1] * idx[2]);
-    double* dst = out + jv * (size_t)outsz * 3 + (size_t)ooff * NNin * 3 + node;
+    const int ooff = x0 + O0 * (x1 + O1 * x2);
+    double* dst = out + jv * (size_t)OUTSZ * 3 + (size_t)ooff * NNIN * 3 + node;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) dst[a * NNin] = res[a];
+    for (int a = 0; a < 3; ++a) dst[a * NNIN] = res[a];
   }
 }
 
-// L4: degree-2 space-time predictor on every subcell of the block -1..Ns
-// (Eq. pde.nc.dg2 with 3 GL nodes per axis, 3 Picard sweeps).
+// L4: degree-2 space-time predictor (Eq. pde.nc.dg2 with 3 GL nodes per axis
+// and in time, 3 Picard sweeps) on the subcells whose traces the sub-face
+// fluxes use: the Ns^d interior subcells and the Ns^(d-1) ghost subcells
+// facing each of the 2d cell faces.  In mixed precision the first two sweeps
+// run in FP32 and the last in FP64.
 constexpr int SUBS_PER_BLOCK_2D = 4;
 constexpr int SUBS_PER_BLOCK_3D = 2;
 
-template <int D, int N>
+// index in the (Ns+2)^d block (array index = local + 1) of the r-th subcell
+// of the interior + face-ghost set
+template <int D, int Ns>
+__device__ __forceinline__ int cross_subcell(int r) {
+  constexpr int NE = Ns + 2, NSD = ipow(Ns, D), NSF = ipow(Ns, D - 1);
+  int c[3] = {0, 0, 0};
+  if (r < NSD) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      c[k] = r % Ns + 1;
+      r /= Ns;
+    }
+  } else {
+    r -= NSD;
+    const int k = r / (2 * NSF);
+    r -= k * 2 * NSF;
+    const int side = r / NSF;
+    int t = r - side * NSF;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      if (a == k) {
+        c[a] = side ? Ns + 1 : 0;
+      } else {
+        c[a] = t % Ns + 1;
+        t /= Ns;
+      }
+    }
+  }
+  return c[0] + NE * (c[1] + NE * c[2]);
+}
+
+template <int D, int N, bool MIXED>
 __global__ void __launch_bounds__(256) k_lim_predict(Params p, int chunk0) {
   using DM = Dims<D, N>;
   constexpr int NV = DM::NV, NST3 = DM::NST3, ND3 = DM::ND3, NED = DM::NED, Ns = DM::Ns;
+  constexpr int NCROSS = DM::NSD + 2 * D * DM::NSF;
   constexpr int SPB = (D == 2) ? SUBS_PER_BLOCK_2D : SUBS_PER_BLOCK_3D;
+  constexpr int SPBF = MIXED ? SPB : 1;
   __shared__ double su[SPB][NV * ND3];
   __shared__ double sq[SPB][NV * NST3];
   __shared__ double sF[SPB][D * NV * NST3];
+  __shared__ float suf[SPBF][NV * ND3];
+  __shared__ float sqf[SPBF][NV * NST3];
+  __shared__ float sFf[SPBF][D * NV * NST3];
   __shared__ double D3[9], K3[9];
+  __shared__ float D3f[9], K3f[9];
   if (threadIdx.x < 9) {
     D3[threadIdx.x] = p.ops->D3[threadIdx.x];
     K3[threadIdx.x] = p.ops->Kt3[threadIdx.x];
+    D3f[threadIdx.x] = (float)p.ops->D3[threadIdx.x];
+    K3f[threadIdx.x] = (float)p.ops->Kt3[threadIdx.x];
   }
   const int len = chunk_len(p, chunk0);
   const int grp = threadIdx.x / NST3, lt = threadIdx.x - grp * NST3;
   const bool active_thread = grp < SPB;
   const double dt = *p.b.dt;
   double c[3];
+  float cf[3];
 #pragma unroll
-  for (int k = 0; k < D; ++k) c[k] = dt * Ns / p.geo.dx[k];
+  for (int k = 0; k < D; ++k) {
+    c[k] = dt * Ns / p.geo.dx[k];
+    cf[k] = (float)c[k];
+  }
   const double gm1 = p.gamma - 1.0;
   const double* W = p.b.sweep[D - 1];          // [j][v][NED][ND3]
-  const long long total = (long long)len * NED;
+  const long long total = (long long)len * NCROSS;
   for (long long base = (long long)blockIdx.x * SPB; base < total;
        base += (long long)gridDim.x * SPB) {
     const long long item = base + grp;
     const bool live = active_thread && item < total;
+    const long long j = live ? item / NCROSS : 0;
+    const int sc = live ? cross_subcell<D, Ns>((int)(item - j * NCROSS)) : 0;
     __syncthreads();
     if (live) {
-      const long long j = item / NED;
-      const int sc = (int)(item - j * NED);
       for (int e = lt; e < NV * ND3; e += NST3) {
         const int v = e / ND3, i = e - v * ND3;
         su[grp][e] = W[((j * NV + v) * NED + sc) * ND3 + i];
       }
     }
     __syncthreads();
-    if (live)
+    int it0 = 0;
+    if (MIXED) {
+      if (live) {
+        for (int e = lt; e < NV * ND3; e += NST3) suf[grp][e] = (float)su[grp][e];
+        for (int e = lt; e < NV * NST3; e += NST3) {
+          const int v = e / NST3, l = e - v * NST3;
+          sqf[grp][e] = (float)su[grp][v * ND3 + (l % ND3)];
+        }
+      }
+      __syncthreads();
+      for (int it = 0; it < 2; ++it) {
+        if (live) picard_flux<D, 3, float>(sqf[grp], sFf[grp], (float)gm1, lt, NST3);
+        __syncthreads();
+        if (live) picard_deriv<D, 3, float>(sFf[grp], sqf[grp], D3f, cf, lt, NST3);
+        __syncthreads();
+        if (live) picard_time<D, 3, float>(sqf[grp], suf[grp], K3f, lt, NST3);
+        __syncthreads();
+      }
+      if (live)
+        for (int e = lt; e < NV * NST3; e += NST3) sq[grp][e] = (double)sqf[grp][e];
+      it0 = 2;
+    } else if (live) {
       for (int e = lt; e < NV * NST3; e += NST3) {
         const int v = e / NST3, l = e - v * NST3;
         sq[grp][e] = su[grp][v * ND3 + (l % ND3)];
       }
+    }
     __syncthreads();
-    for (int it = 0; it < 3; ++it) {
+    for (int it = it0; it < 3; ++it) {
       if (live) picard_flux<D, 3, double>(sq[grp], sF[grp], gm1, lt, NST3);
       __syncthreads();
       if (live) picard_deriv<D, 3, double>(sF[grp], sq[grp], D3, c, lt, NST3);
@@ -233,7 +302,7 @@ __global__ void __launch_bounds__(256) k_lim_predict(Params p, int chunk0) {
       __syncthreads();
     }
     if (live) {
-      double* dst = p.b.qsub + item * (size_t)(NV * NST3);
+      double* dst = p.b.qsub + ((size_t)j * NED + sc) * (size_t)(NV * NST3);
       for (int e = lt; e < NV * NST3; e += NST3) dst[e] = sq[grp][e];
     }
   }
@@ -242,15 +311,15 @@ __global__ void __launch_bounds__(256) k_lim_predict(Params p, int chunk0) {
 // L5: sub-face fluxes normal to axis k: Rusanov at the 3^(d-1) x 3
 // tangential x time GL points, averaged with the GL weights.  Faces f = 0..Ns
 // along k (between local subcells f-1 and f), tangential subcells 0..Ns-1.
-template <int D, int N>
-__global__ void __launch_bounds__(256) k_lim_flux(Params p, int chunk0, int k) {
+template <int D, int N, int k>
+__global__ void __launch_bounds__(256) k_lim_flux(Params p, int chunk0) {
   using DM = Dims<D, N>;
   constexpr int NV = DM::NV, NST3 = DM::NST3, ND3 = DM::ND3, NE = DM::NE, NED = DM::NED,
                 Ns = DM::Ns;
   constexpr int NFK = (Ns + 1) * DM::NSF;
   const int len = chunk_len(p, chunk0);
   const Ops* o = p.ops;
-  const int stk = (k == 0) ? 1 : (k == 1 ? 3 : 9);       // node stride of axis k
+  constexpr int stk = (k == 0) ? 1 : (k == 1 ? 3 : 9);   // node stride of axis k
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)len * NFK;
        e += (long long)gridDim.x * blockDim.x) {
     const long long j = e / NFK;
@@ -328,7 +397,7 @@ __global__ void __launch_bounds__(128) k_lim_update(Params p, int chunk0) {
   double* B = A + NV * NSD;       // NV * NSD
   double* R1 = B + NV * NSD;      // n * Ns
   double* mm = R1 + n * Ns;       // 2 NV
-  double* red = mm + 2 * NV;      // 32
+  double* red = mm + 2 * NV;      // 128
   const int tid = threadIdx.x, nth = blockDim.x;
   for (int i = tid; i < n * Ns; i += nth) R1[i] = p.ops->R1[i];
   const int len = chunk_len(p, chunk0);
@@ -375,10 +444,10 @@ __global__ void __launch_bounds__(128) k_lim_update(Params p, int chunk0) {
       st[e] = val;
     }
     __syncthreads();
-    double lam;
-    const bool bad = check_subcells<D>(A, NSD, nullptr, p.gamma, mm, &lam, red);
+    double lam = 0.0;
+    const bool bad = check_subcells<D>(A, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red);
     if (tid == 0) {
-      p.b.lam[cell] = lam;
+      if (p.lam_mode) p.b.lam[cell] = lam;
       if (bad) atomicAdd(&p.b.counters[CNT_INADM], 1);
     }
     if (tid < 2 * NV) p.b.cmm[nxt][cell * 2 * NV + tid] = mm[tid];
@@ -401,7 +470,7 @@ __global__ void __launch_bounds__(128) k_lim_update(Params p, int chunk0) {
     }
     // reconstruction R of the new subcell data
     __syncthreads();
-    double* u = apply_all_axes<D>(A, B, R1, n, Ns, NV, tid, nth);
+    double* u = apply_ct<D, NV, Ns, n>(A, B, R1, tid, nth);
     double* Uo = p.b.U[nxt] + cell * (NV * ND);
     for (int e = tid; e < NV * ND; e += nth) Uo[e] = u[e];
     // unlimited face neighbours get the flux correction
@@ -504,10 +573,10 @@ __global__ void __launch_bounds__(128) k_lim_fix(Params p) {
       A[e] = U[e];
     }
     __syncthreads();
-    double* vs = apply_all_axes<D>(A, B, P1, Ns, n, NV, tid, nth);
-    double lam;
-    check_subcells<D>(vs, NSD, nullptr, p.gamma, mm, &lam, red);
-    if (tid == 0) p.b.lam[cell] = lam;
+    double* vs = apply_ct<D, NV, n, Ns>(A, B, P1, tid, nth);
+    double lam = 0.0;
+    check_subcells<D>(vs, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red);
+    if (tid == 0 && p.lam_mode) p.b.lam[cell] = lam;
     if (tid < 2 * NV) p.b.cmm[nxt][cell * 2 * NV + tid] = mm[tid];
   }
 }

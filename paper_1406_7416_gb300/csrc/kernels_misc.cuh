@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(128) k_load_detect(Params p, const double* __r
     __syncthreads();
     for (int e = tid; e < NV * ND; e += nth) A[e] = U[e];
     __syncthreads();
-    double* vs = apply_all_axes<D>(A, B, P1, Ns, n, NV, tid, nth);
+    double* vs = apply_ct<D, NV, n, Ns>(A, B, P1, tid, nth);
     if (exact) dmp_interval<D>(p, cmm_ex, ijk, lohi);
     __syncthreads();
     double lam;
@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(128) k_load_detect(Params p, const double* __r
     }
     __syncthreads();
     check_subcells<D>(A, NSD, nullptr, p.gamma, mm, &lam, red);
-    double* u = apply_all_axes<D>(A, B, R1, n, Ns, NV, tid, nth);
+    double* u = apply_ct<D, NV, Ns, n>(A, B, R1, tid, nth);
     for (int e = tid; e < NV * ND; e += nth) U[e] = u[e];
     if (tid == 0) {
       p.b.beta[cur][cell] = 1;
@@ -85,6 +85,42 @@ __global__ void __launch_bounds__(128) k_load_detect(Params p, const double* __r
       p.b.lam[cell] = lam;
     }
     if (tid < 2 * NV) p.b.cmm[cur][cell * 2 * NV + tid] = mm[tid];
+  }
+}
+
+// Wave speeds of the current level from v^n (stored subcell data of troubled
+// cells, P(u^n) elsewhere), for a time step requested after steps that did
+// not keep them current.
+template <int D, int N>
+__global__ void __launch_bounds__(128) k_lambda(Params p) {
+  using DM = Dims<D, N>;
+  constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, Ns = DM::Ns, NSD = DM::NSD;
+  extern __shared__ double sm[];
+  double* A = sm;
+  double* B = A + NV * NSD;
+  double* P1 = B + NV * NSD;
+  double* mm = P1 + Ns * n;
+  double* red = mm + 2 * NV;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = tid; i < Ns * n; i += nth) P1[i] = p.ops->P1[i];
+  const int cur = p.cur;
+  for (long long cell = blockIdx.x; cell < p.geo.cells; cell += gridDim.x) {
+    __syncthreads();
+    double* vs;
+    if (p.b.beta[cur][cell]) {
+      const double* st = p.b.store[cur] + (size_t)p.b.slot[cur][cell] * NV * NSD;
+      for (int e = tid; e < NV * NSD; e += nth) A[e] = st[e];
+      __syncthreads();
+      vs = A;
+    } else {
+      const double* U = p.b.U[cur] + cell * (NV * ND);
+      for (int e = tid; e < NV * ND; e += nth) A[e] = U[e];
+      __syncthreads();
+      vs = apply_ct<D, NV, n, Ns>(A, B, P1, tid, nth);
+    }
+    double lam;
+    check_subcells<D>(vs, NSD, nullptr, p.gamma, mm, &lam, red);
+    if (tid == 0) p.b.lam[cell] = lam;
   }
 }
 
@@ -159,7 +195,7 @@ __global__ void __launch_bounds__(128) k_load_full(Params p, const uint8_t* __re
         p.b.slot[cur][cell] = -1;
       }
       __syncthreads();
-      vs = apply_all_axes<D>(A, B, P1, Ns, n, NV, tid, nth);
+      vs = apply_ct<D, NV, n, Ns>(A, B, P1, tid, nth);
     }
     double lam;
     check_subcells<D>(vs, NSD, nullptr, p.gamma, mm, &lam, red);

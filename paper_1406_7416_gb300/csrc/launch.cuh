@@ -32,11 +32,11 @@ struct Launch {
 
   static int pred_threads() {
     int t = ((NV * DM::NST + 31) / 32) * 32;
-    return t > 256 ? 256 : t;
+    return t > 128 ? 128 : t;
   }
-  static size_t cell_smem() { return (size_t)(2 * NV * NSD + 2 * Ns * n + 4 * NV + 64) * sizeof(double); }
+  static size_t cell_smem() { return (size_t)(2 * NV * NSD + 2 * Ns * n + 4 * NV + 128) * sizeof(double); }
   static size_t fix_smem() {
-    return (size_t)(NV * ND + 2 * NV * NSD + 2 * Ns * n + 4 * NV + 64) * sizeof(double);
+    return (size_t)(NV * ND + 2 * NV * NSD + 2 * Ns * n + 4 * NV + 128) * sizeof(double);
   }
 
   static void mark(cudaEvent_t* ev, int phase, cudaStream_t s) {
@@ -79,12 +79,20 @@ struct Launch {
       const int chunk0 = c * p.chunk;
       const long long ch = p.chunk;
       k_lim_patch<D, N><<<grid_for(ch * DM::LD, 256), 256, 0, s>>>(p, chunk0);
-      for (int k = 0; k < D; ++k)
-        k_lim_sweep<D, N><<<grid_for(ch * NV * DM::LD, 256), 256, 0, s>>>(p, chunk0, k);
-      k_lim_predict<D, N><<<grid_for(ch * DM::NED, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(
-          p, chunk0);
-      for (int k = 0; k < D; ++k)
-        k_lim_flux<D, N><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(p, chunk0, k);
+      k_lim_sweep<D, N, 0><<<grid_for(ch * NV * DM::LD, 256), 256, 0, s>>>(p, chunk0);
+      k_lim_sweep<D, N, 1><<<grid_for(ch * NV * DM::LD, 256), 256, 0, s>>>(p, chunk0);
+      if (D == 3) k_lim_sweep<D, N, (D == 3 ? 2 : 1)><<<grid_for(ch * NV * DM::LD, 256), 256, 0, s>>>(p, chunk0);
+      const long long ncross = ch * (DM::NSD + 2 * D * DM::NSF);
+      if (p.prec == ADG_PREC_MIXED_FP32)
+        k_lim_predict<D, N, true><<<grid_for(ncross, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(
+            p, chunk0);
+      else
+        k_lim_predict<D, N, false><<<grid_for(ncross, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(
+            p, chunk0);
+      k_lim_flux<D, N, 0><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(p, chunk0);
+      k_lim_flux<D, N, 1><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(p, chunk0);
+      if (D == 3)
+        k_lim_flux<D, N, (D == 3 ? 2 : 1)><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(p, chunk0);
       k_lim_update<D, N><<<(int)(ch < kNumSM * 8 ? ch : kNumSM * 8), 128, su, s>>>(p, chunk0);
     }
     mark(ev, PHASE_FIX, s);
@@ -123,6 +131,12 @@ struct Launch {
       case OP_PROJECT:
         k_project<D, N><<<grid, 128, 0, s>>>(p, *a.prob, a.fac, a.out);
         return cudaGetLastError();
+      case OP_LAMBDA: {
+        const size_t sm = cell_smem();
+        if ((e = set_smem(k_lambda<D, N>, sm)) != cudaSuccess) return e;
+        k_lambda<D, N><<<grid, 128, sm, s>>>(p);
+        return cudaGetLastError();
+      }
       case OP_SUB_MINMAX:
         k_sub_minmax<D, N><<<grid_for(p.geo.cells * NV, 256), 256, 0, s>>>(a.sub, a.out,
                                                                             p.geo.cells);
