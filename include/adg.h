@@ -183,6 +183,41 @@ int adg_phase_times(adg_state* st, double* ms, int cap);
 
 const char* adg_last_error(const adg_state* st);
 
+/* Subcell ADER-WENO3 update of caller-owned patches that allocates nothing.
+ * The paper has no counterpart: it is a variant, for one batch of patches, of
+ * the limiter that adg_step runs on its troubled cells.
+ *
+ * Who needs it: callers that cannot call cudaMalloc -- code running inside a
+ * host application that owns all device memory, or a loop that must never
+ * reach an allocator -- but can hand over device buffers they already own.
+ *
+ * Inputs (device pointers; the caller owns them):
+ *   patches [count][dim+2][L^dim], L = 2N+7: the subcell averages of the
+ *           target cell (local subcells 0..2N) and of three ghost layers
+ *           around it (-3..-1 and 2N+1..2N+3 per axis), x fastest;
+ *   h[dim]  subcell widths (host array), dt > 0, gamma > 1, N 1..9 (2D) or
+ *           1..3 (3D).
+ * Outputs (device pointers): vnew [count][dim+2][(2N+1)^dim] the updated
+ * subcell averages; faces [count][dim][2][dim+2][(2N+1)^(dim-1)] the sub-face
+ * fluxes on the low / high faces of each cell, or NULL.
+ * Work is enqueued on `stream` (a cudaStream_t, NULL for the default stream);
+ * the call uploads the operator table of degree N and synchronizes that stream
+ * once before launching.
+ *
+ * Scratch: one static device array of 32 MiB, held by every GPU that loads
+ * the library until the process exits; its address is looked up on the first
+ * call made on each device (make that first call before any stream capture).
+ * count is limited by that size (e.g. about 146 patches for dim 2, N 5); a
+ * larger count returns ADG_ERR_CAPACITY with the limit in `err`.  Every call
+ * shares the array and leaves its contents behind: calls that overlap on the
+ * GPU (other streams, other threads) race and must be serialized by the caller.
+ * No cudaMalloc, cudaFree or allocating library routine is called.
+ * err (may be NULL) receives a message of at most errlen bytes on failure.
+ * Returns ADG_OK, ADG_ERR_ARG, ADG_ERR_CAPACITY or ADG_ERR_CUDA. */
+int adg_subcell_update_noalloc(int dim, int N, double gamma, const double* h, double dt,
+                               const double* patches, int count, double* vnew, double* faces,
+                               void* stream, char* err, size_t errlen);
+
 /* Free every device buffer of the state and the state itself. */
 void adg_destroy(adg_state* st);
 

@@ -32,7 +32,8 @@ IC_RADIAL, IC_QUADRANT = 0, 1
 SYMBOLS = ("adg_create", "adg_set_allocator", "adg_set_stream", "adg_set_option", "adg_load",
            "adg_init_problem", "adg_load_full", "adg_read_full", "adg_step", "adg_step_cfl",
            "adg_max_dt", "adg_flags", "adg_read", "adg_troubled_count", "adg_status",
-           "adg_sizes", "adg_info", "adg_phase_times", "adg_last_error", "adg_destroy")
+           "adg_sizes", "adg_info", "adg_phase_times", "adg_last_error", "adg_destroy",
+           "adg_subcell_update_noalloc")
 
 
 class AdgGrid(ctypes.Structure):
@@ -90,6 +91,8 @@ def load_library(path=None):
     lib.adg_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ip]
     lib.adg_last_error.argtypes = [vp]
     lib.adg_last_error.restype = ctypes.c_char_p
+    lib.adg_subcell_update_noalloc.argtypes = [ip, ip, ctypes.c_double, dp, ctypes.c_double, vp, ip,
+                                               vp, vp, vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.adg_destroy.argtypes = [vp]
     lib.adg_destroy.restype = None
     for name in SYMBOLS:
@@ -110,6 +113,22 @@ def _u8ptr(a):
 
 def _contig(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
+
+
+def subcell_update_noalloc(dim, N, gamma, h, dt, patches_ptr, count, vnew_ptr, faces_ptr=0,
+                           stream=0):
+    """adg_subcell_update_noalloc on caller-owned device buffers (raw pointers).
+    Returns the status code and the library's message."""
+    lib = load_library()
+    hh = np.ascontiguousarray(h, dtype=np.float64)
+    err = ctypes.create_string_buffer(512)
+    rc = lib.adg_subcell_update_noalloc(int(dim), int(N), float(gamma), _dptr(hh), float(dt),
+                                        ctypes.c_void_p(int(patches_ptr)), int(count),
+                                        ctypes.c_void_p(int(vnew_ptr)),
+                                        ctypes.c_void_p(int(faces_ptr)) if faces_ptr else None,
+                                        ctypes.c_void_p(int(stream)) if stream else None,
+                                        err, 512)
+    return rc, err.value.decode()
 
 
 class Solver:
