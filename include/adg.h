@@ -67,6 +67,8 @@ extern "C" {
 #define ADG_OPT_PROFILE 6         /* 1: time the phases of every step with CUDA events */
 #define ADG_OPT_FP64_SWEEPS 7     /* mixed precision: final Picard sweeps run in FP64
                                      (default 1; the others run in FP32)              */
+#define ADG_OPT_END_TIME 8        /* end time of the run: steps are cut to reach it and
+                                     the state idles afterwards (0: none, default)    */
 
 /* Cartesian grid (Sec. 2.1): cells n[k] of size dx[k] from corner x0[k]. */
 typedef struct {
@@ -146,6 +148,32 @@ int adg_step(adg_state* st, double dt);
 /* Same step with dt = min(cfl * min_k dx_k / lambda_max, dt_max) computed on
  * the device from the current state (Eq. cfl); nothing returns to the host. */
 int adg_step_cfl(adg_state* st, double cfl, double dt_max);
+
+/* Simulated time t of the state (0 after a load, advanced by every step);
+ * synchronizes. */
+int adg_time(adg_state* st, double* t);
+
+/* Batched stepping of many independent states (spec batching; no
+ * counterpart in the paper, which steps one grid): states of the same
+ * dimension, degree and precision share every kernel launch, each launch
+ * covering all their cells, faces or troubled cells.  All states must be
+ * loaded; their streams are set to the batch's stream (`stream`, or a stream
+ * the batch creates when NULL).  A state may belong to one live batch at a
+ * time and must not be stepped on its own while it does.
+ *   adg_batch_step with dts (host [count]) takes those steps; with dts = NULL
+ *   every state takes the CFL step of Eq. (cfl) (cfl > 0), cut at its end
+ *   time (ADG_OPT_END_TIME); states past their end time idle.  From the
+ *   second CFL step on, the whole batched step replays as one CUDA graph.
+ * Asynchronous; errors of device-side conditions surface in adg_status of
+ * the states. */
+typedef struct adg_batch adg_batch;
+int adg_batch_create(adg_state* const* states, int count, void* stream, adg_batch** out);
+int adg_batch_step(adg_batch* b, const double* dts, double cfl);
+void adg_batch_destroy(adg_batch* b);
+
+/* One step of `count` states with host steps dts[count] in shared launches
+ * (a batch created and destroyed around the call). */
+int adg_step_batch(adg_state* const* states, const double* dts, int count);
 
 /* Eq. (cfl): dt = cfl * min_k dx_k / lambda_max with lambda_max over the
  * subcell averages v^n of every cell; cfl includes 1/(d (2N+1)).

@@ -25,6 +25,7 @@ PREC_FP64, PREC_MIXED_FP32 = 0, 1
 OPT_DMP_EPS, OPT_DMP_FLOOR, OPT_FORCE_LIMITER, OPT_PICARD_ITERS, OPT_SLOT_CAPACITY = 1, 2, 3, 4, 5
 OPT_PROFILE = 6
 OPT_FP64_SWEEPS = 7
+OPT_END_TIME = 8
 PHASES = ("predictor", "faceflux", "correct_detect", "limiter", "fix")
 IC_RADIAL, IC_QUADRANT = 0, 1
 
@@ -33,7 +34,8 @@ SYMBOLS = ("adg_create", "adg_set_allocator", "adg_set_stream", "adg_set_option"
            "adg_init_problem", "adg_load_full", "adg_read_full", "adg_step", "adg_step_cfl",
            "adg_max_dt", "adg_flags", "adg_read", "adg_troubled_count", "adg_status",
            "adg_sizes", "adg_info", "adg_phase_times", "adg_last_error", "adg_destroy",
-           "adg_subcell_update_noalloc")
+           "adg_subcell_update_noalloc", "adg_time", "adg_batch_create", "adg_batch_step",
+           "adg_batch_destroy", "adg_step_batch")
 
 
 class AdgGrid(ctypes.Structure):
@@ -95,8 +97,14 @@ def load_library(path=None):
                                                vp, vp, vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.adg_destroy.argtypes = [vp]
     lib.adg_destroy.restype = None
+    lib.adg_time.argtypes = [vp, dp]
+    lib.adg_batch_create.argtypes = [ctypes.POINTER(vp), ip, vp, ctypes.POINTER(vp)]
+    lib.adg_batch_step.argtypes = [vp, dp, ctypes.c_double]
+    lib.adg_batch_destroy.argtypes = [vp]
+    lib.adg_batch_destroy.restype = None
+    lib.adg_step_batch.argtypes = [ctypes.POINTER(vp), dp, ip]
     for name in SYMBOLS:
-        if name not in ("adg_last_error", "adg_destroy"):
+        if name not in ("adg_last_error", "adg_destroy", "adg_batch_destroy"):
             getattr(lib, name).restype = ctypes.c_int
     if path is None:
         _lib = lib
@@ -293,10 +301,68 @@ class Solver:
         self._check(self.lib.adg_info(self.h, out, 4), "adg_info")
         return dict(capacity=out[0], chunk=out[1], launches_per_step=out[2], bytes=out[3])
 
+    def time(self):
+        t = ctypes.c_double()
+        self._check(self.lib.adg_time(self.h, ctypes.byref(t)), "adg_time")
+        return t.value
+
     def max_dt(self, cfl):
         dt = ctypes.c_double()
         self._check(self.lib.adg_max_dt(self.h, float(cfl), ctypes.byref(dt)), "adg_max_dt")
         return dt.value
 
 
-__all__ = ["Solver", "AdgError", "load_library", "SYMBOLS", "inputs"]
+def _handles(solvers):
+    arr = (ctypes.c_void_p * len(solvers))()
+    for i, s in enumerate(solvers):
+        arr[i] = s.h
+    return arr
+
+
+class Batch:
+    """adg_batch: states of equal (dim, N, precision) share every launch; CFL
+    steps replay as one CUDA graph from the second step on."""
+
+    def __init__(self, solvers, stream=0):
+        self.lib = load_library()
+        self.solvers = list(solvers)
+        h = ctypes.c_void_p()
+        rc = self.lib.adg_batch_create(_handles(self.solvers), len(self.solvers),
+                                       ctypes.c_void_p(int(stream)) if stream else None,
+                                       ctypes.byref(h))
+        if rc != OK:
+            raise AdgError(rc, "adg_batch_create failed")
+        self.h = h
+
+    def step(self, dts=None, cfl=0.0):
+        if dts is not None:
+            d = _contig(dts, np.float64)
+            rc = self.lib.adg_batch_step(self.h, _dptr(d), 0.0)
+        else:
+            rc = self.lib.adg_batch_step(self.h, None, float(cfl))
+        if rc < 0:
+            msg = self.lib.adg_last_error(self.solvers[0].h).decode()
+            raise AdgError(rc, f"adg_batch_step: {msg}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.adg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def step_batch(solvers, dts):
+    """adg_step_batch: one step of every solver, shared launches."""
+    lib = load_library()
+    d = _contig(dts, np.float64)
+    rc = lib.adg_step_batch(_handles(solvers), _dptr(d), len(solvers))
+    if rc < 0:
+        raise AdgError(rc, "adg_step_batch: " + lib.adg_last_error(solvers[0].h).decode())
+
+
+__all__ = ["Solver", "Batch", "step_batch", "AdgError", "load_library", "SYMBOLS", "inputs"]

@@ -35,6 +35,15 @@ struct adg_state {
   bool profile = false;
   bool lam_mode = false;    // steps keep the per-cell wave speeds current
   bool lam_valid = false;   // b.lam describes the current level
+  // device copy of the Params: during steps the device owns cur and stamp
+  Params* dparams = nullptr;
+  Params** d_pps1 = nullptr;        // [1] = dparams
+  long long* d_pre1 = nullptr;      // cells[2], faces[3][2], lim[2], fix[2]
+  double* d_dts1 = nullptr;         // [1]
+  bool params_dirty = true;         // host fields changed since the last upload
+  bool cur_known = true;            // host cur / stamp equal the device's
+  double t_end = 0.0;               // end time of the simulated interval (0: none)
+  Params hparams;                   // source of the last upload
   cudaEvent_t ev[PHASE_COUNT] = {};
   double phase_ms[PHASE_COUNT] = {};
   int timed_steps = 0;
@@ -126,7 +135,11 @@ cudaError_t dispatch(const adg_state* st, LaunchArgs& a) {
   return dispatch_3d(st->N, a);
 }
 
+int refresh(adg_state* st);
+
 int launch(adg_state* st, LaunchArgs& a, const char* what) {
+  int rc = refresh(st);
+  if (rc) return rc;
   Params p = make_params(st);
   a.p = &p;
   a.stream = st->stream;
@@ -191,8 +204,13 @@ int ensure_allocated(adg_state* st) {
   ALLOC(b.fixlist, int, cells);
   ALLOC(b.fixstamp, int, cells);
   ALLOC(b.edge, double, cap * st->dim * 2 * nv * nsf);
-  ALLOC(b.dt, double, 2);
+  ALLOC(b.dt, double, 4);
   b.lamred = b.dt + 1;
+  b.clock = b.dt + 2;
+  ALLOC(st->dparams, Params, 1);
+  ALLOC(st->d_pps1, Params*, 1);
+  ALLOC(st->d_pre1, long long, 12);
+  ALLOC(st->d_dts1, double, 1);
   ALLOC(b.patch, double, chunk * parts[0]);
   ALLOC(b.sweep[0], double, chunk * parts[1]);
   ALLOC(b.sweep[1], double, chunk * parts[2]);
@@ -204,8 +222,21 @@ int ensure_allocated(adg_state* st) {
                                st->stream));
   CUDA_TRY(st, cudaMemsetAsync(b.counters, 0, sizeof(int) * CNT_COUNT, st->stream));
   CUDA_TRY(st, cudaMemsetAsync(b.fixstamp, 0xff, sizeof(int) * cells, st->stream));
-  CUDA_TRY(st, cudaMemsetAsync(b.dt, 0, sizeof(double) * 2, st->stream));
+  CUDA_TRY(st, cudaMemsetAsync(b.dt, 0, sizeof(double) * 4, st->stream));
+  {
+    long long pre[12] = {0, cells, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < st->dim; ++k) {
+      long long faces = 1;
+      for (int j = 0; j < st->dim; ++j) faces *= (j == k) ? st->geo.n[j] + 1 : st->geo.n[j];
+      pre[2 + 2 * k + 1] = faces * nf;
+    }
+    CUDA_TRY(st, cudaMemcpy(st->d_pre1, pre, sizeof(pre), cudaMemcpyHostToDevice));
+    Params* pp = st->dparams;
+    CUDA_TRY(st, cudaMemcpy(st->d_pps1, &pp, sizeof(Params*), cudaMemcpyHostToDevice));
+  }
   st->allocated = true;
+  st->params_dirty = true;
+  st->cur_known = true;
   return ADG_OK;
 }
 
@@ -214,12 +245,42 @@ int sync(adg_state* st) {
   return ADG_OK;
 }
 
-// Reset the current level's counters before a load
+// Bring the host's cur / stamp up to date with the device Params.
+int refresh(adg_state* st) {
+  if (st->cur_known || !st->allocated) return ADG_OK;
+  Params p;
+  CUDA_TRY(st, cudaMemcpyAsync(&p, st->dparams, sizeof(Params), cudaMemcpyDeviceToHost, st->stream));
+  CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+  st->cur = p.cur;
+  st->stamp = p.stamp;
+  st->cur_known = true;
+  return ADG_OK;
+}
+
+// Upload the host Params (after a refresh, so device cur / stamp survive).
+int upload_params(adg_state* st) {
+  int rc = refresh(st);
+  if (rc) return rc;
+  st->hparams = make_params(st);
+  CUDA_TRY(st, cudaMemcpyAsync(st->dparams, &st->hparams, sizeof(Params), cudaMemcpyHostToDevice,
+                               st->stream));
+  CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+  st->params_dirty = false;
+  return ADG_OK;
+}
+
+// Reset the current level's counters and the clock before a load
 int begin_load(adg_state* st) {
   int rc = ensure_allocated(st);
   if (rc) return rc;
+  rc = refresh(st);
+  if (rc) return rc;
   st->cur = 0;
+  st->params_dirty = true;
   CUDA_TRY(st, cudaMemsetAsync(st->b.counters, 0, sizeof(int) * CNT_COUNT, st->stream));
+  const double clk[2] = {0.0, st->t_end};
+  CUDA_TRY(st, cudaMemcpyAsync(st->b.clock, clk, sizeof(clk), cudaMemcpyHostToDevice, st->stream));
+  CUDA_TRY(st, cudaStreamSynchronize(st->stream));
   return ADG_OK;
 }
 
@@ -289,24 +350,64 @@ int collect_phases(adg_state* st) {
   return ADG_OK;
 }
 
-int common_step(adg_state* st) {
-  const int nxt = 1 - st->cur;
+StepLaunch single_launch(adg_state* st) {
+  StepLaunch sl;
+  std::memset(&sl, 0, sizeof(sl));
+  sl.pps = st->d_pps1;
+  sl.n = 1;
+  sl.pre_cells = st->d_pre1;
+  for (int k = 0; k < 3; ++k) sl.pre_faces[k] = st->d_pre1 + 2 + 2 * k;
+  sl.pre_lim = st->d_pre1 + 8;
+  sl.pre_fix = st->d_pre1 + 10;
+  sl.total_cells = st->geo.cells;
+  for (int k = 0; k < st->dim; ++k) {
+    long long faces = 1;
+    for (int j = 0; j < st->dim; ++j) faces *= (j == k) ? st->geo.n[j] + 1 : st->geo.n[j];
+    long long nf = 1;
+    for (int j = 0; j < st->dim - 1; ++j) nf *= st->N + 1;
+    sl.total_faces[k] = faces * nf;
+  }
+  sl.sum_chunk = st->chunk;
+  sl.max_passes = (st->cap + st->chunk - 1) / st->chunk;
+  sl.prec = st->prec;
+  sl.ev = st->profile ? st->ev : nullptr;
+  return sl;
+}
+
+// Enqueue one step of the states described by `sl` (all of one dimension,
+// degree and precision; `st` selects the kernel instantiation).
+int run_step(adg_state* st, const StepLaunch& sl, cudaStream_t stream) {
+  CUDA_TRY(st, launch_step_begin(sl, stream));
+  LaunchArgs a{};
+  a.step = &sl;
+  a.stream = stream;
+  a.op = OP_STEP_DG;
+  cudaError_t e = dispatch(st, a);
+  if (e != cudaSuccess) return fail(st, ADG_ERR_CUDA, std::string("DG step: ") + cudaGetErrorString(e));
+  a.op = OP_STEP_LIMITER;
+  e = dispatch(st, a);
+  if (e != cudaSuccess)
+    return fail(st, ADG_ERR_CUDA, std::string("subcell limiter: ") + cudaGetErrorString(e));
+  CUDA_TRY(st, launch_step_end(sl, stream));
+  return ADG_OK;
+}
+
+int common_step(adg_state* st, const double* dts_dev, double cfl, double dt_max) {
   if (st->profile) {
     int rc = collect_phases(st);
     if (rc) return rc;
   }
-  CUDA_TRY(st, cudaMemsetAsync(st->b.counters + CNT_TROUBLED0 + nxt, 0, sizeof(int), st->stream));
-  CUDA_TRY(st, cudaMemsetAsync(st->b.counters + CNT_FIX, 0, sizeof(int), st->stream));
-  st->stamp += 1;
-  LaunchArgs a{};
-  a.ev = st->profile ? st->ev : nullptr;
-  a.op = OP_STEP_DG;
-  int rc = launch(st, a, "DG step");
+  if (st->params_dirty) {
+    int rc = upload_params(st);
+    if (rc) return rc;
+  }
+  StepLaunch sl = single_launch(st);
+  sl.dts = dts_dev;
+  sl.cfl = cfl;
+  sl.dt_max = dt_max;
+  int rc = run_step(st, sl, st->stream);
   if (rc) return rc;
-  a.op = OP_STEP_LIMITER;
-  rc = launch(st, a, "subcell limiter");
-  if (rc) return rc;
-  st->cur = nxt;
+  st->cur_known = false;            // the device swapped levels (unless the state idled)
   st->pending = st->profile;
   st->lam_valid = st->lam_mode;
   return ADG_OK;
@@ -314,8 +415,13 @@ int common_step(adg_state* st) {
 
 // Make b.lam describe the current level; later steps keep it current.
 int ensure_lambda(adg_state* st) {
-  st->lam_mode = true;
+  if (!st->lam_mode) {
+    st->lam_mode = true;
+    st->params_dirty = true;
+  }
   if (st->lam_valid) return ADG_OK;
+  int rc0 = refresh(st);
+  if (rc0) return rc0;
   LaunchArgs a{};
   a.op = OP_LAMBDA;
   int rc = launch(st, a, "wave speeds");
@@ -326,7 +432,242 @@ int ensure_lambda(adg_state* st) {
 
 }  // namespace
 
+struct adg_batch {
+  std::vector<adg_state*> states;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  struct Group {
+    adg_state* rep;                 // selects the kernel instantiation
+    std::vector<int> idx;
+    StepLaunch sl;
+    int dts_off;
+  };
+  std::vector<Group> groups;
+  std::vector<void*> mem;
+  double* d_dts = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double graph_cfl = -1.0;
+  int cfl_steps = 0;
+};
+
+namespace {
+
+void batch_free(adg_batch* b) {
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (void* p : b->mem) cudaFree(p);
+  if (b->own_stream) {
+    for (adg_state* st : b->states) st->stream = nullptr;
+    cudaStreamDestroy(b->stream);
+  }
+  delete b;
+}
+
+int batch_run(adg_batch* b, bool fixed, double cfl) {
+  for (auto& g : b->groups) {
+    StepLaunch sl = g.sl;
+    sl.dts = fixed ? b->d_dts + g.dts_off : nullptr;
+    sl.cfl = cfl;
+    sl.dt_max = 0.0;
+    int rc = run_step(g.rep, sl, b->stream);
+    if (rc) return rc;
+  }
+  return ADG_OK;
+}
+
+}  // namespace
+
 extern "C" {
+
+int adg_batch_create(adg_state* const* states, int count, void* stream, adg_batch** out) {
+  if (!out || !states || count < 1) return ADG_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i)
+    if (!states[i] || !states[i]->loaded) return ADG_ERR_ARG;
+  adg_batch* b = new (std::nothrow) adg_batch();
+  if (!b) return ADG_ERR_OOM;
+  b->states.assign(states, states + count);
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return ADG_ERR_CUDA;
+    }
+    b->own_stream = true;
+  }
+  // every state: host view current, Params uploaded, work on the batch stream
+  for (adg_state* st : b->states) {
+    if (refresh(st) || (st->stream && cudaStreamSynchronize(st->stream) != cudaSuccess)) {
+      batch_free(b);
+      return ADG_ERR_CUDA;
+    }
+    st->stream = b->stream;
+    if (st->params_dirty && upload_params(st)) {
+      batch_free(b);
+      return ADG_ERR_CUDA;
+    }
+  }
+  // groups of equal (dimension, degree, precision)
+  std::vector<int> done(count, 0);
+  int off = 0;
+  for (int i = 0; i < count; ++i) {
+    if (done[i]) continue;
+    adg_batch::Group g;
+    g.rep = states[i];
+    for (int j = i; j < count; ++j) {
+      const adg_state* a = states[i];
+      const adg_state* c = states[j];
+      if (!done[j] && a->dim == c->dim && a->N == c->N && a->prec == c->prec) {
+        g.idx.push_back(j);
+        done[j] = 1;
+      }
+    }
+    const int n = (int)g.idx.size();
+    std::vector<Params*> pps(n);
+    std::vector<long long> pc(n + 1, 0), pf[3];
+    for (int k = 0; k < 3; ++k) pf[k].assign(n + 1, 0);
+    long long sum_chunk = 0;
+    int max_passes = 0;
+    StepLaunch sl;
+    std::memset(&sl, 0, sizeof(sl));
+    for (int q = 0; q < n; ++q) {
+      adg_state* st = states[g.idx[q]];
+      pps[q] = st->dparams;
+      const StepLaunch one = single_launch(st);
+      pc[q + 1] = pc[q] + one.total_cells;
+      for (int k = 0; k < 3; ++k) pf[k][q + 1] = pf[k][q] + one.total_faces[k];
+      sum_chunk += st->chunk;
+      const int passes = (st->cap + st->chunk - 1) / st->chunk;
+      if (passes > max_passes) max_passes = passes;
+    }
+    void* d = nullptr;
+    const size_t bytes = sizeof(Params*) * n + sizeof(long long) * (size_t)(n + 1) * 6;
+    if (cudaMalloc(&d, bytes) != cudaSuccess) {
+      batch_free(b);
+      return ADG_ERR_OOM;
+    }
+    b->mem.push_back(d);
+    Params** dpps = (Params**)d;
+    long long* dpre = (long long*)(dpps + n);
+    cudaMemcpy(dpps, pps.data(), sizeof(Params*) * n, cudaMemcpyHostToDevice);
+    cudaMemcpy(dpre, pc.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice);
+    for (int k = 0; k < 3; ++k)
+      cudaMemcpy(dpre + (size_t)(k + 1) * (n + 1), pf[k].data(), sizeof(long long) * (n + 1),
+                 cudaMemcpyHostToDevice);
+    sl.pps = dpps;
+    sl.n = n;
+    sl.pre_cells = dpre;
+    for (int k = 0; k < 3; ++k) sl.pre_faces[k] = dpre + (size_t)(k + 1) * (n + 1);
+    sl.pre_lim = dpre + (size_t)4 * (n + 1);
+    sl.pre_fix = dpre + (size_t)5 * (n + 1);
+    sl.total_cells = pc[n];
+    for (int k = 0; k < 3; ++k) sl.total_faces[k] = pf[k][n];
+    sl.sum_chunk = sum_chunk;
+    sl.max_passes = max_passes;
+    sl.prec = g.rep->prec;
+    sl.ev = nullptr;
+    g.sl = sl;
+    g.dts_off = off;
+    off += n;
+    b->groups.push_back(g);
+  }
+  if (cudaMalloc((void**)&b->d_dts, sizeof(double) * count) != cudaSuccess) {
+    batch_free(b);
+    return ADG_ERR_OOM;
+  }
+  b->mem.push_back(b->d_dts);
+  if (cudaGetLastError() != cudaSuccess) {
+    batch_free(b);
+    return ADG_ERR_CUDA;
+  }
+  *out = b;
+  return ADG_OK;
+}
+
+int adg_batch_step(adg_batch* b, const double* dts, double cfl) {
+  if (!b) return ADG_ERR_ARG;
+  adg_state* st0 = b->states[0];
+  if (dts) {
+    // host steps in group order
+    std::vector<double> ordered(b->states.size());
+    for (auto& g : b->groups)
+      for (size_t q = 0; q < g.idx.size(); ++q) {
+        const double dt = dts[g.idx[q]];
+        if (!(dt > 0.0) || std::isinf(dt)) return fail(st0, ADG_ERR_ARG, "dt must be positive");
+        ordered[g.dts_off + q] = dt;
+      }
+    CUDA_TRY(st0, cudaMemcpyAsync(b->d_dts, ordered.data(), sizeof(double) * ordered.size(),
+                                  cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(st0, cudaStreamSynchronize(b->stream));   // `ordered` leaves scope
+    int rc = batch_run(b, true, 0.0);
+    if (rc) return rc;
+  } else {
+    if (!(cfl > 0.0)) return fail(st0, ADG_ERR_ARG, "cfl must be positive");
+    for (adg_state* st : b->states) {
+      int rc = ensure_lambda(st);
+      if (!rc && st->params_dirty) rc = upload_params(st);
+      if (rc) return rc;
+    }
+    if (b->exec && b->graph_cfl == cfl) {
+      CUDA_TRY(st0, cudaGraphLaunch(b->exec, b->stream));
+    } else if (b->cfl_steps == 0) {
+      int rc = batch_run(b, false, cfl);         // first step: plain launches
+      if (rc) return rc;
+    } else {
+      if (b->exec) cudaGraphExecDestroy(b->exec);
+      if (b->graph) cudaGraphDestroy(b->graph);
+      b->exec = nullptr;
+      b->graph = nullptr;
+      CUDA_TRY(st0, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+      const int rc = batch_run(b, false, cfl);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (ec != cudaSuccess) return fail(st0, ADG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ec));
+      b->graph = g;
+      CUDA_TRY(st0, cudaGraphInstantiate(&b->exec, b->graph, 0));
+      b->graph_cfl = cfl;
+      CUDA_TRY(st0, cudaGraphLaunch(b->exec, b->stream));
+    }
+    b->cfl_steps += 1;
+  }
+  for (adg_state* st : b->states) {
+    st->cur_known = false;
+    st->lam_valid = st->lam_mode;
+  }
+  return ADG_OK;
+}
+
+void adg_batch_destroy(adg_batch* b) {
+  if (b) batch_free(b);
+}
+
+int adg_step_batch(adg_state* const* states, const double* dts, int count) {
+  if (!states || !dts || count < 1 || !states[0]) return ADG_ERR_ARG;
+  adg_batch* b = nullptr;
+  int rc = adg_batch_create(states, count, states[0]->stream, &b);
+  if (rc) return rc;
+  rc = adg_batch_step(b, dts, 0.0);
+  adg_batch_destroy(b);
+  return rc;
+}
+
+int adg_time(adg_state* st, double* t) {
+  if (!st || !t) return ADG_ERR_ARG;
+  if (!st->allocated) {
+    *t = 0.0;
+    return ADG_OK;
+  }
+  CUDA_TRY(st, cudaMemcpyAsync(t, st->b.clock, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+  return sync(st);
+}
+
 
 int adg_create(const adg_grid* grid, int N, double gamma, const int* bc, int prec,
                adg_state** out) {
@@ -389,6 +730,7 @@ int adg_set_stream(adg_state* st, void* stream) {
 
 int adg_set_option(adg_state* st, int key, double value) {
   if (!st) return ADG_ERR_ARG;
+  st->params_dirty = true;
   switch (key) {
     case ADG_OPT_DMP_EPS:
       if (!(value >= 0.0)) return fail(st, ADG_ERR_ARG, "eps must be >= 0");
@@ -408,6 +750,14 @@ int adg_set_option(adg_state* st, int key, double value) {
     case ADG_OPT_FP64_SWEEPS:
       if (!(value >= 1.0 && value <= 64.0)) return fail(st, ADG_ERR_ARG, "FP64 sweeps in 1..64");
       st->fp64_sweeps = (int)value;
+      return ADG_OK;
+    case ADG_OPT_END_TIME:
+      if (!(value >= 0.0)) return fail(st, ADG_ERR_ARG, "end time must be >= 0");
+      st->t_end = value;
+      if (st->allocated)
+        CUDA_TRY(st, cudaMemcpyAsync(st->b.clock + 1, &st->t_end, sizeof(double),
+                                     cudaMemcpyHostToDevice, st->stream));
+      if (st->allocated) CUDA_TRY(st, cudaStreamSynchronize(st->stream));
       return ADG_OK;
     case ADG_OPT_PROFILE:
       if (value != 0.0 && !st->ev[0])
@@ -496,6 +846,10 @@ int adg_load_full(adg_state* st, const double* dofs, const uint8_t* beta, const 
 int adg_read_full(adg_state* st, double* dofs, uint8_t* beta, double* sub) {
   if (!st || !dofs || !beta || !sub) return ADG_ERR_ARG;
   if (!st->loaded) return fail(st, ADG_ERR_ARG, "nothing loaded");
+  {
+    const int rr = refresh(st);
+    if (rr) return rr;
+  }
   const size_t nd = (size_t)st->geo.cells * st->nv * nodes_per_cell(st);
   const size_t ns = (size_t)st->geo.cells * st->nv * subcells_per_cell(st);
   Temp ts(st, ns * sizeof(double));
@@ -517,8 +871,8 @@ int adg_step(adg_state* st, double dt) {
   if (!st) return ADG_ERR_ARG;
   if (!st->loaded) return fail(st, ADG_ERR_ARG, "nothing loaded");
   if (!(dt > 0.0) || std::isinf(dt)) return fail(st, ADG_ERR_ARG, "dt must be positive and finite");
-  CUDA_TRY(st, launch_set_scalar(st->b.dt, dt, st->stream));
-  return common_step(st);
+  CUDA_TRY(st, launch_set_scalar(st->d_dts1, dt, st->stream));
+  return common_step(st, st->d_dts1, 0.0, 0.0);
 }
 
 int adg_step_cfl(adg_state* st, double cfl, double dt_max) {
@@ -527,9 +881,7 @@ int adg_step_cfl(adg_state* st, double cfl, double dt_max) {
   if (!(cfl > 0.0)) return fail(st, ADG_ERR_ARG, "cfl must be positive");
   int rc = ensure_lambda(st);
   if (rc) return rc;
-  Params p = make_params(st);
-  CUDA_TRY(st, launch_dt(p, cfl, dt_max, st->stream));
-  return common_step(st);
+  return common_step(st, nullptr, cfl, dt_max);
 }
 
 int adg_max_dt(adg_state* st, double cfl, double* dt_out) {
@@ -537,6 +889,8 @@ int adg_max_dt(adg_state* st, double cfl, double* dt_out) {
   if (!st->loaded) return fail(st, ADG_ERR_ARG, "nothing loaded");
   if (!(cfl > 0.0)) return fail(st, ADG_ERR_ARG, "cfl must be positive");
   int rc0 = ensure_lambda(st);
+  if (rc0) return rc0;
+  rc0 = refresh(st);
   if (rc0) return rc0;
   Params p = make_params(st);
   CUDA_TRY(st, launch_dt(p, cfl, -1.0, st->stream));
@@ -556,6 +910,10 @@ int adg_max_dt(adg_state* st, double cfl, double* dt_out) {
 int adg_flags(adg_state* st, uint8_t* beta) {
   if (!st || !beta) return ADG_ERR_ARG;
   if (!st->loaded) return fail(st, ADG_ERR_ARG, "nothing loaded");
+  {
+    const int rr = refresh(st);
+    if (rr) return rr;
+  }
   CUDA_TRY(st, cudaMemcpyAsync(beta, st->b.beta[st->cur], st->geo.cells, cudaMemcpyDeviceToHost,
                                st->stream));
   return sync(st);
@@ -564,6 +922,10 @@ int adg_flags(adg_state* st, uint8_t* beta) {
 int adg_read(adg_state* st, double* dofs) {
   if (!st || !dofs) return ADG_ERR_ARG;
   if (!st->loaded) return fail(st, ADG_ERR_ARG, "nothing loaded");
+  {
+    const int rr = refresh(st);
+    if (rr) return rr;
+  }
   const size_t nd = (size_t)st->geo.cells * st->nv * nodes_per_cell(st);
   CUDA_TRY(st, cudaMemcpyAsync(dofs, st->b.U[st->cur], nd * sizeof(double), cudaMemcpyDeviceToHost,
                                st->stream));
@@ -573,6 +935,10 @@ int adg_read(adg_state* st, double* dofs) {
 int adg_troubled_count(adg_state* st, int64_t* out) {
   if (!st || !out) return ADG_ERR_ARG;
   if (!st->loaded) return fail(st, ADG_ERR_ARG, "nothing loaded");
+  {
+    const int rr = refresh(st);
+    if (rr) return rr;
+  }
   int c = 0;
   CUDA_TRY(st, cudaMemcpyAsync(&c, st->b.counters + CNT_TROUBLED0 + st->cur, sizeof(int),
                                cudaMemcpyDeviceToHost, st->stream));

@@ -68,8 +68,9 @@ struct Bufs {
   int* fixlist;          // [cells]
   int* fixstamp;         // [cells]
   double* edge;          // [cap][d][2][nv][Ns^(d-1)] sub-face fluxes on the cell faces
-  double* dt;            // [1] time step of the current step
+  double* dt;            // [1] time step of the current step (0: state idle this step)
   double* lamred;        // [1] reduced lambda
+  double* clock;         // [2] simulated time t and end time t_end (0: none)
   // limiter scratch, sized for one chunk of `chunk` troubled cells
   double* patch;         // [chunk][nv][L^d]
   double* sweep[3];      // [chunk][nv][...] after the x, y, z reconstructions
@@ -97,11 +98,53 @@ struct Params {
   int stamp;             // step counter (fix-list stamps)
   int lam_mode;          // 1: kernels keep the per-cell wave speeds current
   int fp64_sweeps;       // mixed precision: number of final FP64 Picard sweeps
+  int status_pad;
+};
+
+// A batch of states of one (dimension, degree, precision) stepped by the same
+// launches.  Each state's Params lives in device memory (pps[s]); `pre` is the
+// item prefix of the launch (pre[s] = first item of state s, pre[n] = total).
+struct Batch {
+  Params* const* pps;
+  int n;
+  const long long* pre;
+};
+
+// state owning item g: pre[s] <= g < pre[s+1]
+__device__ __forceinline__ int batch_state(const Batch& b, long long g) {
+  int lo = 0, hi = b.n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (b.pre[mid] <= g) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Device descriptors of one batched step (all arrays in device memory).
+struct StepLaunch {
+  Params* const* pps;          // [n] per-state device Params
+  int n;
+  const long long* pre_cells;  // [n+1]
+  const long long* pre_faces[3];  // [n+1] faces x tangential nodes, per axis
+  long long* pre_lim;          // [n+1] troubled cells of one limiter pass (device-computed)
+  long long* pre_fix;          // [n+1] neighbour-fix entries (device-computed)
+  long long total_cells;
+  long long total_faces[3];
+  long long sum_chunk;         // sum over states of the limiter chunk size
+  int max_passes;              // max over states of ceil(capacity / chunk)
+  int prec;
+  cudaEvent_t* ev;             // phase events or null
+  const double* dts;           // [n] fixed steps, or null for CFL steps
+  double cfl;                  // CFL number when dts is null
+  double dt_max;               // cap of CFL steps (<= 0: none)
 };
 
 // Kernel launch interface: one dispatcher per translation unit (2D low N,
 // 2D high N, 3D), selected by dimension and degree.
 enum LaunchOp {
+  OP_STEP_BEGIN = 10,  // per-state dt (fixed or CFL), counters, stamps
+  OP_STEP_END = 11,    // per-state level swap
   OP_STEP_DG = 0,      // predictor, face fluxes, corrector + detector
   OP_STEP_LIMITER,     // subcell limiter over the troubled list + flux correction
   OP_LOAD_DETECT,      // initial detection (exact may be null)
@@ -123,7 +166,8 @@ struct LaunchArgs {
   double* out;             // OP_READ_FULL rows, OP_PROJECT exact averages, OP_SUB_MINMAX result
   const adg_problem* prob; // OP_PROJECT
   const double* fac;       // OP_PROJECT per-cell density factor (device) or null
-  cudaEvent_t* ev;         // OP_STEP_*: phase events (null: none), see PHASE_*
+  cudaEvent_t* ev;         // unused (phase events travel in StepLaunch)
+  const StepLaunch* step;  // OP_STEP_*: the batched step
 };
 
 // Phase boundaries recorded when profiling is on: ev[PHASE_x] before phase x,
@@ -136,6 +180,11 @@ cudaError_t dispatch_2d_hi(int N, const LaunchArgs& a);   // N = 6..9
 cudaError_t dispatch_3d(int N, const LaunchArgs& a);      // N = 1..3
 cudaError_t launch_dt(const Params& p, double cfl, double dt_max, cudaStream_t s);
 cudaError_t launch_set_scalar(double* dst, double v, cudaStream_t s);
+// dimension-independent batch kernels (k3d.cu)
+cudaError_t launch_step_begin(const StepLaunch& sl, cudaStream_t s);
+cudaError_t launch_step_end(const StepLaunch& sl, cudaStream_t s);
+cudaError_t launch_lim_prefix(const StepLaunch& sl, int pass, cudaStream_t s);
+cudaError_t launch_fix_prefix(const StepLaunch& sl, cudaStream_t s);
 
 // Scratch doubles per troubled cell of the limiter chunk buffers.
 size_t limiter_scratch_doubles(int dim, int N, size_t* patch, size_t* sw0, size_t* sw1,

@@ -25,6 +25,75 @@ __global__ void k_dt(Params p, double cfl, double dt_max) {
 
 __global__ void k_set_scalar(double* dst, double v) { *dst = v; }
 
+// Start of a batched step, one block per state: the state's dt (fixed from
+// sl.dts, or Eq. (cfl) from its per-cell wave speeds, capped by sl.dt_max and
+// by its end time), a new step stamp and cleared counters.  A state with
+// dt = 0 idles through the step.
+__global__ void k_step_begin(StepLaunch sl) {
+  __shared__ double red[32];
+  Params& p = *sl.pps[blockIdx.x];
+  double dt = 0.0;
+  if (sl.dts) {
+    dt = sl.dts[blockIdx.x];
+  } else {
+    double l = 0.0;
+    for (long long c = threadIdx.x; c < p.geo.cells; c += blockDim.x) l = nanmax(l, p.b.lam[c]);
+    l = block_reduce_max(l, red);
+    double h = p.geo.dx[0];
+    for (int k = 1; k < p.dim; ++k) h = fmin(h, p.geo.dx[k]);
+    dt = sl.cfl * h / l;
+    if (!(dt > 0.0) || isinf(dt) || l != l) {
+      if (threadIdx.x == 0) atomicOr(&p.b.counters[CNT_STATUS], 2);
+      dt = 0.0;
+    }
+    if (sl.dt_max > 0.0 && dt > sl.dt_max) dt = sl.dt_max;
+  }
+  if (threadIdx.x == 0) {
+    const double t = p.b.clock[0], tend = p.b.clock[1];
+    if (tend > 0.0) {
+      const double rem = tend - t;
+      if (dt > rem) dt = rem;
+      if (!(rem > 1e-12 * tend)) dt = 0.0;
+    }
+    *p.b.dt = dt;
+    if (dt > 0.0) {
+      p.b.counters[CNT_TROUBLED0 + (1 - p.cur)] = 0;
+      p.b.counters[CNT_FIX] = 0;
+      p.stamp += 1;
+      p.b.clock[0] = t + dt;
+    }
+  }
+}
+
+// End of a batched step: states that stepped swap levels.
+__global__ void k_step_end(StepLaunch sl) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= sl.n) return;
+  Params& p = *sl.pps[s];
+  if (*p.b.dt > 0.0) p.cur = 1 - p.cur;
+}
+
+// Prefix of the troubled cells each state handles in limiter pass `pass`.
+__global__ void k_lim_prefix(StepLaunch sl, int pass) {
+  long long acc = 0;
+  for (int s = 0; s < sl.n; ++s) {
+    sl.pre_lim[s] = acc;
+    acc += pass_len(*sl.pps[s], pass);
+  }
+  sl.pre_lim[sl.n] = acc;
+}
+
+// Prefix of the neighbour-fix entries of every state.
+__global__ void k_fix_prefix(StepLaunch sl) {
+  long long acc = 0;
+  for (int s = 0; s < sl.n; ++s) {
+    sl.pre_fix[s] = acc;
+    const Params& p = *sl.pps[s];
+    if (*p.b.dt > 0.0) acc += p.b.counters[CNT_FIX];
+  }
+  sl.pre_fix[sl.n] = acc;
+}
+
 
 cudaError_t dispatch_3d(int N, const LaunchArgs& a) {
   switch (N) {
@@ -42,6 +111,26 @@ cudaError_t launch_dt(const Params& p, double cfl, double dt_max, cudaStream_t s
 
 cudaError_t launch_set_scalar(double* dst, double v, cudaStream_t s) {
   k_set_scalar<<<1, 1, 0, s>>>(dst, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_begin(const StepLaunch& sl, cudaStream_t s) {
+  k_step_begin<<<sl.n, sl.dts ? 32 : 1024, 0, s>>>(sl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_end(const StepLaunch& sl, cudaStream_t s) {
+  k_step_end<<<(sl.n + 127) / 128, 128, 0, s>>>(sl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lim_prefix(const StepLaunch& sl, int pass, cudaStream_t s) {
+  k_lim_prefix<<<1, 1, 0, s>>>(sl, pass);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fix_prefix(const StepLaunch& sl, cudaStream_t s) {
+  k_fix_prefix<<<1, 1, 0, s>>>(sl);
   return cudaGetLastError();
 }
 

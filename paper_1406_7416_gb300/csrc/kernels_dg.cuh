@@ -225,7 +225,7 @@ __host__ __device__ constexpr size_t predictor_smem_bytes() {
 }
 
 template <int D, int N, bool MIXED>
-__global__ void __launch_bounds__(256) k_predictor(Params p) {
+__global__ void __launch_bounds__(256) k_predictor(Batch bt) {
   using DM = Dims<D, N>;
   constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, NST = DM::NST, NF = DM::NF, NT = DM::NT;
   extern __shared__ double sm[];
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(256) k_predictor(Params p) {
   float* uf = Ktf + n * n;
 
   const int tid = threadIdx.x, nth = blockDim.x;
-  const Ops* o = p.ops;
+  const Ops* o = bt.pps[0]->ops;      // every state of a batch has degree N
   for (int i = tid; i < n * n; i += nth) {
     Dm[i] = o->D[i];
     Kt[i] = o->Kt[i];
@@ -261,13 +261,16 @@ __global__ void __launch_bounds__(256) k_predictor(Params p) {
     ph0[i] = o->phi0[i];
     ph1[i] = o->phi1[i];
   }
-  const double dt = *p.b.dt;
-  double c[3];
+  for (long long g = blockIdx.x; g < bt.pre[bt.n]; g += gridDim.x) {
+    const int sidx = batch_state(bt, g);
+    const Params& p = *bt.pps[sidx];
+    const long long cell = g - bt.pre[sidx];
+    const double dt = *p.b.dt;
+    if (!(dt > 0.0)) continue;          // state idle this step (block-uniform)
+    double c[3];
 #pragma unroll
-  for (int k = 0; k < D; ++k) c[k] = dt / p.geo.dx[k];
-  const double gm1 = p.gamma - 1.0;
-
-  for (long long cell = blockIdx.x; cell < p.geo.cells; cell += gridDim.x) {
+    for (int k = 0; k < D; ++k) c[k] = dt / p.geo.dx[k];
+    const double gm1 = p.gamma - 1.0;
     const double* Uc = p.b.U[p.cur] + cell * (NV * ND);
     for (int i = tid; i < NV * ND; i += nth) u[i] = Uc[i];
     __syncthreads();
@@ -374,15 +377,18 @@ __global__ void __launch_bounds__(256) k_predictor(Params p) {
 // interior trace (G = F(q^-)).
 // ---------------------------------------------------------------------------
 template <int D, int N>
-__global__ void __launch_bounds__(256) k_faceflux(Params p, int k) {
+__global__ void __launch_bounds__(256) k_faceflux(Batch bt, int k) {
   using DM = Dims<D, N>;
   constexpr int n = DM::n, NV = DM::NV, NF = DM::NF, NT = DM::NT;
-  const Geo& g = p.geo;
-  const long long nf = face_count<D>(g, k);
-  const double* w = p.ops->w;
-  double* G = p.b.G[k];
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nf * NF;
-       e += (long long)gridDim.x * blockDim.x) {
+  for (long long eg = blockIdx.x * (long long)blockDim.x + threadIdx.x; eg < bt.pre[bt.n];
+       eg += (long long)gridDim.x * blockDim.x) {
+    const int sidx = batch_state(bt, eg);
+    const Params& p = *bt.pps[sidx];
+    if (!(*p.b.dt > 0.0)) continue;
+    const long long e = eg - bt.pre[sidx];
+    const Geo& g = p.geo;
+    const double* w = p.ops->w;
+    double* G = p.b.G[k];
     const long long face = e / NF;
     const int ts = (int)(e - face * NF);
     int ijk[3] = {0, 0, 0};
@@ -585,7 +591,7 @@ __host__ __device__ constexpr size_t correct_smem_bytes() {
 }
 
 template <int D, int N>
-__global__ void __launch_bounds__(128) k_correct_detect(Params p) {
+__global__ void __launch_bounds__(128) k_correct_detect(Batch bt) {
   using DM = Dims<D, N>;
   constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, NF = DM::NF, Ns = DM::Ns, NSD = DM::NSD;
   constexpr int BUF = (DM::NSD > DM::ND * 4 ? DM::NSD : DM::ND * 4);
@@ -597,14 +603,19 @@ __global__ void __launch_bounds__(128) k_correct_detect(Params p) {
   double* mm = lohi + 2 * NV;         // 2 NV
   double* red = mm + 2 * NV;          // 128
   const int tid = threadIdx.x, nth = blockDim.x;
-  const Ops* o = p.ops;
+  const Ops* o = bt.pps[0]->ops;
   for (int i = tid; i < Ns * n; i += nth) P1[i] = o->P1[i];
-  const double dt = *p.b.dt;
-  double c[3];
+  __syncthreads();
+  for (long long g = blockIdx.x; g < bt.pre[bt.n]; g += gridDim.x) {
+    const int sidx = batch_state(bt, g);
+    const Params& p = *bt.pps[sidx];
+    const long long cell = g - bt.pre[sidx];
+    const double dt = *p.b.dt;
+    if (!(dt > 0.0)) continue;
+    double c[3];
 #pragma unroll
-  for (int k = 0; k < D; ++k) c[k] = dt / p.geo.dx[k];
-  const int nxt = 1 - p.cur;
-  for (long long cell = blockIdx.x; cell < p.geo.cells; cell += gridDim.x) {
+    for (int k = 0; k < D; ++k) c[k] = dt / p.geo.dx[k];
+    const int nxt = 1 - p.cur;
     int ijk[3];
     cell_coords<D>(cell, p.geo, ijk);
     double* Uo = p.b.U[nxt] + cell * (NV * ND);

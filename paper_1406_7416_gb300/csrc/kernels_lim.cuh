@@ -12,12 +12,28 @@ namespace adg {
 
 __host__ __device__ __forceinline__ int ipow3(int k) { return k == 0 ? 1 : (k == 1 ? 3 : (k == 2 ? 9 : 27)); }
 
-// number of troubled cells handled by chunk `chunk0` (0 when past the end)
-__device__ __forceinline__ int chunk_len(const Params& p, int chunk0) {
+// Troubled cells handled by limiter pass `pass` of one state (0 past the end,
+// and 0 for a state idle this step).  Pass c covers list entries
+// [c * chunk, (c + 1) * chunk).
+__device__ __forceinline__ int pass_len(const Params& p, int pass) {
+  if (!(*p.b.dt > 0.0)) return 0;
   int nT = p.b.counters[CNT_TROUBLED0 + (1 - p.cur)];
   if (nT > p.cap) nT = p.cap;
-  const int len = nT - chunk0;
+  const int len = nT - pass * p.chunk;
   return len < 0 ? 0 : (len > p.chunk ? p.chunk : len);
+}
+
+// Item t (a troubled cell of the current pass, counted over the batch) ->
+// state index and the cell's position j within its state's pass.
+struct LimItem {
+  int s;
+  int j;
+};
+__device__ __forceinline__ LimItem lim_item(const Batch& bt, long long t) {
+  LimItem it;
+  it.s = batch_state(bt, t);
+  it.j = (int)(t - bt.pre[it.s]);
+  return it;
 }
 
 // v^n at one subcell of cell `o` (Eq. ader.icbc): the stored subgrid data of a
@@ -61,19 +77,21 @@ __device__ __forceinline__ void subcell_value(const Params& p, long long o, cons
 // list[chunk0 + j].  Periodic: wrap; transmissive: clamp the global subcell
 // index into the domain.
 template <int D, int N>
-__global__ void __launch_bounds__(256) k_lim_patch(Params p, int chunk0) {
+__global__ void __launch_bounds__(256) k_lim_patch(Batch bt, int pass) {
   using DM = Dims<D, N>;
   constexpr int n = DM::n, NV = DM::NV, Ns = DM::Ns, L = DM::L, LD = DM::LD;
   __shared__ double P1[DM::Ns * DM::n];
-  for (int i = threadIdx.x; i < Ns * n; i += blockDim.x) P1[i] = p.ops->P1[i];
+  for (int i = threadIdx.x; i < Ns * n; i += blockDim.x) P1[i] = bt.pps[0]->ops->P1[i];
   __syncthreads();
-  const int len = chunk_len(p, chunk0);
-  const Geo& g = p.geo;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)len * LD;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < bt.pre[bt.n] * LD;
        e += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(e / LD);
-    int r = (int)(e - (long long)j * LD);
-    const long long cell = p.b.list[1 - p.cur][chunk0 + j];
+    const long long t = e / LD;
+    const LimItem it = lim_item(bt, t);
+    const Params& p = *bt.pps[it.s];
+    const Geo& g = p.geo;
+    const int j = it.j;
+    int r = (int)(e - t * LD);
+    const long long cell = p.b.list[1 - p.cur][pass * p.chunk + j];
     int ijk[3];
     cell_coords<D>(cell, g, ijk);
     int own[3] = {0, 0, 0}, sub[3] = {0, 0, 0};
@@ -90,7 +108,7 @@ __global__ void __launch_bounds__(256) k_lim_patch(Params p, int chunk0) {
     }
     double val[NV];
     subcell_value<D, N>(p, cell_index<D>(own, g), sub, P1, val);
-    double* dst = p.b.patch + (size_t)j * NV * LD + (e - (long long)j * LD);
+    double* dst = p.b.patch + (size_t)j * NV * LD + (e - t * LD);
 #pragma unroll
     for (int v = 0; v < NV; ++v) dst[v * LD] = val[v];
   }
@@ -140,7 +158,7 @@ __device__ __forceinline__ void weno3(const double* u, const Ops* __restrict__ o
 // nodal values per element; the output has extent Ns+2 along K and 3 NNIN
 // nodes (the new nodal index is the slowest digit).
 template <int D, int N, int K>
-__global__ void __launch_bounds__(256) k_lim_sweep(Params p, int chunk0) {
+__global__ void __launch_bounds__(256) k_lim_sweep(Batch bt, int pass) {
   using DM = Dims<D, N>;
   constexpr int NV = DM::NV, L = DM::L, NE = DM::NE;
   constexpr int I0 = (0 < K) ? NE : L, I1 = (1 < K) ? NE : L, I2 = (D < 3) ? 1 : ((2 < K) ? NE : L);
@@ -149,11 +167,15 @@ __global__ void __launch_bounds__(256) k_lim_sweep(Params p, int chunk0) {
   constexpr int INSZ = I0 * I1 * I2 * NNIN;
   constexpr int OUTSZ = O0 * O1 * O2 * NNIN;          // elements, each producing 3 values
   constexpr int STRIDE = ((K == 0) ? 1 : (K == 1 ? I0 : I0 * I1)) * NNIN;
-  const int len = chunk_len(p, chunk0);
-  const double* in = (K == 0) ? p.b.patch : p.b.sweep[K > 0 ? K - 1 : 0];
-  double* out = p.b.sweep[K];
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-       e < (long long)len * NV * OUTSZ; e += (long long)gridDim.x * blockDim.x) {
+  const Ops* ops = bt.pps[0]->ops;
+  for (long long eg = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       eg < bt.pre[bt.n] * (NV * OUTSZ); eg += (long long)gridDim.x * blockDim.x) {
+    const long long t = eg / (NV * OUTSZ);
+    const LimItem it = lim_item(bt, t);
+    const Params& p = *bt.pps[it.s];
+    const double* in = (K == 0) ? p.b.patch : p.b.sweep[K > 0 ? K - 1 : 0];
+    double* out = p.b.sweep[K];
+    const long long e = eg - t * (NV * OUTSZ) + (long long)it.j * (NV * OUTSZ);
     const long long jv = e / OUTSZ;
     int r = (int)(e - jv * OUTSZ);
     const int node = r % NNIN;
@@ -169,7 +191,7 @@ __global__ void __launch_bounds__(256) k_lim_sweep(Params p, int chunk0) {
 #pragma unroll
     for (int q = 0; q < 5; ++q) u[q] = src[q * STRIDE];
     double res[3];
-    weno3(u, p.ops, res);
+    weno3(u, ops, res);
     const int ooff = x0 + O0 * (x1 + O1 * x2);
     double* dst = out + jv * (size_t)OUTSZ * 3 + (size_t)ooff * NNIN * 3 + node;
 #pragma unroll
@@ -217,7 +239,7 @@ __device__ __forceinline__ int cross_subcell(int r) {
 }
 
 template <int D, int N, bool MIXED>
-__global__ void __launch_bounds__(256) k_lim_predict(Params p, int chunk0) {
+__global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass) {
   using DM = Dims<D, N>;
   constexpr int NV = DM::NV, NST3 = DM::NST3, ND3 = DM::ND3, NED = DM::NED, Ns = DM::Ns;
   constexpr int NCROSS = DM::NSD + 2 * D * DM::NSF;
@@ -232,31 +254,36 @@ __global__ void __launch_bounds__(256) k_lim_predict(Params p, int chunk0) {
   __shared__ double D3[9], K3[9];
   __shared__ float D3f[9], K3f[9];
   if (threadIdx.x < 9) {
-    D3[threadIdx.x] = p.ops->D3[threadIdx.x];
-    K3[threadIdx.x] = p.ops->Kt3[threadIdx.x];
-    D3f[threadIdx.x] = (float)p.ops->D3[threadIdx.x];
-    K3f[threadIdx.x] = (float)p.ops->Kt3[threadIdx.x];
+    const Ops* o = bt.pps[0]->ops;
+    D3[threadIdx.x] = o->D3[threadIdx.x];
+    K3[threadIdx.x] = o->Kt3[threadIdx.x];
+    D3f[threadIdx.x] = (float)o->D3[threadIdx.x];
+    K3f[threadIdx.x] = (float)o->Kt3[threadIdx.x];
   }
-  const int len = chunk_len(p, chunk0);
   const int grp = threadIdx.x / NST3, lt = threadIdx.x - grp * NST3;
   const bool active_thread = grp < SPB;
-  const double dt = *p.b.dt;
-  double c[3];
-  float cf[3];
-#pragma unroll
-  for (int k = 0; k < D; ++k) {
-    c[k] = dt * Ns / p.geo.dx[k];
-    cf[k] = (float)c[k];
-  }
-  const double gm1 = p.gamma - 1.0;
-  const double* W = p.b.sweep[D - 1];          // [j][v][NED][ND3]
-  const long long total = (long long)len * NCROSS;
+  const long long total = bt.pre[bt.n] * NCROSS;
   for (long long base = (long long)blockIdx.x * SPB; base < total;
        base += (long long)gridDim.x * SPB) {
     const long long item = base + grp;
     const bool live = active_thread && item < total;
-    const long long j = live ? item / NCROSS : 0;
-    const int sc = live ? cross_subcell<D, Ns>((int)(item - j * NCROSS)) : 0;
+    const long long tg = live ? item / NCROSS : 0;
+    const LimItem it = lim_item(bt, tg);
+    const Params& p = *bt.pps[it.s];
+    const long long j = it.j;
+    const int sc = live ? cross_subcell<D, Ns>((int)(item - tg * NCROSS)) : 0;
+    double c[3];
+    float cf[3];
+    {
+      const double dt = *p.b.dt;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        c[k] = dt * Ns / p.geo.dx[k];
+        cf[k] = (float)c[k];
+      }
+    }
+    const double gm1 = p.gamma - 1.0;
+    const double* W = p.b.sweep[D - 1];          // [j][v][NED][ND3]
     __syncthreads();
     if (live) {
       for (int e = lt; e < NV * ND3; e += NST3) {
@@ -312,17 +339,20 @@ __global__ void __launch_bounds__(256) k_lim_predict(Params p, int chunk0) {
 // tangential x time GL points, averaged with the GL weights.  Faces f = 0..Ns
 // along k (between local subcells f-1 and f), tangential subcells 0..Ns-1.
 template <int D, int N, int k>
-__global__ void __launch_bounds__(256) k_lim_flux(Params p, int chunk0) {
+__global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
   using DM = Dims<D, N>;
   constexpr int NV = DM::NV, NST3 = DM::NST3, ND3 = DM::ND3, NE = DM::NE, NED = DM::NED,
                 Ns = DM::Ns;
   constexpr int NFK = (Ns + 1) * DM::NSF;
-  const int len = chunk_len(p, chunk0);
-  const Ops* o = p.ops;
+  const Ops* o = bt.pps[0]->ops;
   constexpr int stk = (k == 0) ? 1 : (k == 1 ? 3 : 9);   // node stride of axis k
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)len * NFK;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long j = e / NFK;
+  for (long long eg = blockIdx.x * (long long)blockDim.x + threadIdx.x; eg < bt.pre[bt.n] * NFK;
+       eg += (long long)gridDim.x * blockDim.x) {
+    const long long tg = eg / NFK;
+    const LimItem it = lim_item(bt, tg);
+    const Params& p = *bt.pps[it.s];
+    const long long j = it.j;
+    const long long e = j * NFK + (eg - tg * NFK);
     int r = (int)(e - j * NFK);
     int fc[3] = {0, 0, 0};
 #pragma unroll
@@ -387,7 +417,7 @@ __global__ void __launch_bounds__(256) k_lim_flux(Params p, int chunk0) {
 // min/max and wave speed, sub-face fluxes of the cell faces, and marking of
 // unlimited face neighbours for the flux correction.  One block per cell.
 template <int D, int N>
-__global__ void __launch_bounds__(128) k_lim_update(Params p, int chunk0) {
+__global__ void __launch_bounds__(128) k_lim_update(Batch bt, int pass) {
   using DM = Dims<D, N>;
   constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, Ns = DM::Ns, NSD = DM::NSD, L = DM::L,
                 LD = DM::LD, NSF = DM::NSF;
@@ -399,15 +429,19 @@ __global__ void __launch_bounds__(128) k_lim_update(Params p, int chunk0) {
   double* mm = R1 + n * Ns;       // 2 NV
   double* red = mm + 2 * NV;      // 128
   const int tid = threadIdx.x, nth = blockDim.x;
-  for (int i = tid; i < n * Ns; i += nth) R1[i] = p.ops->R1[i];
-  const int len = chunk_len(p, chunk0);
-  const int nxt = 1 - p.cur;
-  const double dt = *p.b.dt;
-  double c[3];
+  for (int i = tid; i < n * Ns; i += nth) R1[i] = bt.pps[0]->ops->R1[i];
+  for (long long tg = blockIdx.x; tg < bt.pre[bt.n]; tg += gridDim.x) {
+    const LimItem it = lim_item(bt, tg);
+    const Params& p = *bt.pps[it.s];
+    const int j = it.j;
+    const int nxt = 1 - p.cur;
+    double c[3];
+    {
+      const double dt = *p.b.dt;
 #pragma unroll
-  for (int k = 0; k < D; ++k) c[k] = dt * Ns / p.geo.dx[k];
-  for (int j = blockIdx.x; j < len; j += gridDim.x) {
-    const int t = chunk0 + j;
+      for (int k = 0; k < D; ++k) c[k] = dt * Ns / p.geo.dx[k];
+    }
+    const int t = pass * p.chunk + j;
     const long long cell = p.b.list[nxt][t];
     const double* pt = p.b.patch + (size_t)j * NV * LD;
     double* st = p.b.store[nxt] + (size_t)t * NV * NSD;
@@ -497,7 +531,7 @@ __global__ void __launch_bounds__(128) k_lim_update(Params p, int chunk0) {
 // fluxes integrated against the test functions,
 //   Fsub_b = (1/W_b) sum_e Fbar_e prod P1[e][b] / Ns^(d-1).
 template <int D, int N>
-__global__ void __launch_bounds__(128) k_lim_fix(Params p) {
+__global__ void __launch_bounds__(128) k_lim_fix(Batch bt) {
   using DM = Dims<D, N>;
   constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, NF = DM::NF, Ns = DM::Ns, NSD = DM::NSD,
                 NSF = DM::NSF;
@@ -511,13 +545,15 @@ __global__ void __launch_bounds__(128) k_lim_fix(Params p) {
   double* red = mm + 2 * NV;
   const int tid = threadIdx.x, nth = blockDim.x;
   for (int i = tid; i < n * Ns; i += nth) {
-    Mt[i] = p.ops->Mt[i];
-    P1[i] = p.ops->P1[i];
+    Mt[i] = bt.pps[0]->ops->Mt[i];
+    P1[i] = bt.pps[0]->ops->P1[i];
   }
-  const int nfix = p.b.counters[CNT_FIX];
-  const int nxt = 1 - p.cur;
-  const double dt = *p.b.dt;
-  for (int f = blockIdx.x; f < nfix; f += gridDim.x) {
+  for (long long fg = blockIdx.x; fg < bt.pre[bt.n]; fg += gridDim.x) {
+    const int sidx = batch_state(bt, fg);
+    const Params& p = *bt.pps[sidx];
+    const long long f = fg - bt.pre[sidx];
+    const int nxt = 1 - p.cur;
+    const double dt = *p.b.dt;
     const long long cell = p.b.fixlist[f];
     int ijk[3];
     cell_coords<D>(cell, p.geo, ijk);

@@ -43,76 +43,88 @@ struct Launch {
     if (ev) cudaEventRecord(ev[phase], s);
   }
 
-  static cudaError_t step_dg(const Params& p, cudaStream_t s, cudaEvent_t* ev) {
+  static cudaError_t step_dg(const StepLaunch& sl, cudaStream_t s) {
     cudaError_t e;
-    const int grid = cells_grid(p.geo.cells);
+    cudaEvent_t* ev = sl.ev;
+    if (sl.total_cells == 0) return cudaSuccess;
+    const int grid = cells_grid(sl.total_cells);
+    const Batch cells{sl.pps, sl.n, sl.pre_cells};
     mark(ev, PHASE_PREDICTOR, s);
-    if (p.prec == ADG_PREC_MIXED_FP32) {
+    if (sl.prec == ADG_PREC_MIXED_FP32) {
       const size_t sm = predictor_smem_bytes<D, N, true>();
       if ((e = set_smem(k_predictor<D, N, true>, sm)) != cudaSuccess) return e;
-      k_predictor<D, N, true><<<grid, pred_threads(), sm, s>>>(p);
+      k_predictor<D, N, true><<<grid, pred_threads(), sm, s>>>(cells);
     } else {
       const size_t sm = predictor_smem_bytes<D, N, false>();
       if ((e = set_smem(k_predictor<D, N, false>, sm)) != cudaSuccess) return e;
-      k_predictor<D, N, false><<<grid, pred_threads(), sm, s>>>(p);
+      k_predictor<D, N, false><<<grid, pred_threads(), sm, s>>>(cells);
     }
     mark(ev, PHASE_FACEFLUX, s);
     for (int k = 0; k < D; ++k) {
-      const long long work = face_count<D>(p.geo, k) * DM::NF;
-      k_faceflux<D, N><<<grid_for(work, 256), 256, 0, s>>>(p, k);
+      const Batch faces{sl.pps, sl.n, sl.pre_faces[k]};
+      k_faceflux<D, N><<<grid_for(sl.total_faces[k], 256), 256, 0, s>>>(faces, k);
     }
     mark(ev, PHASE_CORRECT, s);
     const size_t sc = correct_smem_bytes<D, N>();
     if ((e = set_smem(k_correct_detect<D, N>, sc)) != cudaSuccess) return e;
-    k_correct_detect<D, N><<<grid, 128, sc, s>>>(p);
+    k_correct_detect<D, N><<<grid, 128, sc, s>>>(cells);
     return cudaGetLastError();
   }
 
-  static cudaError_t step_limiter(const Params& p, cudaStream_t s, cudaEvent_t* ev) {
+  static cudaError_t step_limiter(const StepLaunch& sl, cudaStream_t s) {
     cudaError_t e;
+    cudaEvent_t* ev = sl.ev;
     mark(ev, PHASE_LIMITER, s);
-    const int nchunks = (p.cap + p.chunk - 1) / p.chunk;
     const size_t su = cell_smem();
     if ((e = set_smem(k_lim_update<D, N>, su)) != cudaSuccess) return e;
     constexpr int SPB = (D == 2) ? SUBS_PER_BLOCK_2D : SUBS_PER_BLOCK_3D;
-    for (int c = 0; c < nchunks; ++c) {
-      const int chunk0 = c * p.chunk;
-      const long long ch = p.chunk;
-      k_lim_patch<D, N><<<grid_for(ch * DM::LD, 256), 256, 0, s>>>(p, chunk0);
-      k_lim_sweep<D, N, 0><<<grid_for(ch * NV * DM::LD, 256), 256, 0, s>>>(p, chunk0);
-      k_lim_sweep<D, N, 1><<<grid_for(ch * NV * DM::LD, 256), 256, 0, s>>>(p, chunk0);
-      if (D == 3) k_lim_sweep<D, N, (D == 3 ? 2 : 1)><<<grid_for(ch * NV * DM::LD, 256), 256, 0, s>>>(p, chunk0);
+    const Batch lim{sl.pps, sl.n, sl.pre_lim};
+    const long long ch = sl.sum_chunk;    // upper bound of the troubled cells of one pass
+    for (int pass = 0; pass < sl.max_passes; ++pass) {
+      if ((e = launch_lim_prefix(sl, pass, s)) != cudaSuccess) return e;
+      k_lim_patch<D, N><<<grid_for(ch * DM::LD, 256), 256, 0, s>>>(lim, pass);
+      k_lim_sweep<D, N, 0><<<grid_for(ch * NV * DM::LD, 256), 256, 0, s>>>(lim, pass);
+      k_lim_sweep<D, N, 1><<<grid_for(ch * NV * DM::LD, 256), 256, 0, s>>>(lim, pass);
+      if (D == 3)
+        k_lim_sweep<D, N, (D == 3 ? 2 : 1)><<<grid_for(ch * NV * DM::LD, 256), 256, 0, s>>>(lim, pass);
       const long long ncross = ch * (DM::NSD + 2 * D * DM::NSF);
-      if (p.prec == ADG_PREC_MIXED_FP32)
+      if (sl.prec == ADG_PREC_MIXED_FP32)
         k_lim_predict<D, N, true><<<grid_for(ncross, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(
-            p, chunk0);
+            lim, pass);
       else
         k_lim_predict<D, N, false><<<grid_for(ncross, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(
-            p, chunk0);
-      k_lim_flux<D, N, 0><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(p, chunk0);
-      k_lim_flux<D, N, 1><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(p, chunk0);
+            lim, pass);
+      k_lim_flux<D, N, 0><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, pass);
+      k_lim_flux<D, N, 1><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, pass);
       if (D == 3)
-        k_lim_flux<D, N, (D == 3 ? 2 : 1)><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(p, chunk0);
-      k_lim_update<D, N><<<(int)(ch < kNumSM * 8 ? ch : kNumSM * 8), 128, su, s>>>(p, chunk0);
+        k_lim_flux<D, N, (D == 3 ? 2 : 1)><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(
+            lim, pass);
+      k_lim_update<D, N><<<(int)(ch < kNumSM * 8 ? ch : kNumSM * 8), 128, su, s>>>(lim, pass);
     }
     mark(ev, PHASE_FIX, s);
+    if ((e = launch_fix_prefix(sl, s)) != cudaSuccess) return e;
     const size_t sf = fix_smem();
     if ((e = set_smem(k_lim_fix<D, N>, sf)) != cudaSuccess) return e;
-    k_lim_fix<D, N><<<kNumSM * 8, 128, sf, s>>>(p);
+    const Batch fix{sl.pps, sl.n, sl.pre_fix};
+    k_lim_fix<D, N><<<kNumSM * 8, 128, sf, s>>>(fix);
     mark(ev, PHASE_END, s);
     return cudaGetLastError();
   }
 
   static cudaError_t run(const LaunchArgs& a) {
+    if (a.op == OP_STEP_DG || a.op == OP_STEP_LIMITER) {
+      if (a.op == OP_STEP_DG) return step_dg(*a.step, a.stream);
+      return step_limiter(*a.step, a.stream);
+    }
     const Params& p = *a.p;
     cudaStream_t s = a.stream;
     cudaError_t e;
     const int grid = cells_grid(p.geo.cells);
     switch (a.op) {
       case OP_STEP_DG:
-        return step_dg(p, s, a.ev);
+        return step_dg(*a.step, s);
       case OP_STEP_LIMITER:
-        return step_limiter(p, s, a.ev);
+        return step_limiter(*a.step, s);
       case OP_LOAD_DETECT: {
         const size_t sm = cell_smem();
         if ((e = set_smem(k_load_detect<D, N>, sm)) != cudaSuccess) return e;

@@ -17,8 +17,11 @@ namespace adg {
 namespace {
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;    // 32 MiB
-constexpr size_t CTRL_BYTES = 256;                           // counters + dt
-constexpr size_t OPS_BYTES = (sizeof(Ops) + 255) / 256 * 256;
+// control block: counters at 0, dt / clock at 64, the state pointer at 128,
+// the item prefix at 192; then the Params, the operator table and the buffers
+constexpr size_t CTRL_BYTES = 256;
+constexpr size_t PARAMS_BYTES = (sizeof(Params) + 255) / 256 * 256;
+constexpr size_t OPS_BYTES = (sizeof(Ops) + 255) / 256 * 256 + PARAMS_BYTES;
 constexpr int MAX_DEVICES = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
@@ -26,13 +29,21 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH
 std::mutex g_setup_mutex;
 unsigned char* g_device_base[MAX_DEVICES] = {};
 
-// Start-of-call control words: counters cleared, troubled count and dt set.
-__global__ void k_noalloc_begin(int* counters, double* dt, int count, double dtv) {
+// Start-of-call control words: counters cleared, troubled count and dt set,
+// a one-state batch descriptor whose items are the `count` patches.
+__global__ void k_noalloc_begin(int* counters, double* dt, Params** pps, long long* pre,
+                                Params* params, int count, double dtv) {
   if (threadIdx.x < CNT_COUNT) counters[threadIdx.x] = 0;
   __syncthreads();
   if (threadIdx.x == 0) {
     counters[CNT_TROUBLED1] = count;
     dt[0] = dtv;
+    dt[1] = 0.0;
+    dt[2] = 0.0;
+    dt[3] = 0.0;
+    pps[0] = params;
+    pre[0] = 0;
+    pre[1] = count;
   }
 }
 
@@ -113,23 +124,24 @@ struct NoAlloc {
     return (b + c + d + e + D * f) * sizeof(double);
   }
 
-  static cudaError_t run(Params p, int count, double dt, double* vnew, double* faces,
-                         cudaStream_t s) {
-    k_noalloc_begin<<<1, 32, 0, s>>>(p.b.counters, p.b.dt, count, dt);
+  static cudaError_t run(Params p, Params* pdev, Params** pps, long long* pre, int count,
+                         double dt, double* vnew, double* faces, cudaStream_t s) {
+    k_noalloc_begin<<<1, 32, 0, s>>>(p.b.counters, p.b.dt, pps, pre, pdev, count, dt);
     if (count == 0) return cudaGetLastError();
     constexpr int SPB = (D == 2) ? SUBS_PER_BLOCK_2D : SUBS_PER_BLOCK_3D;
     const long long ch = count;
-    k_lim_sweep<D, N, 0><<<grid_for(ch * DM::NV * DM::LD, 256), 256, 0, s>>>(p, 0);
-    k_lim_sweep<D, N, 1><<<grid_for(ch * DM::NV * DM::LD, 256), 256, 0, s>>>(p, 0);
+    const Batch lim{pps, 1, pre};
+    k_lim_sweep<D, N, 0><<<grid_for(ch * DM::NV * DM::LD, 256), 256, 0, s>>>(lim, 0);
+    k_lim_sweep<D, N, 1><<<grid_for(ch * DM::NV * DM::LD, 256), 256, 0, s>>>(lim, 0);
     if (D == 3)
-      k_lim_sweep<D, N, (D == 3 ? 2 : 1)><<<grid_for(ch * DM::NV * DM::LD, 256), 256, 0, s>>>(p, 0);
+      k_lim_sweep<D, N, (D == 3 ? 2 : 1)><<<grid_for(ch * DM::NV * DM::LD, 256), 256, 0, s>>>(lim, 0);
     const long long ncross = ch * (DM::NSD + 2 * D * DM::NSF);
-    k_lim_predict<D, N, false><<<grid_for(ncross, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(p, 0);
-    k_lim_flux<D, N, 0><<<grid_for(ch * (DM::Ns + 1) * DM::NSF, 256), 256, 0, s>>>(p, 0);
-    k_lim_flux<D, N, 1><<<grid_for(ch * (DM::Ns + 1) * DM::NSF, 256), 256, 0, s>>>(p, 0);
+    k_lim_predict<D, N, false><<<grid_for(ncross, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(lim, 0);
+    k_lim_flux<D, N, 0><<<grid_for(ch * (DM::Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, 0);
+    k_lim_flux<D, N, 1><<<grid_for(ch * (DM::Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, 0);
     if (D == 3)
       k_lim_flux<D, N, (D == 3 ? 2 : 1)><<<grid_for(ch * (DM::Ns + 1) * DM::NSF, 256), 256, 0, s>>>(
-          p, 0);
+          lim, 0);
     k_noalloc_write<D, N><<<grid_for(ch * DM::NV * DM::NSD, 256), 256, 0, s>>>(p, count, vnew, faces);
     return cudaGetLastError();
   }
@@ -170,7 +182,8 @@ int run_noalloc(unsigned char* base, double gamma, const double* h, double dt, c
   }
   Ops ops_host;
   build_ops(N, &ops_host);
-  Ops* ops_dev = reinterpret_cast<Ops*>(base + CTRL_BYTES);
+  Params* params_dev = reinterpret_cast<Params*>(base + CTRL_BYTES);
+  Ops* ops_dev = reinterpret_cast<Ops*>(base + CTRL_BYTES + PARAMS_BYTES);
   cudaError_t e = cudaMemcpyAsync(ops_dev, &ops_host, sizeof(Ops), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // ops_host lives on this stack frame
   if (e != cudaSuccess) {
@@ -197,9 +210,15 @@ int run_noalloc(unsigned char* base, double gamma, const double* h, double dt, c
   p.cur = 0;
   p.b.counters = reinterpret_cast<int*>(base);
   p.b.dt = reinterpret_cast<double*>(base + 64);
+  p.b.lamred = p.b.dt + 1;
+  p.b.clock = p.b.dt + 2;
   p.b.patch = const_cast<double*>(patches);
   NA::carve(base, count, p);
-  e = NA::run(p, count, dt, vnew, faces, s);
+  e = cudaMemcpyAsync(params_dev, &p, sizeof(Params), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // p lives on this stack frame
+  if (e == cudaSuccess)
+    e = NA::run(p, params_dev, reinterpret_cast<Params**>(base + 128),
+                reinterpret_cast<long long*>(base + 192), count, dt, vnew, faces, s);
   if (e != cudaSuccess) {
     if (err && errlen) snprintf(err, errlen, "kernel launch failed: %s", cudaGetErrorString(e));
     return ADG_ERR_CUDA;
