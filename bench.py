@@ -29,20 +29,36 @@ sys.path.insert(0, ROOT)
 
 N_ORDER = 5
 GRID = 512
+WORKLOAD = "quadvortex512"
 METRIC = "space-time DOF updates/s"
 UNIT = "ST-DOF/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 
 
 def workload(n=None, N=N_ORDER):
+    """The benchmark workload (default: 2D quadrants + vortex, N=5, 512^2)."""
     from paper_1406_7416_gb300 import inputs
+    if WORKLOAD == "explosion2d":
+        return inputs.explosion_2d(n=n or 32, N=3)
+    if WORKLOAD == "explosion3d":
+        return inputs.explosion_3d(n=n or 128, N=3)
+    if WORKLOAD == "quadrants200":
+        return inputs.quadrants_2d(n=n or 200, N=9)
     return inputs.quadrants_vortex_2d(n=n or GRID, N=N, steps=None)
 
 
 def config_dict(w, extra=None):
-    c = {"workload": w["name"], "grid": f"{w['ncell'][0]}x{w['ncell'][1]}", "N": w["N"],
-         "cells": int(w["ncell"][0] * w["ncell"][1]), "dim": w["dim"],
-         "l2": "inputs larger than L2: DOF state 302 MB and face traces 1.2 GB per step"}
+    import numpy as np
+    cells = int(np.prod(w["ncell"]))
+    nv, nd = w["dim"] + 2, (w["N"] + 1) ** w["dim"]
+    state = cells * nv * nd * 8
+    traces = cells * w["dim"] * 2 * nv * (w["N"] + 1) ** w["dim"] * 8
+    big = state + traces > 129e6
+    c = {"workload": w["name"], "grid": "x".join(str(x) for x in w["ncell"]), "N": w["N"],
+         "cells": cells, "dim": w["dim"],
+         "l2": (f"inputs larger than L2: DOF state {state / 1e6:.0f} MB and face traces "
+                f"{traces / 1e6:.0f} MB per step") if big else
+               f"inputs smaller than L2 (state {state / 1e6:.1f} MB): steps run L2-warm"}
     if extra:
         c.update(extra)
     return c
@@ -126,47 +142,62 @@ def traffic_record():
 # CPU oracle timing (test infrastructure, timed as a baseline only)
 # ---------------------------------------------------------------------------
 def oracle_sample(block=32):
-    """The central block x block cells of the workload (quadrant corner and
-    vortex core), transmissive at the block edges, projected by the oracle."""
+    """The central block^d cells of the workload (quadrant corner and vortex
+    core, or the centre of the explosion), transmissive at the block edges,
+    projected by the oracle."""
     from oracle.dg import Grid
     from oracle.ic import initial_state, project_problem
     from oracle.step import Scheme
     w = workload()
-    i0 = GRID // 2 - block // 2
-    x0 = tuple(w["x0"][k] + i0 * w["dx"][k] for k in range(2))
-    g = Grid((block, block), x0, w["dx"], (1, 1, 1, 1))
+    d = w["dim"]
+    block = min(block, w["ncell"][0])
+    i0 = [w["ncell"][k] // 2 - block // 2 for k in range(d)]
+    x0 = tuple(w["x0"][k] + i0[k] * w["dx"][k] for k in range(d))
+    g = Grid((block,) * d, x0, w["dx"], (1,) * (2 * d))
+    if w["problem"].get("cell_rho_factor") is not None:
+        w["problem"]["cell_rho_factor"] = w["problem"]["cell_rho_factor"][
+            tuple(slice(i0[k], i0[k] + block) for k in range(d))]
     sch = Scheme(g, w["N"], w["gamma"])
     U0, V0 = project_problem(sch, w["problem"])
     return w, sch, initial_state(sch, U0, V0)
 
 
-def oracle_rate(steps, warmup, block=32):
+def oracle_rate(steps, warmup, block=32, budget_s=20.0):
+    """Oracle ST-DOF/s on the central sample: up to `steps` timed steps, fewer
+    when they would exceed budget_s seconds (at least one)."""
+    import numpy as np
     from oracle.step import stable_dt, step
     w, sch, st = oracle_sample(block)
     dt = stable_dt(sch, st, w["cfl"])
     for _ in range(warmup):
         st, _ = step(sch, st, dt)
     t0 = time.perf_counter()
-    for _ in range(steps):
+    done = 0
+    while done < steps:
         st, _ = step(sch, st, dt)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    steps = done
     el = time.perf_counter() - t0
-    dofs = block * block * (w["N"] + 1) ** 3
-    return dofs * steps / el, el
+    d = w["dim"]
+    dofs = int(np.prod(sch.grid.ncell)) * (w["N"] + 1) ** (d + 1)
+    return dofs * steps / el, el, steps
 
 
 def run_cpu_baseline(steps, warmup, block):
     """Times the oracle in a child process pinned to one BLAS thread."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-rate",
-                        str(steps), str(warmup), str(block)], env=env, capture_output=True,
-                       text=True, timeout=1800)
+                        str(steps), str(warmup), str(block), WORKLOAD], env=env,
+                       capture_output=True, text=True, timeout=1800)
     if r.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                 "sample": f"failed: {r.stderr.strip()[-300:]}"}
-    rate, el = json.loads(r.stdout.strip().splitlines()[-1])
+    rate, el, steps = json.loads(r.stdout.strip().splitlines()[-1])
     return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{steps} oracle steps (after {warmup} warm-up) on the central "
-                      f"{block}x{block} cells of the same workload, transmissive block edges, "
+                      f"{block}^d cells of the same workload, transmissive block edges, "
                       f"{el:.1f} s, one BLAS thread"}
 
 
@@ -194,7 +225,7 @@ def run_gpu(args):
     w = workload()
     D, N = w["dim"], w["N"]
     n = N + 1
-    cells = w["ncell"][0] * w["ncell"][1]
+    cells = int(np.prod(w["ncell"]))
     stdofs = cells * n ** (D + 1)
     stream = torch.cuda.Stream()
 
@@ -216,17 +247,15 @@ def run_gpu(args):
         return float(t.item())
 
     results = {}
-    fixed_dt = None
+    cfl = w["cfl"]
     precs = [("fp64", adg.PREC_FP64), ("mixed", adg.PREC_MIXED_FP32)]
     if args.only != "both":
         precs = [p for p in precs if p[0] == args.only]
     for name, prec in precs:
         s = make(prec)
-        if fixed_dt is None:
-            fixed_dt = s.max_dt(w["cfl"])          # same dt sequence for both precisions
         s.set_option(adg.OPT_PROFILE, 1)
         for _ in range(args.warmup):
-            s.step(fixed_dt)
+            s.step_cfl(cfl)
         s.phase_times()                             # discard warm-up phases
         torch.cuda.synchronize()
         barrier()
@@ -235,7 +264,7 @@ def run_gpu(args):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            s.step(fixed_dt)
+            s.step_cfl(cfl)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -259,16 +288,38 @@ def run_gpu(args):
         return
     # L1 distance of the density, mixed vs FP64, after warmup + steps equal steps
     W = 0.5 * np.polynomial.legendre.leggauss(n)[1]
-    Wd = np.outer(W, W).ravel()
+    Wd = W
+    for _ in range(D - 1):
+        Wd = np.outer(W, Wd).ravel()
     rho64 = results["fp64"]["solver"].read()[:, 0, :]
     rhomx = results["mixed"]["solver"].read()[:, 0, :]
-    area = w["dx"][0] * w["dx"][1]
+    area = float(np.prod(w["dx"]))
     l1 = float(np.sum(np.abs(rhomx - rho64) @ Wd) * area)
     l1ref = float(np.sum(np.abs(rho64) @ Wd) * area)
 
     # end-to-end through the C ABI with host buffers (rank-local)
     e2e = None
     s = results["mixed"]["solver"]
+    if args.no_e2e:
+        s = None
+    if s is not None:
+        e2e = end_to_end(s, args, stdofs, world, cfl, barrier, max_over_ranks)
+    if rank == 0:
+        emit_line(args, w, results, stdofs, world, cells, cfl, l1, l1ref, e2e, D, N, n)
+    for r in results.values():
+        r["solver"].close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def end_to_end(s, args, stdofs, world, cfl, barrier, max_over_ranks):
+    """The metric through the C ABI with host buffers: adg_load_full from pinned
+    host memory, then per step adg_step_cfl + adg_flags to pinned host memory,
+    then adg_read of the DOFs."""
+    import numpy as np
+    import torch
+    from paper_1406_7416_gb300 import adg
     dofs, beta, sub = s.read_full()
     pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
     hd, hb, hs = pin(dofs), pin(beta), pin(sub)
@@ -279,63 +330,98 @@ def run_gpu(args):
     t0 = time.perf_counter()
     s.load_full(hd, hb, hs)
     for _ in range(args.steps):
-        s.step(fixed_dt)
+        s.step_cfl(cfl)
         s.lib.adg_flags(s.h, adg._u8ptr(flags))
     s.read(out)
     el = max_over_ranks(time.perf_counter() - t0)
     h2d = (hd.nbytes + hb.nbytes + hs.nbytes) / args.steps + 8
     d2h = flags.nbytes + out.nbytes / args.steps
-    e2e = {"value": stdofs * args.steps * world / el, "unit": UNIT,
-           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-           "timed": "adg_load_full from pinned host, then per step adg_step(dt) + adg_flags to "
-                    "pinned host, then adg_read of the DOFs"}
+    return {"value": stdofs * args.steps * world / el, "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "timed": "adg_load_full from pinned host, then per step adg_step_cfl + adg_flags to "
+                     "pinned host, then adg_read of the DOFs"}
 
-    if rank == 0:
-        mx, f64 = results["mixed"], results["fp64"]
-        value = stdofs * world / (mx["ms"] / 1e3)
-        iters = N + 1
-        fl64, fl32 = predictor_flops(D, N, iters, True)
-        pred_ms = mx["phases"]["predictor"]
-        achieved = fl64 * cells / (pred_ms / 1e3) / 1e12
-        fl64f, _ = predictor_flops(D, N, iters, False)
-        achieved_f64 = fl64f * cells / (f64["phases"]["predictor"] / 1e3) / 1e12
-        traffic = traffic_record()
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mx["ms"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64", "data": "synthetic",
-            "config": config_dict(w, {"precision": "mixed: FP32 Picard sweeps + final FP64 sweep, "
-                                                   "FP64 corrector/detector/limiter",
-                                      "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                                      "dt": fixed_dt}),
-            "fp64": {"value": stdofs * world / (f64["ms"] / 1e3), "ms_per_step": f64["ms"],
-                     "dtype": "f64", "phases_ms": f64["phases"],
-                     "roofline": {"bound": "alu", "achieved": achieved_f64,
-                                  "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                  "frac": achieved_f64 / FP64_PEAK_TFLOPS}},
-            "mixed_vs_fp64": {"l1_density": l1, "l1_density_rel": l1 / l1ref,
-                              "steps": args.warmup + args.steps},
-            "phases_ms": mx["phases"],
-            "troubled_cells": mx["troubled"], "status": mx["status"],
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "kernel": "k_predictor (FP64 pipe: final sweep + corrector terms)",
-                         "fp32_flops_per_launch": fl32 * cells,
-                         "fp64_flops_per_launch": fl64 * cells,
-                         "traffic": traffic["bytes_per_launch"] if traffic else None},
-            "e2e": e2e,
-            "gpu_launches": int(mx["info"]["launches_per_step"]) * args.steps,
-            "clocks": mx["clocks"],
-        }
-        if not args.no_cpu_baseline:
-            line["cpu_baseline"] = run_cpu_baseline(args.cpu_steps, 1, 32)
-        print(json.dumps(line), flush=True)
-    for r in results.values():
-        r["solver"].close()
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+
+def emit_line(args, w, results, stdofs, world, cells, cfl, l1, l1ref, e2e, D, N, n):
+    mx, f64 = results["mixed"], results["fp64"]
+    value = stdofs * world / (mx["ms"] / 1e3)
+    iters = N + 1
+    fl64, fl32 = predictor_flops(D, N, iters, True)
+    pred_ms = mx["phases"]["predictor"]
+    achieved = fl64 * cells / (pred_ms / 1e3) / 1e12
+    fl64f, _ = predictor_flops(D, N, iters, False)
+    achieved_f64 = fl64f * cells / (f64["phases"]["predictor"] / 1e3) / 1e12
+    traffic = traffic_record() if (WORKLOAD == "quadvortex512" and GRID == 512) else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mx["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": config_dict(w, {"precision": "mixed: FP32 Picard sweeps + final FP64 sweep, "
+                                               "FP64 corrector/detector/limiter",
+                                  "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                                  "time_step": f"CFL {cfl:.6g} of Eq. (cfl), dt from the "
+                                               "current subcell data every step"}),
+        "fp64": {"value": stdofs * world / (f64["ms"] / 1e3), "ms_per_step": f64["ms"],
+                 "dtype": "f64", "phases_ms": f64["phases"],
+                 "roofline": {"bound": "alu", "achieved": achieved_f64,
+                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": achieved_f64 / FP64_PEAK_TFLOPS}},
+        "mixed_vs_fp64": {"l1_density": l1, "l1_density_rel": l1 / l1ref,
+                          "steps": args.warmup + args.steps},
+        "phases_ms": mx["phases"],
+        "troubled_cells": mx["troubled"], "status": mx["status"],
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                     "kernel": "k_predictor (FP64 pipe: final sweep + corrector terms)",
+                     "fp32_flops_per_launch": fl32 * cells,
+                     "fp64_flops_per_launch": fl64 * cells,
+                     "traffic": traffic["bytes_per_launch"] if traffic else None},
+        "e2e": e2e,
+        "gpu_launches": int(mx["info"]["launches_per_step"]) * args.steps,
+        "clocks": mx["clocks"],
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = run_cpu_baseline(args.cpu_steps, 1, 32 if D == 2 else 6)
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """Serving: independent 2D runs (grids from {32,64,128,256}^2, N in {3,5},
+    the 2D Riemann problems of Sec. 5.6 with seeded jitter, each to
+    min(--t-end, its final time)) with Poisson arrivals, admitted by an HBM budget and
+    stepped together in batched CUDA-graph launches; p50/p99 latency and the
+    aggregate space-time DOF rate.  First a closed-loop pass (all runs at t=0)
+    measures capacity, then an open-loop pass at 80% of it."""
+    import torch
+    from paper_1406_7416_gb300 import adg, build_lib, inputs
+    from paper_1406_7416_gb300.serving import RunSpec, Server, poisson_arrivals
+    build_lib.build()
+    adg.load_library()
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.5 * free)
+    specs = inputs.serving_runs(count=args.runs)
+    for w in specs:
+        w["t_end"] = min(w["t_end"], args.t_end)
+    runs = [RunSpec(w, w["t_end"], 0.0, i) for i, w in enumerate(specs)]
+    closed = Server(budget, adg.PREC_MIXED_FP32).serve(runs, max_wall=args.max_wall)
+    print(json.dumps({"closed_loop": closed}), file=sys.stderr, flush=True)
+    capacity = closed["runs"] / closed["wall_s"]
+    rate = 0.8 * capacity
+    arrivals = poisson_arrivals(len(specs), rate, seed=1406 + 4)
+    runs = [RunSpec(w, w["t_end"], a, i) for i, (w, a) in enumerate(zip(specs, arrivals))]
+    opened = Server(budget, adg.PREC_MIXED_FP32).serve(runs, max_wall=args.max_wall)
+    line = {"metric": METRIC, "value": opened["stdof_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": opened["steps"], "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"serving: {len(specs)} independent 2D Riemann-problem runs "
+                                   f"(Sec. 5.6 RP1-RP5, 2% jitter), grids from "
+                                   f"{{32,64,128,256}}^2, N in {{3,5}}, t_end={args.t_end}, "
+                                   "Poisson arrivals at 80% of the measured capacity",
+                       "hbm_budget_bytes": budget, "mixed precision": True},
+            "latency_p50_s": opened["latency_p50_s"], "latency_p99_s": opened["latency_p99_s"],
+            "closed_loop": closed, "open_loop": opened, "arrival_rate_per_s": rate}
+    print(json.dumps(line), flush=True)
 
 
 def run_reference(args):
@@ -345,7 +431,7 @@ def run_reference(args):
         return
     w = workload()
     block = 32
-    rate, el = oracle_rate(args.steps, args.warmup, block)
+    rate, el, _ = oracle_rate(args.steps, args.warmup, block, budget_s=120.0)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -361,7 +447,9 @@ def run_reference(args):
 def main():
     if len(sys.argv) >= 2 and sys.argv[1] == "--oracle-rate":
         steps, warmup, block = (int(x) for x in sys.argv[2:5])
-        print(json.dumps(oracle_rate(steps, warmup, block)))
+        if len(sys.argv) > 5:
+            globals()["WORKLOAD"] = sys.argv[5]
+        print(json.dumps(list(oracle_rate(steps, warmup, block))))
         return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -370,14 +458,25 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-steps", type=int, default=15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer timing")
     ap.add_argument("--grid", type=int, default=GRID, help="cells per axis (profiling runs)")
     ap.add_argument("--only", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--workload", default="quadvortex512",
+                    choices=["quadvortex512", "explosion2d", "explosion3d", "quadrants200", "serving"])
+    ap.add_argument("--runs", type=int, default=32, help="serving: number of runs")
+    ap.add_argument("--t-end", type=float, default=0.02,
+                    help="serving: end time cap of every run (each stops at min(cap, its final time))")
+    ap.add_argument("--max-wall", type=float, default=120.0,
+                    help="serving: no admissions after this many seconds per pass")
     args = ap.parse_args()
     globals()["GRID"] = args.grid
+    globals()["WORKLOAD"] = args.workload
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_gpu(args)
 

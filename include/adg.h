@@ -69,6 +69,11 @@ extern "C" {
                                      (default 1; the others run in FP32)              */
 #define ADG_OPT_END_TIME 8        /* end time of the run: steps are cut to reach it and
                                      the state idles afterwards (0: none, default)    */
+#define ADG_OPT_CFL 9             /* the state's CFL number for batched CFL steps
+                                     called with cfl <= 0 (includes 1/(d(2N+1)))      */
+#define ADG_OPT_SCRATCH_BYTES 10  /* limiter scratch budget in bytes (before the first
+                                     load; default 2 GiB, used up to a quarter of the
+                                     cells per limiter pass)                          */
 
 /* Cartesian grid (Sec. 2.1): cells n[k] of size dx[k] from corner x0[k]. */
 typedef struct {
@@ -149,9 +154,9 @@ int adg_step(adg_state* st, double dt);
  * the device from the current state (Eq. cfl); nothing returns to the host. */
 int adg_step_cfl(adg_state* st, double cfl, double dt_max);
 
-/* Simulated time t of the state (0 after a load, advanced by every step);
- * synchronizes. */
-int adg_time(adg_state* st, double* t);
+/* Simulated time t of the state and the number of steps it has taken since
+ * the last load (either may be NULL); synchronizes. */
+int adg_time(adg_state* st, double* t, int64_t* steps);
 
 /* Batched stepping of many independent states (spec batching; no
  * counterpart in the paper, which steps one grid): states of the same
@@ -161,8 +166,9 @@ int adg_time(adg_state* st, double* t);
  * the batch creates when NULL).  A state may belong to one live batch at a
  * time and must not be stepped on its own while it does.
  *   adg_batch_step with dts (host [count]) takes those steps; with dts = NULL
- *   every state takes the CFL step of Eq. (cfl) (cfl > 0), cut at its end
- *   time (ADG_OPT_END_TIME); states past their end time idle.  From the
+ *   every state takes the CFL step of Eq. (cfl) with the number `cfl`, or
+ *   with its own ADG_OPT_CFL when cfl <= 0, cut at its end time
+ *   (ADG_OPT_END_TIME); states past their end time idle.  From the
  *   second CFL step on, the whole batched step replays as one CUDA graph.
  * Asynchronous; errors of device-side conditions surface in adg_status of
  * the states. */

@@ -26,6 +26,8 @@ OPT_DMP_EPS, OPT_DMP_FLOOR, OPT_FORCE_LIMITER, OPT_PICARD_ITERS, OPT_SLOT_CAPACI
 OPT_PROFILE = 6
 OPT_FP64_SWEEPS = 7
 OPT_END_TIME = 8
+OPT_CFL = 9
+OPT_SCRATCH_BYTES = 10
 PHASES = ("predictor", "faceflux", "correct_detect", "limiter", "fix")
 IC_RADIAL, IC_QUADRANT = 0, 1
 
@@ -97,7 +99,7 @@ def load_library(path=None):
                                                vp, vp, vp, ctypes.c_char_p, ctypes.c_size_t]
     lib.adg_destroy.argtypes = [vp]
     lib.adg_destroy.restype = None
-    lib.adg_time.argtypes = [vp, dp]
+    lib.adg_time.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_int64)]
     lib.adg_batch_create.argtypes = [ctypes.POINTER(vp), ip, vp, ctypes.POINTER(vp)]
     lib.adg_batch_step.argtypes = [vp, dp, ctypes.c_double]
     lib.adg_batch_destroy.argtypes = [vp]
@@ -302,9 +304,13 @@ class Solver:
         return dict(capacity=out[0], chunk=out[1], launches_per_step=out[2], bytes=out[3])
 
     def time(self):
-        t = ctypes.c_double()
-        self._check(self.lib.adg_time(self.h, ctypes.byref(t)), "adg_time")
-        return t.value
+        """(simulated time, steps taken since the last load)."""
+        t, n = ctypes.c_double(), ctypes.c_int64()
+        self._check(self.lib.adg_time(self.h, ctypes.byref(t), ctypes.byref(n)), "adg_time")
+        return t.value, n.value
+
+    def bytes_held(self):
+        return self.info()["bytes"]
 
     def max_dt(self, cfl):
         dt = ctypes.c_double()

@@ -43,6 +43,8 @@ struct adg_state {
   bool params_dirty = true;         // host fields changed since the last upload
   bool cur_known = true;            // host cur / stamp equal the device's
   double t_end = 0.0;               // end time of the simulated interval (0: none)
+  double cfl = 0.0;                 // CFL number of batched CFL steps with cfl <= 0
+  size_t scratch_budget = (size_t)2 << 30;   // bytes of limiter scratch
   Params hparams;                   // source of the last upload
   cudaEvent_t ev[PHASE_COUNT] = {};
   double phase_ms[PHASE_COUNT] = {};
@@ -127,6 +129,8 @@ Params make_params(const adg_state* st) {
   p.stamp = st->stamp;
   p.lam_mode = st->lam_mode ? 1 : 0;
   p.fp64_sweeps = st->fp64_sweeps < st->iters ? st->fp64_sweeps : st->iters;
+  p.cfl = st->cfl;
+  p.status_pad = 0;
   return p;
 }
 
@@ -169,7 +173,10 @@ int ensure_allocated(adg_state* st) {
   }
   long long cap = st->cap_req;
   if (cap <= 0) {
-    cap = cells / 8;
+    // a slot for every cell when the two subcell stores fit in 8 GiB,
+    // otherwise for a quarter of the cells
+    const double store_bytes = 2.0 * (double)cells * nv * nsd * sizeof(double);
+    cap = store_bytes <= 8.0 * (1 << 30) ? cells : cells / 4;
     if (cap < 4096) cap = 4096;
   }
   if (cap > cells) cap = cells;
@@ -177,8 +184,12 @@ int ensure_allocated(adg_state* st) {
   size_t parts[6];
   const size_t per = limiter_scratch_doubles(st->dim, st->N, &parts[0], &parts[1], &parts[2],
                                              &parts[3], &parts[4], &parts[5]);
-  const size_t budget = (size_t)2 << 30;   // bytes of limiter scratch
-  long long chunk = (long long)(budget / (per * sizeof(double)));
+  // limiter scratch: room for a quarter of the cells (at least 256) per pass,
+  // within the state's scratch budget (default 2 GiB)
+  long long chunk = (long long)(st->scratch_budget / (per * sizeof(double)));
+  long long want = cells / 4;
+  if (want < 256) want = 256;
+  if (chunk > want) chunk = want;
   if (chunk < 1) chunk = 1;
   if (chunk > cap) chunk = cap;
   st->chunk = (int)chunk;
@@ -204,7 +215,7 @@ int ensure_allocated(adg_state* st) {
   ALLOC(b.fixlist, int, cells);
   ALLOC(b.fixstamp, int, cells);
   ALLOC(b.edge, double, cap * st->dim * 2 * nv * nsf);
-  ALLOC(b.dt, double, 4);
+  ALLOC(b.dt, double, 5);
   b.lamred = b.dt + 1;
   b.clock = b.dt + 2;
   ALLOC(st->dparams, Params, 1);
@@ -222,7 +233,7 @@ int ensure_allocated(adg_state* st) {
                                st->stream));
   CUDA_TRY(st, cudaMemsetAsync(b.counters, 0, sizeof(int) * CNT_COUNT, st->stream));
   CUDA_TRY(st, cudaMemsetAsync(b.fixstamp, 0xff, sizeof(int) * cells, st->stream));
-  CUDA_TRY(st, cudaMemsetAsync(b.dt, 0, sizeof(double) * 4, st->stream));
+  CUDA_TRY(st, cudaMemsetAsync(b.dt, 0, sizeof(double) * 5, st->stream));
   {
     long long pre[12] = {0, cells, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int k = 0; k < st->dim; ++k) {
@@ -278,7 +289,7 @@ int begin_load(adg_state* st) {
   st->cur = 0;
   st->params_dirty = true;
   CUDA_TRY(st, cudaMemsetAsync(st->b.counters, 0, sizeof(int) * CNT_COUNT, st->stream));
-  const double clk[2] = {0.0, st->t_end};
+  const double clk[3] = {0.0, st->t_end, 0.0};
   CUDA_TRY(st, cudaMemcpyAsync(st->b.clock, clk, sizeof(clk), cudaMemcpyHostToDevice, st->stream));
   CUDA_TRY(st, cudaStreamSynchronize(st->stream));
   return ADG_OK;
@@ -605,7 +616,9 @@ int adg_batch_step(adg_batch* b, const double* dts, double cfl) {
     int rc = batch_run(b, true, 0.0);
     if (rc) return rc;
   } else {
-    if (!(cfl > 0.0)) return fail(st0, ADG_ERR_ARG, "cfl must be positive");
+    for (adg_state* st : b->states)
+      if (!(cfl > 0.0) && !(st->cfl > 0.0))
+        return fail(st0, ADG_ERR_ARG, "cfl must be positive (argument or ADG_OPT_CFL)");
     for (adg_state* st : b->states) {
       int rc = ensure_lambda(st);
       if (!rc && st->params_dirty) rc = upload_params(st);
@@ -658,14 +671,17 @@ int adg_step_batch(adg_state* const* states, const double* dts, int count) {
   return rc;
 }
 
-int adg_time(adg_state* st, double* t) {
-  if (!st || !t) return ADG_ERR_ARG;
-  if (!st->allocated) {
-    *t = 0.0;
-    return ADG_OK;
+int adg_time(adg_state* st, double* t, int64_t* steps) {
+  if (!st) return ADG_ERR_ARG;
+  double clk[3] = {0.0, 0.0, 0.0};
+  if (st->allocated) {
+    CUDA_TRY(st, cudaMemcpyAsync(clk, st->b.clock, sizeof(clk), cudaMemcpyDeviceToHost, st->stream));
+    int rc = sync(st);
+    if (rc) return rc;
   }
-  CUDA_TRY(st, cudaMemcpyAsync(t, st->b.clock, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
-  return sync(st);
+  if (t) *t = clk[0];
+  if (steps) *steps = (int64_t)clk[2];
+  return ADG_OK;
 }
 
 
@@ -758,6 +774,15 @@ int adg_set_option(adg_state* st, int key, double value) {
         CUDA_TRY(st, cudaMemcpyAsync(st->b.clock + 1, &st->t_end, sizeof(double),
                                      cudaMemcpyHostToDevice, st->stream));
       if (st->allocated) CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+      return ADG_OK;
+    case ADG_OPT_SCRATCH_BYTES:
+      if (st->allocated) return fail(st, ADG_ERR_ARG, "scratch budget must be set before the first load");
+      if (!(value >= 1.0)) return fail(st, ADG_ERR_ARG, "scratch budget must be positive");
+      st->scratch_budget = (size_t)value;
+      return ADG_OK;
+    case ADG_OPT_CFL:
+      if (!(value >= 0.0)) return fail(st, ADG_ERR_ARG, "cfl must be >= 0");
+      st->cfl = value;
       return ADG_OK;
     case ADG_OPT_PROFILE:
       if (value != 0.0 && !st->ev[0])

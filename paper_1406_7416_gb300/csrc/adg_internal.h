@@ -70,7 +70,7 @@ struct Bufs {
   double* edge;          // [cap][d][2][nv][Ns^(d-1)] sub-face fluxes on the cell faces
   double* dt;            // [1] time step of the current step (0: state idle this step)
   double* lamred;        // [1] reduced lambda
-  double* clock;         // [2] simulated time t and end time t_end (0: none)
+  double* clock;         // [3] simulated time t, end time t_end (0: none), steps taken
   // limiter scratch, sized for one chunk of `chunk` troubled cells
   double* patch;         // [chunk][nv][L^d]
   double* sweep[3];      // [chunk][nv][...] after the x, y, z reconstructions
@@ -99,6 +99,7 @@ struct Params {
   int lam_mode;          // 1: kernels keep the per-cell wave speeds current
   int fp64_sweeps;       // mixed precision: number of final FP64 Picard sweeps
   int status_pad;
+  double cfl;            // the state's CFL number for batched CFL steps (0: none)
 };
 
 // A batch of states of one (dimension, degree, precision) stepped by the same

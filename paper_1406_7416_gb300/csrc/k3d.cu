@@ -41,7 +41,7 @@ __global__ void k_step_begin(StepLaunch sl) {
     l = block_reduce_max(l, red);
     double h = p.geo.dx[0];
     for (int k = 1; k < p.dim; ++k) h = fmin(h, p.geo.dx[k]);
-    dt = sl.cfl * h / l;
+    dt = (sl.cfl > 0.0 ? sl.cfl : p.cfl) * h / l;
     if (!(dt > 0.0) || isinf(dt) || l != l) {
       if (threadIdx.x == 0) atomicOr(&p.b.counters[CNT_STATUS], 2);
       dt = 0.0;
@@ -61,6 +61,7 @@ __global__ void k_step_begin(StepLaunch sl) {
       p.b.counters[CNT_FIX] = 0;
       p.stamp += 1;
       p.b.clock[0] = t + dt;
+      p.b.clock[2] += 1.0;
     }
   }
 }

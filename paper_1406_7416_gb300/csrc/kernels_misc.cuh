@@ -293,6 +293,35 @@ __global__ void __launch_bounds__(128) k_project(Params p, adg_problem pr,
     cell_coords<D>(cell, p.geo, ijk);
     const double f = fac ? fac[cell] : 1.0;
     __syncthreads();
+    if (pr.kind == ADG_IC_RADIAL) {
+      // a cell wholly inside or outside the sphere holds one constant state,
+      // whose projection and subcell averages are that state (what the
+      // composite rule gives up to rounding); only cut cells need the rule
+      double rmin2 = 0.0, rmax2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double lo = p.geo.x0[k] + ijk[k] * p.geo.dx[k] - pr.center[k];
+        const double hi = lo + p.geo.dx[k];
+        const double near = (lo > 0.0) ? lo : (hi < 0.0 ? -hi : 0.0);
+        const double far = fmax(fabs(lo), fabs(hi));
+        rmin2 += near * near;
+        rmax2 += far * far;
+      }
+      const double R2 = pr.radius * pr.radius;
+      if (rmax2 < R2 * (1.0 - 1e-12) || rmin2 > R2 * (1.0 + 1e-12)) {
+        double x[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          x[k] = (k < D) ? p.geo.x0[k] + (ijk[k] + 0.5) * p.geo.dx[k] : 0.0;
+        double Q[NV];
+        problem_state<D>(pr, x, f, p.gamma, Q);
+        double* U = p.b.U[p.cur] + cell * (NV * ND);
+        for (int e = tid; e < NV * ND; e += nth) U[e] = Q[e / ND];
+        double* ex = exact + cell * (size_t)(NV * NSD);
+        for (int e = tid; e < NV * NSD; e += nth) ex[e] = Q[e / NSD];
+        continue;
+      }
+    }
     for (int e = tid; e < NV * ND; e += nth) Ua[e] = 0.0;
     for (int e = tid; e < NV * NSD; e += nth) Va[e] = 0.0;
     for (int rw = 0; rw < nrows; ++rw) {

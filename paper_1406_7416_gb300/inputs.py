@@ -6,6 +6,8 @@ with its own code.  Shapes follow the paper's test problems:
   * circular / spherical explosion (Sec. 5.8, radius and the Sod states),
   * four-quadrant 2D Riemann data (Sec. 5.6 quadrant convention), with seeded
     states rho ~ U[0.1, 1.5], p ~ U[0.02, 1.5], u, v ~ U[-1, 1],
+  * the five 2D Riemann problems of Sec. 5.6 (the serving runs draw from
+    them, densities and pressures jittered by 2%),
   * isentropic vortex (Sec. 5.2, strength 5), alone or superposed.
 Seeds are 1406 + workload index with numpy's default_rng.
 
@@ -101,19 +103,56 @@ def vortex_2d(n, N, steps=None):
     return w
 
 
-def serving_runs(count=256, index=4, sizes=(32, 64, 128, 256), orders=(3, 5), t_end=0.2):
-    """Independent 2D runs with grid sizes and orders drawn uniformly; seeded
-    quadrant states on [-0.5,0.5]^2; each run goes to t_end."""
+# Sec. 5.6, the initial states of the five 2D Riemann problems RP1..RP5 as
+# (rho, u, v, p) in quadrant order (1: x>0,y>0; 2: x<=0,y>0; 3: x<=0,y<=0;
+# 4: x>0,y<=0), each with its final time.
+RP2D = (
+    (((1.5, 0.0, 0.0, 1.5), (0.5323, 1.206, 0.0, 0.3),
+      (0.138, 1.206, 1.206, 0.029), (0.5323, 0.0, 1.206, 0.3)), 0.25),
+    (((1.1, 0.0, 0.0, 1.1), (0.5065, 0.8939, 0.0, 0.35),
+      (1.1, 0.8939, 0.8939, 1.1), (0.5065, 0.0, 0.8939, 0.35)), 0.25),
+    (((1.0, 0.75, -0.5, 1.0), (2.0, 0.75, 0.5, 1.0),
+      (1.0, -0.75, 0.5, 1.0), (3.0, -0.75, -0.5, 1.0)), 0.30),
+    (((0.5197, 0.1, 0.1, 0.4), (1.0, -0.6259, 0.1, 1.0),
+      (0.8, 0.1, 0.1, 1.0), (1.0, 0.1, -0.6259, 1.0)), 0.25),
+    (((0.5313, 0.0, 0.0, 0.4), (1.0, 0.7276, 0.0, 1.0),
+      (0.8, 0.0, 0.0, 1.0), (1.0, 0.0, 0.7276, 1.0)), 0.25),
+)
+
+
+def riemann_2d(n, N, config, jitter=0.0, rng=None, bc=TRANSMISSIVE):
+    """One of the five 2D Riemann problems of Sec. 5.6 on [-0.5,0.5]^2
+    (config 0..4 = RP1..RP5).  With jitter > 0 every density and pressure is
+    scaled by a seeded factor in [1 - jitter, 1 + jitter]."""
+    states, t_final = RP2D[config]
+    states = [list(s) for s in states]
+    if jitter > 0.0:
+        for s in states:
+            s[0] *= 1.0 + rng.uniform(-jitter, jitter)
+            s[3] *= 1.0 + rng.uniform(-jitter, jitter)
+    w = _grid(-0.5, 0.5, n, 2, bc)
+    w.update(N=N, gamma=GAMMA, cfl=0.9 / (2 * (2 * N + 1)), steps=None, t_end=t_final,
+             name=f"2D Riemann problem RP{config + 1} N={N} {n}x{n}")
+    w["problem"] = dict(kind="quadrant", center=(0.0, 0.0),
+                        states=[tuple(s) for s in states], vortex=None)
+    return w
+
+
+def serving_runs(count=256, index=4, sizes=(32, 64, 128, 256), orders=(3, 5), t_end=None):
+    """Independent runs of the 2D Riemann problems of Sec. 5.6: per run a
+    seeded configuration RP1..RP5 (densities and pressures jittered by 2%),
+    grid size and order drawn uniformly; each run goes to t_end (default: the
+    configuration's final time)."""
     rng = np.random.default_rng(seed_of(index))
     runs = []
     for r in range(count):
         n = int(rng.choice(sizes))
         N = int(rng.choice(orders))
-        w = _grid(-0.5, 0.5, n, 2, PERIODIC)
-        w.update(N=N, gamma=GAMMA, cfl=0.9 / (2 * (2 * N + 1)), steps=None, t_end=t_end,
-                 name=f"serving run {r}: N={N} {n}x{n}")
-        w["problem"] = dict(kind="quadrant", center=(0.0, 0.0),
-                            states=random_quadrants(rng), vortex=None)
+        cfg = int(rng.integers(len(RP2D)))
+        w = riemann_2d(n, N, cfg, jitter=0.02, rng=rng)
+        if t_end is not None:
+            w["t_end"] = float(t_end)
+        w["name"] = f"serving run {r}: " + w["name"]
         runs.append(w)
     return runs
 
