@@ -87,6 +87,15 @@ def detect(vstar, m, M, gamma, dim, eps=EPS, floor=FLOOR):
     return (~(pad_ok & dmp_ok)).astype(np.int32)
 
 
+def admissible(V, gamma, dim):
+    """PAD of Eq. (positivity) on subcell data V (nvar, ..., N_s^dim): True
+    where rho > 0 and p > 0 on every subcell of the trailing dim axes (NaN
+    fails)."""
+    axes = tuple(range(V.ndim - 1 - dim, V.ndim - 1))
+    ok = (V[0] > 0.0) & (euler.pressure(V, gamma) > 0.0)
+    return np.all(ok, axis=axes)
+
+
 def detector_margin(vstar, m, M, gamma, dim, eps=EPS, floor=FLOOR):
     """Per cell, the smallest relative distance of any detector quantity to its
     threshold: min |x - bound| / max(1, |bound|).  Cells with a margin below

@@ -10,7 +10,15 @@ Sec. 4.4, the five acts, plus the neighbour flux correction that follows them:
      the ADER-WENO3 operator A, with ghost data from V_i built the same way;
   5. gather u^{n+1} = R(v^{n+1}) for troubled cells; v^{n+1} is kept for the
      next step.
-Each zone is decremented at most once (no MOOD cascade).  Unlimited cells that
+With cascade=False each zone is decremented at most once, as in the paper's
+experiments.  With cascade=True (default) the extra MOOD layer of Sec. 6
+(Fig. algo2) follows act 4: a troubled cell whose WENO3 result fails PAD is
+recomputed from v^n by the first-order Rusanov scheme on its subgrid
+(godunov.godunov1), and every troubled WENO3 neighbour sharing a face with it
+takes that first-order flux on the shared face instead of its own, so each
+face carries one flux (its subcells next to the face are corrected by
+-+(dt/h)(F_new - F_old) in the order axis 0 low, high, axis 1 low, ...).  The
+first-order result is not checked again.  Unlimited cells that
 share a face with a troubled cell have their DG face flux on that face
 replaced by the sub-face ADER-WENO fluxes (flux correction of Sec. 4.4): with
 the sub-face flux constant on each sub-face, the exact integral against the
@@ -28,6 +36,7 @@ import numpy as np
 from . import detect as det
 from . import dg
 from .basis import Basis
+from .godunov import godunov1
 from .subcell import projection_matrix, project, reconstruct, reconstruction_matrix
 from .weno import ader_weno
 
@@ -35,7 +44,7 @@ from .weno import ader_weno
 class Scheme:
     """Fixed operators of one (grid, N, gamma) configuration."""
 
-    def __init__(self, grid, N, gamma, eps=det.EPS, floor=det.FLOOR, n_iter=None):
+    def __init__(self, grid, N, gamma, eps=det.EPS, floor=det.FLOOR, n_iter=None, cascade=True):
         self.grid = grid
         self.N = N
         self.gamma = gamma
@@ -46,6 +55,7 @@ class Scheme:
         self.eps = eps
         self.floor = floor
         self.n_iter = N + 1 if n_iter is None else n_iter
+        self.cascade = cascade
 
     @property
     def dim(self):
@@ -120,6 +130,38 @@ def neighbour(sch, cell, k, side):
     return tuple(c)
 
 
+def cascade_layer(sch, troubled, fallback, patches, vnew, faces, dt, h):
+    """First-order layer after WENO3 (in place on vnew / faces)."""
+    d, Ns = sch.dim, sch.Ns
+    v1, f1 = godunov1(patches[:, fallback], dt, h, sch.gamma, d)
+    for i, t in enumerate(fallback):
+        vnew[:, t] = v1[:, i]
+        for k in range(d):
+            for s in (0, 1):
+                faces[k][s][:, t] = f1[k][s][:, i]
+    slot = {c: t for t, c in enumerate(troubled)}
+    is_fb = set(fallback)
+    for t, c in enumerate(troubled):
+        if t in is_fb:
+            continue
+        for k in range(d):
+            for side in (-1, 1):
+                nb = neighbour(sch, c, k, side)
+                tf = slot.get(nb) if nb is not None else None
+                if tf is None or tf not in is_fb:
+                    continue
+                own = 0 if side == -1 else 1          # this cell's face
+                new = faces[k][1 - own][:, tf]        # the fallback cell's side of it
+                diff = (dt / h[k]) * (new - faces[k][own][:, t])
+                layer = [slice(None)] * (1 + d)
+                layer[1 + k] = 0 if side == -1 else Ns - 1
+                vt = vnew[:, t]
+                if side == -1:
+                    vt[tuple(layer)] += diff
+                else:
+                    vt[tuple(layer)] -= diff
+
+
 def step(sch, st, dt, force_all=False):
     """Advance `st` by dt; returns (new state, info dict)."""
     g, gam, b, d = sch.grid, sch.gamma, sch.basis, sch.dim
@@ -138,7 +180,7 @@ def step(sch, st, dt, force_all=False):
     Unew = Ustar.copy()
     Vs_new = np.full((U.shape[0],) + g.ncell + (sch.Ns,) * d, np.nan)
     troubled = [tuple(int(x) for x in c) for c in np.argwhere(beta == 1)]
-    info = {"troubled": len(troubled), "beta": beta.copy(), "m": m, "M": M,
+    info = {"troubled": len(troubled), "fallback": 0, "beta": beta.copy(), "m": m, "M": M,
             "vstar": vstar, "Ustar": Ustar.copy(), "fixed": 0}
     if not troubled:
         return State(Unew, beta, Vs_new), info
@@ -147,6 +189,11 @@ def step(sch, st, dt, force_all=False):
     patches = np.stack([patch(sch, G, c) for c in troubled], axis=1)
     h = [g.dx[k] / sch.Ns for k in range(d)]
     vnew, faces = ader_weno(patches, dt, h, gam, d)
+    if sch.cascade:
+        fallback = [t for t in range(len(troubled)) if not det.admissible(vnew[:, t], gam, d)]
+        info["fallback"] = len(fallback)
+        if fallback:
+            cascade_layer(sch, troubled, fallback, patches, vnew, faces, dt, h)
     # act 5: gather, keep v^{n+1}
     for t, c in enumerate(troubled):
         sel = (slice(None),) + c
