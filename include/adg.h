@@ -74,6 +74,14 @@ extern "C" {
 #define ADG_OPT_SCRATCH_BYTES 10  /* limiter scratch budget in bytes (before the first
                                      load; default 2 GiB, used up to a quarter of the
                                      cells per limiter pass)                          */
+#define ADG_OPT_CASCADE 11        /* 1 (default): the extra MOOD layer of Sec. 6
+                                     (Fig. algo2): a troubled cell whose WENO3 subcell
+                                     result fails the admissibility test of
+                                     Eq. (positivity) is recomputed from v^n by a
+                                     first-order Rusanov step on its subgrid, and its
+                                     WENO3 face neighbours take that flux on the shared
+                                     face; 0: the two-level scheme (DG or WENO3), where
+                                     such a cell raises ADG_WARN_SUBCELL_INADMISSIBLE */
 
 /* Cartesian grid (Sec. 2.1): cells n[k] of size dx[k] from corner x0[k]. */
 typedef struct {
@@ -194,6 +202,10 @@ int adg_read(adg_state* st, double* dofs);
 
 /* Number of troubled cells of the last step. */
 int adg_troubled_count(adg_state* st, int64_t* out);
+
+/* Cells recomputed by the first-order layer (ADG_OPT_CASCADE): in the last
+ * step, and since the last load.  Either pointer may be null. */
+int adg_fallback_count(adg_state* st, int64_t* last_step, int64_t* total);
 
 /* Synchronize and report pending device-side conditions of earlier steps
  * (ADG_ERR_CAPACITY, ADG_WARN_SUBCELL_INADMISSIBLE); clears them. */

@@ -28,6 +28,7 @@ OPT_FP64_SWEEPS = 7
 OPT_END_TIME = 8
 OPT_CFL = 9
 OPT_SCRATCH_BYTES = 10
+OPT_CASCADE = 11
 PHASES = ("predictor", "faceflux", "correct_detect", "limiter", "fix")
 IC_RADIAL, IC_QUADRANT = 0, 1
 
@@ -37,7 +38,7 @@ SYMBOLS = ("adg_create", "adg_set_allocator", "adg_set_stream", "adg_set_option"
            "adg_max_dt", "adg_flags", "adg_read", "adg_troubled_count", "adg_status",
            "adg_sizes", "adg_info", "adg_phase_times", "adg_last_error", "adg_destroy",
            "adg_subcell_update_noalloc", "adg_time", "adg_batch_create", "adg_batch_step",
-           "adg_batch_destroy", "adg_step_batch")
+           "adg_batch_destroy", "adg_step_batch", "adg_fallback_count")
 
 
 class AdgGrid(ctypes.Structure):
@@ -88,6 +89,7 @@ def load_library(path=None):
     lib.adg_flags.argtypes = [vp, ctypes.POINTER(ctypes.c_uint8)]
     lib.adg_read.argtypes = [vp, dp]
     lib.adg_troubled_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.adg_fallback_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.adg_status.argtypes = [vp]
     lib.adg_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
@@ -280,6 +282,13 @@ class Solver:
         c = ctypes.c_int64()
         self._check(self.lib.adg_troubled_count(self.h, ctypes.byref(c)), "adg_troubled_count")
         return c.value
+
+    def fallback_count(self):
+        """(cells recomputed by the first-order layer in the last step, since the load)."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.adg_fallback_count(self.h, ctypes.byref(a), ctypes.byref(b)),
+                    "adg_fallback_count")
+        return a.value, b.value
 
     def status(self):
         return self._check(self.lib.adg_status(self.h), "adg_status")

@@ -17,6 +17,7 @@ struct adg_state {
   int N = 0, dim = 0, nv = 0, prec = 0;
   double gamma = 1.4, eps = 1e-3, floor = 1e-4;
   int force = 0, iters = 0, fp64_sweeps = 1;
+  int cascade = 1;          // first-order layer after WENO3
   long long cap_req = -1;
   int cap = 0, chunk = 0;
   void* (*alloc)(size_t, void*) = nullptr;
@@ -38,7 +39,7 @@ struct adg_state {
   // device copy of the Params: during steps the device owns cur and stamp
   Params* dparams = nullptr;
   Params** d_pps1 = nullptr;        // [1] = dparams
-  long long* d_pre1 = nullptr;      // cells[2], faces[3][2], lim[2], fix[2]
+  long long* d_pre1 = nullptr;      // cells[2], faces[3][2], lim[2], fix[2], fb[2], refix[2]
   double* d_dts1 = nullptr;         // [1]
   bool params_dirty = true;         // host fields changed since the last upload
   bool cur_known = true;            // host cur / stamp equal the device's
@@ -130,7 +131,7 @@ Params make_params(const adg_state* st) {
   p.lam_mode = st->lam_mode ? 1 : 0;
   p.fp64_sweeps = st->fp64_sweeps < st->iters ? st->fp64_sweeps : st->iters;
   p.cfl = st->cfl;
-  p.status_pad = 0;
+  p.cascade = st->cascade;
   return p;
 }
 
@@ -215,12 +216,15 @@ int ensure_allocated(adg_state* st) {
   ALLOC(b.fixlist, int, cells);
   ALLOC(b.fixstamp, int, cells);
   ALLOC(b.edge, double, cap * st->dim * 2 * nv * nsf);
+  ALLOC(b.fblist, int, 3 * cap);
+  b.fbflag = b.fblist + cap;
+  b.refixlist = b.fblist + 2 * cap;
   ALLOC(b.dt, double, 5);
   b.lamred = b.dt + 1;
   b.clock = b.dt + 2;
   ALLOC(st->dparams, Params, 1);
   ALLOC(st->d_pps1, Params*, 1);
-  ALLOC(st->d_pre1, long long, 12);
+  ALLOC(st->d_pre1, long long, 16);
   ALLOC(st->d_dts1, double, 1);
   ALLOC(b.patch, double, chunk * parts[0]);
   ALLOC(b.sweep[0], double, chunk * parts[1]);
@@ -233,9 +237,10 @@ int ensure_allocated(adg_state* st) {
                                st->stream));
   CUDA_TRY(st, cudaMemsetAsync(b.counters, 0, sizeof(int) * CNT_COUNT, st->stream));
   CUDA_TRY(st, cudaMemsetAsync(b.fixstamp, 0xff, sizeof(int) * cells, st->stream));
+  CUDA_TRY(st, cudaMemsetAsync(b.fbflag, 0xff, sizeof(int) * cap, st->stream));
   CUDA_TRY(st, cudaMemsetAsync(b.dt, 0, sizeof(double) * 5, st->stream));
   {
-    long long pre[12] = {0, cells, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    long long pre[16] = {0, cells, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int k = 0; k < st->dim; ++k) {
       long long faces = 1;
       for (int j = 0; j < st->dim; ++j) faces *= (j == k) ? st->geo.n[j] + 1 : st->geo.n[j];
@@ -370,6 +375,9 @@ StepLaunch single_launch(adg_state* st) {
   for (int k = 0; k < 3; ++k) sl.pre_faces[k] = st->d_pre1 + 2 + 2 * k;
   sl.pre_lim = st->d_pre1 + 8;
   sl.pre_fix = st->d_pre1 + 10;
+  sl.pre_fb = st->d_pre1 + 12;
+  sl.pre_refix = st->d_pre1 + 14;
+  sl.cascade = st->cascade;
   sl.total_cells = st->geo.cells;
   for (int k = 0; k < st->dim; ++k) {
     long long faces = 1;
@@ -551,11 +559,12 @@ int adg_batch_create(adg_state* const* states, int count, void* stream, adg_batc
       pc[q + 1] = pc[q] + one.total_cells;
       for (int k = 0; k < 3; ++k) pf[k][q + 1] = pf[k][q] + one.total_faces[k];
       sum_chunk += st->chunk;
+      if (st->cascade) sl.cascade = 1;
       const int passes = (st->cap + st->chunk - 1) / st->chunk;
       if (passes > max_passes) max_passes = passes;
     }
     void* d = nullptr;
-    const size_t bytes = sizeof(Params*) * n + sizeof(long long) * (size_t)(n + 1) * 6;
+    const size_t bytes = sizeof(Params*) * n + sizeof(long long) * (size_t)(n + 1) * 8;
     if (cudaMalloc(&d, bytes) != cudaSuccess) {
       batch_free(b);
       return ADG_ERR_OOM;
@@ -574,6 +583,8 @@ int adg_batch_create(adg_state* const* states, int count, void* stream, adg_batc
     for (int k = 0; k < 3; ++k) sl.pre_faces[k] = dpre + (size_t)(k + 1) * (n + 1);
     sl.pre_lim = dpre + (size_t)4 * (n + 1);
     sl.pre_fix = dpre + (size_t)5 * (n + 1);
+    sl.pre_fb = dpre + (size_t)6 * (n + 1);
+    sl.pre_refix = dpre + (size_t)7 * (n + 1);
     sl.total_cells = pc[n];
     for (int k = 0; k < 3; ++k) sl.total_faces[k] = pf[k][n];
     sl.sum_chunk = sum_chunk;
@@ -780,6 +791,9 @@ int adg_set_option(adg_state* st, int key, double value) {
       if (!(value >= 1.0)) return fail(st, ADG_ERR_ARG, "scratch budget must be positive");
       st->scratch_budget = (size_t)value;
       return ADG_OK;
+    case ADG_OPT_CASCADE:
+      st->cascade = value != 0.0;
+      return ADG_OK;
     case ADG_OPT_CFL:
       if (!(value >= 0.0)) return fail(st, ADG_ERR_ARG, "cfl must be >= 0");
       st->cfl = value;
@@ -973,6 +987,19 @@ int adg_troubled_count(adg_state* st, int64_t* out) {
   return ADG_OK;
 }
 
+int adg_fallback_count(adg_state* st, int64_t* last_step, int64_t* total) {
+  if (!st) return ADG_ERR_ARG;
+  int c[CNT_COUNT] = {};
+  if (st->allocated) {
+    CUDA_TRY(st, cudaMemcpyAsync(c, st->b.counters, sizeof(c), cudaMemcpyDeviceToHost, st->stream));
+    int rc = sync(st);
+    if (rc) return rc;
+  }
+  if (last_step) *last_step = c[CNT_FB];
+  if (total) *total = c[CNT_FB_TOTAL];
+  return ADG_OK;
+}
+
 int adg_status(adg_state* st) {
   if (!st) return ADG_ERR_ARG;
   if (!st->allocated) return ADG_OK;
@@ -1019,7 +1046,11 @@ int adg_info(const adg_state* st, int64_t* out, int cap) {
   const int nchunks = (st->cap + st->chunk - 1) / st->chunk;
   out[0] = st->cap;
   out[1] = st->chunk;
-  out[2] = 1 + 1 + D + 1 + (int64_t)nchunks * (1 + D + 1 + D + 1) + 1;
+  // step begin; predictor, D face-flux kernels, corrector; per limiter pass a
+  // prefix, the patch, D sweeps, the subcell predictor, D flux kernels and the
+  // update; the first-order layer (two prefixes, two kernels); the fix prefix
+  // and the fix; step end
+  out[2] = 1 + (1 + D + 1) + (int64_t)nchunks * (2 * D + 4) + (st->cascade ? 4 : 0) + 2 + 1;
   out[3] = (int64_t)st->bytes_held;
   return ADG_OK;
 }

@@ -68,6 +68,9 @@ struct Bufs {
   int* fixlist;          // [cells]
   int* fixstamp;         // [cells]
   double* edge;          // [cap][d][2][nv][Ns^(d-1)] sub-face fluxes on the cell faces
+  int* fblist;           // [cap] slots whose WENO3 result failed PAD this step
+  int* fbflag;           // [cap] step stamp of the slots in fblist
+  int* refixlist;        // [cap] WENO3 cells sharing a face with a fallback cell
   double* dt;            // [1] time step of the current step (0: state idle this step)
   double* lamred;        // [1] reduced lambda
   double* clock;         // [3] simulated time t, end time t_end (0: none), steps taken
@@ -85,6 +88,9 @@ enum {
   CNT_FIX = 2,           // neighbour-fix list length
   CNT_STATUS = 3,        // bit 0: slot capacity exceeded, bit 1: bad dt
   CNT_INADM = 4,         // subcells left inadmissible after the limiter
+  CNT_FB = 5,            // first-order fallback cells of the current step
+  CNT_REFIX = 6,         // WENO3 cells rebalanced against a fallback neighbour
+  CNT_FB_TOTAL = 7,      // fallback cells since the last load
   CNT_COUNT = 8
 };
 
@@ -98,7 +104,7 @@ struct Params {
   int stamp;             // step counter (fix-list stamps)
   int lam_mode;          // 1: kernels keep the per-cell wave speeds current
   int fp64_sweeps;       // mixed precision: number of final FP64 Picard sweeps
-  int status_pad;
+  int cascade;           // 1: first-order layer after WENO3 (Sec. 6, Fig. algo2)
   double cfl;            // the state's CFL number for batched CFL steps (0: none)
 };
 
@@ -130,6 +136,9 @@ struct StepLaunch {
   const long long* pre_faces[3];  // [n+1] faces x tangential nodes, per axis
   long long* pre_lim;          // [n+1] troubled cells of one limiter pass (device-computed)
   long long* pre_fix;          // [n+1] neighbour-fix entries (device-computed)
+  long long* pre_fb;           // [n+1] first-order fallback cells (device-computed)
+  long long* pre_refix;        // [n+1] rebalanced WENO3 neighbours (device-computed)
+  int cascade;                 // any state of the launch runs the first-order layer
   long long total_cells;
   long long total_faces[3];
   long long sum_chunk;         // sum over states of the limiter chunk size
@@ -186,6 +195,7 @@ cudaError_t launch_step_begin(const StepLaunch& sl, cudaStream_t s);
 cudaError_t launch_step_end(const StepLaunch& sl, cudaStream_t s);
 cudaError_t launch_lim_prefix(const StepLaunch& sl, int pass, cudaStream_t s);
 cudaError_t launch_fix_prefix(const StepLaunch& sl, cudaStream_t s);
+cudaError_t launch_count_prefix(const StepLaunch& sl, long long* pre, int counter, cudaStream_t s);
 
 // Scratch doubles per troubled cell of the limiter chunk buffers.
 size_t limiter_scratch_doubles(int dim, int N, size_t* patch, size_t* sw0, size_t* sw1,

@@ -59,6 +59,8 @@ __global__ void k_step_begin(StepLaunch sl) {
     if (dt > 0.0) {
       p.b.counters[CNT_TROUBLED0 + (1 - p.cur)] = 0;
       p.b.counters[CNT_FIX] = 0;
+      p.b.counters[CNT_FB] = 0;
+      p.b.counters[CNT_REFIX] = 0;
       p.stamp += 1;
       p.b.clock[0] = t + dt;
       p.b.clock[2] += 1.0;
@@ -82,6 +84,18 @@ __global__ void k_lim_prefix(StepLaunch sl, int pass) {
     acc += pass_len(*sl.pps[s], pass);
   }
   sl.pre_lim[sl.n] = acc;
+}
+
+// Prefix of the entries of one per-step list counter (states idle this step
+// contribute none).
+__global__ void k_count_prefix(StepLaunch sl, long long* pre, int counter) {
+  long long acc = 0;
+  for (int s = 0; s < sl.n; ++s) {
+    pre[s] = acc;
+    const Params& p = *sl.pps[s];
+    if (*p.b.dt > 0.0) acc += p.b.counters[counter];
+  }
+  pre[sl.n] = acc;
 }
 
 // Prefix of the neighbour-fix entries of every state.
@@ -132,6 +146,11 @@ cudaError_t launch_lim_prefix(const StepLaunch& sl, int pass, cudaStream_t s) {
 
 cudaError_t launch_fix_prefix(const StepLaunch& sl, cudaStream_t s) {
   k_fix_prefix<<<1, 1, 0, s>>>(sl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_prefix(const StepLaunch& sl, long long* pre, int counter, cudaStream_t s) {
+  k_count_prefix<<<1, 1, 0, s>>>(sl, pre, counter);
   return cudaGetLastError();
 }
 

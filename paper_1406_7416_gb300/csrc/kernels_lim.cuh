@@ -482,7 +482,15 @@ __global__ void __launch_bounds__(128) k_lim_update(Batch bt, int pass) {
     const bool bad = check_subcells<D>(A, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red);
     if (tid == 0) {
       if (p.lam_mode) p.b.lam[cell] = lam;
-      if (bad) atomicAdd(&p.b.counters[CNT_INADM], 1);
+      if (bad && p.cascade) {
+        // first-order layer: recomputed by k_lim_fallback after all passes
+        const int i = atomicAdd(&p.b.counters[CNT_FB], 1);
+        p.b.fblist[i] = t;
+        p.b.fbflag[t] = p.stamp;
+        atomicAdd(&p.b.counters[CNT_FB_TOTAL], 1);
+      } else if (bad) {
+        atomicAdd(&p.b.counters[CNT_INADM], 1);
+      }
     }
     if (tid < 2 * NV) p.b.cmm[nxt][cell * 2 * NV + tid] = mm[tid];
     // sub-face fluxes on the faces of the cell: edge[t][k][side][v][NSF]
@@ -614,6 +622,263 @@ __global__ void __launch_bounds__(128) k_lim_fix(Batch bt) {
     check_subcells<D>(vs, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red);
     if (tid == 0 && p.lam_mode) p.b.lam[cell] = lam;
     if (tid < 2 * NV) p.b.cmm[nxt][cell * 2 * NV + tid] = mm[tid];
+  }
+}
+
+// Cascade layer (Sec. 6, Fig. algo2), part 1: each troubled cell whose WENO3
+// result failed PAD is recomputed from v^n by one first-order Rusanov step on
+// its subgrid: sub-face fluxes between the piecewise-constant subcell data,
+// ghost data from Eq. (ader.icbc) as for the WENO3 patch (wrapped or clamped
+// global subcell index).  Writes v^{n+1}, min / max, wave speed, u = R(v) and
+// the cell-face fluxes (the flux correction of unlimited neighbours uses
+// them), and lists the WENO3 face neighbours, which must take the
+// first-order flux on the shared face (part 2).  One block per cell.
+template <int D, int N>
+__global__ void __launch_bounds__(128) k_lim_fallback(Batch bt) {
+  using DM = Dims<D, N>;
+  constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, Ns = DM::Ns, NSD = DM::NSD, NSF = DM::NSF;
+  constexpr int NE = Ns + 2;                          // local subcells -1..Ns per axis
+  constexpr int NB = (D == 3) ? NE * NE * NE : NE * NE;
+  constexpr int NFK = (Ns + 1) * NSF;
+  extern __shared__ double sm[];
+  double* blk = sm;                 // NV * NB   v^n with one ghost layer
+  double* A = blk + NV * NB;        // NV * NSD
+  double* B = A + NV * NSD;         // NV * NSD
+  double* F = B + NV * NSD;         // NV * NFK  sub-face fluxes of one axis
+  double* R1 = F + NV * NFK;        // n * Ns
+  double* P1 = R1 + n * Ns;         // Ns * n
+  double* mm = P1 + Ns * n;         // 2 NV
+  double* red = mm + 2 * NV;        // 128
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = tid; i < n * Ns; i += nth) {
+    R1[i] = bt.pps[0]->ops->R1[i];
+    P1[i] = bt.pps[0]->ops->P1[i];
+  }
+  for (long long fg = blockIdx.x; fg < bt.pre[bt.n]; fg += gridDim.x) {
+    const int sidx = batch_state(bt, fg);
+    const Params& p = *bt.pps[sidx];
+    const long long f = fg - bt.pre[sidx];
+    const int nxt = 1 - p.cur;
+    const Geo& g = p.geo;
+    const int t = p.b.fblist[f];
+    const long long cell = p.b.list[nxt][t];
+    const double dt = *p.b.dt;
+    int ijk[3];
+    cell_coords<D>(cell, g, ijk);
+    __syncthreads();
+    for (int e = tid; e < NB; e += nth) {
+      int r = e;
+      int own[3] = {0, 0, 0}, sub[3] = {0, 0, 0};
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const int loc = r % NE - 1;
+        r /= NE;
+        const int ng = g.n[k] * Ns;
+        int gi = ijk[k] * Ns + loc;
+        if (g.periodic[k]) gi = (gi % ng + ng) % ng;
+        else gi = gi < 0 ? 0 : (gi >= ng ? ng - 1 : gi);
+        own[k] = gi / Ns;
+        sub[k] = gi - own[k] * Ns;
+      }
+      double val[NV];
+      subcell_value<D, N>(p, cell_index<D>(own, g), sub, P1, val);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) blk[v * NB + e] = val[v];
+    }
+    __syncthreads();
+    for (int e = tid; e < NV * NSD; e += nth) {
+      const int v = e / NSD;
+      int s = e - v * NSD, bi = 0, mul = 1;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        bi += (s % Ns + 1) * mul;
+        s /= Ns;
+        mul *= NE;
+      }
+      A[e] = blk[v * NB + bi];
+    }
+    for (int k = 0; k < D; ++k) {
+      const double ck = dt * Ns / g.dx[k];
+      __syncthreads();
+      // faces c_k = 0..Ns between local subcells c_k - 1 and c_k
+      for (int e = tid; e < NFK; e += nth) {
+        int r = e, bl = 0, mul = 1, stk = 1;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const int ext = (a == k) ? Ns + 1 : Ns;
+          const int c = r % ext;
+          r /= ext;
+          bl += (a == k ? c : c + 1) * mul;
+          if (a == k) stk = mul;
+          mul *= NE;
+        }
+        double QL[NV], QR[NV], G[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          QL[v] = blk[v * NB + bl];
+          QR[v] = blk[v * NB + bl + stk];
+        }
+        rusanov<D>(QL, QR, k, p.gamma, G);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) F[v * NFK + e] = G[v];
+      }
+      __syncthreads();
+      const int kst = (k == 0) ? 1 : (k == 1 ? Ns : Ns * Ns);   // stride of axis k
+      for (int e = tid; e < NV * NSD; e += nth) {
+        const int v = e / NSD;
+        int s = e - v * NSD, flo = 0, mul = 1;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          flo += (s % Ns) * mul;
+          s /= Ns;
+          mul *= (a == k) ? Ns + 1 : Ns;
+        }
+        A[e] -= ck * (F[v * NFK + flo + kst] - F[v * NFK + flo]);
+      }
+      // cell-face fluxes: edge[t][k][side][v][NSF]
+      for (int e = tid; e < 2 * NV * NSF; e += nth) {
+        const int side = e / (NV * NSF);
+        const int r = e - side * NV * NSF;
+        const int v = r / NSF, ts = r - v * NSF;
+        const int tc[2] = {ts % Ns, ts / Ns};
+        int fidx = 0, mul = 1, q = 0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          const int cc = (a == k) ? (side ? Ns : 0) : tc[q++];
+          fidx += cc * mul;
+          mul *= (a == k) ? Ns + 1 : Ns;
+        }
+        p.b.edge[((size_t)t * D * 2 + (size_t)k * 2 + side) * NV * NSF + r] = F[v * NFK + fidx];
+      }
+    }
+    __syncthreads();
+    double* st = p.b.store[nxt] + (size_t)t * NV * NSD;
+    for (int e = tid; e < NV * NSD; e += nth) st[e] = A[e];
+    double lam = 0.0;
+    const bool bad = check_subcells<D>(A, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red);
+    if (tid == 0) {
+      if (p.lam_mode) p.b.lam[cell] = lam;
+      if (bad) atomicAdd(&p.b.counters[CNT_INADM], 1);
+    }
+    if (tid < 2 * NV) p.b.cmm[nxt][cell * 2 * NV + tid] = mm[tid];
+    __syncthreads();
+    double* u = apply_ct<D, NV, Ns, n>(A, B, R1, tid, nth);
+    double* Uo = p.b.U[nxt] + cell * (NV * ND);
+    for (int e = tid; e < NV * ND; e += nth) Uo[e] = u[e];
+    if (tid < 2 * D) {
+      const int k = tid >> 1, side = (tid & 1) ? 1 : -1;
+      int nb[3];
+      if (face_neighbour<D>(g, ijk, k, side, nb)) {
+        const long long nc = cell_index<D>(nb, g);
+        if (p.b.beta[nxt][nc]) {
+          const int sl = p.b.slot[nxt][nc];
+          // fixstamp marks unlimited cells for k_lim_fix; troubled cells are
+          // never in that list, so it marks the WENO3 neighbours here
+          if (sl >= 0 && p.b.fbflag[sl] != p.stamp) {
+            const int old = atomicExch(&p.b.fixstamp[nc], p.stamp);
+            if (old != p.stamp) {
+              const int idx = atomicAdd(&p.b.counters[CNT_REFIX], 1);
+              p.b.refixlist[idx] = (int)nc;
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+// Cascade layer, part 2: a WENO3 cell with fallback face neighbours takes
+// their first-order flux on each shared face.  Its subcells next to such a
+// face change by -+(dt/h_k)(F_first - F_weno), applied in the order axis 0
+// low, axis 0 high, axis 1 low, ...; then min / max, wave speed and u = R(v)
+// again.  One block per cell.
+template <int D, int N>
+__global__ void __launch_bounds__(128) k_lim_refix(Batch bt) {
+  using DM = Dims<D, N>;
+  constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, Ns = DM::Ns, NSD = DM::NSD, NSF = DM::NSF;
+  constexpr size_t EDGE = (size_t)D * 2 * NV * NSF;
+  extern __shared__ double sm[];
+  double* A = sm;                   // NV * NSD
+  double* B = A + NV * NSD;         // NV * NSD
+  double* R1 = B + NV * NSD;        // n * Ns
+  double* mm = R1 + n * Ns;         // 2 NV
+  double* red = mm + 2 * NV;        // 128
+  __shared__ int fbslot[6];         // slot of the fallback neighbour per face, -1: none
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int i = tid; i < n * Ns; i += nth) R1[i] = bt.pps[0]->ops->R1[i];
+  for (long long fg = blockIdx.x; fg < bt.pre[bt.n]; fg += gridDim.x) {
+    const int sidx = batch_state(bt, fg);
+    const Params& p = *bt.pps[sidx];
+    const long long f = fg - bt.pre[sidx];
+    const int nxt = 1 - p.cur;
+    const Geo& g = p.geo;
+    const long long cell = p.b.refixlist[f];
+    const int t = p.b.slot[nxt][cell];
+    const double dt = *p.b.dt;
+    int ijk[3];
+    cell_coords<D>(cell, g, ijk);
+    __syncthreads();
+    if (tid < 2 * D) {
+      const int k = tid >> 1, side = (tid & 1) ? 1 : -1;
+      int nb[3], fs = -1;
+      if (face_neighbour<D>(g, ijk, k, side, nb)) {
+        const long long nc = cell_index<D>(nb, g);
+        if (p.b.beta[nxt][nc]) {
+          const int sl = p.b.slot[nxt][nc];
+          if (sl >= 0 && p.b.fbflag[sl] == p.stamp) fs = sl;
+        }
+      }
+      fbslot[tid] = fs;
+    }
+    double* st = p.b.store[nxt] + (size_t)t * NV * NSD;
+    __syncthreads();
+    const double* Et = p.b.edge + (size_t)t * EDGE;
+    for (int e = tid; e < NV * NSD; e += nth) {
+      const int v = e / NSD;
+      int s = e - v * NSD;
+      int sc[3] = {0, 0, 0};
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        sc[a] = s % Ns;
+        s /= Ns;
+      }
+      double val = st[e];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const double ck = dt * Ns / g.dx[k];
+        int ts = 0, mul = 1;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+          if (a != k) {
+            ts += sc[a] * mul;
+            mul *= Ns;
+          }
+#pragma unroll
+        for (int own = 0; own < 2; ++own) {
+          const int fs = fbslot[2 * k + own];
+          if (fs < 0 || sc[k] != (own ? Ns - 1 : 0)) continue;
+          const double Fnew = p.b.edge[(size_t)fs * EDGE + ((size_t)k * 2 + (1 - own)) * NV * NSF + v * NSF + ts];
+          const double Fold = Et[((size_t)k * 2 + own) * NV * NSF + v * NSF + ts];
+          const double diff = ck * (Fnew - Fold);
+          if (own) val -= diff;
+          else val += diff;
+        }
+      }
+      A[e] = val;
+      st[e] = val;
+    }
+    __syncthreads();
+    double lam = 0.0;
+    const bool bad = check_subcells<D>(A, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red);
+    if (tid == 0) {
+      if (p.lam_mode) p.b.lam[cell] = lam;
+      if (bad) atomicAdd(&p.b.counters[CNT_INADM], 1);
+    }
+    if (tid < 2 * NV) p.b.cmm[nxt][cell * 2 * NV + tid] = mm[tid];
+    __syncthreads();
+    double* u = apply_ct<D, NV, Ns, n>(A, B, R1, tid, nth);
+    double* Uo = p.b.U[nxt] + cell * (NV * ND);
+    for (int e = tid; e < NV * ND; e += nth) Uo[e] = u[e];
   }
 }
 

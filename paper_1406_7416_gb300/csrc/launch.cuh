@@ -35,6 +35,11 @@ struct Launch {
     return t > 128 ? 128 : t;
   }
   static size_t cell_smem() { return (size_t)(2 * NV * NSD + 2 * Ns * n + 4 * NV + 128) * sizeof(double); }
+  static size_t fallback_smem() {
+    constexpr size_t NE = Ns + 2, NB = (D == 3) ? NE * NE * NE : NE * NE;
+    return (size_t)(NV * NB + 2 * NV * NSD + NV * (Ns + 1) * DM::NSF + 2 * Ns * n + 2 * NV + 128) *
+           sizeof(double);
+  }
   static size_t fix_smem() {
     return (size_t)(NV * ND + 2 * NV * NSD + 2 * Ns * n + 4 * NV + 128) * sizeof(double);
   }
@@ -100,6 +105,17 @@ struct Launch {
         k_lim_flux<D, N, (D == 3 ? 2 : 1)><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(
             lim, pass);
       k_lim_update<D, N><<<(int)(ch < kNumSM * 8 ? ch : kNumSM * 8), 128, su, s>>>(lim, pass);
+    }
+    if (sl.cascade) {
+      // first-order layer after WENO3 (Sec. 6, Fig. algo2); both lists are
+      // empty in most steps and the kernels then return at once
+      if ((e = launch_count_prefix(sl, sl.pre_fb, CNT_FB, s)) != cudaSuccess) return e;
+      const size_t sfb = fallback_smem();
+      if ((e = set_smem(k_lim_fallback<D, N>, sfb)) != cudaSuccess) return e;
+      k_lim_fallback<D, N><<<kNumSM, 128, sfb, s>>>(Batch{sl.pps, sl.n, sl.pre_fb});
+      if ((e = launch_count_prefix(sl, sl.pre_refix, CNT_REFIX, s)) != cudaSuccess) return e;
+      if ((e = set_smem(k_lim_refix<D, N>, su)) != cudaSuccess) return e;
+      k_lim_refix<D, N><<<kNumSM, 128, su, s>>>(Batch{sl.pps, sl.n, sl.pre_refix});
     }
     mark(ev, PHASE_FIX, s);
     if ((e = launch_fix_prefix(sl, s)) != cudaSuccess) return e;

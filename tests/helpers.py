@@ -103,3 +103,51 @@ def neighbourhood_mask(mask, layers, periodic):
 
 def state_copy(st):
     return State(st.U.copy(), st.beta.copy(), st.Vs.copy())
+
+
+def rough_conserved(shape, d, rng, mach=3.0, gamma=1.4, rho=(0.02, 5.0), p=(0.005, 5.0)):
+    """Admissible conserved states with strong contrasts over `shape`: rho and
+    p log-uniform over the given ranges (by default two to three decades),
+    velocities up to `mach` (nvar first in the result)."""
+    from oracle import euler
+    rho = np.exp(rng.uniform(np.log(rho[0]), np.log(rho[1]), size=shape))
+    p = np.exp(rng.uniform(np.log(p[0]), np.log(p[1]), size=shape))
+    vel = [rng.uniform(-mach, mach, size=shape) for _ in range(d)]
+    return euler.prim_to_cons(rho, vel, p, gamma)
+
+
+def rough_forced_state(sch, rng, rough_cells, mild=False):
+    """Every cell flagged (beta = 1, subcell data stored): per-cell states with
+    strong jumps between cells (mild: within a factor 2, Mach 0.5) and 5%
+    variation between subcells, plus cells whose subcells are rough on their
+    own -- WENO3 fails the admissibility test in some cells and passes in
+    others."""
+    d = sch.dim
+    nc = tuple(sch.grid.ncell)
+    if mild:
+        Vc = rough_conserved(nc, d, rng, mach=0.5, rho=(0.7, 1.4), p=(0.7, 1.4))
+    else:
+        Vc = rough_conserved(nc, d, rng)
+    Vs = np.broadcast_to(Vc[(Ellipsis,) + (None,) * d], Vc.shape + (sch.Ns,) * d).copy()
+    Vs *= 1.0 + 0.05 * rng.uniform(-1.0, 1.0, size=Vs.shape[1:])
+    for c in rough_cells:
+        Vs[(slice(None),) + tuple(c)] = rough_conserved((sch.Ns,) * d, d, rng)
+    return State(sch.R(Vs), np.ones(nc, dtype=np.int32), Vs)
+
+
+def rough_island_state(sch, rng, rough_cells, gamma=1.4):
+    """A uniform flow (rho = p = 1, velocity 0.3 per axis) with a few flagged
+    cells holding rough subcell data: the limiter runs in and around them
+    while their unlimited neighbours take the flux correction."""
+    from oracle import euler
+    d, Ns = sch.dim, sch.Ns
+    nc = tuple(sch.grid.ncell)
+    base = euler.prim_to_cons(np.array(1.0), [np.array(0.3)] * d, np.array(1.0), gamma)
+    Vs = np.broadcast_to(base.reshape((d + 2,) + (1,) * (2 * d)), (d + 2,) + nc + (Ns,) * d).copy()
+    beta = np.zeros(nc, dtype=np.int32)
+    for c in rough_cells:
+        Vs[(slice(None),) + tuple(c)] = rough_conserved((Ns,) * d, d, rng, mach=2.0)
+        beta[tuple(c)] = 1
+    U = sch.R(Vs)
+    stored = np.where(beta[(None, Ellipsis) + (None,) * d] == 1, Vs, np.nan)
+    return State(U, beta, stored)

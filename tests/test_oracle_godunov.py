@@ -19,6 +19,8 @@ from oracle.step import Scheme, State, global_subgrid, stable_dt, step
 from oracle.weno import ader_weno
 from paper_1406_7416_gb300 import inputs
 
+from helpers import rough_forced_state
+
 GAMMA = 1.4
 
 
@@ -127,26 +129,12 @@ def test_first_order_convergence():
     assert 0.75 < rates[-1] < 1.3, (errs, rates)
 
 
-def _rough_state(sch, rng):
-    """Per-cell states with strong jumps between cells and 5% variation
-    between subcells (so WENO3 and first-order fluxes differ on every face),
-    and two cells whose subcells are rough on their own."""
-    nc = tuple(sch.grid.ncell)
-    Vc = _rough(nc, 2, rng, mach=3.0)
-    Vs = np.broadcast_to(Vc[..., None, None], Vc.shape + (sch.Ns,) * 2).copy()
-    Vs *= 1.0 + 0.05 * rng.uniform(-1.0, 1.0, size=Vs.shape[1:])   # same factor for all variables
-    for c in [(1, 1), (2, 3)]:
-        Vs[(slice(None),) + c] = _rough((sch.Ns,) * 2, 2, rng, mach=3.0)
-    beta = np.ones(nc, dtype=np.int32)
-    return State(sch.R(Vs), beta, Vs)
-
-
 def _cascade_case():
     g = Grid((4, 4), (0.0, 0.0), (0.25, 0.25), (0, 0, 0, 0))
     for seed in range(40):
         rng = np.random.default_rng(100 + seed)
         sch = Scheme(g, 1, GAMMA, cascade=True)
-        st = _rough_state(sch, rng)
+        st = rough_forced_state(sch, rng, [(1, 1), (2, 3)])
         dt = stable_dt(sch, st, 0.9 / (2 * 3))
         new, info = step(sch, st, dt, force_all=True)
         if 0 < info["fallback"] < 16:
