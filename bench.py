@@ -29,6 +29,7 @@ sys.path.insert(0, ROOT)
 
 N_ORDER = 5
 GRID = 512
+GRID_SET = None
 WORKLOAD = "quadvortex512"
 METRIC = "space-time DOF updates/s"
 UNIT = "ST-DOF/s"
@@ -38,6 +39,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2
 def workload(n=None, N=N_ORDER):
     """The benchmark workload (default: 2D quadrants + vortex, N=5, 512^2)."""
     from paper_1406_7416_gb300 import inputs
+    n = n or GRID_SET
     if WORKLOAD == "explosion2d":
         return inputs.explosion_2d(n=n or 32, N=3)
     if WORKLOAD == "explosion3d":
@@ -262,11 +264,13 @@ def run_gpu(args):
         clk = clocks_sampler() if (name == "mixed" and rank == 0) else None
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        l0 = s.info()["launches"]
         e0.record(stream)
         for _ in range(args.steps):
             s.step_cfl(cfl)
         e1.record(stream)
         torch.cuda.synchronize()
+        launches = s.info()["launches"] - l0
         barrier()
         ms = e0.elapsed_time(e1) / args.steps
         clocks = clocks_summary(clk, local) if clk is not None else None
@@ -275,7 +279,8 @@ def run_gpu(args):
         troubled = s.troubled_count()
         info = s.info()
         results[name] = dict(ms=max_over_ranks(ms), solver=s, phases={k: v / nsteps for k, v in phases.items()},
-                             status=status, troubled=troubled, info=info, clocks=clocks)
+                             status=status, troubled=troubled, info=info, clocks=clocks,
+                             launches=launches)
     if args.only != "both":
         # profiling run of one precision: timings only
         if rank == 0:
@@ -378,7 +383,7 @@ def emit_line(args, w, results, stdofs, world, cells, cfl, l1, l1ref, e2e, D, N,
                      "fp64_flops_per_launch": fl64 * cells,
                      "traffic": traffic["bytes_per_launch"] if traffic else None},
         "e2e": e2e,
-        "gpu_launches": int(mx["info"]["launches_per_step"]) * args.steps,
+        "gpu_launches": int(mx["launches"]),
         "clocks": mx["clocks"],
     }
     if not args.no_cpu_baseline:
@@ -459,7 +464,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer timing")
-    ap.add_argument("--grid", type=int, default=GRID, help="cells per axis (profiling runs)")
+    ap.add_argument("--grid", type=int, default=None,
+                    help="cells per axis (profiling runs; default: the workload's own)")
     ap.add_argument("--only", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--workload", default="quadvortex512",
                     choices=["quadvortex512", "explosion2d", "explosion3d", "quadrants200", "serving"])
@@ -469,7 +475,8 @@ def main():
     ap.add_argument("--max-wall", type=float, default=120.0,
                     help="serving: no admissions after this many seconds per pass")
     args = ap.parse_args()
-    globals()["GRID"] = args.grid
+    globals()["GRID"] = args.grid or GRID
+    globals()["GRID_SET"] = args.grid
     globals()["WORKLOAD"] = args.workload
     if args.warmup < 3:
         args.warmup = 3

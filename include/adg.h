@@ -72,8 +72,9 @@ extern "C" {
 #define ADG_OPT_CFL 9             /* the state's CFL number for batched CFL steps
                                      called with cfl <= 0 (includes 1/(d(2N+1)))      */
 #define ADG_OPT_SCRATCH_BYTES 10  /* limiter scratch budget in bytes (before the first
-                                     load; default 2 GiB, used up to a quarter of the
-                                     cells per limiter pass)                          */
+                                     load; default an eighth of the free device memory
+                                     at the first load, clamped to 2..32 GiB; used up to
+                                     a quarter of the cells per limiter pass)         */
 #define ADG_OPT_CASCADE 11        /* 1 (default): the extra MOOD layer of Sec. 6
                                      (Fig. algo2): a troubled cell whose WENO3 subcell
                                      result fails the admissibility test of
@@ -82,6 +83,29 @@ extern "C" {
                                      WENO3 face neighbours take that flux on the shared
                                      face; 0: the two-level scheme (DG or WENO3), where
                                      such a cell raises ADG_WARN_SUBCELL_INADMISSIBLE */
+#define ADG_OPT_FLUX 12           /* numerical flux of the DG faces and the WENO3
+                                     sub-faces (Sec. 2.3): ADG_FLUX_RUSANOV (default)
+                                     or ADG_FLUX_OSHER, the universal Osher-type flux
+                                     of Dumbser and Toro (three-point Gauss-Legendre
+                                     path integral), used for the vortex table of
+                                     Sec. 5.2; the first-order layer keeps Rusanov */
+
+#define ADG_OPT_HOST_PASSES 13    /* 1 (default): adg_step / adg_step_cfl wait once per
+                                     step, after the DG phase, for the step's troubled
+                                     count and launch only the limiter passes it needs;
+                                     0: fully asynchronous steps that launch every pass
+                                     the slot capacity allows (empty ones return at
+                                     once).  Batched steps are always asynchronous.  */
+
+#define ADG_OPT_SUBCELL_FP64_SWEEPS 14  /* mixed precision: how many of the three
+                                     Picard sweeps of the degree-2 subcell predictor
+                                     run in FP64 after the FP32 ones (0..3, default
+                                     0: all FP32; the sub-face fluxes and the finite
+                                     volume update stay FP64).  States batched
+                                     together share one launch per value.          */
+
+#define ADG_FLUX_RUSANOV 0
+#define ADG_FLUX_OSHER 1
 
 /* Cartesian grid (Sec. 2.1): cells n[k] of size dx[k] from corner x0[k]. */
 typedef struct {
@@ -152,8 +176,10 @@ int adg_read_full(adg_state* st, double* dofs, uint8_t* beta, double* subcells);
 /* One full time step of size dt > 0 (Sec. 4.4): predictor (Eq. pde.nc.dg2),
  * corrector (Eq. pde.nc.gw2), detection (Eqs. positivity, dmp, relax),
  * subcell ADER-WENO3 recomputation of troubled cells (Eq. aderweno with the
- * data of Eq. ader.icbc), reconstruction R, and the flux correction of their
- * unlimited face neighbours.  Asynchronous.  Errors: ADG_ERR_ARG (dt <= 0,
+ * data of Eq. ader.icbc), reconstruction R, the flux correction of their
+ * unlimited face neighbours, and with ADG_OPT_CASCADE the first-order layer.
+ * Waits once for the step's troubled count after the DG phase unless
+ * ADG_OPT_HOST_PASSES is 0 (then fully asynchronous).  Errors: ADG_ERR_ARG (dt <= 0,
  * nothing loaded), ADG_ERR_CUDA.  Device-side conditions (capacity overflow,
  * inadmissible subcells) surface on the next synchronizing call. */
 int adg_step(adg_state* st, double dt);
@@ -217,7 +243,10 @@ int adg_sizes(const adg_state* st, int64_t* cells, int* nvar, int* nodes, int* s
 
 /* Launch layout after the first load: out[0] = subcell slot capacity,
  * out[1] = troubled cells per limiter chunk, out[2] = kernels launched by one
- * adg_step, out[3] = device bytes held by the state.  Needs cap >= 4. */
+ * adg_step at most (every limiter pass the capacity allows), out[3] = device
+ * bytes held by the state, and with cap >= 5, out[4] = kernels issued by this
+ * state's steps so far (batched steps count on the first state of each group
+ * of one dimension, degree and precision).  Needs cap >= 4. */
 int adg_info(const adg_state* st, int64_t* out, int cap);
 
 /* Phase timing (ADG_OPT_PROFILE = 1): accumulated milliseconds of the steps

@@ -94,12 +94,13 @@ def _face_states(qlo, qhi, cell_axis, periodic):
     return left, right
 
 
-def corrector(U, q, dt, basis, grid, gamma):
+def corrector(U, q, dt, basis, grid, gamma, face_flux=euler.rusanov):
     """Candidate u* of Eq. (pde.nc.gw2) and the DG face fluxes.
 
     Returns (Ustar, Gbar) where Gbar[k] has shape
     (nvar, cells with axis k extended to n_k + 1 faces, tangential nodes...):
-    the time-averaged Rusanov flux at each tangential GL node of each face."""
+    the time-averaged numerical flux (Rusanov unless `face_flux` says
+    otherwise) at each tangential GL node of each face."""
     d = grid.dim
     w, D = basis.w, basis.D
     Ustar = U.copy()
@@ -116,7 +117,7 @@ def corrector(U, q, dt, basis, grid, gamma):
         qlo = np.tensordot(q, basis.phi0, axes=([qnode_axis], [0]))
         qhi = np.tensordot(q, basis.phi1, axes=([qnode_axis], [0]))
         left, right = _face_states(qlo, qhi, 1 + k, grid.periodic(k))
-        G = euler.rusanov(left, right, gamma, k)
+        G = face_flux(left, right, gamma, k)
         Gb = np.tensordot(G, w, axes=([G.ndim - 1], [0]))
         Gbar.append(Gb)
         nk = grid.ncell[k]

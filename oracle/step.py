@@ -35,6 +35,7 @@ import numpy as np
 
 from . import detect as det
 from . import dg
+from . import euler
 from .basis import Basis
 from .godunov import godunov1
 from .subcell import projection_matrix, project, reconstruct, reconstruction_matrix
@@ -44,7 +45,8 @@ from .weno import ader_weno
 class Scheme:
     """Fixed operators of one (grid, N, gamma) configuration."""
 
-    def __init__(self, grid, N, gamma, eps=det.EPS, floor=det.FLOOR, n_iter=None, cascade=True):
+    def __init__(self, grid, N, gamma, eps=det.EPS, floor=det.FLOOR, n_iter=None, cascade=True,
+                 flux="rusanov"):
         self.grid = grid
         self.N = N
         self.gamma = gamma
@@ -56,6 +58,7 @@ class Scheme:
         self.floor = floor
         self.n_iter = N + 1 if n_iter is None else n_iter
         self.cascade = cascade
+        self.flux = flux                 # numerical flux of DG faces and WENO3 sub-faces
 
     @property
     def dim(self):
@@ -168,7 +171,8 @@ def step(sch, st, dt, force_all=False):
     U = st.U
     # act 1: unlimited candidate
     q = dg.predictor(U, [dt / g.dx[k] for k in range(d)], b, dg.euler_flux_fn(gam), sch.n_iter)
-    Ustar, Gbar = dg.corrector(U, q, dt, b, g, gam)
+    ff = euler.numerical_flux(sch.flux)
+    Ustar, Gbar = dg.corrector(U, q, dt, b, g, gam, ff)
     # act 2 + 3: scatter and detect against bounds from v^n over V_i
     Vn = subcell_data(sch, st)
     cmin, cmax = det.cell_minmax(Vn, d)
@@ -188,7 +192,7 @@ def step(sch, st, dt, force_all=False):
     G = global_subgrid(Vn, d)
     patches = np.stack([patch(sch, G, c) for c in troubled], axis=1)
     h = [g.dx[k] / sch.Ns for k in range(d)]
-    vnew, faces = ader_weno(patches, dt, h, gam, d)
+    vnew, faces = ader_weno(patches, dt, h, gam, d, ff)
     if sch.cascade:
         fallback = [t for t in range(len(troubled)) if not det.admissible(vnew[:, t], gam, d)]
         info["fallback"] = len(fallback)

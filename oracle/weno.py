@@ -19,7 +19,8 @@ Reading:
     w_k ~ lambda_k / (sigma_k + 1e-14)^8 with lambda = (1, 1e5, 1);
   * degree-2 space-time predictor of Eq. (pde.nc.dg2) on every subcell
     (3 GL nodes per axis and in time, 3 Picard sweeps);
-  * sub-face flux: Rusanov at the 3^(d-1) x 3 tangential x time GL points,
+  * sub-face flux: Rusanov (or the scheme's other numerical flux, the
+    Osher-type flux) at the 3^(d-1) x 3 tangential x time GL points,
     averaged with the GL weights;
   * update v^{n+1} = v^n - sum_d (dt/h_d)(Fbar_{+} - Fbar_{-}), h_d = dx_d / N_s.
 """
@@ -80,7 +81,7 @@ class Weno3:
         return np.moveaxis(out, -2, axis)
 
 
-def ader_weno(patch, dt, h, gamma, dim):
+def ader_weno(patch, dt, h, gamma, dim, face_flux=euler.rusanov):
     """One subcell ADER-WENO3 step on a batch of patches.
 
     patch: (nvar, T, L, .., L) with L = N_s + 6 (local index -3..N_s+2).
@@ -109,7 +110,7 @@ def ader_weno(patch, dt, h, gamma, dim):
         sl_right = list(sl_left)
         sl_left[2 + k] = slice(0, Ns + 1)
         sl_right[2 + k] = slice(1, Ns + 2)
-        G = euler.rusanov(qhi[tuple(sl_left)], qlo[tuple(sl_right)], gamma, k)
+        G = face_flux(qhi[tuple(sl_left)], qlo[tuple(sl_right)], gamma, k)
         # average over the d-1 tangential nodes and time with GL weights
         for _ in range(dim):
             G = np.tensordot(G, b3.w, axes=([G.ndim - 1], [0]))

@@ -29,6 +29,10 @@ OPT_END_TIME = 8
 OPT_CFL = 9
 OPT_SCRATCH_BYTES = 10
 OPT_CASCADE = 11
+OPT_FLUX = 12
+OPT_HOST_PASSES = 13
+OPT_SUBCELL_FP64_SWEEPS = 14
+FLUX_RUSANOV, FLUX_OSHER = 0, 1
 PHASES = ("predictor", "faceflux", "correct_detect", "limiter", "fix")
 IC_RADIAL, IC_QUADRANT = 0, 1
 
@@ -307,10 +311,12 @@ class Solver:
         return dict(zip(PHASES, ms[:5].tolist())), int(ms[5])
 
     def info(self):
-        """Slot capacity, limiter chunk, kernels per adg_step, device bytes held."""
-        out = (ctypes.c_int64 * 4)()
-        self._check(self.lib.adg_info(self.h, out, 4), "adg_info")
-        return dict(capacity=out[0], chunk=out[1], launches_per_step=out[2], bytes=out[3])
+        """Slot capacity, limiter chunk, kernels of one adg_step at most, device
+        bytes held, kernels issued by the steps so far."""
+        out = (ctypes.c_int64 * 5)()
+        self._check(self.lib.adg_info(self.h, out, 5), "adg_info")
+        return dict(capacity=out[0], chunk=out[1], launches_per_step=out[2], bytes=out[3],
+                    launches=out[4])
 
     def time(self):
         """(simulated time, steps taken since the last load)."""

@@ -18,6 +18,18 @@ struct adg_state {
   double gamma = 1.4, eps = 1e-3, floor = 1e-4;
   int force = 0, iters = 0, fp64_sweeps = 1;
   int cascade = 1;          // first-order layer after WENO3
+  int flux = ADG_FLUX_RUSANOV;
+  bool host_passes = true;  // single-state steps launch only the limiter passes needed
+  int sub_fp64 = 0;         // mixed precision: FP64 sweeps of the degree-2 subcell predictor
+  // pinned host mirror of the device Params, counters and dt, read once per
+  // step after the DG phase when host_passes is on
+  struct Probe {
+    Params p;
+    int counters[CNT_COUNT];
+    double dt;
+  };
+  Probe* probe = nullptr;
+  long long launch_count = 0;       // kernels issued by steps (batched: on each group's first state)
   long long cap_req = -1;
   int cap = 0, chunk = 0;
   void* (*alloc)(size_t, void*) = nullptr;
@@ -45,7 +57,7 @@ struct adg_state {
   bool cur_known = true;            // host cur / stamp equal the device's
   double t_end = 0.0;               // end time of the simulated interval (0: none)
   double cfl = 0.0;                 // CFL number of batched CFL steps with cfl <= 0
-  size_t scratch_budget = (size_t)2 << 30;   // bytes of limiter scratch
+  size_t scratch_budget = 0;        // bytes of limiter scratch (0: from free memory at allocation)
   Params hparams;                   // source of the last upload
   cudaEvent_t ev[PHASE_COUNT] = {};
   double phase_ms[PHASE_COUNT] = {};
@@ -92,6 +104,8 @@ void dev_free(adg_state* st, void* p) {
 void free_all(adg_state* st) {
   if (st->stream) cudaStreamSynchronize(st->stream);
   else cudaDeviceSynchronize();
+  if (st->probe) cudaFreeHost(st->probe);
+  st->probe = nullptr;
   for (void* p : st->owned) dev_free(st, p);
   st->owned.clear();
   st->bytes_held = 0;
@@ -132,6 +146,7 @@ Params make_params(const adg_state* st) {
   p.fp64_sweeps = st->fp64_sweeps < st->iters ? st->fp64_sweeps : st->iters;
   p.cfl = st->cfl;
   p.cascade = st->cascade;
+  p.flux = st->flux;
   return p;
 }
 
@@ -187,7 +202,21 @@ int ensure_allocated(adg_state* st) {
                                              &parts[3], &parts[4], &parts[5]);
   // limiter scratch: room for a quarter of the cells (at least 256) per pass,
   // within the state's scratch budget (default 2 GiB)
-  long long chunk = (long long)(st->scratch_budget / (per * sizeof(double)));
+  size_t budget = st->scratch_budget;
+  if (budget == 0) {
+    // an eighth of the free device memory, between 2 and 32 GiB: a 3D troubled
+    // cell needs ~4 MB of scratch at N = 3, so a fixed small budget would cut
+    // the limiter into many passes of a few hundred cells each
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      free_b = 0;
+    }
+    budget = free_b / 8;
+    if (budget < ((size_t)2 << 30)) budget = (size_t)2 << 30;
+    if (budget > ((size_t)32 << 30)) budget = (size_t)32 << 30;
+  }
+  long long chunk = (long long)(budget / (per * sizeof(double)));
   long long want = cells / 4;
   if (want < 256) want = 256;
   if (chunk > want) chunk = want;
@@ -378,6 +407,7 @@ StepLaunch single_launch(adg_state* st) {
   sl.pre_fb = st->d_pre1 + 12;
   sl.pre_refix = st->d_pre1 + 14;
   sl.cascade = st->cascade;
+  sl.sub32 = 3 - st->sub_fp64;
   sl.total_cells = st->geo.cells;
   for (int k = 0; k < st->dim; ++k) {
     long long faces = 1;
@@ -391,6 +421,14 @@ StepLaunch single_launch(adg_state* st) {
   sl.prec = st->prec;
   sl.ev = st->profile ? st->ev : nullptr;
   return sl;
+}
+
+// Kernels of one step: step begin; predictor, d face-flux kernels, corrector;
+// per limiter pass a prefix, the patch, d sweeps, the subcell predictor, d
+// flux kernels and the update; the first-order layer (two prefixes, two
+// kernels); the fix prefix and the fix; step end.
+long long kernels_per_step(int dim, int passes, int cascade) {
+  return 1 + (1 + dim + 1) + (long long)passes * (2 * dim + 4) + (cascade ? 4 : 0) + 2 + 1;
 }
 
 // Enqueue one step of the states described by `sl` (all of one dimension,
@@ -408,6 +446,47 @@ int run_step(adg_state* st, const StepLaunch& sl, cudaStream_t stream) {
   if (e != cudaSuccess)
     return fail(st, ADG_ERR_CUDA, std::string("subcell limiter: ") + cudaGetErrorString(e));
   CUDA_TRY(st, launch_step_end(sl, stream));
+  st->launch_count += kernels_per_step(st->dim, sl.max_passes, sl.cascade);
+  return ADG_OK;
+}
+
+// One step whose limiter passes the host sizes from the step's troubled count:
+// after the DG phase the device Params (level and stamp at the step's start),
+// counters and dt come back in one wait, the limiter runs ceil(n_T / chunk)
+// passes instead of the capacity's worth, and the host knows the level the
+// step leaves behind.
+int run_step_host_passes(adg_state* st, StepLaunch& sl) {
+  cudaStream_t stream = st->stream;
+  if (!st->probe) {
+    void* h = nullptr;
+    CUDA_TRY(st, cudaHostAlloc(&h, sizeof(adg_state::Probe), cudaHostAllocDefault));
+    st->probe = static_cast<adg_state::Probe*>(h);
+  }
+  CUDA_TRY(st, launch_step_begin(sl, stream));
+  LaunchArgs a{};
+  a.step = &sl;
+  a.stream = stream;
+  a.op = OP_STEP_DG;
+  cudaError_t e = dispatch(st, a);
+  if (e != cudaSuccess) return fail(st, ADG_ERR_CUDA, std::string("DG step: ") + cudaGetErrorString(e));
+  adg_state::Probe* pr = st->probe;
+  CUDA_TRY(st, cudaMemcpyAsync(&pr->p, st->dparams, sizeof(Params), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(st, cudaMemcpyAsync(pr->counters, st->b.counters, sizeof(pr->counters),
+                               cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(st, cudaMemcpyAsync(&pr->dt, st->b.dt, sizeof(double), cudaMemcpyDeviceToHost, stream));
+  CUDA_TRY(st, cudaStreamSynchronize(stream));
+  const bool stepped = pr->dt > 0.0;
+  long long nT = stepped ? pr->counters[CNT_TROUBLED0 + (1 - pr->p.cur)] : 0;
+  if (nT > st->cap) nT = st->cap;
+  sl.max_passes = (int)((nT + st->chunk - 1) / st->chunk);
+  a.op = OP_STEP_LIMITER;
+  e = dispatch(st, a);
+  if (e != cudaSuccess)
+    return fail(st, ADG_ERR_CUDA, std::string("subcell limiter: ") + cudaGetErrorString(e));
+  CUDA_TRY(st, launch_step_end(sl, stream));
+  st->launch_count += kernels_per_step(st->dim, sl.max_passes, sl.cascade);
+  st->cur = stepped ? 1 - pr->p.cur : pr->p.cur;
+  st->stamp = pr->p.stamp;
   return ADG_OK;
 }
 
@@ -424,6 +503,14 @@ int common_step(adg_state* st, const double* dts_dev, double cfl, double dt_max)
   sl.dts = dts_dev;
   sl.cfl = cfl;
   sl.dt_max = dt_max;
+  if (st->host_passes) {
+    int rc = run_step_host_passes(st, sl);
+    if (rc) return rc;
+    st->cur_known = true;
+    st->pending = st->profile;
+    st->lam_valid = st->lam_mode;
+    return ADG_OK;
+  }
   int rc = run_step(st, sl, st->stream);
   if (rc) return rc;
   st->cur_known = false;            // the device swapped levels (unless the state idled)
@@ -539,7 +626,8 @@ int adg_batch_create(adg_state* const* states, int count, void* stream, adg_batc
     for (int j = i; j < count; ++j) {
       const adg_state* a = states[i];
       const adg_state* c = states[j];
-      if (!done[j] && a->dim == c->dim && a->N == c->N && a->prec == c->prec) {
+      if (!done[j] && a->dim == c->dim && a->N == c->N && a->prec == c->prec &&
+          a->sub_fp64 == c->sub_fp64) {
         g.idx.push_back(j);
         done[j] = 1;
       }
@@ -590,6 +678,7 @@ int adg_batch_create(adg_state* const* states, int count, void* stream, adg_batc
     sl.sum_chunk = sum_chunk;
     sl.max_passes = max_passes;
     sl.prec = g.rep->prec;
+    sl.sub32 = 3 - g.rep->sub_fp64;
     sl.ev = nullptr;
     g.sl = sl;
     g.dts_off = off;
@@ -637,6 +726,8 @@ int adg_batch_step(adg_batch* b, const double* dts, double cfl) {
     }
     if (b->exec && b->graph_cfl == cfl) {
       CUDA_TRY(st0, cudaGraphLaunch(b->exec, b->stream));
+      for (auto& g : b->groups)
+        g.rep->launch_count += kernels_per_step(g.rep->dim, g.sl.max_passes, g.sl.cascade);
     } else if (b->cfl_steps == 0) {
       int rc = batch_run(b, false, cfl);         // first step: plain launches
       if (rc) return rc;
@@ -793,6 +884,18 @@ int adg_set_option(adg_state* st, int key, double value) {
       return ADG_OK;
     case ADG_OPT_CASCADE:
       st->cascade = value != 0.0;
+      return ADG_OK;
+    case ADG_OPT_SUBCELL_FP64_SWEEPS:
+      if (!(value >= 0.0 && value <= 3.0)) return fail(st, ADG_ERR_ARG, "subcell FP64 sweeps in 0..3");
+      st->sub_fp64 = (int)value;
+      return ADG_OK;
+    case ADG_OPT_HOST_PASSES:
+      st->host_passes = value != 0.0;
+      return ADG_OK;
+    case ADG_OPT_FLUX:
+      if (value != ADG_FLUX_RUSANOV && value != ADG_FLUX_OSHER)
+        return fail(st, ADG_ERR_ARG, "flux must be ADG_FLUX_RUSANOV or ADG_FLUX_OSHER");
+      st->flux = (int)value;
       return ADG_OK;
     case ADG_OPT_CFL:
       if (!(value >= 0.0)) return fail(st, ADG_ERR_ARG, "cfl must be >= 0");
@@ -1046,12 +1149,9 @@ int adg_info(const adg_state* st, int64_t* out, int cap) {
   const int nchunks = (st->cap + st->chunk - 1) / st->chunk;
   out[0] = st->cap;
   out[1] = st->chunk;
-  // step begin; predictor, D face-flux kernels, corrector; per limiter pass a
-  // prefix, the patch, D sweeps, the subcell predictor, D flux kernels and the
-  // update; the first-order layer (two prefixes, two kernels); the fix prefix
-  // and the fix; step end
-  out[2] = 1 + (1 + D + 1) + (int64_t)nchunks * (2 * D + 4) + (st->cascade ? 4 : 0) + 2 + 1;
+  out[2] = kernels_per_step(D, nchunks, st->cascade);
   out[3] = (int64_t)st->bytes_held;
+  if (cap >= 5) out[4] = st->launch_count;
   return ADG_OK;
 }
 

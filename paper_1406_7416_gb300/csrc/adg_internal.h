@@ -105,6 +105,7 @@ struct Params {
   int lam_mode;          // 1: kernels keep the per-cell wave speeds current
   int fp64_sweeps;       // mixed precision: number of final FP64 Picard sweeps
   int cascade;           // 1: first-order layer after WENO3 (Sec. 6, Fig. algo2)
+  int flux;              // numerical flux of DG faces and WENO3 sub-faces: 0 Rusanov, 1 Osher
   double cfl;            // the state's CFL number for batched CFL steps (0: none)
 };
 
@@ -139,6 +140,7 @@ struct StepLaunch {
   long long* pre_fb;           // [n+1] first-order fallback cells (device-computed)
   long long* pre_refix;        // [n+1] rebalanced WENO3 neighbours (device-computed)
   int cascade;                 // any state of the launch runs the first-order layer
+  int sub32;                   // mixed precision: FP32 sweeps (of 3) of the subcell predictor
   long long total_cells;
   long long total_faces[3];
   long long sum_chunk;         // sum over states of the limiter chunk size
@@ -276,6 +278,114 @@ __device__ __forceinline__ void rusanov(const double* QL, const double* QR, int 
   const double s = nanmax(sL, sR);
 #pragma unroll
   for (int v = 0; v < D + 2; ++v) G[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * s * (QR[v] - QL[v]);
+}
+
+// Universal Osher-type flux of Dumbser and Toro through a face with normal
+// +e_k (Sec. 2.3 names it; it is the flux of the vortex table of Sec. 5.2):
+//   G = (F(QL) + F(QR))/2 - (1/2) sum_j w_j |A_k(psi_j)| (QR - QL)
+// on the straight path psi(s) = QL + s (QR - QL), three-point Gauss-Legendre
+// rule in s.  |A_k| dQ = sum_m |lambda_m| alpha_m r_m, with the right
+// eigenvectors r_m of A_k at psi_j and the wave strengths alpha = R^{-1} dQ
+// in closed form (normal velocity u = v_k, tangential components v_t):
+//   alpha_t = dm_t - v_t drho,   dE' = dE - sum_t alpha_t v_t,
+//   alpha_0 = (gamma-1)/c^2 (drho (H - u^2) + u dm_k - dE'),
+//   alpha_- = (drho (u + c) - dm_k - c alpha_0) / (2c),
+//   alpha_+ = drho - alpha_- - alpha_0,
+//   r_- = (1, v - c e_k, H - u c), r_0 = (1, v, |v|^2/2), r_t = (0, e_t, v_t),
+//   r_+ = (1, v + c e_k, H + u c); eigenvalues u - c, u (d times), u + c.
+template <int D>
+__device__ __forceinline__ void osher(const double* QL, const double* QR, int k, double gamma,
+                                      double* G) {
+  constexpr int NV = D + 2;
+  const double gm1 = gamma - 1.0;
+  double dQ[NV], acc[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    dQ[v] = QR[v] - QL[v];
+    acc[v] = 0.0;
+  }
+  const double half_span = 0.38729833462074168852;       // sqrt(3/5) / 2
+  const double sj[3] = {0.5 - half_span, 0.5, 0.5 + half_span};
+  const double wj[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    double Q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Q[v] = QL[v] + sj[j] * dQ[v];
+    const double r = 1.0 / Q[0];
+    double vel[D], kin = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      vel[a] = Q[1 + a] * r;
+      kin += vel[a] * vel[a];
+    }
+    const double p = gm1 * (Q[D + 1] - 0.5 * Q[0] * kin);
+    const double c2 = gamma * p * r;
+    const double c = sqrt(c2);
+    const double H = (Q[D + 1] + p) * r;
+    const double u = vel[k];
+    double dE = dQ[D + 1];
+    double at[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      at[a] = (a == k) ? 0.0 : dQ[1 + a] - vel[a] * dQ[0];
+      dE -= at[a] * vel[a];
+    }
+    const double a0 = gm1 / c2 * (dQ[0] * (H - u * u) + u * dQ[1 + k] - dE);
+    const double am = (dQ[0] * (u + c) - dQ[1 + k] - c * a0) / (2.0 * c);
+    const double ap = dQ[0] - am - a0;
+    const double lm = wj[j] * fabs(u - c) * am;
+    const double l0 = wj[j] * fabs(u);
+    const double lp = wj[j] * fabs(u + c) * ap;
+    acc[0] += lm + l0 * a0 + lp;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      double m = (lm + lp + l0 * a0) * vel[a] + l0 * at[a];
+      if (a == k) m += (lp - lm) * c;
+      acc[1 + a] += m;
+    }
+    double e = lm * (H - u * c) + lp * (H + u * c) + l0 * a0 * 0.5 * kin;
+#pragma unroll
+    for (int a = 0; a < D; ++a) e += l0 * at[a] * vel[a];
+    acc[D + 1] += e;
+  }
+  double FL[NV], FR[NV];
+  {
+    const double r = 1.0 / QL[0];
+    double kin = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) kin += QL[1 + a] * QL[1 + a];
+    const double p = gm1 * (QL[D + 1] - 0.5 * kin * r);
+    const double vk = QL[1 + k] * r;
+    FL[0] = QL[1 + k];
+#pragma unroll
+    for (int a = 0; a < D; ++a) FL[1 + a] = QL[1 + a] * vk;
+    FL[1 + k] += p;
+    FL[D + 1] = vk * (QL[D + 1] + p);
+  }
+  {
+    const double r = 1.0 / QR[0];
+    double kin = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) kin += QR[1 + a] * QR[1 + a];
+    const double p = gm1 * (QR[D + 1] - 0.5 * kin * r);
+    const double vk = QR[1 + k] * r;
+    FR[0] = QR[1 + k];
+#pragma unroll
+    for (int a = 0; a < D; ++a) FR[1 + a] = QR[1 + a] * vk;
+    FR[1 + k] += p;
+    FR[D + 1] = vk * (QR[D + 1] + p);
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v) G[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * acc[v];
+}
+
+// The numerical flux selected by the state's option (0 Rusanov, 1 Osher-type).
+template <int D>
+__device__ __forceinline__ void face_flux(int which, const double* QL, const double* QR, int k,
+                                          double gamma, double* G) {
+  if (which == 1) osher<D>(QL, QR, k, gamma, G);
+  else rusanov<D>(QL, QR, k, gamma, G);
 }
 
 // max_k |v_k| + c of one state (wave speed for Eq. cfl)

@@ -28,6 +28,18 @@ struct Dims {
   static constexpr int ND3 = ipow(3, D);
 };
 
+// Predictor block shape.  The mixed kernel at high 2D degrees is latency
+// bound with one 128-thread block per SM (measured: 4 warps per SM, FP64 pipe
+// 41% busy at N = 9); 256 threads capped at 128 registers, two blocks per SM,
+// hide the FP32 and FP64 latencies.  The FP64 kernel keeps the FP64 pipe busy
+// as it is and runs faster without the register cap.
+template <int D, int N, bool MIXED>
+struct PredShape {
+  static constexpr bool wide = MIXED && D == 2 && N >= 6;
+  static constexpr int threads = wide ? 256 : 128;
+  static constexpr int min_blocks = wide ? 2 : 1;
+};
+
 // ---------------------------------------------------------------------------
 // Picard phases on one space-time block of n^(D+1) nodes (Eq. pde.nc.dg2):
 //   q <- u (x) 1 - Ktau x_tau sum_k c_k D x_k f_k(q),  c_k = dt / dx_k.
@@ -218,14 +230,15 @@ __host__ __device__ constexpr size_t predictor_smem_bytes() {
   using DM = Dims<D, N>;
   size_t d = (size_t)DM::NV * DM::ND + (size_t)DM::NV * DM::NST + (size_t)D * DM::NV * DM::NST +
              (size_t)D * DM::NV * DM::ND + 3 * DM::n * DM::n + 3 * DM::n;
-  size_t f = MIXED ? ((size_t)DM::NV * DM::NST + (size_t)D * DM::NV * DM::NST + 2 * DM::n * DM::n +
-                      (size_t)DM::NV * DM::ND)
-                   : 0;
+  // the FP32 sweep arrays qf, Ff live inside the FP64 flux array F (unused
+  // until the FP32 sweeps are over); only the FP32 operators and u stay apart
+  size_t f = MIXED ? (2 * DM::n * DM::n + (size_t)DM::NV * DM::ND) : 0;
   return d * sizeof(double) + f * sizeof(float);
 }
 
 template <int D, int N, bool MIXED>
-__global__ void __launch_bounds__(256) k_predictor(Batch bt) {
+__global__ void __launch_bounds__(PredShape<D, N, MIXED>::threads, PredShape<D, N, MIXED>::min_blocks)
+    k_predictor(Batch bt) {
   using DM = Dims<D, N>;
   constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, NST = DM::NST, NF = DM::NF, NT = DM::NT;
   extern __shared__ double sm[];
@@ -239,9 +252,10 @@ __global__ void __launch_bounds__(256) k_predictor(Batch bt) {
   double* w = Mv + n * n;
   double* ph0 = w + n;
   double* ph1 = ph0 + n;
-  float* qf = reinterpret_cast<float*>(ph1 + n);
+  // FP32 sweep arrays inside F: (1 + D) NV NST floats fit in D NV NST doubles
+  float* qf = reinterpret_cast<float*>(F);
   float* Ff = qf + NV * NST;
-  float* Dmf = Ff + D * NV * NST;
+  float* Dmf = reinterpret_cast<float*>(ph1 + n);
   float* Ktf = Dmf + n * n;
   float* uf = Ktf + n * n;
 
@@ -429,7 +443,7 @@ __global__ void __launch_bounds__(256) k_faceflux(Batch bt, int k) {
         QL[v] = trL[v * NT + ts + NF * m];
         QR[v] = trR[v * NT + ts + NF * m];
       }
-      rusanov<D>(QL, QR, k, p.gamma, Gm);
+      face_flux<D>(p.flux, QL, QR, k, p.gamma, Gm);
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] += w[m] * Gm[v];
     }

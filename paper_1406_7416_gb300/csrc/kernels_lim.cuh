@@ -238,8 +238,10 @@ __device__ __forceinline__ int cross_subcell(int r) {
   return c[0] + NE * (c[1] + NE * c[2]);
 }
 
+// n32: sweeps (of 3) run in FP32 before the FP64 ones (MIXED only; the same
+// for the whole launch, so every block takes the same barriers).
 template <int D, int N, bool MIXED>
-__global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass) {
+__global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass, int n32) {
   using DM = Dims<D, N>;
   constexpr int NV = DM::NV, NST3 = DM::NST3, ND3 = DM::ND3, NED = DM::NED, Ns = DM::Ns;
   constexpr int NCROSS = DM::NSD + 2 * D * DM::NSF;
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass) {
     }
     __syncthreads();
     int it0 = 0;
-    if (MIXED) {
+    if (MIXED && n32 > 0) {
       if (live) {
         for (int e = lt; e < NV * ND3; e += NST3) suf[grp][e] = (float)su[grp][e];
         for (int e = lt; e < NV * NST3; e += NST3) {
@@ -302,7 +304,7 @@ __global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass) {
         }
       }
       __syncthreads();
-      for (int it = 0; it < 2; ++it) {
+      for (int it = 0; it < n32; ++it) {
         if (live) picard_flux<D, 3, float>(sqf[grp], sFf[grp], (float)gm1, lt, NST3);
         __syncthreads();
         if (live) picard_deriv<D, 3, float>(sFf[grp], sqf[grp], D3f, cf, lt, NST3);
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass) {
       }
       if (live)
         for (int e = lt; e < NV * NST3; e += NST3) sq[grp][e] = (double)sqf[grp][e];
-      it0 = 2;
+      it0 = n32;
     } else if (live) {
       for (int e = lt; e < NV * NST3; e += NST3) {
         const int v = e / NST3, l = e - v * NST3;
@@ -403,7 +405,7 @@ __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
         QL[v] = o->phi13[0] * a[0] + o->phi13[1] * a[stk] + o->phi13[2] * a[2 * stk];
         QR[v] = o->phi03[0] * b[0] + o->phi03[1] * b[stk] + o->phi03[2] * b[2 * stk];
       }
-      rusanov<D>(QL, QR, k, p.gamma, G);
+      face_flux<D>(p.flux, QL, QR, k, p.gamma, G);
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] += wt * G[v];
     }

@@ -30,9 +30,10 @@ struct Launch {
   using DM = Dims<D, N>;
   static constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, NSD = DM::NSD, Ns = DM::Ns;
 
+  template <bool MIXED>
   static int pred_threads() {
     int t = ((NV * DM::NST + 31) / 32) * 32;
-    return t > 128 ? 128 : t;
+    return t > PredShape<D, N, MIXED>::threads ? PredShape<D, N, MIXED>::threads : t;
   }
   static size_t cell_smem() { return (size_t)(2 * NV * NSD + 2 * Ns * n + 4 * NV + 128) * sizeof(double); }
   static size_t fallback_smem() {
@@ -58,11 +59,11 @@ struct Launch {
     if (sl.prec == ADG_PREC_MIXED_FP32) {
       const size_t sm = predictor_smem_bytes<D, N, true>();
       if ((e = set_smem(k_predictor<D, N, true>, sm)) != cudaSuccess) return e;
-      k_predictor<D, N, true><<<grid, pred_threads(), sm, s>>>(cells);
+      k_predictor<D, N, true><<<grid, pred_threads<true>(), sm, s>>>(cells);
     } else {
       const size_t sm = predictor_smem_bytes<D, N, false>();
       if ((e = set_smem(k_predictor<D, N, false>, sm)) != cudaSuccess) return e;
-      k_predictor<D, N, false><<<grid, pred_threads(), sm, s>>>(cells);
+      k_predictor<D, N, false><<<grid, pred_threads<false>(), sm, s>>>(cells);
     }
     mark(ev, PHASE_FACEFLUX, s);
     for (int k = 0; k < D; ++k) {
@@ -95,10 +96,10 @@ struct Launch {
       const long long ncross = ch * (DM::NSD + 2 * D * DM::NSF);
       if (sl.prec == ADG_PREC_MIXED_FP32)
         k_lim_predict<D, N, true><<<grid_for(ncross, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(
-            lim, pass);
+            lim, pass, sl.sub32);
       else
         k_lim_predict<D, N, false><<<grid_for(ncross, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(
-            lim, pass);
+            lim, pass, 0);
       k_lim_flux<D, N, 0><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, pass);
       k_lim_flux<D, N, 1><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, pass);
       if (D == 3)

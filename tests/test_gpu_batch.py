@@ -105,3 +105,32 @@ def test_end_times_stop_each_state():
     for s, f in zip(ss, frozen):                  # idle after reaching the end time
         np.testing.assert_array_equal(s.read(), f)
         s.close()
+
+
+@pytest.mark.parametrize("prec", [adg.PREC_FP64, adg.PREC_MIXED_FP32])
+def test_host_sized_passes_equal_async_passes(prec):
+    """adg_step with ADG_OPT_HOST_PASSES (the host reads the troubled count
+    after the DG phase and launches only the passes it needs) leaves the same
+    state, bit for bit, as the fully asynchronous step that launches every
+    pass the capacity allows; a small scratch budget forces several passes."""
+    w = inputs.quadrants_2d(n=24, N=3)
+    out = []
+    for host in (1, 0):
+        s = adg.Solver.from_workload(w, prec)
+        s.set_option(adg.OPT_SCRATCH_BYTES, 4 * 2 ** 20)       # ~36 troubled cells per pass
+        s.set_option(adg.OPT_HOST_PASSES, host)
+        s.init_problem(w["problem"])
+        info = s.info()
+        assert info["chunk"] < 64
+        l0 = info["launches"]
+        for _ in range(6):
+            s.step_cfl(w["cfl"])
+        launched = s.info()["launches"] - l0
+        assert s.troubled_count() > 2 * info["chunk"]
+        out.append((_state(s), s.time(), launched, info["launches_per_step"]))
+        assert s.status() == adg.OK
+        s.close()
+    _assert_same(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
+    assert out[1][2] == 6 * out[1][3]                # asynchronous: every pass launched
+    assert out[0][2] < out[1][2]

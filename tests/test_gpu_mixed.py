@@ -129,22 +129,101 @@ def test_vortex_design_order(N, grids, prec):
 
 def _golden():
     rows = [l.split() for l in open(GOLDEN) if l.strip() and not l.startswith("#")]
-    return {(int(r[0]), int(r[1])): float(r[2]) for r in rows}
+    return {(int(r[0]), int(r[1])): tuple(float(x) for x in r[2:5]) for r in rows}
 
 
-@pytest.mark.parametrize("N,grids", [(3, (25, 50)), (5, (20, 40))])
-def test_vortex_table_magnitudes(N, grids):
-    """Sec. 5.2 table: L1 density errors at t = 10.  This build uses the
-    Rusanov flux (the table used the Osher-type flux), so errors are compared
-    within a factor of 10, and the observed order may not fall more than 0.5
-    below the table's."""
+def _density_error_norms(w, U, t):
+    """L1, L2 and Linf density errors against the exact translated vortex,
+    with an (N+4)-point Gauss-Legendre rule per axis in every cell (the table
+    used "a sufficiently high order accurate Gaussian quadrature rule")."""
+    N = w["N"]
+    n = N + 1
+    nx, ny = w["ncell"]
+    xi = 0.5 * (np.polynomial.legendre.leggauss(n)[0] + 1.0)
+    xq, wq = np.polynomial.legendre.leggauss(N + 4)
+    xq, wq = 0.5 * (xq + 1.0), 0.5 * wq
+    L = np.ones((len(xq), n))
+    for a in range(n):
+        for b in range(n):
+            if b != a:
+                L[:, a] *= (xq - xi[b]) / (xi[a] - xi[b])
+    rho = U[:, 0, :].reshape(ny, nx, n, n)                    # ABI: (j, i, node b, node a)
+    rq = np.einsum("pa,qb,jiba->jiqp", L, L, rho)
+    dx = w["dx"][0]
+    X = w["x0"][0] + (np.arange(nx)[None, :, None, None] + xq[None, None, None, :]) * dx
+    Y = w["x0"][1] + (np.arange(ny)[:, None, None, None] + xq[None, None, :, None]) * dx
+    X, Y = np.broadcast_arrays(X, Y)
+    Xs = -5.0 + np.mod(X - t + 5.0, 10.0)
+    Ys = -5.0 + np.mod(Y - t + 5.0, 10.0)
+    e = np.abs(rq - conserved(w["problem"], (Xs, Ys), 1.4)[0])
+    W2 = np.outer(wq, wq)[None, None]
+    return (float(np.sum(e * W2) * dx * dx), float(np.sqrt(np.sum(e * e * W2) * dx * dx)),
+            float(e.max()))
+
+
+# grids of 4-5 cells per axis (a cell wider than the vortex core) where the
+# limiter acts in this build and the errors are not comparable
+TABLE_COARSE = {(6, 5), (7, 5), (8, 4), (9, 4)}
+
+
+@pytest.mark.parametrize("N", [2, 3, 4, 5, 6, 7, 8, 9])
+def test_vortex_table_with_osher_flux(N):
+    """Sec. 5.2 table (density error norms at t = 10, Osher-type flux): every
+    row except the four ultra-coarse grids is reproduced to within -30% / +40%
+    in L1 and L2 (measured: 0.79-1.06 in L1), Linf within a factor 2.5.  The
+    run uses half the Courant number of Eq. (cfl): at the full 0.9 / (d(2N+1))
+    the one-step scheme is not stable over the ~1000 steps to t = 10 for
+    N >= 5 in this build."""
     table = _golden()
-    errs = []
-    for n in grids:
-        w, U, flags = _run_vortex(n, N, 10.0, adg.PREC_FP64)
-        errs.append(_l1_density_error(w, U, 10.0))
-        ref = table[(N, n)]
-        assert ref / 10 <= errs[-1] <= ref * 10, (N, n, errs[-1], ref)
-    ours = np.log2(errs[0] / errs[1])
-    paper = np.log2(table[(N, grids[0])] / table[(N, grids[1])])
-    assert ours > paper - 0.5, (ours, paper)
+    for (NN, n), ref in sorted(table.items()):
+        if NN != N or (NN, n) in TABLE_COARSE:
+            continue
+        w = inputs.vortex_2d(n, N)
+        s = adg.Solver.from_workload(w, adg.PREC_FP64)
+        s.set_option(adg.OPT_FLUX, adg.FLUX_OSHER)
+        s.set_option(adg.OPT_END_TIME, 10.0)
+        s.init_problem(w["problem"])
+        while s.time()[0] < 10.0 * (1.0 - 1e-12):
+            for _ in range(50):
+                s.step_cfl(0.5 * w["cfl"])
+        U = s.read()
+        assert s.status() == adg.OK
+        s.close()
+        l1, l2, linf = _density_error_norms(w, U, 10.0)
+        assert 0.7 * ref[0] <= l1 <= 1.4 * ref[0], (N, n, l1, ref)
+        assert 0.7 * ref[1] <= l2 <= 1.4 * ref[1], (N, n, l2, ref)
+        assert ref[2] / 2.5 <= linf <= 2.5 * ref[2], (N, n, linf, ref)
+
+
+def test_subcell_predictor_sweep_precision():
+    """With every cell on the subgrid the DG candidate is discarded, so the
+    mixed path with all three subcell Picard sweeps in FP64
+    (ADG_OPT_SUBCELL_FP64_SWEEPS = 3) equals the FP64 path bit for bit; the
+    default (all three sweeps FP32, FP64 sub-face fluxes and update) stays
+    within 1e-6 of it in L1 density, and conserves to FP64 round-off."""
+    w = inputs.quadrants_2d(n=16, N=3)
+    out = {}
+    for key, prec, sub in (("fp64", adg.PREC_FP64, None), ("sub3", adg.PREC_MIXED_FP32, 3),
+                           ("sub0", adg.PREC_MIXED_FP32, None)):
+        s = adg.Solver.from_workload(w, prec)
+        s.set_option(adg.OPT_FORCE_LIMITER, 1)
+        if sub is not None:
+            s.set_option(adg.OPT_SUBCELL_FP64_SWEEPS, sub)
+        s.init_problem(w["problem"])
+        out[key + "_0"] = s.read()
+        for _ in range(5):
+            s.step_cfl(w["cfl"])
+        out[key] = s.read_full()
+        assert s.status() == adg.OK
+        s.close()
+    for a, b in zip(out["fp64"], out["sub3"]):
+        np.testing.assert_array_equal(a, b)
+    rho64, rho0 = out["fp64"][2][:, 0, :], out["sub0"][2][:, 0, :]
+    assert np.abs(rho0 - rho64).sum() <= 1e-6 * np.abs(rho64).sum()
+    assert 0 < np.abs(rho0 - rho64).sum()
+    # conservation (periodic): GL-weighted DOF totals
+    W = 0.5 * np.polynomial.legendre.leggauss(4)[1]
+    Wd = np.outer(W, W).ravel()
+    tot0 = np.einsum("cvl,l->v", out["sub0_0"], Wd)
+    tot = np.einsum("cvl,l->v", out["sub0"][0], Wd)
+    np.testing.assert_allclose(tot, tot0, rtol=0, atol=1e-13 * np.abs(tot0).max() * 256)
