@@ -36,8 +36,11 @@ struct Dims {
 template <int D, int N, bool MIXED>
 struct PredShape {
   static constexpr bool wide = MIXED && D == 2 && N >= 6;
-  static constexpr int threads = wide ? 256 : 128;
-  static constexpr int min_blocks = wide ? 2 : 1;
+  static constexpr int threads = wide ? 256 : 128;      // launched per block
+  static constexpr int bound = 256;                      // __launch_bounds__ maximum
+  // <= 128 registers (two 256-thread or four 128-thread blocks per SM), except
+  // the FP64 kernel at 2D N >= 6, which would spill under that cap
+  static constexpr int min_blocks = (!MIXED && D == 2 && N >= 6) ? 1 : 2;
 };
 
 // ---------------------------------------------------------------------------
@@ -237,7 +240,7 @@ __host__ __device__ constexpr size_t predictor_smem_bytes() {
 }
 
 template <int D, int N, bool MIXED>
-__global__ void __launch_bounds__(PredShape<D, N, MIXED>::threads, PredShape<D, N, MIXED>::min_blocks)
+__global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N, MIXED>::min_blocks)
     k_predictor(Batch bt) {
   using DM = Dims<D, N>;
   constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, NST = DM::NST, NF = DM::NF, NT = DM::NT;
