@@ -7,8 +7,10 @@ Sec. 4.3:
   NAD  Eq. (dmp): componentwise  m_i - delta <= v* <= M_i + delta  on every
        subcell, where m_i / M_i are the min / max of the subcell data v^n over
        the Voronoi neighbourhood V_i (the cell and every cell sharing a node
-       with it: the 3^d block; wrapped at periodic boundaries, cells outside a
-       transmissive boundary are left out).
+       with it: the 3^d block; wrapped at periodic boundaries; at a reflective
+       wall the mirror images of the cells across it take part, with their
+       wall-normal momentum bounds negated and swapped; cells outside a
+       transmissive or inflow boundary are left out).
   Eq. (relax): delta = eps (M - m), eps = 1e-3.  Reading: a floor is added,
        delta = max(eps (M - m), floor * max(1, |M|, |m|)) with floor = 1e-4.
        The literal Eq. (relax) (floor = 0), or a round-off-only floor such as
@@ -23,33 +25,43 @@ Sec. 4.3:
 import numpy as np
 
 from . import euler
+from .dg import REFLECTIVE
 
 EPS = 1e-3
 FLOOR = 1e-4
 
 
-def _shift_pad(a, grid, fill):
-    """Pad every cell axis (axes 1..d) by one cell: wrap if periodic, `fill` if
-    transmissive (fill = +inf / -inf excludes the outside cell from a min / max)."""
-    out = a
+def _shift_pad(amin, amax, grid):
+    """Pad every cell axis (axes 1..d) of the per-cell minima / maxima by one
+    cell: wrap if periodic; at a reflective wall the mirror image of the
+    boundary cell (its wall-normal momentum bounds negated and swapped);
+    otherwise +inf / -inf, which leaves the outside cell out of V_i.  Axes are
+    padded in order, so corner images combine the axes' rules."""
+    pmin, pmax = amin, amax
     for k in range(grid.dim):
         ax = 1 + k
-        if grid.periodic(k):
-            lo = np.take(out, [-1], axis=ax)
-            hi = np.take(out, [0], axis=ax)
-        else:
-            shp = list(out.shape)
-            shp[ax] = 1
-            lo = np.full(shp, fill)
-            hi = np.full(shp, fill)
-        out = np.concatenate([lo, out, hi], axis=ax)
-    return out
+        pads = []
+        for side, i in ((-1, 0), (1, -1)):
+            kind = grid.kind(k, side)
+            if grid.periodic(k):
+                j = -1 if side < 0 else 0
+                lo, hi = np.take(pmin, [j], axis=ax), np.take(pmax, [j], axis=ax)
+            elif kind == REFLECTIVE:
+                lo, hi = np.take(pmin, [i], axis=ax).copy(), np.take(pmax, [i], axis=ax).copy()
+                lo[1 + k], hi[1 + k] = -hi[1 + k], -lo[1 + k]
+            else:
+                shp = list(pmin.shape)
+                shp[ax] = 1
+                lo, hi = np.full(shp, np.inf), np.full(shp, -np.inf)
+            pads.append((lo, hi))
+        pmin = np.concatenate([pads[0][0], pmin, pads[1][0]], axis=ax)
+        pmax = np.concatenate([pads[0][1], pmax, pads[1][1]], axis=ax)
+    return pmin, pmax
 
 
 def neighbourhood_bounds(cmin, cmax, grid):
     """(m, M) over V_i from per-cell minima / maxima (shape (nvar, cells...))."""
-    pmin = _shift_pad(cmin, grid, np.inf)
-    pmax = _shift_pad(cmax, grid, -np.inf)
+    pmin, pmax = _shift_pad(cmin, cmax, grid)
     m = np.full(cmin.shape, np.inf)
     M = np.full(cmax.shape, -np.inf)
     d = grid.dim

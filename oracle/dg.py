@@ -31,24 +31,57 @@ from . import euler
 
 PERIODIC = 0
 TRANSMISSIVE = 1
+REFLECTIVE = 2
+INFLOW = 3
 
 
 class Grid:
     """Cartesian grid: cells per axis, lower corner, spacing, and boundary kind
-    per face (bc[2k] low side, bc[2k+1] high side of axis k)."""
+    per face (bc[2k] low side, bc[2k+1] high side of axis k); `states` gives the
+    conserved state of every INFLOW face (dict face -> vector).
 
-    def __init__(self, ncell, x0, dx, bc):
+    Boundary kinds (the paper's tests name periodic, transmissive/outflow,
+    reflecting-wall and inflow/Dirichlet boundaries without formulas; the
+    ghost rules are this oracle's reading):
+      PERIODIC      wrap;
+      TRANSMISSIVE  the ghost copies the interior (zero-gradient);
+      REFLECTIVE    the ghost is the mirror image with the wall-normal momentum
+                    negated;
+      INFLOW        the ghost is the face's fixed state."""
+
+    def __init__(self, ncell, x0, dx, bc, states=None):
         self.dim = len(ncell)
         self.ncell = tuple(int(c) for c in ncell)
         self.x0 = tuple(float(v) for v in x0)
         self.dx = tuple(float(v) for v in dx)
         self.bc = tuple(int(b) for b in bc)
+        self.states = {int(f): np.asarray(q, dtype=np.float64) for f, q in (states or {}).items()}
         for k in range(self.dim):
             if (self.bc[2 * k] == PERIODIC) != (self.bc[2 * k + 1] == PERIODIC):
                 raise ValueError("periodic boundaries must come in pairs")
+        for f, b in enumerate(self.bc):
+            if b == INFLOW and f not in self.states:
+                raise ValueError(f"inflow face {f} needs a state")
 
     def periodic(self, k):
         return self.bc[2 * k] == PERIODIC
+
+    def kind(self, k, side):
+        """Boundary kind of the low (side -1) or high (side +1) face of axis k."""
+        return self.bc[2 * k + (1 if side > 0 else 0)]
+
+    def ghost(self, Q, k, side):
+        """Ghost state beyond the low / high face of axis k for the interior
+        state Q[v, ...] next to that face (non-periodic kinds)."""
+        kind = self.kind(k, side)
+        if kind == REFLECTIVE:
+            G = Q.copy()
+            G[1 + k] = -G[1 + k]
+            return G
+        if kind == INFLOW:
+            q = self.states[2 * k + (1 if side > 0 else 0)]
+            return np.broadcast_to(q.reshape((-1,) + (1,) * (Q.ndim - 1)), Q.shape).copy()
+        return Q.copy()
 
 
 def along(M, X, axis):
@@ -77,18 +110,21 @@ def predictor(U, dt_over_dx, basis, flux_fn, n_iter):
     return q
 
 
-def _face_states(qlo, qhi, cell_axis, periodic):
-    """Left/right states on the n_k + 1 faces of one axis.
+def _face_states(qlo, qhi, cell_axis, grid, k):
+    """Left/right states on the n_k + 1 faces of axis k.
 
     qlo / qhi: traces at the low / high face of every cell.  Face f lies
-    between cells f-1 and f.  Periodic: wrap.  Transmissive: the missing side
-    copies the interior trace, so the Rusanov flux there is F(q^-)."""
+    between cells f-1 and f.  Periodic: wrap.  Otherwise the missing side is
+    the boundary's ghost of the interior trace at the same node (transmissive:
+    a copy, so the flux there is F(q^-); reflective: normal momentum negated;
+    inflow: the face's state)."""
     nk = qlo.shape[cell_axis]
     take = lambda a, i: np.take(a, [i], axis=cell_axis)
-    if periodic:
+    if grid.periodic(k):
         left0, rightN = take(qhi, nk - 1), take(qlo, 0)
     else:
-        left0, rightN = take(qlo, 0), take(qhi, nk - 1)
+        left0 = grid.ghost(take(qlo, 0), k, -1)
+        rightN = grid.ghost(take(qhi, nk - 1), k, +1)
     left = np.concatenate([left0, qhi], axis=cell_axis)
     right = np.concatenate([qlo, rightN], axis=cell_axis)
     return left, right
@@ -116,7 +152,7 @@ def corrector(U, q, dt, basis, grid, gamma, face_flux=euler.rusanov):
         # face term
         qlo = np.tensordot(q, basis.phi0, axes=([qnode_axis], [0]))
         qhi = np.tensordot(q, basis.phi1, axes=([qnode_axis], [0]))
-        left, right = _face_states(qlo, qhi, 1 + k, grid.periodic(k))
+        left, right = _face_states(qlo, qhi, 1 + k, grid, k)
         G = face_flux(left, right, gamma, k)
         Gb = np.tensordot(G, w, axes=([G.ndim - 1], [0]))
         Gbar.append(Gb)

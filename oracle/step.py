@@ -36,6 +36,8 @@ import numpy as np
 from . import detect as det
 from . import dg
 from . import euler
+from .dg import INFLOW as INFLOW_KIND
+from .dg import REFLECTIVE as REFLECTIVE_KIND
 from .basis import Basis
 from .godunov import godunov1
 from .subcell import projection_matrix, project, reconstruct, reconstruction_matrix
@@ -109,16 +111,47 @@ def global_subgrid(V, dim):
     return G.reshape((nv,) + tuple(c * Ns for c in cells))
 
 
-def patch(sch, G, cell):
-    """(nvar, L, .., L) subgrid patch around `cell` (local -3..N_s+2)."""
+def patch(sch, G, cell, width=3):
+    """(nvar, L, .., L) subgrid patch around `cell` (local -width..N_s+width-1,
+    L = N_s + 2 width).  Ghost subcells outside the domain: periodic wrap;
+    transmissive clamp (constant extrapolation); reflective mirror index
+    (-1 - g below, 2 n - 1 - g above) with the wall-normal momentum negated;
+    inflow the face's state.  The per-axis transforms apply in axis order."""
     Ns = sch.Ns
-    idx = []
+    g_ = sch.grid
+    idx, modes = [], []
     for k in range(sch.dim):
-        nk = sch.grid.ncell[k] * Ns
-        g = cell[k] * Ns - 3 + np.arange(Ns + 6)
-        g = np.mod(g, nk) if sch.grid.periodic(k) else np.clip(g, 0, nk - 1)
+        nk = g_.ncell[k] * Ns
+        g = cell[k] * Ns - width + np.arange(Ns + 2 * width)
+        mode = np.zeros(len(g), dtype=np.int64)            # 0 inside, +-1 mirror, +-2 inflow
+        if g_.periodic(k):
+            g = np.mod(g, nk)
+        else:
+            lo, hi = g < 0, g >= nk
+            for side, sel in ((-1, lo), (1, hi)):
+                kind = g_.kind(k, side)
+                if kind == REFLECTIVE_KIND:
+                    g = np.where(sel, (-1 - g) if side < 0 else (2 * nk - 1 - g), g)
+                    mode[sel] = side
+                elif kind == INFLOW_KIND:
+                    mode[sel] = 2 * side
+            g = np.clip(g, 0, nk - 1)
         idx.append(g)
-    return G[(slice(None),) + np.ix_(*idx)]
+        modes.append(mode)
+    P = G[(slice(None),) + np.ix_(*idx)].copy()
+    for k in range(sch.dim):
+        shape = [1] * sch.dim
+        shape[k] = -1
+        m = modes[k].reshape(shape)
+        mirror = np.broadcast_to(np.abs(m) == 1, P.shape[1:])
+        P[1 + k][mirror] = -P[1 + k][mirror]
+        for side in (-1, 1):
+            sel = np.broadcast_to(m == 2 * side, P.shape[1:])
+            if sel.any():
+                q = g_.states[2 * k + (1 if side > 0 else 0)]
+                for v in range(P.shape[0]):
+                    P[v][sel] = q[v]
+    return P
 
 
 def neighbour(sch, cell, k, side):
