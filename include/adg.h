@@ -51,8 +51,22 @@ extern "C" {
 #define ADG_WARN_SUBCELL_INADMISSIBLE 1 /* a subcell average left the
                                            admissible set after the limiter */
 
+/* Boundary kinds, one per face (adg_create `bc[2k]` low, `bc[2k+1]` high side
+ * of axis k).  The paper's tests use periodic, transmissive (outflow),
+ * reflecting-wall and inflow (Dirichlet) boundaries (Sec. 5.1, 5.4, 5.5)
+ * without printing their discrete form; this library's rules:
+ *   PERIODIC      wrap (both faces of an axis, or neither);
+ *   TRANSMISSIVE  ghost = copy of the interior (DG traces and subcells);
+ *   REFLECTIVE    ghost = mirror image with the wall-normal momentum negated
+ *                 (subcells mirror across the wall); the mirror images of the
+ *                 boundary cells take part in the detector's neighbourhood V_i;
+ *   INFLOW        ghost = the face's fixed conserved state
+ *                 (adg_set_boundary_state); no cell beyond it joins V_i
+ *                 (nor beyond a transmissive face). */
 #define ADG_BC_PERIODIC 0
 #define ADG_BC_TRANSMISSIVE 1
+#define ADG_BC_REFLECTIVE 2
+#define ADG_BC_INFLOW 3
 
 #define ADG_PREC_FP64 0
 #define ADG_PREC_MIXED_FP32 1
@@ -228,6 +242,12 @@ int adg_read(adg_state* st, double* dofs);
 
 /* Number of troubled cells of the last step. */
 int adg_troubled_count(adg_state* st, int64_t* out);
+
+/* The fixed conserved state q[nvar] of inflow face `face` (2k low, 2k+1 high
+ * side of axis k), host memory, copied.  Needed for every ADG_BC_INFLOW face
+ * before the first load.  Errors: ADG_ERR_ARG (face out of range or not an
+ * inflow face, rho <= 0 or p <= 0). */
+int adg_set_boundary_state(adg_state* st, int face, const double* q);
 
 /* Cells recomputed by the first-order layer (ADG_OPT_CASCADE): in the last
  * step, and since the last load.  Either pointer may be null. */

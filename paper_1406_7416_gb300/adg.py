@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libadg.so")
 OK = 0
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_CAPACITY, ERR_STATE = -1, -2, -3, -4, -5, -6
 WARN_SUBCELL_INADMISSIBLE = 1
-BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_INFLOW = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED_FP32 = 0, 1
 OPT_DMP_EPS, OPT_DMP_FLOOR, OPT_FORCE_LIMITER, OPT_PICARD_ITERS, OPT_SLOT_CAPACITY = 1, 2, 3, 4, 5
 OPT_PROFILE = 6
@@ -42,7 +42,7 @@ SYMBOLS = ("adg_create", "adg_set_allocator", "adg_set_stream", "adg_set_option"
            "adg_max_dt", "adg_flags", "adg_read", "adg_troubled_count", "adg_status",
            "adg_sizes", "adg_info", "adg_phase_times", "adg_last_error", "adg_destroy",
            "adg_subcell_update_noalloc", "adg_time", "adg_batch_create", "adg_batch_step",
-           "adg_batch_destroy", "adg_step_batch", "adg_fallback_count")
+           "adg_batch_destroy", "adg_step_batch", "adg_fallback_count", "adg_set_boundary_state")
 
 
 class AdgGrid(ctypes.Structure):
@@ -94,6 +94,7 @@ def load_library(path=None):
     lib.adg_read.argtypes = [vp, dp]
     lib.adg_troubled_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     lib.adg_fallback_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.adg_set_boundary_state.argtypes = [vp, ip, dp]
     lib.adg_status.argtypes = [vp]
     lib.adg_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
@@ -173,7 +174,17 @@ class Solver:
 
     @classmethod
     def from_workload(cls, w, prec=PREC_FP64):
-        return cls(w["dim"], w["ncell"], w["x0"], w["dx"], w["bc"], w["N"], w["gamma"], prec)
+        s = cls(w["dim"], w["ncell"], w["x0"], w["dx"], w["bc"], w["N"], w["gamma"], prec)
+        for face, q in (w.get("bc_states") or {}).items():
+            s.set_boundary_state(face, q)
+        return s
+
+    def set_boundary_state(self, face, q):
+        """Conserved state of inflow face `face` (2k low, 2k+1 high of axis k)."""
+        a = np.ascontiguousarray(q, dtype=np.float64)
+        self._check(self.lib.adg_set_boundary_state(self.h, int(face),
+                                                     a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                    "adg_set_boundary_state")
 
     # -- helpers ------------------------------------------------------------
     def _check(self, rc, what):

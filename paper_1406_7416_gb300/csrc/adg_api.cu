@@ -21,6 +21,7 @@ struct adg_state {
   int flux = ADG_FLUX_RUSANOV;
   bool host_passes = true;  // single-state steps launch only the limiter passes needed
   int sub_fp64 = 0;         // mixed precision: FP64 sweeps of the degree-2 subcell predictor
+  int bstate_set = 0;       // bit f: inflow face f has a state
   // pinned host mirror of the device Params, counters and dt, read once per
   // step after the DG phase when host_passes is on
   struct Probe {
@@ -316,6 +317,10 @@ int upload_params(adg_state* st) {
 
 // Reset the current level's counters and the clock before a load
 int begin_load(adg_state* st) {
+  for (int f = 0; f < 2 * st->dim; ++f)
+    if (st->geo.bc[f] == ADG_BC_INFLOW && !(st->bstate_set & (1 << f)))
+      return fail(st, ADG_ERR_ARG, "inflow face " + std::to_string(f) +
+                                       " has no state (adg_set_boundary_state)");
   int rc = ensure_allocated(st);
   if (rc) return rc;
   rc = refresh(st);
@@ -799,8 +804,7 @@ int adg_create(const adg_grid* grid, int N, double gamma, const int* bc, int pre
   for (int k = 0; k < grid->dim; ++k) {
     if (grid->n[k] < 1 || !(grid->dx[k] > 0.0)) return ADG_ERR_ARG;
     const int lo = bc[2 * k], hi = bc[2 * k + 1];
-    if ((lo != ADG_BC_PERIODIC && lo != ADG_BC_TRANSMISSIVE) ||
-        (hi != ADG_BC_PERIODIC && hi != ADG_BC_TRANSMISSIVE))
+    if (lo < ADG_BC_PERIODIC || lo > ADG_BC_INFLOW || hi < ADG_BC_PERIODIC || hi > ADG_BC_INFLOW)
       return ADG_ERR_ARG;
     if ((lo == ADG_BC_PERIODIC) != (hi == ADG_BC_PERIODIC)) return ADG_ERR_ARG;
   }
@@ -822,6 +826,8 @@ int adg_create(const adg_grid* grid, int N, double gamma, const int* bc, int pre
     st->geo.dx[k] = (k < grid->dim) ? grid->dx[k] : 1.0;
     st->geo.x0[k] = (k < grid->dim) ? grid->x0[k] : 0.0;
     st->geo.periodic[k] = (k < grid->dim) ? (bc[2 * k] == ADG_BC_PERIODIC) : 0;
+    st->geo.bc[2 * k] = (k < grid->dim) ? bc[2 * k] : ADG_BC_PERIODIC;
+    st->geo.bc[2 * k + 1] = (k < grid->dim) ? bc[2 * k + 1] : ADG_BC_PERIODIC;
   }
   st->geo.cells = cells;
   build_ops(N, &st->ops_host);
@@ -1087,6 +1093,21 @@ int adg_troubled_count(adg_state* st, int64_t* out) {
   int rc = sync(st);
   if (rc) return rc;
   *out = c;
+  return ADG_OK;
+}
+
+int adg_set_boundary_state(adg_state* st, int face, const double* q) {
+  if (!st || !q) return ADG_ERR_ARG;
+  if (face < 0 || face >= 2 * st->dim) return fail(st, ADG_ERR_ARG, "face out of range");
+  if (st->geo.bc[face] != ADG_BC_INFLOW) return fail(st, ADG_ERR_ARG, "face is not an inflow face");
+  const int d = st->dim;
+  double kin = 0.0;
+  for (int k = 0; k < d; ++k) kin += q[1 + k] * q[1 + k];
+  if (!(q[0] > 0.0) || !(q[d + 1] * q[0] - 0.5 * kin > 0.0))
+    return fail(st, ADG_ERR_ARG, "inflow state must have rho > 0 and p > 0");
+  for (int v = 0; v < st->nv; ++v) st->geo.bstate[face][v] = q[v];
+  st->bstate_set |= 1 << face;
+  st->params_dirty = true;
   return ADG_OK;
 }
 

@@ -48,8 +48,10 @@ struct Geo {
   int dim;
   int n[3];
   int periodic[3];
+  int bc[6];             // boundary kind (ADG_BC_*) of face 2k (low) / 2k+1 (high) of axis k
   double x0[3];
   double dx[3];
+  double bstate[6][5];   // conserved state of every ADG_BC_INFLOW face
   long long cells;
 };
 
@@ -438,6 +440,23 @@ __device__ __forceinline__ bool face_neighbour(const Geo& g, const int* ijk, int
   }
   out[k] = c;
   return true;
+}
+
+// Ghost state beyond boundary face `face` (2k low, 2k+1 high of axis k) for
+// the interior state Q at the same point: transmissive a copy
+// (zero-gradient), reflective the mirror image (wall-normal momentum
+// negated), inflow the face's fixed state.  Not used for periodic faces.
+template <int D>
+__device__ __forceinline__ void boundary_ghost(const Geo& g, int face, const double* Q, double* G) {
+  const int kind = g.bc[face];
+  if (kind == ADG_BC_INFLOW) {
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) G[v] = g.bstate[face][v];
+    return;
+  }
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) G[v] = Q[v];
+  if (kind == ADG_BC_REFLECTIVE) G[1 + (face >> 1)] = -G[1 + (face >> 1)];
 }
 
 // Face index along axis k: faces (n_k + 1) along k, cells along the others.

@@ -446,6 +446,8 @@ __global__ void __launch_bounds__(256) k_faceflux(Batch bt, int k) {
         QL[v] = trL[v * NT + ts + NF * m];
         QR[v] = trR[v * NT + ts + NF * m];
       }
+      if (!hasL) boundary_ghost<D>(g, 2 * k, QR, QL);
+      if (!hasR) boundary_ghost<D>(g, 2 * k + 1, QL, QR);
       face_flux<D>(p.flux, QL, QR, k, p.gamma, Gm);
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] += w[m] * Gm[v];
@@ -485,21 +487,31 @@ __device__ __forceinline__ void dmp_interval(const Params& p, const double* __re
   const int nb3 = ipow(3, D);
   for (int o = 0; o < nb3; ++o) {
     int c[3] = {0, 0, 0}, oo = o;
-    bool in = true;
+    bool in = true, flip = false;
 #pragma unroll
     for (int j = 0; j < D; ++j) {
       int cj = ijk[j] + (oo % 3) - 1;
       oo /= 3;
       if (cj < 0 || cj >= g.n[j]) {
-        if (!g.periodic[j]) in = false;
-        cj = (cj + g.n[j]) % g.n[j];
+        const int kind = g.bc[2 * j + (cj < 0 ? 0 : 1)];
+        if (kind == ADG_BC_PERIODIC) {
+          cj = (cj + g.n[j]) % g.n[j];
+        } else if (kind == ADG_BC_REFLECTIVE) {
+          // mirror image of the boundary cell: its wall-normal momentum
+          // bounds negate and swap
+          cj = cj < 0 ? 0 : g.n[j] - 1;
+          if (v == 1 + j) flip = !flip;
+        } else {
+          in = false;
+        }
       }
       c[j] = cj;
     }
     if (!in) continue;
     const long long nb = cell_index<D>(c, g);
-    mn = fmin(mn, cmm[(nb * NV + v) * 2 + 0]);
-    mx = fmax(mx, cmm[(nb * NV + v) * 2 + 1]);
+    const double lo = cmm[(nb * NV + v) * 2 + 0], hi = cmm[(nb * NV + v) * 2 + 1];
+    mn = fmin(mn, flip ? -hi : lo);
+    mx = fmax(mx, flip ? -lo : hi);
   }
   const double scale = fmax(1.0, fmax(fabs(mx), fabs(mn)));
   const double delta = fmax(p.eps * (mx - mn), p.floor * scale);

@@ -73,9 +73,56 @@ __device__ __forceinline__ void subcell_value(const Params& p, long long o, cons
   }
 }
 
+// v^n at local subcell loc[k] (may lie outside the cell, up to three
+// layers) around cell ijk, with the ghost rules of the boundary kinds: a
+// global subcell index outside the domain wraps (periodic), is clamped
+// (transmissive: constant extrapolation), is mirrored with the wall-normal
+// momentum negated (reflective: -1 - g below, 2 n - 1 - g above), or takes
+// the face's fixed state (inflow).  The per-axis transforms apply in axis
+// order.
+template <int D, int N>
+__device__ __forceinline__ void patch_value(const Params& p, const int* ijk, const int* loc,
+                                            const double* __restrict__ P1, double* val) {
+  using DM = Dims<D, N>;
+  constexpr int NV = DM::NV, Ns = DM::Ns;
+  const Geo& g = p.geo;
+  int own[3] = {0, 0, 0}, sub[3] = {0, 0, 0}, mode[3] = {0, 0, 0};
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const int ng = g.n[k] * Ns;
+    int gi = ijk[k] * Ns + loc[k];
+    if (gi < 0 || gi >= ng) {
+      const int face = 2 * k + (gi < 0 ? 0 : 1);
+      const int kind = g.bc[face];
+      if (kind == ADG_BC_PERIODIC) {
+        gi = (gi % ng + ng) % ng;
+      } else {
+        if (kind == ADG_BC_REFLECTIVE) {
+          gi = gi < 0 ? -1 - gi : 2 * ng - 1 - gi;
+          mode[k] = 1;
+        } else if (kind == ADG_BC_INFLOW) {
+          mode[k] = 2 + face;
+        }
+        gi = gi < 0 ? 0 : (gi >= ng ? ng - 1 : gi);
+      }
+    }
+    own[k] = gi / Ns;
+    sub[k] = gi - own[k] * Ns;
+  }
+  subcell_value<D, N>(p, cell_index<D>(own, g), sub, P1, val);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    if (mode[k] == 1) {
+      val[1 + k] = -val[1 + k];
+    } else if (mode[k] >= 2) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) val[v] = g.bstate[mode[k] - 2][v];
+    }
+  }
+}
+
 // L0: patch[j][v][L^d], local subcell -3..Ns+2 per axis around troubled cell
-// list[chunk0 + j].  Periodic: wrap; transmissive: clamp the global subcell
-// index into the domain.
+// list[chunk0 + j], ghosts by patch_value.
 template <int D, int N>
 __global__ void __launch_bounds__(256) k_lim_patch(Batch bt, int pass) {
   using DM = Dims<D, N>;
@@ -94,20 +141,14 @@ __global__ void __launch_bounds__(256) k_lim_patch(Batch bt, int pass) {
     const long long cell = p.b.list[1 - p.cur][pass * p.chunk + j];
     int ijk[3];
     cell_coords<D>(cell, g, ijk);
-    int own[3] = {0, 0, 0}, sub[3] = {0, 0, 0};
+    int loc[3] = {0, 0, 0};
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-      const int loc = r % L - 3;
+      loc[k] = r % L - 3;
       r /= L;
-      const int ng = g.n[k] * Ns;
-      int gi = ijk[k] * Ns + loc;
-      if (g.periodic[k]) gi = (gi % ng + ng) % ng;
-      else gi = gi < 0 ? 0 : (gi >= ng ? ng - 1 : gi);
-      own[k] = gi / Ns;
-      sub[k] = gi - own[k] * Ns;
     }
     double val[NV];
-    subcell_value<D, N>(p, cell_index<D>(own, g), sub, P1, val);
+    patch_value<D, N>(p, ijk, loc, P1, val);
     double* dst = p.b.patch + (size_t)j * NV * LD + (e - t * LD);
 #pragma unroll
     for (int v = 0; v < NV; ++v) dst[v * LD] = val[v];
@@ -670,20 +711,14 @@ __global__ void __launch_bounds__(128) k_lim_fallback(Batch bt) {
     __syncthreads();
     for (int e = tid; e < NB; e += nth) {
       int r = e;
-      int own[3] = {0, 0, 0}, sub[3] = {0, 0, 0};
+      int loc[3] = {0, 0, 0};
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        const int loc = r % NE - 1;
+        loc[k] = r % NE - 1;
         r /= NE;
-        const int ng = g.n[k] * Ns;
-        int gi = ijk[k] * Ns + loc;
-        if (g.periodic[k]) gi = (gi % ng + ng) % ng;
-        else gi = gi < 0 ? 0 : (gi >= ng ? ng - 1 : gi);
-        own[k] = gi / Ns;
-        sub[k] = gi - own[k] * Ns;
       }
       double val[NV];
-      subcell_value<D, N>(p, cell_index<D>(own, g), sub, P1, val);
+      patch_value<D, N>(p, ijk, loc, P1, val);
 #pragma unroll
       for (int v = 0; v < NV; ++v) blk[v * NB + e] = val[v];
     }

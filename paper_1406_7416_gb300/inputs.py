@@ -12,8 +12,9 @@ with its own code.  Shapes follow the paper's test problems:
 Seeds are 1406 + workload index with numpy's default_rng.
 
 A workload dict carries:
-  dim, ncell, x0, dx, bc (per face: 0 periodic, 1 transmissive), N, gamma,
-  cfl, steps, problem (see below), name.
+  dim, ncell, x0, dx, bc (per face: 0 periodic, 1 transmissive, 2 reflective,
+  3 inflow), bc_states (conserved state of each inflow face, optional), N,
+  gamma, cfl, steps, problem (see below), name.
 Problem dicts: {"kind": "radial", "center", "radius", "inner", "outer",
 "cell_rho_factor"} with states (rho, vel..., p); {"kind": "quadrant", "center",
 "states" (4 x (rho, u, v, p)), "vortex": None | {"center", "strength"}}.
@@ -155,6 +156,51 @@ def serving_runs(count=256, index=4, sizes=(32, 64, 128, 256), orders=(3, 5), t_
         w["name"] = f"serving run {r}: " + w["name"]
         runs.append(w)
     return runs
+
+
+REFLECTIVE = 2
+INFLOW = 3
+
+
+def conserved_state(rho, vel, p, gamma=GAMMA):
+    """Conserved vector (rho, rho v, rho E) of one primitive state."""
+    kin = 0.5 * rho * sum(v * v for v in vel)
+    return [rho] + [rho * v for v in vel] + [p / (gamma - 1.0) + kin]
+
+
+# Sec. 5.1 table: left / right primitive states (rho, u, p) and final times of
+# the Sod and Lax shock tubes (initial discontinuity at x = 0.5, v = 0)
+SHOCK_TUBES = {"sod": ((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 0.2),
+               "lax": ((0.445, 0.698, 3.528), (0.5, 0.0, 0.571), 0.14)}
+
+
+def shock_tube(name, nx=20, ny=5, N=9):
+    """Sod or Lax shock tube of Sec. 5.1 on [0,1] x [-0.5,0.5]: Dirichlet
+    (inflow with the initial left / right state) in x, periodic in y; the
+    paper's mesh is 20 x 5 cells at N = 9."""
+    left, right, t_final = SHOCK_TUBES[name]
+    w = dict(dim=2, ncell=(nx, ny), x0=(0.0, -0.5), dx=(1.0 / nx, 1.0 / ny),
+             bc=(INFLOW, INFLOW, PERIODIC, PERIODIC))
+    w.update(N=N, gamma=GAMMA, cfl=0.9 / (2 * (2 * N + 1)), steps=None, t_end=t_final,
+             name=f"{name} shock tube N={N} {nx}x{ny}")
+    lp = (left[0], left[1], 0.0, left[2])
+    rp = (right[0], right[1], 0.0, right[2])
+    w["bc_states"] = {0: conserved_state(left[0], (left[1], 0.0), left[2]),
+                      1: conserved_state(right[0], (right[1], 0.0), right[2])}
+    w["problem"] = dict(kind="quadrant", center=(0.5, 0.0), states=[rp, lp, lp, rp], vortex=None)
+    return w
+
+
+def closed_box(n=32, N=3, dim=2):
+    """Off-centre explosion in the unit box with reflecting walls everywhere
+    (mass and energy stay constant)."""
+    w = _grid(0.0, 1.0, n, dim, REFLECTIVE)
+    w.update(N=N, gamma=GAMMA, cfl=0.9 / (dim * (2 * N + 1)), steps=None,
+             name=f"{dim}D explosion in a closed box N={N} {n}^{dim}")
+    c = (0.31, 0.42, 0.55)[:dim]
+    w["problem"] = dict(kind="radial", center=c, radius=0.3, inner=(1.0,) + (0.0,) * dim + (1.0,),
+                        outer=(0.125,) + (0.0,) * dim + (0.1,), cell_rho_factor=None)
+    return w
 
 
 def random_state_perturbation(shape, seed, scale=1e-3):

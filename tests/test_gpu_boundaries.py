@@ -1,0 +1,151 @@
+"""GPU: reflective and inflow boundaries (the boundaries of the paper's
+shock-tube, double-Mach and forward-step tests).
+
+  * one step through the C ABI against the oracle on closed boxes,
+    half-domain wall problems and shock tubes, 2D and 3D, with the limiter
+    as detected and forced on every cell (1e-12 relative, flags identical);
+  * a closed box keeps mass and energy to round-off over many steps;
+  * the Sod and Lax tubes of Sec. 5.1 on the paper's 20 x 5 mesh at N = 9
+    reach the exact Riemann solution as closely as the oracle does."""
+import numpy as np
+import pytest
+
+from oracle.step import stable_dt, step
+from paper_1406_7416_gb300 import adg, build_lib, inputs
+
+import riemann_exact
+from helpers import (assert_close_rel, beta_from_abi, from_abi, load_state, near_threshold_cells,
+                     oracle_setup)
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build_lib.build()
+    adg.load_library()
+
+
+def _half_collision(N=2):
+    """Streams colliding at a wall at x = 0 (quadrant data, transmissive
+    elsewhere)."""
+    w = dict(dim=2, ncell=(8, 12), x0=(0.0, -1.0), dx=(0.125, 2.0 / 12),
+             bc=(inputs.REFLECTIVE, inputs.TRANSMISSIVE, inputs.TRANSMISSIVE, inputs.TRANSMISSIVE))
+    w.update(N=N, gamma=1.4, cfl=0.9 / (2 * (2 * N + 1)), steps=None, name="half collision")
+    w["problem"] = dict(kind="quadrant", center=(0.0, 0.15), vortex=None,
+                        states=[(1.0, -0.6, 0.1, 1.0), (1.0, 0.6, 0.1, 1.0),
+                                (0.5, 0.4, -0.2, 0.8), (0.5, -0.4, -0.2, 0.8)])
+    return w
+
+
+def _inflow_3d():
+    """3D: a stream entering through an inflow face (x low) into a box with
+    a reflecting floor (z low), an explosion inside."""
+    w = inputs.closed_box(n=4, N=2, dim=3)
+    w["bc"] = (inputs.INFLOW, inputs.TRANSMISSIVE, inputs.PERIODIC, inputs.PERIODIC,
+               inputs.REFLECTIVE, inputs.TRANSMISSIVE)
+    w["bc_states"] = {0: inputs.conserved_state(0.8, (0.5, 0.0, 0.1), 0.6)}
+    return w
+
+
+CASES = {
+    "closed_box_2d_N3": (lambda: inputs.closed_box(n=10, N=3), False),
+    "closed_box_2d_N2_forced": (lambda: inputs.closed_box(n=8, N=2), True),
+    "half_collision_N2": (_half_collision, False),
+    "half_collision_N2_forced": (_half_collision, True),
+    "sod_N4_16x3": (lambda: inputs.shock_tube("sod", 16, 3, 4), False),
+    "lax_N3_12x2_forced": (lambda: inputs.shock_tube("lax", 12, 2, 3), True),
+    "closed_box_3d_N2": (lambda: inputs.closed_box(n=4, N=2, dim=3), False),
+    "inflow_floor_3d_N2_forced": (_inflow_3d, True),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_boundary_step_matches_oracle(name):
+    make, force = CASES[name]
+    w = make()
+    sch, st, _, _ = oracle_setup(w)
+    dt = 0.5 * stable_dt(sch, st, w["cfl"])
+    s = adg.Solver.from_workload(w)
+    if force:
+        s.set_option(adg.OPT_FORCE_LIMITER, 1)
+    load_state(s, sch, st)
+    s.step(dt)
+    d, b, sub = s.read_full()
+    assert s.status() == adg.OK
+    ref, info = step(sch, st, dt, force_all=force)
+    beta = beta_from_abi(b, sch.grid.ncell)
+    if not force:
+        near = near_threshold_cells(sch, info)
+        assert not np.any((beta != ref.beta) & ~near)
+    np.testing.assert_array_equal(beta, ref.beta)
+    assert_close_rel(from_abi(d, sch.dim, sch.grid.ncell, sch.N + 1), ref.U, RTOL, "DOFs")
+    tr = (slice(None),) + (ref.beta == 1,)
+    if (ref.beta == 1).any():
+        assert_close_rel(from_abi(sub, sch.dim, sch.grid.ncell, sch.Ns)[tr], ref.Vs[tr], RTOL,
+                         "subcell data")
+    s.close()
+
+
+def test_inflow_face_needs_a_state():
+    w = inputs.shock_tube("sod", 8, 2, 2)
+    s = adg.Solver(w["dim"], w["ncell"], w["x0"], w["dx"], w["bc"], w["N"], w["gamma"])
+    with pytest.raises(adg.AdgError):
+        s.init_problem(w["problem"])
+    with pytest.raises(adg.AdgError):
+        s.set_boundary_state(2, w["bc_states"][0])          # face 2 is periodic
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [adg.PREC_FP64, adg.PREC_MIXED_FP32])
+def test_closed_box_keeps_mass_and_energy(prec):
+    w = inputs.closed_box(n=32, N=3)
+    s = adg.Solver.from_workload(w, prec)
+    s.init_problem(w["problem"])
+    n = w["N"] + 1
+    W = 0.5 * np.polynomial.legendre.leggauss(n)[1]
+    Wd = np.outer(W, W).ravel()
+    tot0 = np.einsum("cvl,l->v", s.read(), Wd)
+    troubled = 0
+    for _ in range(30):
+        s.step_cfl(0.5 * w["cfl"])
+        troubled += s.troubled_count()
+    tot = np.einsum("cvl,l->v", s.read(), Wd)
+    assert s.status() == adg.OK and troubled > 0
+    for v in (0, 3):
+        assert abs(tot[v] - tot0[v]) <= 1e-13 * abs(tot0[v]) * 10, (v, tot[v], tot0[v])
+    s.close()
+
+
+@pytest.mark.parametrize("name,bound", [("sod", 2.5e-3), ("lax", 9e-3)])
+def test_shock_tube_on_the_papers_mesh(name, bound):
+    """20 x 5 cells, N = 9, CFL steps of Eq. (cfl) to the table's final time;
+    L1 density error against the exact solution within the bound set by the
+    oracle's own error on the same mesh (1.9e-3 Sod, 6.8e-3 Lax)."""
+    w = inputs.shock_tube(name)
+    s = adg.Solver.from_workload(w)
+    s.set_option(adg.OPT_END_TIME, w["t_end"])
+    s.init_problem(w["problem"])
+    while s.time()[0] < w["t_end"] * (1.0 - 1e-12):
+        s.step_cfl(w["cfl"])
+    U = s.read()
+    assert s.status() == adg.OK
+    s.close()
+    N, nx = w["N"], w["ncell"][0]
+    n = N + 1
+    xi = 0.5 * (np.polynomial.legendre.leggauss(n)[0] + 1.0)
+    xq, wq = np.polynomial.legendre.leggauss(N + 3)
+    xq, wq = 0.5 * (xq + 1.0), 0.5 * wq
+    L = np.ones((len(xq), n))
+    for a in range(n):
+        for b in range(n):
+            if b != a:
+                L[:, a] *= (xq - xi[b]) / (xi[a] - xi[b])
+    rho = U[:nx, 0, :].reshape(nx, n, n)                  # first row of cells: (i, node y, node x)
+    rq = np.einsum("qa,iba->iqb", L, rho).mean(axis=-1)
+    left, right, t_end = inputs.SHOCK_TUBES[name]
+    x = (np.arange(nx)[:, None] + xq[None, :]) / nx
+    ex = riemann_exact.sample(left, right, (x - 0.5) / t_end)[0]
+    err = float(np.sum(np.abs(rq - ex) * wq[None, :]) / nx)
+    assert err < bound, (name, err)
