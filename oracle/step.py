@@ -225,7 +225,10 @@ def step(sch, st, dt, force_all=False):
     G = global_subgrid(Vn, d)
     patches = np.stack([patch(sch, G, c) for c in troubled], axis=1)
     h = [g.dx[k] / sch.Ns for k in range(d)]
-    vnew, faces = ader_weno(patches, dt, h, gam, d, ff)
+    walls = np.array([[[g.kind(k, side) == REFLECTIVE_KIND and
+                        c[k] == (0 if side < 0 else g.ncell[k] - 1)
+                        for side in (-1, 1)] for k in range(d)] for c in troubled])
+    vnew, faces = ader_weno(patches, dt, h, gam, d, ff, walls=walls)
     if sch.cascade:
         fallback = [t for t in range(len(troubled)) if not det.admissible(vnew[:, t], gam, d)]
         info["fallback"] = len(fallback)

@@ -81,14 +81,20 @@ class Weno3:
         return np.moveaxis(out, -2, axis)
 
 
-def ader_weno(patch, dt, h, gamma, dim, face_flux=euler.rusanov):
+def ader_weno(patch, dt, h, gamma, dim, face_flux=euler.rusanov, walls=None):
     """One subcell ADER-WENO3 step on a batch of patches.
 
     patch: (nvar, T, L, .., L) with L = N_s + 6 (local index -3..N_s+2).
     h: subcell widths per axis.  Returns (v_new (nvar, T, N_s, .., N_s),
     faces) where faces[k] = (low, high) sub-face fluxes on the cell's two
     faces normal to axis k, each (nvar, T, N_s, .., N_s) over the d-1
-    tangential subcell axes (in axis order)."""
+    tangential subcell axes (in axis order).
+
+    walls: optional bool array (T, dim, 2); where walls[t, k, side] is set, the
+    cell's low (0) / high (1) face on axis k is a reflecting wall and its
+    sub-face fluxes are taken between the interior trace and its mirror image
+    (wall-normal momentum negated), like the DG flux at a wall, so that the
+    wall passes exactly no mass and no energy."""
     wn = Weno3()
     b3 = Basis(2)
     L = patch.shape[2]
@@ -110,7 +116,24 @@ def ader_weno(patch, dt, h, gamma, dim, face_flux=euler.rusanov):
         sl_right = list(sl_left)
         sl_left[2 + k] = slice(0, Ns + 1)
         sl_right[2 + k] = slice(1, Ns + 2)
-        G = face_flux(qhi[tuple(sl_left)], qlo[tuple(sl_right)], gamma, k)
+        QL, QR = qhi[tuple(sl_left)], qlo[tuple(sl_right)]
+        if walls is not None and np.any(walls[:, k]):
+            QL, QR = QL.copy(), QR.copy()
+            for side, f in ((0, 0), (1, Ns)):
+                t = np.nonzero(walls[:, k, side])[0]
+                if len(t) == 0:
+                    continue
+                sel = [slice(None)] * QL.ndim
+                sel[1] = t
+                sel[2 + k] = f
+                sel = tuple(sel)
+                if side == 0:                    # ghost on the left of the low wall
+                    QL[sel] = QR[sel]
+                    QL[(1 + k,) + sel[1:]] = -QR[(1 + k,) + sel[1:]]
+                else:                            # ghost on the right of the high wall
+                    QR[sel] = QL[sel]
+                    QR[(1 + k,) + sel[1:]] = -QL[(1 + k,) + sel[1:]]
+        G = face_flux(QL, QR, gamma, k)
         # average over the d-1 tangential nodes and time with GL weights
         for _ in range(dim):
             G = np.tensordot(G, b3.w, axes=([G.ndim - 1], [0]))

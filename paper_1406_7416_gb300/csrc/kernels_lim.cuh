@@ -416,6 +416,20 @@ __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
     }
     const double* qL = p.b.qsub + ((size_t)j * NED + sl) * NV * NST3;
     const double* qR = p.b.qsub + ((size_t)j * NED + sr) * NV * NST3;
+    // a sub-face on a reflecting wall takes its flux between the interior
+    // trace and its mirror image (no mass or energy through the wall)
+    // (the troubled-cell list is read only when the face can be a wall: the
+    // no-allocation entry point runs this kernel with periodic kinds and no list)
+    int wall = 0;                          // -1: low wall (ghost left), +1: high wall (ghost right)
+    const bool lo_wall = fc[k] == 0 && p.geo.bc[2 * k] == ADG_BC_REFLECTIVE;
+    const bool hi_wall = fc[k] == Ns && p.geo.bc[2 * k + 1] == ADG_BC_REFLECTIVE;
+    if (lo_wall || hi_wall) {
+      const long long cell = p.b.list[1 - p.cur][pass * p.chunk + j];
+      int ijk[3];
+      cell_coords<D>(cell, p.geo, ijk);
+      if (lo_wall && ijk[k] == 0) wall = -1;
+      if (hi_wall && ijk[k] == p.geo.n[k] - 1) wall = 1;
+    }
     double acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = 0.0;
@@ -445,6 +459,15 @@ __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
         const double* b = qR + v * NST3 + base;
         QL[v] = o->phi13[0] * a[0] + o->phi13[1] * a[stk] + o->phi13[2] * a[2 * stk];
         QR[v] = o->phi03[0] * b[0] + o->phi03[1] * b[stk] + o->phi03[2] * b[2 * stk];
+      }
+      if (wall < 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) QL[v] = QR[v];
+        QL[1 + k] = -QR[1 + k];
+      } else if (wall > 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) QR[v] = QL[v];
+        QR[1 + k] = -QL[1 + k];
       }
       face_flux<D>(p.flux, QL, QR, k, p.gamma, G);
 #pragma unroll

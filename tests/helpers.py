@@ -59,9 +59,13 @@ def load_state(solver, sch, st):
 
 
 def scale_per_var(U):
-    """max |U_v| per variable, broadcastable against U."""
+    """max |U_v| per variable, broadcastable against U; a variable that
+    vanishes identically (e.g. the transverse momentum of a planar problem,
+    zero up to round-off) is measured against 1e-3 of the largest variable's
+    scale instead of its own round-off."""
     ax = tuple(range(1, U.ndim))
     s = np.max(np.abs(U), axis=ax)
+    s = np.maximum(s, 1e-3 * np.max(s))
     return np.maximum(s, 1e-300).reshape((-1,) + (1,) * (U.ndim - 1))
 
 
