@@ -210,19 +210,15 @@ def run_gpu(args):
     import numpy as np
     import torch
     from paper_1406_7416_gb300 import adg, build_lib
+    from paper_1406_7416_gb300.replicas import Replicas
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    rep = Replicas("nccl", torch.device("cuda", local))
+    world, rank = rep.world, rep.rank
     if rank == 0:
         build_lib.build()
-    if dist:
-        dist.barrier()
+    rep.barrier()
     adg.load_library()
     w = workload()
     D, N = w["dim"], w["N"]
@@ -237,16 +233,8 @@ def run_gpu(args):
         s.init_problem(w["problem"])
         return s
 
-    def barrier():
-        if dist:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier = rep.barrier
+    max_over_ranks = rep.max_over_ranks
 
     results = {}
     cfl = w["cfl"]
@@ -290,6 +278,7 @@ def run_gpu(args):
                               "config": config_dict(w)}), flush=True)
         for r in results.values():
             r["solver"].close()
+        rep.close()
         return
     # L1 distance of the density, mixed vs FP64, after warmup + steps equal steps
     W = 0.5 * np.polynomial.legendre.leggauss(n)[1]
@@ -313,9 +302,7 @@ def run_gpu(args):
         emit_line(args, w, results, stdofs, world, cells, cfl, l1, l1ref, e2e, D, N, n)
     for r in results.values():
         r["solver"].close()
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+    rep.close()
 
 
 def end_to_end(s, args, stdofs, world, cfl, barrier, max_over_ranks):
