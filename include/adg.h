@@ -62,11 +62,19 @@ extern "C" {
  *                 boundary cells take part in the detector's neighbourhood V_i;
  *   INFLOW        ghost = the face's fixed conserved state
  *                 (adg_set_boundary_state); no cell beyond it joins V_i
- *                 (nor beyond a transmissive face). */
+ *                 (nor beyond a transmissive face);
+ *   FRONT         the face is split at a point moving along one tangential
+ *                 axis, x_f(t) = a + b t (adg_set_boundary_front): points with
+ *                 x < x_f(t) follow one transmissive / reflective / inflow rule,
+ *                 the others another -- the double-Mach boundaries of Sec. 5.4.
+ *                 DG face nodes use their own position and time t^n + tau dt,
+ *                 ghost subcells their centre at t^n; no cell beyond it joins
+ *                 V_i. */
 #define ADG_BC_PERIODIC 0
 #define ADG_BC_TRANSMISSIVE 1
 #define ADG_BC_REFLECTIVE 2
 #define ADG_BC_INFLOW 3
+#define ADG_BC_FRONT 4
 
 #define ADG_PREC_FP64 0
 #define ADG_PREC_MIXED_FP32 1
@@ -248,6 +256,19 @@ int adg_troubled_count(adg_state* st, int64_t* out);
  * before the first load.  Errors: ADG_ERR_ARG (face out of range or not an
  * inflow face, rho <= 0 or p <= 0). */
 int adg_set_boundary_state(adg_state* st, int face, const double* q);
+
+/* The moving split of front face `face`: points whose coordinate along
+ * tangential axis `axis` is below a + b t follow `kind_before` (with state
+ * q_before[nvar] if it is ADG_BC_INFLOW, else NULL), the others `kind_after`.
+ * Needed for every ADG_BC_FRONT face before the first load.  Errors:
+ * ADG_ERR_ARG (not a front face, axis not tangential, a part not transmissive /
+ * reflective / inflow, an inflow part without an admissible state). */
+int adg_set_boundary_front(adg_state* st, int face, int axis, double a, double b, int kind_before,
+                           const double* q_before, int kind_after, const double* q_after);
+
+/* Set the simulated time (time-dependent boundaries, restarts from adg_load_full,
+ * which starts the clock at 0).  Needs a loaded state. */
+int adg_set_time(adg_state* st, double t);
 
 /* Cells recomputed by the first-order layer (ADG_OPT_CASCADE): in the last
  * step, and since the last load.  Either pointer may be null. */

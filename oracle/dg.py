@@ -33,6 +33,7 @@ PERIODIC = 0
 TRANSMISSIVE = 1
 REFLECTIVE = 2
 INFLOW = 3
+FRONT = 4
 
 
 class Grid:
@@ -47,21 +48,32 @@ class Grid:
       TRANSMISSIVE  the ghost copies the interior (zero-gradient);
       REFLECTIVE    the ghost is the mirror image with the wall-normal momentum
                     negated;
-      INFLOW        the ghost is the face's fixed state."""
+      INFLOW        the ghost is the face's fixed state;
+      FRONT         the face is split at a point moving along one tangential
+                    axis, x_f(t) = a + b t: points with x < x_f(t) follow one
+                    of the kinds above ("before"), the others another
+                    ("after") -- the double-Mach boundaries of Sec. 5.4 (the
+                    moving shock on the upper boundary; post-shock inflow
+                    before the wall on the lower one).  `fronts` gives, per
+                    FRONT face, dict(axis, a, b, before=(kind, state or None),
+                    after=(kind, state or None))."""
 
-    def __init__(self, ncell, x0, dx, bc, states=None):
+    def __init__(self, ncell, x0, dx, bc, states=None, fronts=None):
         self.dim = len(ncell)
         self.ncell = tuple(int(c) for c in ncell)
         self.x0 = tuple(float(v) for v in x0)
         self.dx = tuple(float(v) for v in dx)
         self.bc = tuple(int(b) for b in bc)
         self.states = {int(f): np.asarray(q, dtype=np.float64) for f, q in (states or {}).items()}
+        self.fronts = {int(f): fr for f, fr in (fronts or {}).items()}
         for k in range(self.dim):
             if (self.bc[2 * k] == PERIODIC) != (self.bc[2 * k + 1] == PERIODIC):
                 raise ValueError("periodic boundaries must come in pairs")
         for f, b in enumerate(self.bc):
             if b == INFLOW and f not in self.states:
                 raise ValueError(f"inflow face {f} needs a state")
+            if b == FRONT and f not in self.fronts:
+                raise ValueError(f"front face {f} needs its front")
 
     def periodic(self, k):
         return self.bc[2 * k] == PERIODIC
@@ -70,18 +82,37 @@ class Grid:
         """Boundary kind of the low (side -1) or high (side +1) face of axis k."""
         return self.bc[2 * k + (1 if side > 0 else 0)]
 
-    def ghost(self, Q, k, side):
+    def front_before(self, face, pos, t):
+        """True where a point at coordinate `pos` (along the front's axis) lies
+        before the front of FRONT face `face` at time t."""
+        fr = self.fronts[face]
+        return pos < fr["a"] + fr["b"] * t
+
+    def ghost(self, Q, k, side, pos=None, t=0.0):
         """Ghost state beyond the low / high face of axis k for the interior
-        state Q[v, ...] next to that face (non-periodic kinds)."""
-        kind = self.kind(k, side)
-        if kind == REFLECTIVE:
-            G = Q.copy()
-            G[1 + k] = -G[1 + k]
-            return G
-        if kind == INFLOW:
-            q = self.states[2 * k + (1 if side > 0 else 0)]
-            return np.broadcast_to(q.reshape((-1,) + (1,) * (Q.ndim - 1)), Q.shape).copy()
-        return Q.copy()
+        state Q[v, ...] next to that face (non-periodic kinds).  For a FRONT
+        face, pos (broadcastable to Q[0]) is each point's coordinate along the
+        front's axis and t the time."""
+        face = 2 * k + (1 if side > 0 else 0)
+        kind = self.bc[face]
+        if kind == FRONT:
+            fr = self.fronts[face]
+            before = np.broadcast_to(self.front_before(face, pos, t), Q.shape[1:])
+            Gb = _ghost_of_kind(Q, k, *fr["before"])
+            Ga = _ghost_of_kind(Q, k, *fr["after"])
+            return np.where(before[None], Gb, Ga)
+        return _ghost_of_kind(Q, k, kind, self.states.get(face))
+
+
+def _ghost_of_kind(Q, k, kind, state):
+    if kind == REFLECTIVE:
+        G = Q.copy()
+        G[1 + k] = -G[1 + k]
+        return G
+    if kind == INFLOW:
+        q = np.asarray(state, dtype=np.float64)
+        return np.broadcast_to(q.reshape((-1,) + (1,) * (Q.ndim - 1)), Q.shape).copy()
+    return Q.copy()
 
 
 def along(M, X, axis):
@@ -110,27 +141,53 @@ def predictor(U, dt_over_dx, basis, flux_fn, n_iter):
     return q
 
 
-def _face_states(qlo, qhi, cell_axis, grid, k):
+def _face_points(grid, k, face, xi, t0, dt, shape):
+    """Coordinate along the front axis of FRONT face `face` of every node of a
+    boundary trace of axis k (shape (cells..., tangential nodes..., time
+    nodes)), and the node times t0 + tau_m dt."""
+    d = grid.dim
+    j = grid.fronts[face]["axis"]
+    node_ax = d + (j if j < k else j - 1)          # node axis of axis j in the trace
+    sh_c = [1] * len(shape)
+    sh_c[j] = grid.ncell[j]
+    sh_n = [1] * len(shape)
+    sh_n[node_ax] = len(xi)
+    pos = grid.x0[j] + (np.arange(grid.ncell[j]).reshape(sh_c) + xi.reshape(sh_n)) * grid.dx[j]
+    sh_t = [1] * len(shape)
+    sh_t[-1] = len(xi)
+    t = t0 + xi.reshape(sh_t) * dt
+    return pos, t
+
+
+def _face_states(qlo, qhi, cell_axis, grid, k, xi=None, t0=0.0, dt=0.0):
     """Left/right states on the n_k + 1 faces of axis k.
 
     qlo / qhi: traces at the low / high face of every cell.  Face f lies
     between cells f-1 and f.  Periodic: wrap.  Otherwise the missing side is
     the boundary's ghost of the interior trace at the same node (transmissive:
     a copy, so the flux there is F(q^-); reflective: normal momentum negated;
-    inflow: the face's state)."""
+    inflow: the face's state; front: either, by the node's position and time
+    t0 + tau dt)."""
     nk = qlo.shape[cell_axis]
     take = lambda a, i: np.take(a, [i], axis=cell_axis)
     if grid.periodic(k):
         left0, rightN = take(qhi, nk - 1), take(qlo, 0)
     else:
-        left0 = grid.ghost(take(qlo, 0), k, -1)
-        rightN = grid.ghost(take(qhi, nk - 1), k, +1)
+        ends = []
+        for side, tr in ((-1, take(qlo, 0)), (1, take(qhi, nk - 1))):
+            face = 2 * k + (1 if side > 0 else 0)
+            if grid.bc[face] == FRONT:
+                pos, t = _face_points(grid, k, face, xi, t0, dt, tr.shape[1:])
+                ends.append(grid.ghost(tr, k, side, pos, t))
+            else:
+                ends.append(grid.ghost(tr, k, side))
+        left0, rightN = ends
     left = np.concatenate([left0, qhi], axis=cell_axis)
     right = np.concatenate([qlo, rightN], axis=cell_axis)
     return left, right
 
 
-def corrector(U, q, dt, basis, grid, gamma, face_flux=euler.rusanov):
+def corrector(U, q, dt, basis, grid, gamma, face_flux=euler.rusanov, t0=0.0):
     """Candidate u* of Eq. (pde.nc.gw2) and the DG face fluxes.
 
     Returns (Ustar, Gbar) where Gbar[k] has shape
@@ -152,7 +209,7 @@ def corrector(U, q, dt, basis, grid, gamma, face_flux=euler.rusanov):
         # face term
         qlo = np.tensordot(q, basis.phi0, axes=([qnode_axis], [0]))
         qhi = np.tensordot(q, basis.phi1, axes=([qnode_axis], [0]))
-        left, right = _face_states(qlo, qhi, 1 + k, grid, k)
+        left, right = _face_states(qlo, qhi, 1 + k, grid, k, basis.xi, t0, dt)
         G = face_flux(left, right, gamma, k)
         Gb = np.tensordot(G, w, axes=([G.ndim - 1], [0]))
         Gbar.append(Gb)

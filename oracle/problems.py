@@ -6,6 +6,9 @@ Problem descriptions are plain dicts (built by the seeded input generators):
       Sec. 5.8 Eq. (RP3D) explosion (inner state for r <= R); its 2D circular
       analogue uses the same rule.  An optional per-cell density factor
       multiplies rho inside each cell (seeded noise, constant per cell).
+  {"kind": "planar", "normal": (n_1, .., n_d), "offset": c, "inner": (rho,
+   vel.., p), "outer": (..)}: the inner state where n . x < c (a planar front,
+      the oblique shock of the double-Mach problem, Sec. 5.4), else outer.
   {"kind": "quadrant", "center": (xc, yc), "states": 4 x (rho, u, v, p),
    "vortex": None or {"center": (xv, yv), "strength": beta}}
       Sec. 5.6: state 1 for x > xc and y > yc, 2 for x <= xc and y > yc,
@@ -51,6 +54,14 @@ def primitive(problem, X, gamma, cell_index=None):
         fac = problem.get("cell_rho_factor")
         if fac is not None:
             rho = rho * fac[cell_index]
+        return rho, vel, p
+    if kind == "planar":
+        nrm, off = problem["normal"], problem["offset"]
+        behind = sum(nrm[k] * X[k] for k in range(dim)) < off
+        si, so = problem["inner"], problem["outer"]
+        rho = np.where(behind, si[0], so[0])
+        vel = [np.where(behind, si[1 + k], so[1 + k]) for k in range(dim)]
+        p = np.where(behind, si[1 + dim], so[1 + dim])
         return rho, vel, p
     if kind == "quadrant":
         xc, yc = problem["center"]

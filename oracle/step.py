@@ -36,6 +36,7 @@ import numpy as np
 from . import detect as det
 from . import dg
 from . import euler
+from .dg import FRONT as FRONT_KIND
 from .dg import INFLOW as INFLOW_KIND
 from .dg import REFLECTIVE as REFLECTIVE_KIND
 from .basis import Basis
@@ -77,13 +78,14 @@ class State:
     """u (nvar, cells..., n^d nodes), beta (cells...), Vs (nvar, cells..., N_s^d)
     holding v^n for cells with beta = 1 (NaN elsewhere)."""
 
-    def __init__(self, U, beta, Vs):
+    def __init__(self, U, beta, Vs, t=0.0):
         self.U = U
         self.beta = beta
         self.Vs = Vs
+        self.t = t                       # simulated time (time-dependent boundaries)
 
     def copy(self):
-        return State(self.U.copy(), self.beta.copy(), self.Vs.copy())
+        return State(self.U.copy(), self.beta.copy(), self.Vs.copy(), self.t)
 
 
 def subcell_data(sch, st):
@@ -111,46 +113,63 @@ def global_subgrid(V, dim):
     return G.reshape((nv,) + tuple(c * Ns for c in cells))
 
 
-def patch(sch, G, cell, width=3):
+def patch(sch, G, cell, width=3, t=0.0):
     """(nvar, L, .., L) subgrid patch around `cell` (local -width..N_s+width-1,
     L = N_s + 2 width).  Ghost subcells outside the domain: periodic wrap;
     transmissive clamp (constant extrapolation); reflective mirror index
     (-1 - g below, 2 n - 1 - g above) with the wall-normal momentum negated;
-    inflow the face's state.  The per-axis transforms apply in axis order."""
+    inflow the face's state; front: one of those by the position of the ghost
+    subcell's centre along the front's axis (its unmapped global index) at
+    time t.  The per-axis transforms apply in axis order."""
     Ns = sch.Ns
     g_ = sch.grid
-    idx, modes = [], []
-    for k in range(sch.dim):
+    d = sch.dim
+    L = Ns + 2 * width
+    raw = [cell[k] * Ns - width + np.arange(L) for k in range(d)]
+    # per axis and element: (mapped index, transform): transform 0 none,
+    # 1 mirror, ("in", state) inflow -- decided per element because a front's
+    # part depends on the position along another axis
+    idx = np.empty((d,) + (L,) * d, dtype=np.int64)
+    kinds = np.zeros((d,) + (L,) * d, dtype=np.int64)        # 0 none, 1 mirror, 2 inflow
+    states = {}
+    grids = np.meshgrid(*raw, indexing="ij")
+    for k in range(d):
         nk = g_.ncell[k] * Ns
-        g = cell[k] * Ns - width + np.arange(Ns + 2 * width)
-        mode = np.zeros(len(g), dtype=np.int64)            # 0 inside, +-1 mirror, +-2 inflow
+        gk = grids[k].copy()
         if g_.periodic(k):
-            g = np.mod(g, nk)
-        else:
-            lo, hi = g < 0, g >= nk
-            for side, sel in ((-1, lo), (1, hi)):
-                kind = g_.kind(k, side)
-                if kind == REFLECTIVE_KIND:
-                    g = np.where(sel, (-1 - g) if side < 0 else (2 * nk - 1 - g), g)
-                    mode[sel] = side
-                elif kind == INFLOW_KIND:
-                    mode[sel] = 2 * side
-            g = np.clip(g, 0, nk - 1)
-        idx.append(g)
-        modes.append(mode)
-    P = G[(slice(None),) + np.ix_(*idx)].copy()
-    for k in range(sch.dim):
-        shape = [1] * sch.dim
-        shape[k] = -1
-        m = modes[k].reshape(shape)
-        mirror = np.broadcast_to(np.abs(m) == 1, P.shape[1:])
+            idx[k] = np.mod(gk, nk)
+            continue
+        out_idx = gk.copy()
+        for side, sel in ((-1, gk < 0), (1, gk >= nk)):
+            if not sel.any():
+                continue
+            face = 2 * k + (1 if side > 0 else 0)
+            kind = g_.bc[face]
+            if kind == FRONT_KIND:
+                fr = g_.fronts[face]
+                j = fr["axis"]
+                pos = g_.x0[j] + (grids[j] + 0.5) * (g_.dx[j] / Ns)
+                before = g_.front_before(face, pos, t)
+                parts = ((sel & before, fr["before"]), (sel & ~before, fr["after"]))
+            else:
+                parts = ((sel, (kind, g_.states.get(face))),)
+            for psel, (pkind, pstate) in parts:
+                if pkind == REFLECTIVE_KIND:
+                    out_idx = np.where(psel, (-1 - gk) if side < 0 else (2 * nk - 1 - gk), out_idx)
+                    kinds[k][psel] = 1
+                elif pkind == INFLOW_KIND:
+                    kinds[k][psel] = 2
+                    states[(k, side, id(pstate))] = (psel, np.asarray(pstate, dtype=np.float64))
+        idx[k] = np.clip(out_idx, 0, nk - 1)
+    P = G[(slice(None),) + tuple(idx[k] for k in range(d))].copy()
+    for k in range(d):
+        mirror = kinds[k] == 1
         P[1 + k][mirror] = -P[1 + k][mirror]
-        for side in (-1, 1):
-            sel = np.broadcast_to(m == 2 * side, P.shape[1:])
-            if sel.any():
-                q = g_.states[2 * k + (1 if side > 0 else 0)]
-                for v in range(P.shape[0]):
-                    P[v][sel] = q[v]
+        for (kk, side, _), (psel, q) in states.items():
+            if kk != k:
+                continue
+            for v in range(P.shape[0]):
+                P[v][psel] = q[v]
     return P
 
 
@@ -205,7 +224,7 @@ def step(sch, st, dt, force_all=False):
     # act 1: unlimited candidate
     q = dg.predictor(U, [dt / g.dx[k] for k in range(d)], b, dg.euler_flux_fn(gam), sch.n_iter)
     ff = euler.numerical_flux(sch.flux)
-    Ustar, Gbar = dg.corrector(U, q, dt, b, g, gam, ff)
+    Ustar, Gbar = dg.corrector(U, q, dt, b, g, gam, ff, t0=st.t)
     # act 2 + 3: scatter and detect against bounds from v^n over V_i
     Vn = subcell_data(sch, st)
     cmin, cmax = det.cell_minmax(Vn, d)
@@ -220,10 +239,10 @@ def step(sch, st, dt, force_all=False):
     info = {"troubled": len(troubled), "fallback": 0, "beta": beta.copy(), "m": m, "M": M,
             "vstar": vstar, "Ustar": Ustar.copy(), "fixed": 0}
     if not troubled:
-        return State(Unew, beta, Vs_new), info
+        return State(Unew, beta, Vs_new, st.t + dt), info
     # act 4: subcell ADER-WENO3 from v^n
     G = global_subgrid(Vn, d)
-    patches = np.stack([patch(sch, G, c) for c in troubled], axis=1)
+    patches = np.stack([patch(sch, G, c, t=st.t) for c in troubled], axis=1)
     h = [g.dx[k] / sch.Ns for k in range(d)]
     walls = np.array([[[g.kind(k, side) == REFLECTIVE_KIND and
                         c[k] == (0 if side < 0 else g.ncell[k] - 1)
@@ -272,4 +291,4 @@ def step(sch, st, dt, force_all=False):
                 fixed += 1
     info["faces"] = faces
     info["fixed"] = fixed
-    return State(Unew, beta, Vs_new), info
+    return State(Unew, beta, Vs_new, st.t + dt), info

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libadg.so")
 OK = 0
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_CAPACITY, ERR_STATE = -1, -2, -3, -4, -5, -6
 WARN_SUBCELL_INADMISSIBLE = 1
-BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_INFLOW = 0, 1, 2, 3
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_INFLOW, BC_FRONT = 0, 1, 2, 3, 4
 PREC_FP64, PREC_MIXED_FP32 = 0, 1
 OPT_DMP_EPS, OPT_DMP_FLOOR, OPT_FORCE_LIMITER, OPT_PICARD_ITERS, OPT_SLOT_CAPACITY = 1, 2, 3, 4, 5
 OPT_PROFILE = 6
@@ -42,7 +42,8 @@ SYMBOLS = ("adg_create", "adg_set_allocator", "adg_set_stream", "adg_set_option"
            "adg_max_dt", "adg_flags", "adg_read", "adg_troubled_count", "adg_status",
            "adg_sizes", "adg_info", "adg_phase_times", "adg_last_error", "adg_destroy",
            "adg_subcell_update_noalloc", "adg_time", "adg_batch_create", "adg_batch_step",
-           "adg_batch_destroy", "adg_step_batch", "adg_fallback_count", "adg_set_boundary_state")
+           "adg_batch_destroy", "adg_step_batch", "adg_fallback_count", "adg_set_boundary_state",
+           "adg_set_boundary_front", "adg_set_time")
 
 
 class AdgGrid(ctypes.Structure):
@@ -95,6 +96,8 @@ def load_library(path=None):
     lib.adg_troubled_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     lib.adg_fallback_count.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.adg_set_boundary_state.argtypes = [vp, ip, dp]
+    lib.adg_set_boundary_front.argtypes = [vp, ip, ip, ctypes.c_double, ctypes.c_double, ip, dp, ip, dp]
+    lib.adg_set_time.argtypes = [vp, ctypes.c_double]
     lib.adg_status.argtypes = [vp]
     lib.adg_sizes.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
@@ -177,7 +180,26 @@ class Solver:
         s = cls(w["dim"], w["ncell"], w["x0"], w["dx"], w["bc"], w["N"], w["gamma"], prec)
         for face, q in (w.get("bc_states") or {}).items():
             s.set_boundary_state(face, q)
+        for face, fr in (w.get("bc_fronts") or {}).items():
+            s.set_boundary_front(face, fr["axis"], fr["a"], fr["b"], fr["before"], fr["after"])
         return s
+
+    def set_boundary_front(self, face, axis, a, b, before, after):
+        """Moving split of front face `face`; before / after = (kind, state or None)."""
+        def arg(q):
+            if q is None:
+                return None, None
+            arr = np.ascontiguousarray(q, dtype=np.float64)
+            return arr, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        qb, pb = arg(before[1])
+        qa, pa = arg(after[1])
+        self._check(self.lib.adg_set_boundary_front(self.h, int(face), int(axis), float(a), float(b),
+                                                    int(before[0]), pb, int(after[0]), pa),
+                    "adg_set_boundary_front")
+
+    def set_time(self, t):
+        """Set the simulated time (restarts, time-dependent boundaries)."""
+        self._check(self.lib.adg_set_time(self.h, float(t)), "adg_set_time")
 
     def set_boundary_state(self, face, q):
         """Conserved state of inflow face `face` (2k low, 2k+1 high of axis k)."""

@@ -22,6 +22,7 @@ struct adg_state {
   bool host_passes = true;  // single-state steps launch only the limiter passes needed
   int sub_fp64 = 0;         // mixed precision: FP64 sweeps of the degree-2 subcell predictor
   int bstate_set = 0;       // bit f: inflow face f has a state
+  int front_set = 0;        // bit f: front face f has its front
   // pinned host mirror of the device Params, counters and dt, read once per
   // step after the DG phase when host_passes is on
   struct Probe {
@@ -249,9 +250,10 @@ int ensure_allocated(adg_state* st) {
   ALLOC(b.fblist, int, 3 * cap);
   b.fbflag = b.fblist + cap;
   b.refixlist = b.fblist + 2 * cap;
-  ALLOC(b.dt, double, 5);
+  ALLOC(b.dt, double, 6);
   b.lamred = b.dt + 1;
   b.clock = b.dt + 2;
+  b.tstart = b.dt + 5;
   ALLOC(st->dparams, Params, 1);
   ALLOC(st->d_pps1, Params*, 1);
   ALLOC(st->d_pre1, long long, 16);
@@ -268,7 +270,7 @@ int ensure_allocated(adg_state* st) {
   CUDA_TRY(st, cudaMemsetAsync(b.counters, 0, sizeof(int) * CNT_COUNT, st->stream));
   CUDA_TRY(st, cudaMemsetAsync(b.fixstamp, 0xff, sizeof(int) * cells, st->stream));
   CUDA_TRY(st, cudaMemsetAsync(b.fbflag, 0xff, sizeof(int) * cap, st->stream));
-  CUDA_TRY(st, cudaMemsetAsync(b.dt, 0, sizeof(double) * 5, st->stream));
+  CUDA_TRY(st, cudaMemsetAsync(b.dt, 0, sizeof(double) * 6, st->stream));
   {
     long long pre[16] = {0, cells, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int k = 0; k < st->dim; ++k) {
@@ -317,10 +319,14 @@ int upload_params(adg_state* st) {
 
 // Reset the current level's counters and the clock before a load
 int begin_load(adg_state* st) {
-  for (int f = 0; f < 2 * st->dim; ++f)
+  for (int f = 0; f < 2 * st->dim; ++f) {
     if (st->geo.bc[f] == ADG_BC_INFLOW && !(st->bstate_set & (1 << f)))
       return fail(st, ADG_ERR_ARG, "inflow face " + std::to_string(f) +
                                        " has no state (adg_set_boundary_state)");
+    if (st->geo.bc[f] == ADG_BC_FRONT && !(st->front_set & (1 << f)))
+      return fail(st, ADG_ERR_ARG, "front face " + std::to_string(f) +
+                                       " has no front (adg_set_boundary_front)");
+  }
   int rc = ensure_allocated(st);
   if (rc) return rc;
   rc = refresh(st);
@@ -804,7 +810,7 @@ int adg_create(const adg_grid* grid, int N, double gamma, const int* bc, int pre
   for (int k = 0; k < grid->dim; ++k) {
     if (grid->n[k] < 1 || !(grid->dx[k] > 0.0)) return ADG_ERR_ARG;
     const int lo = bc[2 * k], hi = bc[2 * k + 1];
-    if (lo < ADG_BC_PERIODIC || lo > ADG_BC_INFLOW || hi < ADG_BC_PERIODIC || hi > ADG_BC_INFLOW)
+    if (lo < ADG_BC_PERIODIC || lo > ADG_BC_FRONT || hi < ADG_BC_PERIODIC || hi > ADG_BC_FRONT)
       return ADG_ERR_ARG;
     if ((lo == ADG_BC_PERIODIC) != (hi == ADG_BC_PERIODIC)) return ADG_ERR_ARG;
   }
@@ -1108,6 +1114,49 @@ int adg_set_boundary_state(adg_state* st, int face, const double* q) {
   for (int v = 0; v < st->nv; ++v) st->geo.bstate[face][v] = q[v];
   st->bstate_set |= 1 << face;
   st->params_dirty = true;
+  return ADG_OK;
+}
+
+int adg_set_boundary_front(adg_state* st, int face, int axis, double a, double b, int kind_before,
+                           const double* q_before, int kind_after, const double* q_after) {
+  if (!st) return ADG_ERR_ARG;
+  if (face < 0 || face >= 2 * st->dim) return fail(st, ADG_ERR_ARG, "face out of range");
+  if (st->geo.bc[face] != ADG_BC_FRONT) return fail(st, ADG_ERR_ARG, "face is not a front face");
+  if (axis < 0 || axis >= st->dim || axis == face / 2)
+    return fail(st, ADG_ERR_ARG, "the front moves along a tangential axis of its face");
+  const int kinds[2] = {kind_before, kind_after};
+  const double* qs[2] = {q_before, q_after};
+  for (int part = 0; part < 2; ++part) {
+    const int kd = kinds[part];
+    if (kd != ADG_BC_TRANSMISSIVE && kd != ADG_BC_REFLECTIVE && kd != ADG_BC_INFLOW)
+      return fail(st, ADG_ERR_ARG, "a front part is transmissive, reflective or inflow");
+    for (int v = 0; v < 5; ++v) st->geo.front_state[face][part][v] = 0.0;
+    if (kd == ADG_BC_INFLOW) {
+      const double* q = qs[part];
+      if (!q) return fail(st, ADG_ERR_ARG, "an inflow part needs its state");
+      double kin = 0.0;
+      for (int k = 0; k < st->dim; ++k) kin += q[1 + k] * q[1 + k];
+      if (!(q[0] > 0.0) || !(q[st->dim + 1] * q[0] - 0.5 * kin > 0.0))
+        return fail(st, ADG_ERR_ARG, "inflow state must have rho > 0 and p > 0");
+      for (int v = 0; v < st->nv; ++v) st->geo.front_state[face][part][v] = q[v];
+    }
+    st->geo.front_kind[face][part] = kd;
+  }
+  if (!std::isfinite(a) || !std::isfinite(b)) return fail(st, ADG_ERR_ARG, "front position must be finite");
+  st->geo.front_axis[face] = axis;
+  st->geo.front_a[face] = a;
+  st->geo.front_b[face] = b;
+  st->front_set |= 1 << face;
+  st->params_dirty = true;
+  return ADG_OK;
+}
+
+int adg_set_time(adg_state* st, double t) {
+  if (!st) return ADG_ERR_ARG;
+  if (!st->loaded) return fail(st, ADG_ERR_ARG, "nothing loaded");
+  if (!std::isfinite(t)) return fail(st, ADG_ERR_ARG, "time must be finite");
+  CUDA_TRY(st, cudaMemcpyAsync(st->b.clock, &t, sizeof(double), cudaMemcpyHostToDevice, st->stream));
+  CUDA_TRY(st, cudaStreamSynchronize(st->stream));
   return ADG_OK;
 }
 

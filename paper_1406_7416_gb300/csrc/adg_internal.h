@@ -52,6 +52,11 @@ struct Geo {
   double x0[3];
   double dx[3];
   double bstate[6][5];   // conserved state of every ADG_BC_INFLOW face
+  // ADG_BC_FRONT faces: split at x_axis = a + b t; part 0 before, part 1 after
+  int front_axis[6];
+  int front_kind[6][2];
+  double front_a[6], front_b[6];
+  double front_state[6][2][5];
   long long cells;
 };
 
@@ -76,6 +81,7 @@ struct Bufs {
   double* dt;            // [1] time step of the current step (0: state idle this step)
   double* lamred;        // [1] reduced lambda
   double* clock;         // [3] simulated time t, end time t_end (0: none), steps taken
+  double* tstart;        // [1] simulated time at the start of the current step
   // limiter scratch, sized for one chunk of `chunk` troubled cells
   double* patch;         // [chunk][nv][L^d]
   double* sweep[3];      // [chunk][nv][...] after the x, y, z reconstructions
@@ -442,21 +448,43 @@ __device__ __forceinline__ bool face_neighbour(const Geo& g, const int* ijk, int
   return true;
 }
 
-// Ghost state beyond boundary face `face` (2k low, 2k+1 high of axis k) for
-// the interior state Q at the same point: transmissive a copy
-// (zero-gradient), reflective the mirror image (wall-normal momentum
-// negated), inflow the face's fixed state.  Not used for periodic faces.
+// Ghost state of one boundary kind for the interior state Q at a face normal
+// to axis k: transmissive a copy (zero-gradient), reflective the mirror image
+// (wall-normal momentum negated), inflow the fixed state q.
 template <int D>
-__device__ __forceinline__ void boundary_ghost(const Geo& g, int face, const double* Q, double* G) {
-  const int kind = g.bc[face];
+__device__ __forceinline__ void ghost_of_kind(int kind, int k, const double* q, const double* Q,
+                                              double* G) {
   if (kind == ADG_BC_INFLOW) {
 #pragma unroll
-    for (int v = 0; v < D + 2; ++v) G[v] = g.bstate[face][v];
+    for (int v = 0; v < D + 2; ++v) G[v] = q[v];
     return;
   }
 #pragma unroll
   for (int v = 0; v < D + 2; ++v) G[v] = Q[v];
-  if (kind == ADG_BC_REFLECTIVE) G[1 + (face >> 1)] = -G[1 + (face >> 1)];
+  if (kind == ADG_BC_REFLECTIVE) G[1 + k] = -G[1 + k];
+}
+
+// Part (0 before, 1 after) of front face `face` at coordinate pos along the
+// front's axis and time t.
+__device__ __forceinline__ int front_part(const Geo& g, int face, double pos, double t) {
+  return pos < g.front_a[face] + g.front_b[face] * t ? 0 : 1;
+}
+
+// Ghost state beyond boundary face `face` (2k low, 2k+1 high of axis k) for
+// the interior state Q at the same point; a front face picks its part by the
+// point's coordinate `pos` along the front's axis and the time t.  Not used
+// for periodic faces.
+template <int D>
+__device__ __forceinline__ void boundary_ghost(const Geo& g, int face, const double* Q, double* G,
+                                               double pos = 0.0, double t = 0.0) {
+  int kind = g.bc[face];
+  const double* q = g.bstate[face];
+  if (kind == ADG_BC_FRONT) {
+    const int part = front_part(g, face, pos, t);
+    kind = g.front_kind[face][part];
+    q = g.front_state[face][part];
+  }
+  ghost_of_kind<D>(kind, face >> 1, q, Q, G);
 }
 
 // Face index along axis k: faces (n_k + 1) along k, cells along the others.

@@ -56,6 +56,7 @@ __global__ void k_step_begin(StepLaunch sl) {
       if (!(rem > 1e-12 * tend)) dt = 0.0;
     }
     *p.b.dt = dt;
+    *p.b.tstart = t;
     if (dt > 0.0) {
       p.b.counters[CNT_TROUBLED0 + (1 - p.cur)] = 0;
       p.b.counters[CNT_FIX] = 0;

@@ -446,8 +446,25 @@ __global__ void __launch_bounds__(256) k_faceflux(Batch bt, int k) {
         QL[v] = trL[v * NT + ts + NF * m];
         QR[v] = trR[v * NT + ts + NF * m];
       }
-      if (!hasL) boundary_ghost<D>(g, 2 * k, QR, QL);
-      if (!hasR) boundary_ghost<D>(g, 2 * k + 1, QL, QR);
+      if (!hasL || !hasR) {
+        const int face = 2 * k + (hasL ? 1 : 0);
+        double pos = 0.0, t = 0.0;
+        if (g.bc[face] == ADG_BC_FRONT) {
+          // the node's coordinate along the front's axis, and its time
+          const int j = g.front_axis[face];
+          int a = 0, tt = ts;
+#pragma unroll
+          for (int jj = 0; jj < D; ++jj)
+            if (jj != k) {
+              if (jj == j) a = tt % n;
+              tt /= n;
+            }
+          pos = g.x0[j] + (ijk[j] + p.ops->xi[a]) * g.dx[j];
+          t = *p.b.tstart + p.ops->xi[m] * *p.b.dt;
+        }
+        if (!hasL) boundary_ghost<D>(g, face, QR, QL, pos, t);
+        else boundary_ghost<D>(g, face, QL, QR, pos, t);
+      }
       face_flux<D>(p.flux, QL, QR, k, p.gamma, Gm);
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] += w[m] * Gm[v];

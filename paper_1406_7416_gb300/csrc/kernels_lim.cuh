@@ -93,7 +93,16 @@ __device__ __forceinline__ void patch_value(const Params& p, const int* ijk, con
     int gi = ijk[k] * Ns + loc[k];
     if (gi < 0 || gi >= ng) {
       const int face = 2 * k + (gi < 0 ? 0 : 1);
-      const int kind = g.bc[face];
+      int kind = g.bc[face];
+      int part = -1;
+      if (kind == ADG_BC_FRONT) {
+        // the ghost subcell's centre along the front's axis (unmapped index)
+        const int j = g.front_axis[face];
+        const double h = g.dx[j] / Ns;
+        const double pos = g.x0[j] + ((ijk[j] * Ns + loc[j]) + 0.5) * h;
+        part = front_part(g, face, pos, *p.b.tstart);
+        kind = g.front_kind[face][part];
+      }
       if (kind == ADG_BC_PERIODIC) {
         gi = (gi % ng + ng) % ng;
       } else {
@@ -101,7 +110,8 @@ __device__ __forceinline__ void patch_value(const Params& p, const int* ijk, con
           gi = gi < 0 ? -1 - gi : 2 * ng - 1 - gi;
           mode[k] = 1;
         } else if (kind == ADG_BC_INFLOW) {
-          mode[k] = 2 + face;
+          // which fixed state: 2 + 2 face an inflow face's, 14 + 2 face + part a front part's
+          mode[k] = (part < 0) ? 2 + 2 * face : 14 + 2 * face + part;
         }
         gi = gi < 0 ? 0 : (gi >= ng ? ng - 1 : gi);
       }
@@ -115,8 +125,11 @@ __device__ __forceinline__ void patch_value(const Params& p, const int* ijk, con
     if (mode[k] == 1) {
       val[1 + k] = -val[1 + k];
     } else if (mode[k] >= 2) {
+      // 2 + 2 face: the inflow face's state; 14 + 2 face + part: a front part's
+      const int m = mode[k] - 2;
+      const double* q = (m < 12) ? g.bstate[m / 2] : g.front_state[(m - 12) / 2][(m - 12) % 2];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) val[v] = g.bstate[mode[k] - 2][v];
+      for (int v = 0; v < NV; ++v) val[v] = q[v];
     }
   }
 }

@@ -13,7 +13,8 @@ Seeds are 1406 + workload index with numpy's default_rng.
 
 A workload dict carries:
   dim, ncell, x0, dx, bc (per face: 0 periodic, 1 transmissive, 2 reflective,
-  3 inflow), bc_states (conserved state of each inflow face, optional), N,
+  3 inflow, 4 front), bc_states (conserved state of each inflow face),
+  bc_fronts (per front face: axis, a, b, before / after = (kind, state)), N,
   gamma, cfl, steps, problem (see below), name.
 Problem dicts: {"kind": "radial", "center", "radius", "inner", "outer",
 "cell_rho_factor"} with states (rho, vel..., p); {"kind": "quadrant", "center",
@@ -188,6 +189,50 @@ def shock_tube(name, nx=20, ny=5, N=9):
     w["bc_states"] = {0: conserved_state(left[0], (left[1], 0.0), left[2]),
                       1: conserved_state(right[0], (right[1], 0.0), right[2])}
     w["problem"] = dict(kind="quadrant", center=(0.5, 0.0), states=[rp, lp, lp, rp], vortex=None)
+    return w
+
+
+FRONT = 4
+
+
+def oblique_shock_states(gamma=GAMMA):
+    """Sec. 5.4: the Mach 10 shock of the double-Mach problem in the rotated
+    frame (x' along the shock normal): behind it (rho, u', v', p) =
+    (8/gamma, 8.25, 0, 116.5/gamma), ahead (1, 0, 0, 1/gamma).  Reading: the
+    printed factor 1/gamma scales density and pressure only -- with it on the
+    velocity too the pair would not satisfy the Rankine-Hugoniot conditions of
+    a shock moving at Mach 10 into the state ahead (sound speed 1)."""
+    return (8.0 / gamma, 8.25, 0.0, 116.5 / gamma), (1.0, 0.0, 0.0, 1.0 / gamma)
+
+
+def double_mach(nx=350, ny=100, N=5, length=3.5, shock_x=0.1, angle_deg=30.0, height=1.0):
+    """Double Mach reflection of Sec. 5.4 on [0, length] x [0, 1]: the shock
+    x' = x cos(angle) - y sin(angle) = shock_x (60 degrees to the wall),
+    moving along x' at speed 10.  Boundaries: post-shock inflow on the left,
+    outflow on the right; the bottom is post-shock inflow before the shock's
+    foot x = shock_x / cos(angle) and a reflecting wall after it; the top
+    follows the exact moving shock (post-shock state behind it, pre-shock
+    state ahead).  The paper's mesh is 350 x 100 (h = 1/100), N = 1, 2, 5, 9,
+    t_final = 0.2, Rusanov flux."""
+    a = np.radians(angle_deg)
+    c, s = np.cos(a), np.sin(a)
+    post_rot, pre = oblique_shock_states()
+    post = (post_rot[0], post_rot[1] * c, -post_rot[1] * s, post_rot[3])
+    qpost = conserved_state(post[0], (post[1], post[2]), post[3])
+    qpre = conserved_state(pre[0], (pre[1], pre[2]), pre[3])
+    w = dict(dim=2, ncell=(nx, ny), x0=(0.0, 0.0), dx=(length / nx, height / ny),
+             bc=(INFLOW, TRANSMISSIVE, FRONT, FRONT))
+    w.update(N=N, gamma=GAMMA, cfl=0.9 / (2 * (2 * N + 1)), steps=None, t_end=0.2,
+             name=f"double Mach reflection N={N} {nx}x{ny}")
+    w["bc_states"] = {0: qpost}
+    w["bc_fronts"] = {
+        # bottom: post-shock inflow before the foot of the shock, wall after it
+        2: dict(axis=0, a=shock_x / c, b=0.0, before=(INFLOW, qpost), after=(REFLECTIVE, None)),
+        # top (y = height): x'(x, height) = shock_x + 10 t <=> x = (shock_x + height s + 10 t) / c
+        3: dict(axis=0, a=(shock_x + height * s) / c, b=10.0 / c, before=(INFLOW, qpost),
+                after=(INFLOW, qpre)),
+    }
+    w["problem"] = dict(kind="planar", normal=(c, -s), offset=shock_x, inner=post, outer=pre)
     return w
 
 

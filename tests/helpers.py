@@ -37,7 +37,7 @@ def beta_from_abi(b, ncell):
 
 
 def oracle_setup(w, detect_ic=True, **kw):
-    g = Grid(w["ncell"], w["x0"], w["dx"], w["bc"], w.get("bc_states"))
+    g = Grid(w["ncell"], w["x0"], w["dx"], w["bc"], w.get("bc_states"), w.get("bc_fronts"))
     sch = Scheme(g, w["N"], w["gamma"], **kw)
     U0, V0 = project_problem(sch, w["problem"])
     return sch, initial_state(sch, U0, V0, detect_ic=detect_ic), U0, V0

@@ -149,3 +149,87 @@ def test_shock_tube_on_the_papers_mesh(name, bound):
     ex = riemann_exact.sample(left, right, (x - 0.5) / t_end)[0]
     err = float(np.sum(np.abs(rq - ex) * wq[None, :]) / nx)
     assert err < bound, (name, err)
+
+
+@pytest.mark.parametrize("force", [False, True])
+def test_double_mach_step_matches_oracle_mid_run(force):
+    """The double-Mach boundaries (front faces, time-dependent on the top):
+    two oracle steps, then the state goes to the GPU with its time
+    (adg_load_full + adg_set_time) and one more step on both sides."""
+    w = inputs.double_mach(nx=35, ny=10, N=2)
+    sch, st, _, _ = oracle_setup(w)
+    for _ in range(2):
+        st, _ = step(sch, st, stable_dt(sch, st, w["cfl"]))
+    dt = stable_dt(sch, st, w["cfl"])
+    s = adg.Solver.from_workload(w)
+    if force:
+        s.set_option(adg.OPT_FORCE_LIMITER, 1)
+    load_state(s, sch, st)
+    s.set_time(st.t)
+    s.step(dt)
+    d, b, sub = s.read_full()
+    assert s.status() == adg.OK
+    assert s.time()[0] == pytest.approx(st.t + dt, rel=1e-14)
+    ref, info = step(sch, st, dt, force_all=force)
+    beta = beta_from_abi(b, sch.grid.ncell)
+    if not force:
+        near = near_threshold_cells(sch, info)
+        assert not np.any((beta != ref.beta) & ~near)
+    np.testing.assert_array_equal(beta, ref.beta)
+    assert_close_rel(from_abi(d, 2, sch.grid.ncell, sch.N + 1), ref.U, RTOL, "DOFs")
+    tr = (slice(None),) + (ref.beta == 1,)
+    assert_close_rel(from_abi(sub, 2, sch.grid.ncell, sch.Ns)[tr], ref.Vs[tr], RTOL, "subcell data")
+    assert info["troubled"] > 0
+    s.close()
+
+
+def test_isolated_oblique_shock_moves_with_its_front():
+    """As the oracle pin: the shock alone, both horizontal boundaries following
+    the exact moving shock; after 80 GPU steps every row's shock stands within
+    one cell of x_s = (0.1 + 10 t + y sin 30) / cos 30."""
+    w = inputs.double_mach(nx=48, ny=6, N=2, length=1.2, height=0.25)
+    c, sn = np.cos(np.radians(30.0)), np.sin(np.radians(30.0))
+    w["bc_fronts"][2] = dict(axis=0, a=0.1 / c, b=10.0 / c, before=w["bc_fronts"][3]["before"],
+                             after=w["bc_fronts"][3]["after"])
+    s = adg.Solver.from_workload(w)
+    s.init_problem(w["problem"])
+    for _ in range(80):
+        s.step_cfl(w["cfl"])
+    t = s.time()[0]
+    U = s.read()
+    assert s.status() == adg.OK
+    s.close()
+    n = w["N"] + 1
+    W = 0.5 * np.polynomial.legendre.leggauss(n)[1]
+    nx, ny = w["ncell"]
+    rho = (U[:, 0, :] @ np.outer(W, W).ravel()).reshape(ny, nx)   # (row j, column i)
+    mid = 0.5 * (w["problem"]["inner"][0] + w["problem"]["outer"][0])
+    for j in range(ny):
+        y = (j + 0.5) * w["dx"][1]
+        row = rho[j]
+        i = int(np.nonzero(row < mid)[0][0])
+        x = (i - 1 + 0.5 + (row[i - 1] - mid) / (row[i - 1] - row[i])) * w["dx"][0]
+        exact = (0.1 + 10.0 * t + y * sn) / c
+        assert abs(x - exact) < w["dx"][0], (j, x, exact, t)
+
+
+@pytest.mark.parametrize("prec", [adg.PREC_FP64, adg.PREC_MIXED_FP32])
+def test_double_mach_runs_to_the_final_time(prec):
+    """Sec. 5.4 on a 175 x 50 mesh at N = 3 to t = 0.2: every step admissible
+    (the first-order layer takes the cells where WENO3 fails at the Mach 10
+    shock), the limiter stays on a small part of the grid."""
+    w = inputs.double_mach(nx=175, ny=50, N=3)
+    s = adg.Solver.from_workload(w, prec)
+    s.set_option(adg.OPT_END_TIME, w["t_end"])
+    s.init_problem(w["problem"])
+    worst = 0
+    while s.time()[0] < w["t_end"] * (1.0 - 1e-12):
+        for _ in range(50):
+            s.step_cfl(w["cfl"])
+        worst = max(worst, s.troubled_count())
+    U = s.read()
+    assert s.status() == adg.OK
+    assert np.isfinite(U).all()
+    cells = 175 * 50
+    assert 0 < worst < 0.25 * cells
+    s.close()

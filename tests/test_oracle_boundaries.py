@@ -181,3 +181,55 @@ def test_wall_bounds_equal_mirrored_domain_bounds(d):
     mf, Mf = det.neighbourhood_bounds(fmin, fmax, full)
     np.testing.assert_array_equal(mh, mf[:, nh[0]:])
     np.testing.assert_array_equal(Mh, Mf[:, nh[0]:])
+
+
+def test_double_mach_states_satisfy_rankine_hugoniot():
+    """Sec. 5.4 prints the post-shock state as (1/gamma)(8.0, 8.25, 0.0, 116.5)
+    ahead of (1, 0, 0, 1/gamma).  Read with 1/gamma on density and pressure
+    only, the pair satisfies the jump conditions of a shock moving at Mach 10
+    (speed 10: the sound speed ahead is 1) to the printed rounding; with the
+    velocity scaled as well it does not."""
+    from paper_1406_7416_gb300 import inputs
+    post, pre = inputs.oblique_shock_states()
+
+    def jumps(post):
+        r1, u1, p1 = post[0], post[1], post[3]
+        r0, u0, p0 = pre[0], pre[1], pre[3]
+        E1 = p1 / (GAMMA - 1) + 0.5 * r1 * u1 * u1
+        E0 = p0 / (GAMMA - 1) + 0.5 * r0 * u0 * u0
+        s = 10.0
+        return np.array([s * (r1 - r0) - (r1 * u1 - r0 * u0),
+                         s * (r1 * u1 - r0 * u0) - (r1 * u1 * u1 + p1 - r0 * u0 * u0 - p0),
+                         s * (E1 - E0) - (u1 * (E1 + p1) - u0 * (E0 + p0))]) / np.array(
+                             [s * r1, s * r1 * u1, s * E1])
+    assert np.abs(jumps(post)).max() < 2e-3
+    scaled = (post[0], post[1] / GAMMA, 0.0, post[3])
+    assert np.abs(jumps(scaled)).max() > 0.1
+
+
+def test_isolated_oblique_shock_moves_with_its_front():
+    """The double-Mach shock alone: both the lower and the upper boundary
+    follow the exact moving shock (post-shock state behind it, pre-shock state
+    ahead), the left is post-shock inflow, the right outflow.  After 20 steps
+    the shock in the middle row stands where the exact solution puts it, to
+    within one cell: x_s = (0.1 + 10 t + y sin 30) / cos 30."""
+    from paper_1406_7416_gb300 import inputs
+    w = inputs.double_mach(nx=48, ny=6, N=2, length=1.2, height=0.25)
+    c, s = np.cos(np.radians(30.0)), np.sin(np.radians(30.0))
+    post = w["bc_fronts"][3]["before"]
+    pre = w["bc_fronts"][3]["after"]
+    w["bc_fronts"][2] = dict(axis=0, a=0.1 / c, b=10.0 / c, before=post, after=pre)
+    g = Grid(w["ncell"], w["x0"], w["dx"], w["bc"], w["bc_states"], w["bc_fronts"])
+    sch, st = _setup(g, 2, w["problem"])
+    for _ in range(80):
+        st, _ = step(sch, st, stable_dt(sch, st, w["cfl"]))
+    wq = sch.basis.w
+    rho = (st.U[0] * np.outer(wq, wq)).sum(axis=(2, 3))      # cell averages (nx, ny)
+    mid = 0.5 * (w["problem"]["inner"][0] + w["problem"]["outer"][0])
+    for j in range(w["ncell"][1]):                             # every row, boundary rows too
+        y = (j + 0.5) * w["dx"][1]
+        row = rho[:, j]
+        i = int(np.nonzero(row < mid)[0][0])                    # first cell ahead of the shock
+        x = (i - 1 + 0.5 + (row[i - 1] - mid) / (row[i - 1] - row[i])) * w["dx"][0]
+        exact = (0.1 + 10.0 * st.t + y * s) / c
+        assert abs(x - exact) < 1.0 * w["dx"][0], (j, x, exact, st.t)
