@@ -46,6 +46,9 @@ def workload(n=None, N=N_ORDER):
         return inputs.explosion_3d(n=n or 128, N=3)
     if WORKLOAD == "quadrants200":
         return inputs.quadrants_2d(n=n or 200, N=9)
+    if WORKLOAD == "dmr":
+        nx = n or 350
+        return inputs.double_mach(nx=nx, ny=max(1, nx * 2 // 7), N=5)
     return inputs.quadrants_vortex_2d(n=n or GRID, N=N, steps=None)
 
 
@@ -455,7 +458,8 @@ def main():
                     help="cells per axis (profiling runs; default: the workload's own)")
     ap.add_argument("--only", default="both", choices=["both", "mixed", "fp64"])
     ap.add_argument("--workload", default="quadvortex512",
-                    choices=["quadvortex512", "explosion2d", "explosion3d", "quadrants200", "serving"])
+                    choices=["quadvortex512", "explosion2d", "explosion3d", "quadrants200", "dmr",
+                             "serving"])
     ap.add_argument("--runs", type=int, default=32, help="serving: number of runs")
     ap.add_argument("--t-end", type=float, default=0.02,
                     help="serving: end time cap of every run (each stops at min(cap, its final time))")

@@ -141,6 +141,8 @@ typedef struct {
  * adg_init_problem.  States are primitive: (rho, u, v, [w], p). */
 #define ADG_IC_RADIAL 0   /* inner state for |x - center| <= radius, else outer */
 #define ADG_IC_QUADRANT 1 /* 2D: state 1 x>xc,y>yc; 2 x<=xc,y>yc; 3 x<=xc,y<=yc; 4 x>xc,y<=yc */
+#define ADG_IC_PLANAR 2   /* inner state where normal . x < offset (a planar front, e.g. the
+                             oblique shock of Sec. 5.4), else outer */
 typedef struct {
   int kind;
   double center[3];
@@ -152,6 +154,8 @@ typedef struct {
   double vortex_center[2];
   double vortex_strength;         /* beta of Sec. 5.2                            */
   const double* cell_rho_factor;  /* host [cells] density factor, or NULL        */
+  double normal[3];               /* ADG_IC_PLANAR: front normal and offset      */
+  double offset;
 } adg_problem;
 
 typedef struct adg_state adg_state;

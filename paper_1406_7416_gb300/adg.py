@@ -34,7 +34,7 @@ OPT_HOST_PASSES = 13
 OPT_SUBCELL_FP64_SWEEPS = 14
 FLUX_RUSANOV, FLUX_OSHER = 0, 1
 PHASES = ("predictor", "faceflux", "correct_detect", "limiter", "fix")
-IC_RADIAL, IC_QUADRANT = 0, 1
+IC_RADIAL, IC_QUADRANT, IC_PLANAR = 0, 1, 2
 
 # every entry point declared in include/adg.h
 SYMBOLS = ("adg_create", "adg_set_allocator", "adg_set_stream", "adg_set_option", "adg_load",
@@ -57,7 +57,8 @@ class AdgProblem(ctypes.Structure):
                 ("outer", ctypes.c_double * 5), ("quad", (ctypes.c_double * 4) * 4),
                 ("vortex", ctypes.c_int), ("vortex_center", ctypes.c_double * 2),
                 ("vortex_strength", ctypes.c_double),
-                ("cell_rho_factor", ctypes.POINTER(ctypes.c_double))]
+                ("cell_rho_factor", ctypes.POINTER(ctypes.c_double)),
+                ("normal", ctypes.c_double * 3), ("offset", ctypes.c_double)]
 
 
 class AdgError(RuntimeError):
@@ -279,6 +280,15 @@ class Solver:
                 # per-cell factors in the ABI's cell order (x fastest)
                 fac = _contig(np.asarray(problem["cell_rho_factor"]).transpose().ravel(), np.float64)
                 pr.cell_rho_factor = _dptr(fac)
+        elif problem["kind"] == "planar":
+            pr.kind = IC_PLANAR
+            for k, c in enumerate(problem["normal"]):
+                pr.normal[k] = c
+            pr.offset = problem["offset"]
+            for k, v in enumerate(problem["inner"]):
+                pr.inner[k] = v
+            for k, v in enumerate(problem["outer"]):
+                pr.outer[k] = v
         else:
             pr.kind = IC_QUADRANT
             pr.center[0], pr.center[1] = problem["center"]

@@ -944,7 +944,7 @@ int adg_load(adg_state* st, const double* dofs, const double* exact) {
 
 int adg_init_problem(adg_state* st, const adg_problem* pr) {
   if (!st || !pr) return ADG_ERR_ARG;
-  if (pr->kind != ADG_IC_RADIAL && pr->kind != ADG_IC_QUADRANT)
+  if (pr->kind != ADG_IC_RADIAL && pr->kind != ADG_IC_QUADRANT && pr->kind != ADG_IC_PLANAR)
     return fail(st, ADG_ERR_ARG, "unknown problem kind");
   if (pr->kind == ADG_IC_QUADRANT && st->dim != 2)
     return fail(st, ADG_ERR_ARG, "quadrant problems are 2D");

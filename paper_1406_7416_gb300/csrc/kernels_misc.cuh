@@ -228,7 +228,16 @@ template <int D>
 __device__ __forceinline__ void problem_state(const adg_problem& pr, const double* x, double fac,
                                               double gamma, double* Q) {
   double rho, vel[3] = {0.0, 0.0, 0.0}, p;
-  if (pr.kind == ADG_IC_RADIAL) {
+  if (pr.kind == ADG_IC_PLANAR) {
+    double sdot = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) sdot += pr.normal[k] * x[k];
+    const double* s = (sdot < pr.offset) ? pr.inner : pr.outer;
+    rho = s[0] * fac;
+#pragma unroll
+    for (int k = 0; k < D; ++k) vel[k] = s[1 + k];
+    p = s[1 + D];
+  } else if (pr.kind == ADG_IC_RADIAL) {
     double r2 = 0.0;
 #pragma unroll
     for (int k = 0; k < D; ++k) r2 += (x[k] - pr.center[k]) * (x[k] - pr.center[k]);
