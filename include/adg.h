@@ -126,6 +126,13 @@ extern "C" {
                                      volume update stay FP64).  States batched
                                      together share one launch per value.          */
 
+#define ADG_OPT_WENO_FP32 15      /* mixed precision: the WENO3 reconstruction of the
+                                     subcell scheme runs in FP32 (default 1; the weights
+                                     use the ratio form (sigma_min+eps)/(sigma_k+eps),
+                                     which cannot underflow to 0/0); 0: FP64.  Like the
+                                     subcell predictor it only feeds the sub-face
+                                     fluxes, which stay FP64 with the FV update.     */
+
 #define ADG_FLUX_RUSANOV 0
 #define ADG_FLUX_OSHER 1
 

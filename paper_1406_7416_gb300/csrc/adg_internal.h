@@ -39,6 +39,11 @@ struct Ops {
   double E[9];
   // float copies for the reduced-precision Picard sweeps
   float Df[MAXN * MAXN], Ktf[MAXN * MAXN];
+  // FP32 WENO3 (mixed precision): per stencil k the rows of C for c1, c2
+  // (Cf[k][0..2], Cf[k][3..5]) and the nodal values straight from the stencil
+  // averages, Wf[k][node * 3 + r] = sum_p E[node][p] C[k][p][r]
+  float Cf[3][6];
+  float Wf[3][9];
 };
 
 // Builds the operator table of degree N (host, long double arithmetic).
@@ -149,6 +154,7 @@ struct StepLaunch {
   long long* pre_refix;        // [n+1] rebalanced WENO3 neighbours (device-computed)
   int cascade;                 // any state of the launch runs the first-order layer
   int sub32;                   // mixed precision: FP32 sweeps (of 3) of the subcell predictor
+  int weno32;                  // mixed precision: WENO3 reconstruction in FP32
   long long total_cells;
   long long total_faces[3];
   long long sum_chunk;         // sum over states of the limiter chunk size

@@ -208,10 +208,44 @@ __device__ __forceinline__ void weno3(const double* u, const Ops* __restrict__ o
   out[2] = (a0 * p2[0] + a1 * p2[1] + a2 * p2[2]) * inv;
 }
 
+// FP32 form of weno3 (mixed precision).  (sigma_k + eps)^8 underflows in FP32
+// for smooth data, so every t_k is divided by the smallest:
+// t_k = ((sigma_min + eps) / (sigma_k + eps))^8 lies in [0, 1] and the weights
+// lambda_k t_k / sum_j lambda_j t_j are those of weno3 (an underflow to 0 is
+// the exact limit).  The nodal values come straight from the stencil
+// averages (Wf = E C per stencil).
+__device__ __forceinline__ void weno3f(const float* u, const Ops* __restrict__ o, float* out) {
+  float sg[3], v[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float* C = o->Cf[k];
+    const float c1 = C[0] * u[k] + C[1] * u[k + 1] + C[2] * u[k + 2];
+    const float c2 = C[3] * u[k] + C[4] * u[k + 1] + C[5] * u[k + 2];
+    sg[k] = c1 * (c1 + 2.0f * c2) + (16.0f / 3.0f) * c2 * c2 + (float)WENO_EPS;
+    const float* W = o->Wf[k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) v[k][a] = W[a * 3] * u[k] + W[a * 3 + 1] * u[k + 1] + W[a * 3 + 2] * u[k + 2];
+  }
+  const float smin = fminf(sg[0], fminf(sg[1], sg[2]));
+  float wt[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float r = smin / sg[k];
+    r = r * r;
+    r = r * r;
+    wt[k] = r * r * (k == 1 ? (float)WENO_LAMBDA_C : 1.0f);
+  }
+  const float inv = 1.0f / (wt[0] + wt[1] + wt[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) out[a] = (wt[0] * v[0][a] + wt[1] * v[1][a] + wt[2] * v[2][a]) * inv;
+}
+
 // L1..L3: sweep along axis K.  Input extents (L or Ns+2 per axis) with NNIN
 // nodal values per element; the output has extent Ns+2 along K and 3 NNIN
 // nodes (the new nodal index is the slowest digit).
-template <int D, int N, int K>
+// T: the sweeps' precision (double; float for the mixed-precision FP32
+// reconstruction); the patch (input of the x sweep) is always FP64.
+template <int D, int N, int K, typename T>
 __global__ void __launch_bounds__(256) k_lim_sweep(Batch bt, int pass) {
   using DM = Dims<D, N>;
   constexpr int NV = DM::NV, L = DM::L, NE = DM::NE;
@@ -227,8 +261,7 @@ __global__ void __launch_bounds__(256) k_lim_sweep(Batch bt, int pass) {
     const long long t = eg / (NV * OUTSZ);
     const LimItem it = lim_item(bt, t);
     const Params& p = *bt.pps[it.s];
-    const double* in = (K == 0) ? p.b.patch : p.b.sweep[K > 0 ? K - 1 : 0];
-    double* out = p.b.sweep[K];
+    T* out = reinterpret_cast<T*>(p.b.sweep[K]);
     const long long e = eg - t * (NV * OUTSZ) + (long long)it.j * (NV * OUTSZ);
     const long long jv = e / OUTSZ;
     int r = (int)(e - jv * OUTSZ);
@@ -240,14 +273,22 @@ __global__ void __launch_bounds__(256) k_lim_sweep(Batch bt, int pass) {
     const int x2 = r / O1;
     // input element whose axis-K index equals the output's (stencil x_K .. x_K + 4)
     const int off = x0 + I0 * (x1 + I1 * x2);
-    const double* src = in + jv * INSZ + (size_t)off * NNIN + node;
-    double u[5];
+    const size_t src_off = jv * INSZ + (size_t)off * NNIN + node;
+    T u[5];
+    if (K == 0) {
+      const double* src = p.b.patch + src_off;
 #pragma unroll
-    for (int q = 0; q < 5; ++q) u[q] = src[q * STRIDE];
-    double res[3];
-    weno3(u, ops, res);
+      for (int q = 0; q < 5; ++q) u[q] = (T)src[q * STRIDE];
+    } else {
+      const T* src = reinterpret_cast<const T*>(p.b.sweep[K > 0 ? K - 1 : 0]) + src_off;
+#pragma unroll
+      for (int q = 0; q < 5; ++q) u[q] = src[q * STRIDE];
+    }
+    T res[3];
+    if constexpr (sizeof(T) == sizeof(double)) weno3(u, ops, res);
+    else weno3f(u, ops, res);
     const int ooff = x0 + O0 * (x1 + O1 * x2);
-    double* dst = out + jv * (size_t)OUTSZ * 3 + (size_t)ooff * NNIN * 3 + node;
+    T* dst = out + jv * (size_t)OUTSZ * 3 + (size_t)ooff * NNIN * 3 + node;
 #pragma unroll
     for (int a = 0; a < 3; ++a) dst[a * NNIN] = res[a];
   }
@@ -294,7 +335,7 @@ __device__ __forceinline__ int cross_subcell(int r) {
 
 // n32: sweeps (of 3) run in FP32 before the FP64 ones (MIXED only; the same
 // for the whole launch, so every block takes the same barriers).
-template <int D, int N, bool MIXED>
+template <int D, int N, bool MIXED, typename WT>
 __global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass, int n32) {
   using DM = Dims<D, N>;
   constexpr int NV = DM::NV, NST3 = DM::NST3, ND3 = DM::ND3, NED = DM::NED, Ns = DM::Ns;
@@ -339,12 +380,12 @@ __global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass, int n32
       }
     }
     const double gm1 = p.gamma - 1.0;
-    const double* W = p.b.sweep[D - 1];          // [j][v][NED][ND3]
+    const WT* W = reinterpret_cast<const WT*>(p.b.sweep[D - 1]);   // [j][v][NED][ND3]
     __syncthreads();
     if (live) {
       for (int e = lt; e < NV * ND3; e += NST3) {
         const int v = e / ND3, i = e - v * ND3;
-        su[grp][e] = W[((j * NV + v) * NED + sc) * ND3 + i];
+        su[grp][e] = (double)W[((j * NV + v) * NED + sc) * ND3 + i];
       }
     }
     __syncthreads();

@@ -89,17 +89,23 @@ struct Launch {
     for (int pass = 0; pass < sl.max_passes; ++pass) {
       if ((e = launch_lim_prefix(sl, pass, s)) != cudaSuccess) return e;
       k_lim_patch<D, N><<<grid_for(ch * DM::LD, 256), 256, 0, s>>>(lim, pass);
-      k_lim_sweep<D, N, 0><<<grid_for(ch * NV * DM::LD, 256), 256, 0, s>>>(lim, pass);
-      k_lim_sweep<D, N, 1><<<grid_for(ch * NV * DM::LD, 256), 256, 0, s>>>(lim, pass);
-      if (D == 3)
-        k_lim_sweep<D, N, (D == 3 ? 2 : 1)><<<grid_for(ch * NV * DM::LD, 256), 256, 0, s>>>(lim, pass);
       const long long ncross = ch * (DM::NSD + 2 * D * DM::NSF);
-      if (sl.prec == ADG_PREC_MIXED_FP32)
-        k_lim_predict<D, N, true><<<grid_for(ncross, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(
-            lim, pass, sl.sub32);
-      else
-        k_lim_predict<D, N, false><<<grid_for(ncross, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(
-            lim, pass, 0);
+      const int gs = grid_for(ch * NV * DM::LD, 256), gp = grid_for(ncross, SPB, kNumSM * 16);
+      if (sl.prec == ADG_PREC_MIXED_FP32 && sl.weno32) {
+        // mixed precision: FP32 reconstruction feeding the FP32 subcell predictor
+        k_lim_sweep<D, N, 0, float><<<gs, 256, 0, s>>>(lim, pass);
+        k_lim_sweep<D, N, 1, float><<<gs, 256, 0, s>>>(lim, pass);
+        if (D == 3) k_lim_sweep<D, N, (D == 3 ? 2 : 1), float><<<gs, 256, 0, s>>>(lim, pass);
+        k_lim_predict<D, N, true, float><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, sl.sub32);
+      } else {
+        k_lim_sweep<D, N, 0, double><<<gs, 256, 0, s>>>(lim, pass);
+        k_lim_sweep<D, N, 1, double><<<gs, 256, 0, s>>>(lim, pass);
+        if (D == 3) k_lim_sweep<D, N, (D == 3 ? 2 : 1), double><<<gs, 256, 0, s>>>(lim, pass);
+        if (sl.prec == ADG_PREC_MIXED_FP32)
+          k_lim_predict<D, N, true, double><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, sl.sub32);
+        else
+          k_lim_predict<D, N, false, double><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, 0);
+      }
       k_lim_flux<D, N, 0><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, pass);
       k_lim_flux<D, N, 1><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, pass);
       if (D == 3)

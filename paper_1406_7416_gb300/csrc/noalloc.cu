@@ -131,12 +131,12 @@ struct NoAlloc {
     constexpr int SPB = (D == 2) ? SUBS_PER_BLOCK_2D : SUBS_PER_BLOCK_3D;
     const long long ch = count;
     const Batch lim{pps, 1, pre};
-    k_lim_sweep<D, N, 0><<<grid_for(ch * DM::NV * DM::LD, 256), 256, 0, s>>>(lim, 0);
-    k_lim_sweep<D, N, 1><<<grid_for(ch * DM::NV * DM::LD, 256), 256, 0, s>>>(lim, 0);
+    k_lim_sweep<D, N, 0, double><<<grid_for(ch * DM::NV * DM::LD, 256), 256, 0, s>>>(lim, 0);
+    k_lim_sweep<D, N, 1, double><<<grid_for(ch * DM::NV * DM::LD, 256), 256, 0, s>>>(lim, 0);
     if (D == 3)
-      k_lim_sweep<D, N, (D == 3 ? 2 : 1)><<<grid_for(ch * DM::NV * DM::LD, 256), 256, 0, s>>>(lim, 0);
+      k_lim_sweep<D, N, (D == 3 ? 2 : 1), double><<<grid_for(ch * DM::NV * DM::LD, 256), 256, 0, s>>>(lim, 0);
     const long long ncross = ch * (DM::NSD + 2 * D * DM::NSF);
-    k_lim_predict<D, N, false><<<grid_for(ncross, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(lim, 0, 0);
+    k_lim_predict<D, N, false, double><<<grid_for(ncross, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(lim, 0, 0);
     k_lim_flux<D, N, 0><<<grid_for(ch * (DM::Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, 0);
     k_lim_flux<D, N, 1><<<grid_for(ch * (DM::Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, 0);
     if (D == 3)

@@ -221,6 +221,18 @@ void build_ops(int N, Ops* o) {
     }
     invert(A, 3);   // A^{-1}[p][r]: monomial p from cell r
     for (int i = 0; i < 9; ++i) o->C[k][i] = (double)A[i];
+    for (int r = 0; r < 3; ++r) {
+      o->Cf[k][r] = (float)A[3 + r];
+      o->Cf[k][3 + r] = (float)A[6 + r];
+    }
+    // nodes of the degree-2 subcell basis (3 GL points on [0, 1])
+    const ld x3n[3] = {0.5L - sqrtl(0.15L), 0.5L, 0.5L + sqrtl(0.15L)};
+    for (int j = 0; j < 3; ++j)
+      for (int r = 0; r < 3; ++r) {
+        ld v = 0.0L;
+        for (int q = 0; q < 3; ++q) v += powl(x3n[j], (ld)q) * A[q * 3 + r];
+        o->Wf[k][j * 3 + r] = (float)v;
+      }
   }
 }
 
