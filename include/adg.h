@@ -126,12 +126,15 @@ extern "C" {
                                      volume update stay FP64).  States batched
                                      together share one launch per value.          */
 
-#define ADG_OPT_WENO_FP32 15      /* mixed precision: the WENO3 reconstruction of the
-                                     subcell scheme runs in FP32 (default 1; the weights
-                                     use the ratio form (sigma_min+eps)/(sigma_k+eps),
-                                     which cannot underflow to 0/0); 0: FP64.  Like the
-                                     subcell predictor it only feeds the sub-face
-                                     fluxes, which stay FP64 with the FV update.     */
+#define ADG_OPT_SUBCELL_FP32 15   /* mixed precision: the subcell scheme's WENO3
+                                     reconstruction (weights in the ratio form
+                                     ((sigma_min+eps)/(sigma_k+eps))^8, which cannot
+                                     underflow to 0/0) and its sub-face Rusanov fluxes
+                                     run in FP32 (default 1); the finite volume update,
+                                     R and the flux correction stay FP64, and each
+                                     sub-face flux is one value for both sides, so the
+                                     scheme stays conservative.  0: FP64.  With the
+                                     Osher-type flux the sub-faces stay FP64.        */
 
 #define ADG_FLUX_RUSANOV 0
 #define ADG_FLUX_OSHER 1

@@ -21,7 +21,7 @@ struct adg_state {
   int flux = ADG_FLUX_RUSANOV;
   bool host_passes = true;  // single-state steps launch only the limiter passes needed
   int sub_fp64 = 0;         // mixed precision: FP64 sweeps of the degree-2 subcell predictor
-  int weno32 = 1;           // mixed precision: FP32 WENO3 reconstruction
+  int sub_f32 = 1;          // mixed precision: FP32 subcell reconstruction and sub-face fluxes
   int bstate_set = 0;       // bit f: inflow face f has a state
   int front_set = 0;        // bit f: front face f has its front
   // pinned host mirror of the device Params, counters and dt, read once per
@@ -420,7 +420,8 @@ StepLaunch single_launch(adg_state* st) {
   sl.pre_refix = st->d_pre1 + 14;
   sl.cascade = st->cascade;
   sl.sub32 = 3 - st->sub_fp64;
-  sl.weno32 = st->weno32;
+  sl.sub_f32 = st->sub_f32;
+  sl.flux = st->flux;
   sl.total_cells = st->geo.cells;
   for (int k = 0; k < st->dim; ++k) {
     long long faces = 1;
@@ -640,7 +641,7 @@ int adg_batch_create(adg_state* const* states, int count, void* stream, adg_batc
       const adg_state* a = states[i];
       const adg_state* c = states[j];
       if (!done[j] && a->dim == c->dim && a->N == c->N && a->prec == c->prec &&
-          a->sub_fp64 == c->sub_fp64 && a->weno32 == c->weno32) {
+          a->sub_fp64 == c->sub_fp64 && a->sub_f32 == c->sub_f32 && a->flux == c->flux) {
         g.idx.push_back(j);
         done[j] = 1;
       }
@@ -692,7 +693,8 @@ int adg_batch_create(adg_state* const* states, int count, void* stream, adg_batc
     sl.max_passes = max_passes;
     sl.prec = g.rep->prec;
     sl.sub32 = 3 - g.rep->sub_fp64;
-    sl.weno32 = g.rep->weno32;
+    sl.sub_f32 = g.rep->sub_f32;
+    sl.flux = g.rep->flux;
     sl.ev = nullptr;
     g.sl = sl;
     g.dts_off = off;
@@ -904,8 +906,8 @@ int adg_set_option(adg_state* st, int key, double value) {
       if (!(value >= 0.0 && value <= 3.0)) return fail(st, ADG_ERR_ARG, "subcell FP64 sweeps in 0..3");
       st->sub_fp64 = (int)value;
       return ADG_OK;
-    case ADG_OPT_WENO_FP32:
-      st->weno32 = value != 0.0;
+    case ADG_OPT_SUBCELL_FP32:
+      st->sub_f32 = value != 0.0;
       return ADG_OK;
     case ADG_OPT_HOST_PASSES:
       st->host_passes = value != 0.0;

@@ -154,7 +154,8 @@ struct StepLaunch {
   long long* pre_refix;        // [n+1] rebalanced WENO3 neighbours (device-computed)
   int cascade;                 // any state of the launch runs the first-order layer
   int sub32;                   // mixed precision: FP32 sweeps (of 3) of the subcell predictor
-  int weno32;                  // mixed precision: WENO3 reconstruction in FP32
+  int sub_f32;                  // mixed precision: WENO3 reconstruction and sub-face fluxes in FP32
+  int flux;                    // numerical flux of the launch's states (ADG_FLUX_*)
   long long total_cells;
   long long total_faces[3];
   long long sum_chunk;         // sum over states of the limiter chunk size
@@ -392,6 +393,33 @@ __device__ __forceinline__ void osher(const double* QL, const double* QR, int k,
   }
 #pragma unroll
   for (int v = 0; v < NV; ++v) G[v] = 0.5 * (FL[v] + FR[v]) - 0.5 * acc[v];
+}
+
+// FP32 Rusanov flux (mixed-precision sub-faces), the same formulas as rusanov.
+template <int D>
+__device__ __forceinline__ void rusanov_f(const float* QL, const float* QR, int k, float gamma,
+                                          float* G) {
+  const float gm1 = gamma - 1.0f;
+  float s[2], F[2][D + 2];
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const float* Q = side ? QR : QL;
+    const float r = 1.0f / Q[0];
+    float kin = 0.0f;
+#pragma unroll
+    for (int j = 0; j < D; ++j) kin += Q[1 + j] * Q[1 + j];
+    const float p = gm1 * (Q[D + 1] - 0.5f * kin * r);
+    const float vk = Q[1 + k] * r;
+    s[side] = fabsf(vk) + sqrtf(gamma * p * r);
+    F[side][0] = Q[1 + k];
+#pragma unroll
+    for (int j = 0; j < D; ++j) F[side][1 + j] = Q[1 + j] * vk;
+    F[side][1 + k] += p;
+    F[side][D + 1] = vk * (Q[D + 1] + p);
+  }
+  const float sm = (s[0] > s[1] || s[0] != s[0]) ? s[0] : s[1];   // NaN propagates
+#pragma unroll
+  for (int v = 0; v < D + 2; ++v) G[v] = 0.5f * (F[0][v] + F[1][v]) - 0.5f * sm * (QR[v] - QL[v]);
 }
 
 // The numerical flux selected by the state's option (0 Rusanov, 1 Osher-type).

@@ -435,7 +435,9 @@ __global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass, int n32
 // L5: sub-face fluxes normal to axis k: Rusanov at the 3^(d-1) x 3
 // tangential x time GL points, averaged with the GL weights.  Faces f = 0..Ns
 // along k (between local subcells f-1 and f), tangential subcells 0..Ns-1.
-template <int D, int N, int k>
+// T: the flux precision (double; float for the mixed-precision FP32 subcell
+// scheme, Rusanov only); the result is stored in FP64.
+template <int D, int N, int k, typename T>
 __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
   using DM = Dims<D, N>;
   constexpr int NV = DM::NV, NST3 = DM::NST3, ND3 = DM::ND3, NE = DM::NE, NED = DM::NED,
@@ -484,13 +486,13 @@ __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
       if (lo_wall && ijk[k] == 0) wall = -1;
       if (hi_wall && ijk[k] == p.geo.n[k] - 1) wall = 1;
     }
-    double acc[NV];
+    T acc[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+    for (int v = 0; v < NV; ++v) acc[v] = T(0);
     // tangential x time nodes: digits over axes != k, then time
     for (int t = 0; t < ND3; ++t) {
       int base = 0, tt = t, wmul = 1;
-      double wt = 1.0;
+      T wt = T(1);
       int st = 1;
 #pragma unroll
       for (int a = 0; a < D; ++a) {
@@ -498,21 +500,21 @@ __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
           const int dg = tt % 3;
           tt /= 3;
           base += dg * st;
-          wt *= o->w3[dg];
+          wt *= (T)o->w3[dg];
         }
         st *= 3;
       }
       const int m = tt;                 // remaining digit: time node
-      wt *= o->w3[m];
+      wt *= (T)o->w3[m];
       base += m * ND3;
       (void)wmul;
-      double QL[NV], QR[NV], G[NV];
+      T QL[NV], QR[NV], G[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         const double* a = qL + v * NST3 + base;
         const double* b = qR + v * NST3 + base;
-        QL[v] = o->phi13[0] * a[0] + o->phi13[1] * a[stk] + o->phi13[2] * a[2 * stk];
-        QR[v] = o->phi03[0] * b[0] + o->phi03[1] * b[stk] + o->phi03[2] * b[2 * stk];
+        QL[v] = (T)o->phi13[0] * (T)a[0] + (T)o->phi13[1] * (T)a[stk] + (T)o->phi13[2] * (T)a[2 * stk];
+        QR[v] = (T)o->phi03[0] * (T)b[0] + (T)o->phi03[1] * (T)b[stk] + (T)o->phi03[2] * (T)b[2 * stk];
       }
       if (wall < 0) {
 #pragma unroll
@@ -523,13 +525,14 @@ __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
         for (int v = 0; v < NV; ++v) QR[v] = QL[v];
         QR[1 + k] = -QL[1 + k];
       }
-      face_flux<D>(p.flux, QL, QR, k, p.gamma, G);
+      if constexpr (sizeof(T) == sizeof(double)) face_flux<D>(p.flux, QL, QR, k, p.gamma, G);
+      else rusanov_f<D>(QL, QR, k, (float)p.gamma, G);
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] += wt * G[v];
     }
     double* dst = p.b.fsub[k] + (size_t)j * NV * NFK + (e - j * NFK);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) dst[v * NFK] = acc[v];
+    for (int v = 0; v < NV; ++v) dst[v * NFK] = (double)acc[v];
   }
 }
 

@@ -91,7 +91,7 @@ struct Launch {
       k_lim_patch<D, N><<<grid_for(ch * DM::LD, 256), 256, 0, s>>>(lim, pass);
       const long long ncross = ch * (DM::NSD + 2 * D * DM::NSF);
       const int gs = grid_for(ch * NV * DM::LD, 256), gp = grid_for(ncross, SPB, kNumSM * 16);
-      if (sl.prec == ADG_PREC_MIXED_FP32 && sl.weno32) {
+      if (sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32) {
         // mixed precision: FP32 reconstruction feeding the FP32 subcell predictor
         k_lim_sweep<D, N, 0, float><<<gs, 256, 0, s>>>(lim, pass);
         k_lim_sweep<D, N, 1, float><<<gs, 256, 0, s>>>(lim, pass);
@@ -106,11 +106,16 @@ struct Launch {
         else
           k_lim_predict<D, N, false, double><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, 0);
       }
-      k_lim_flux<D, N, 0><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, pass);
-      k_lim_flux<D, N, 1><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, pass);
-      if (D == 3)
-        k_lim_flux<D, N, (D == 3 ? 2 : 1)><<<grid_for(ch * (Ns + 1) * DM::NSF, 256), 256, 0, s>>>(
-            lim, pass);
+      const int gf = grid_for(ch * (Ns + 1) * DM::NSF, 256);
+      if (sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32 && sl.flux == ADG_FLUX_RUSANOV) {
+        k_lim_flux<D, N, 0, float><<<gf, 256, 0, s>>>(lim, pass);
+        k_lim_flux<D, N, 1, float><<<gf, 256, 0, s>>>(lim, pass);
+        if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), float><<<gf, 256, 0, s>>>(lim, pass);
+      } else {
+        k_lim_flux<D, N, 0, double><<<gf, 256, 0, s>>>(lim, pass);
+        k_lim_flux<D, N, 1, double><<<gf, 256, 0, s>>>(lim, pass);
+        if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), double><<<gf, 256, 0, s>>>(lim, pass);
+      }
       k_lim_update<D, N><<<(int)(ch < kNumSM * 8 ? ch : kNumSM * 8), 128, su, s>>>(lim, pass);
     }
     if (sl.cascade) {

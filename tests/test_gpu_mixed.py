@@ -197,7 +197,7 @@ def test_vortex_table_with_osher_flux(N):
 
 def test_subcell_predictor_sweep_precision():
     """With every cell on the subgrid the DG candidate is discarded, so the
-    mixed path with an FP64 reconstruction (ADG_OPT_WENO_FP32 = 0) and all
+    mixed path with an FP64 reconstruction (ADG_OPT_SUBCELL_FP32 = 0) and all
     three subcell Picard sweeps in FP64 (ADG_OPT_SUBCELL_FP64_SWEEPS = 3)
     equals the FP64 path bit for bit; the default (FP32 reconstruction and
     sweeps, FP64 sub-face fluxes and update) stays within 1e-6 of it in L1
@@ -210,7 +210,7 @@ def test_subcell_predictor_sweep_precision():
         s.set_option(adg.OPT_FORCE_LIMITER, 1)
         if sub is not None:
             s.set_option(adg.OPT_SUBCELL_FP64_SWEEPS, sub)
-            s.set_option(adg.OPT_WENO_FP32, 0)
+            s.set_option(adg.OPT_SUBCELL_FP32, 0)
         s.init_problem(w["problem"])
         out[key + "_0"] = s.read()
         for _ in range(5):
