@@ -335,16 +335,19 @@ __device__ __forceinline__ int cross_subcell(int r) {
 
 // n32: sweeps (of 3) run in FP32 before the FP64 ones (MIXED only; the same
 // for the whole launch, so every block takes the same barriers).
-template <int D, int N, bool MIXED, typename WT>
+// QF: the whole predictor in FP32 (n32 = 3) from an FP32 reconstruction, the
+// space-time nodal values stored in FP32 (qsub read as float by k_lim_flux).
+template <int D, int N, bool MIXED, typename WT, bool QF>
 __global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass, int n32) {
   using DM = Dims<D, N>;
   constexpr int NV = DM::NV, NST3 = DM::NST3, ND3 = DM::ND3, NED = DM::NED, Ns = DM::Ns;
   constexpr int NCROSS = DM::NSD + 2 * D * DM::NSF;
   constexpr int SPB = (D == 2) ? SUBS_PER_BLOCK_2D : SUBS_PER_BLOCK_3D;
   constexpr int SPBF = MIXED ? SPB : 1;
-  __shared__ double su[SPB][NV * ND3];
-  __shared__ double sq[SPB][NV * NST3];
-  __shared__ double sF[SPB][D * NV * NST3];
+  constexpr int SPBD = QF ? 1 : SPB;           // FP64 staging (unused when QF)
+  __shared__ double su[SPBD][NV * ND3];
+  __shared__ double sq[SPBD][NV * NST3];
+  __shared__ double sF[SPBD][D * NV * NST3];
   __shared__ float suf[SPBF][NV * ND3];
   __shared__ float sqf[SPBF][NV * NST3];
   __shared__ float sFf[SPBF][D * NV * NST3];
@@ -382,6 +385,33 @@ __global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass, int n32
     const double gm1 = p.gamma - 1.0;
     const WT* W = reinterpret_cast<const WT*>(p.b.sweep[D - 1]);   // [j][v][NED][ND3]
     __syncthreads();
+    if constexpr (QF) {
+      if (live)
+        for (int e = lt; e < NV * ND3; e += NST3) {
+          const int v = e / ND3, i = e - v * ND3;
+          suf[grp][e] = (float)W[((j * NV + v) * NED + sc) * ND3 + i];
+        }
+      __syncthreads();
+      if (live)
+        for (int e = lt; e < NV * NST3; e += NST3) {
+          const int v = e / NST3, l = e - v * NST3;
+          sqf[grp][e] = suf[grp][v * ND3 + (l % ND3)];
+        }
+      __syncthreads();
+      for (int it = 0; it < 3; ++it) {
+        if (live) picard_flux<D, 3, float>(sqf[grp], sFf[grp], (float)gm1, lt, NST3);
+        __syncthreads();
+        if (live) picard_deriv<D, 3, float>(sFf[grp], sqf[grp], D3f, cf, lt, NST3);
+        __syncthreads();
+        if (live) picard_time<D, 3, float>(sqf[grp], suf[grp], K3f, lt, NST3);
+        __syncthreads();
+      }
+      if (live) {
+        float* dst = reinterpret_cast<float*>(p.b.qsub) + ((size_t)j * NED + sc) * (size_t)(NV * NST3);
+        for (int e = lt; e < NV * NST3; e += NST3) dst[e] = sqf[grp][e];
+      }
+      continue;
+    }
     if (live) {
       for (int e = lt; e < NV * ND3; e += NST3) {
         const int v = e / ND3, i = e - v * ND3;
@@ -437,7 +467,9 @@ __global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass, int n32
 // along k (between local subcells f-1 and f), tangential subcells 0..Ns-1.
 // T: the flux precision (double; float for the mixed-precision FP32 subcell
 // scheme, Rusanov only); the result is stored in FP64.
-template <int D, int N, int k, typename T>
+// QT: the element type of the stored subcell predictor (float when it ran
+// wholly in FP32, see k_lim_predict).
+template <int D, int N, int k, typename T, typename QT>
 __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
   using DM = Dims<D, N>;
   constexpr int NV = DM::NV, NST3 = DM::NST3, ND3 = DM::ND3, NE = DM::NE, NED = DM::NED,
@@ -470,8 +502,8 @@ __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
       sr += ir * mul;
       mul *= NE;
     }
-    const double* qL = p.b.qsub + ((size_t)j * NED + sl) * NV * NST3;
-    const double* qR = p.b.qsub + ((size_t)j * NED + sr) * NV * NST3;
+    const QT* qL = reinterpret_cast<const QT*>(p.b.qsub) + ((size_t)j * NED + sl) * NV * NST3;
+    const QT* qR = reinterpret_cast<const QT*>(p.b.qsub) + ((size_t)j * NED + sr) * NV * NST3;
     // a sub-face on a reflecting wall takes its flux between the interior
     // trace and its mirror image (no mass or energy through the wall)
     // (the troubled-cell list is read only when the face can be a wall: the
@@ -511,8 +543,8 @@ __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
       T QL[NV], QR[NV], G[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const double* a = qL + v * NST3 + base;
-        const double* b = qR + v * NST3 + base;
+        const QT* a = qL + v * NST3 + base;
+        const QT* b = qR + v * NST3 + base;
         QL[v] = (T)o->phi13[0] * (T)a[0] + (T)o->phi13[1] * (T)a[stk] + (T)o->phi13[2] * (T)a[2 * stk];
         QR[v] = (T)o->phi03[0] * (T)b[0] + (T)o->phi03[1] * (T)b[stk] + (T)o->phi03[2] * (T)b[2 * stk];
       }

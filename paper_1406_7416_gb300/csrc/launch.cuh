@@ -91,30 +91,45 @@ struct Launch {
       k_lim_patch<D, N><<<grid_for(ch * DM::LD, 256), 256, 0, s>>>(lim, pass);
       const long long ncross = ch * (DM::NSD + 2 * D * DM::NSF);
       const int gs = grid_for(ch * NV * DM::LD, 256), gp = grid_for(ncross, SPB, kNumSM * 16);
+      // the subcell predictor stored in FP32 when it runs wholly in FP32
+      const bool qf = sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32 && sl.sub32 == 3;
       if (sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32) {
         // mixed precision: FP32 reconstruction feeding the FP32 subcell predictor
         k_lim_sweep<D, N, 0, float><<<gs, 256, 0, s>>>(lim, pass);
         k_lim_sweep<D, N, 1, float><<<gs, 256, 0, s>>>(lim, pass);
         if (D == 3) k_lim_sweep<D, N, (D == 3 ? 2 : 1), float><<<gs, 256, 0, s>>>(lim, pass);
-        k_lim_predict<D, N, true, float><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, sl.sub32);
+        if (qf)
+          k_lim_predict<D, N, true, float, true><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, 3);
+        else
+          k_lim_predict<D, N, true, float, false><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, sl.sub32);
       } else {
         k_lim_sweep<D, N, 0, double><<<gs, 256, 0, s>>>(lim, pass);
         k_lim_sweep<D, N, 1, double><<<gs, 256, 0, s>>>(lim, pass);
         if (D == 3) k_lim_sweep<D, N, (D == 3 ? 2 : 1), double><<<gs, 256, 0, s>>>(lim, pass);
         if (sl.prec == ADG_PREC_MIXED_FP32)
-          k_lim_predict<D, N, true, double><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, sl.sub32);
+          k_lim_predict<D, N, true, double, false><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, sl.sub32);
         else
-          k_lim_predict<D, N, false, double><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, 0);
+          k_lim_predict<D, N, false, double, false><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, 0);
       }
       const int gf = grid_for(ch * (Ns + 1) * DM::NSF, 256);
       if (sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32 && sl.flux == ADG_FLUX_RUSANOV) {
-        k_lim_flux<D, N, 0, float><<<gf, 256, 0, s>>>(lim, pass);
-        k_lim_flux<D, N, 1, float><<<gf, 256, 0, s>>>(lim, pass);
-        if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), float><<<gf, 256, 0, s>>>(lim, pass);
+        if (qf) {
+          k_lim_flux<D, N, 0, float, float><<<gf, 256, 0, s>>>(lim, pass);
+          k_lim_flux<D, N, 1, float, float><<<gf, 256, 0, s>>>(lim, pass);
+          if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), float, float><<<gf, 256, 0, s>>>(lim, pass);
+        } else {
+          k_lim_flux<D, N, 0, float, double><<<gf, 256, 0, s>>>(lim, pass);
+          k_lim_flux<D, N, 1, float, double><<<gf, 256, 0, s>>>(lim, pass);
+          if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), float, double><<<gf, 256, 0, s>>>(lim, pass);
+        }
+      } else if (qf) {
+        k_lim_flux<D, N, 0, double, float><<<gf, 256, 0, s>>>(lim, pass);
+        k_lim_flux<D, N, 1, double, float><<<gf, 256, 0, s>>>(lim, pass);
+        if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), double, float><<<gf, 256, 0, s>>>(lim, pass);
       } else {
-        k_lim_flux<D, N, 0, double><<<gf, 256, 0, s>>>(lim, pass);
-        k_lim_flux<D, N, 1, double><<<gf, 256, 0, s>>>(lim, pass);
-        if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), double><<<gf, 256, 0, s>>>(lim, pass);
+        k_lim_flux<D, N, 0, double, double><<<gf, 256, 0, s>>>(lim, pass);
+        k_lim_flux<D, N, 1, double, double><<<gf, 256, 0, s>>>(lim, pass);
+        if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), double, double><<<gf, 256, 0, s>>>(lim, pass);
       }
       k_lim_update<D, N><<<(int)(ch < kNumSM * 8 ? ch : kNumSM * 8), 128, su, s>>>(lim, pass);
     }

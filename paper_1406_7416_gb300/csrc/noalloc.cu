@@ -136,11 +136,11 @@ struct NoAlloc {
     if (D == 3)
       k_lim_sweep<D, N, (D == 3 ? 2 : 1), double><<<grid_for(ch * DM::NV * DM::LD, 256), 256, 0, s>>>(lim, 0);
     const long long ncross = ch * (DM::NSD + 2 * D * DM::NSF);
-    k_lim_predict<D, N, false, double><<<grid_for(ncross, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(lim, 0, 0);
-    k_lim_flux<D, N, 0, double><<<grid_for(ch * (DM::Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, 0);
-    k_lim_flux<D, N, 1, double><<<grid_for(ch * (DM::Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, 0);
+    k_lim_predict<D, N, false, double, false><<<grid_for(ncross, SPB, kNumSM * 16), SPB * DM::NST3, 0, s>>>(lim, 0, 0);
+    k_lim_flux<D, N, 0, double, double><<<grid_for(ch * (DM::Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, 0);
+    k_lim_flux<D, N, 1, double, double><<<grid_for(ch * (DM::Ns + 1) * DM::NSF, 256), 256, 0, s>>>(lim, 0);
     if (D == 3)
-      k_lim_flux<D, N, (D == 3 ? 2 : 1), double><<<grid_for(ch * (DM::Ns + 1) * DM::NSF, 256), 256, 0, s>>>(
+      k_lim_flux<D, N, (D == 3 ? 2 : 1), double, double><<<grid_for(ch * (DM::Ns + 1) * DM::NSF, 256), 256, 0, s>>>(
           lim, 0);
     k_noalloc_write<D, N><<<grid_for(ch * DM::NV * DM::NSD, 256), 256, 0, s>>>(p, count, vnew, faces);
     return cudaGetLastError();
