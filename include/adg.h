@@ -88,7 +88,9 @@ extern "C" {
 #define ADG_OPT_SLOT_CAPACITY 5   /* max troubled cells per step (before first load)  */
 #define ADG_OPT_PROFILE 6         /* 1: time the phases of every step with CUDA events */
 #define ADG_OPT_FP64_SWEEPS 7     /* mixed precision: final Picard sweeps run in FP64
-                                     (default 1; the others run in FP32)              */
+                                     (the others in FP32); 0: none, the last FP32
+                                     sweep's space-time correction is subtracted from
+                                     the FP64 u.  Default 0 for N <= 5, 1 for N >= 6  */
 #define ADG_OPT_END_TIME 8        /* end time of the run: steps are cut to reach it and
                                      the state idles afterwards (0: none, default)    */
 #define ADG_OPT_CFL 9             /* the state's CFL number for batched CFL steps

@@ -108,6 +108,32 @@ __device__ __forceinline__ void picard_time(T* __restrict__ q, const UT* __restr
   }
 }
 
+// The time phase of the last FP32 Picard sweep when no FP64 sweep follows:
+// the space-time correction Ktau S is formed in FP32 from the FP32 sweep's
+// S = sum_k c_k D x_k f_k(q) and subtracted from the FP64 u, so q carries no
+// FP32 rounding of u itself (the dominant error of a plain FP32 sweep).
+template <int D, int n>
+__device__ __forceinline__ void picard_time_to64(const float* __restrict__ S,
+                                                 const double* __restrict__ u,
+                                                 const float* __restrict__ Kt,
+                                                 double* __restrict__ q, int tid, int nth) {
+  constexpr int NV = D + 2, ND = ipow(n, D), NST = ipow(n, D + 1);
+  for (int e = tid; e < NV * ND; e += nth) {
+    const int v = e / ND, i = e - v * ND;
+    float Sl[n];
+#pragma unroll
+    for (int m = 0; m < n; ++m) Sl[m] = S[v * NST + i + m * ND];
+    const double u0 = u[v * ND + i];
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int j = 0; j < n; ++j) acc += Kt[m * n + j] * Sl[j];
+      q[v * NST + i + m * ND] = u0 - (double)acc;
+    }
+  }
+}
+
 // Apply a matrix along axis k of a (nv, e0, e1, e2) tensor (x fastest):
 // out[v][.., r, ..] = sum_c M[r * cols + c] in[v][.., c, ..].
 // ein: extents of `in`; out has extent `rows` along k.
@@ -304,15 +330,18 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
         qf[e] = uf[v * ND + (l % ND)];
       }
       __syncthreads();
+      const bool last64 = p.fp64_sweeps == 0;     // no FP64 sweep: close on the FP64 u
       for (int it = 0; it < n32; ++it) {
         picard_flux<D, n, float>(qf, Ff, (float)gm1, tid, nth);
         __syncthreads();
         picard_deriv<D, n, float>(Ff, qf, Dmf, cf, tid, nth);
         __syncthreads();
-        picard_time<D, n, float>(qf, uf, Ktf, tid, nth);
+        if (last64 && it == n32 - 1) picard_time_to64<D, n>(qf, u, Ktf, q, tid, nth);
+        else picard_time<D, n, float>(qf, uf, Ktf, tid, nth);
         __syncthreads();
       }
-      for (int e = tid; e < NV * NST; e += nth) q[e] = (double)qf[e];
+      if (!last64)
+        for (int e = tid; e < NV * NST; e += nth) q[e] = (double)qf[e];
       it0 = n32;
     } else {
       for (int e = tid; e < NV * NST; e += nth) {

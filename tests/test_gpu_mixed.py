@@ -77,11 +77,12 @@ def test_mixed_within_budget_of_fp64_scheme_error():
 
 
 def test_more_fp64_sweeps_reduce_the_mixed_distance():
-    """ADG_OPT_FP64_SWEEPS = 2 brings the mixed path closer to the FP64 path."""
+    """Each FP64 Picard sweep (ADG_OPT_FP64_SWEEPS = 0, 1, 2; 0 closes the last
+    FP32 sweep on the FP64 u) brings the mixed path closer to the FP64 path."""
     t = 0.5
     w, U64, _ = _run_vortex(16, 5, t, adg.PREC_FP64)
     dists = []
-    for sweeps in (1, 2):
+    for sweeps in (0, 1, 2):
         s = adg.Solver.from_workload(w, adg.PREC_MIXED_FP32)
         s.set_option(adg.OPT_FP64_SWEEPS, sweeps)
         s.init_problem(w["problem"])
@@ -91,7 +92,7 @@ def test_more_fp64_sweeps_reduce_the_mixed_distance():
             s.step(t / steps)
         dists.append(float(np.abs(s.read()[:, 0, :] - U64[:, 0, :]).max()))
         s.close()
-    assert dists[1] < dists[0], dists
+    assert dists[2] < dists[1] < dists[0], dists
 
 
 @pytest.mark.parametrize("prec", [adg.PREC_FP64, adg.PREC_MIXED_FP32])
