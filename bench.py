@@ -78,15 +78,19 @@ def flux_flops(D):
     return D * D + 5 * D + 5
 
 
-def predictor_flops(D, N, iters, mixed):
-    """(fp64, fp32) flops of the predictor kernel for one cell."""
+def predictor_flops(D, N, iters, fp64_sweeps):
+    """(fp64, fp32) flops of the predictor kernel for one cell: `iters` Picard
+    sweeps of which `fp64_sweeps` in FP64 (the others in FP32; with none the
+    last FP32 sweep's correction is subtracted from the FP64 u, one FP64
+    operation per space-time value), then the FP64 time average, volume term
+    and traces."""
     n, nv = N + 1, D + 2
     nst, nd = n ** (D + 1), n ** D
     it = nst * flux_flops(D) + nv * nst * D * (2 * n + 2) + nv * nd * n * (2 * n + 1)
     final = (nst * flux_flops(D) + D * nv * nd * 2 * n + nv * nd * D * (2 * n + 2)
              + 2 * D * nv * n ** (D - 1) * n * 2 * n)
-    n32 = (iters - 1) if mixed and iters > 1 else 0
-    return (iters - n32) * it + final, n32 * it
+    close = nv * nst if fp64_sweeps == 0 else 0
+    return fp64_sweeps * it + final + close, (iters - fp64_sweeps) * it
 
 
 def clocks_sampler():
@@ -340,11 +344,11 @@ def end_to_end(s, args, stdofs, world, cfl, barrier, max_over_ranks):
 def emit_line(args, w, results, stdofs, world, cells, cfl, l1, l1ref, e2e, D, N, n):
     mx, f64 = results["mixed"], results["fp64"]
     value = stdofs * world / (mx["ms"] / 1e3)
-    iters = N + 1
-    fl64, fl32 = predictor_flops(D, N, iters, True)
+    iters = int(mx["info"]["picard_iters"])
+    fl64, fl32 = predictor_flops(D, N, iters, int(mx["info"]["fp64_sweeps"]))
     pred_ms = mx["phases"]["predictor"]
     achieved = fl64 * cells / (pred_ms / 1e3) / 1e12
-    fl64f, _ = predictor_flops(D, N, iters, False)
+    fl64f, _ = predictor_flops(D, N, iters, iters)
     achieved_f64 = fl64f * cells / (f64["phases"]["predictor"] / 1e3) / 1e12
     traffic = traffic_record() if (WORKLOAD == "quadvortex512" and GRID == 512) else None
     line = {
@@ -352,8 +356,12 @@ def emit_line(args, w, results, stdofs, world, cells, cfl, l1, l1ref, e2e, D, N,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mx["ms"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
-        "config": config_dict(w, {"precision": "mixed: FP32 Picard sweeps + final FP64 sweep, "
-                                               "FP64 corrector/detector/limiter",
+        "config": config_dict(w, {"precision": ("mixed: FP32 Picard sweeps (%d of %d in FP64; with "
+                                                "none the last closes on the FP64 u), FP64 "
+                                                "corrector/detector; subcell scheme: FP32 "
+                                                "reconstruction, predictor and sub-face fluxes, "
+                                                "FP64 update" % (int(mx["info"]["fp64_sweeps"]),
+                                                                 int(mx["info"]["picard_iters"]))),
                                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                                   "time_step": f"CFL {cfl:.6g} of Eq. (cfl), dt from the "
                                                "current subcell data every step"}),
@@ -368,7 +376,8 @@ def emit_line(args, w, results, stdofs, world, cells, cfl, l1, l1ref, e2e, D, N,
         "troubled_cells": mx["troubled"], "status": mx["status"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "kernel": "k_predictor (FP64 pipe: final sweep + corrector terms)",
+                     "kernel": "k_predictor (FP64 pipe: FP64 sweeps, closing subtraction and "
+                               "corrector terms; its FP32 sweeps in fp32_flops_per_launch)",
                      "fp32_flops_per_launch": fl32 * cells,
                      "fp64_flops_per_launch": fl64 * cells,
                      "traffic": traffic["bytes_per_launch"] if traffic else None},

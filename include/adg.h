@@ -303,7 +303,9 @@ int adg_sizes(const adg_state* st, int64_t* cells, int* nvar, int* nodes, int* s
  * adg_step at most (every limiter pass the capacity allows), out[3] = device
  * bytes held by the state, and with cap >= 5, out[4] = kernels issued by this
  * state's steps so far (batched steps count on the first state of each group
- * of one dimension, degree and precision).  Needs cap >= 4. */
+ * of one dimension, degree and precision); with cap >= 7, out[5] = Picard
+ * sweeps of the predictor, out[6] = how many of them run in FP64.  Needs
+ * cap >= 4. */
 int adg_info(const adg_state* st, int64_t* out, int cap);
 
 /* Phase timing (ADG_OPT_PROFILE = 1): accumulated milliseconds of the steps

@@ -356,11 +356,12 @@ class Solver:
 
     def info(self):
         """Slot capacity, limiter chunk, kernels of one adg_step at most, device
-        bytes held, kernels issued by the steps so far."""
-        out = (ctypes.c_int64 * 5)()
-        self._check(self.lib.adg_info(self.h, out, 5), "adg_info")
+        bytes held, kernels issued by the steps so far, Picard sweeps and how
+        many run in FP64."""
+        out = (ctypes.c_int64 * 7)()
+        self._check(self.lib.adg_info(self.h, out, 7), "adg_info")
         return dict(capacity=out[0], chunk=out[1], launches_per_step=out[2], bytes=out[3],
-                    launches=out[4])
+                    launches=out[4], picard_iters=out[5], fp64_sweeps=out[6])
 
     def time(self):
         """(simulated time, steps taken since the last load)."""

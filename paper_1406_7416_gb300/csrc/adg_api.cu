@@ -1235,6 +1235,11 @@ int adg_info(const adg_state* st, int64_t* out, int cap) {
   out[2] = kernels_per_step(D, nchunks, st->cascade);
   out[3] = (int64_t)st->bytes_held;
   if (cap >= 5) out[4] = st->launch_count;
+  if (cap >= 7) {
+    out[5] = st->iters;
+    out[6] = st->prec == ADG_PREC_MIXED_FP32 ? (st->fp64_sweeps < st->iters ? st->fp64_sweeps : st->iters)
+                                             : st->iters;
+  }
   return ADG_OK;
 }
 
