@@ -251,10 +251,11 @@ int ensure_allocated(adg_state* st) {
   ALLOC(b.fblist, int, 3 * cap);
   b.fbflag = b.fblist + cap;
   b.refixlist = b.fblist + 2 * cap;
-  ALLOC(b.dt, double, 6);
+  ALLOC(b.dt, double, 12);
   b.lamred = b.dt + 1;
   b.clock = b.dt + 2;
   b.tstart = b.dt + 5;
+  b.coef = b.dt + 6;
   ALLOC(st->dparams, Params, 1);
   ALLOC(st->d_pps1, Params*, 1);
   ALLOC(st->d_pre1, long long, 16);
@@ -271,7 +272,7 @@ int ensure_allocated(adg_state* st) {
   CUDA_TRY(st, cudaMemsetAsync(b.counters, 0, sizeof(int) * CNT_COUNT, st->stream));
   CUDA_TRY(st, cudaMemsetAsync(b.fixstamp, 0xff, sizeof(int) * cells, st->stream));
   CUDA_TRY(st, cudaMemsetAsync(b.fbflag, 0xff, sizeof(int) * cap, st->stream));
-  CUDA_TRY(st, cudaMemsetAsync(b.dt, 0, sizeof(double) * 6, st->stream));
+  CUDA_TRY(st, cudaMemsetAsync(b.dt, 0, sizeof(double) * 12, st->stream));
   {
     long long pre[16] = {0, cells, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int k = 0; k < st->dim; ++k) {

@@ -87,6 +87,7 @@ struct Bufs {
   double* lamred;        // [1] reduced lambda
   double* clock;         // [3] simulated time t, end time t_end (0: none), steps taken
   double* tstart;        // [1] simulated time at the start of the current step
+  double* coef;          // [6] dt / dx_k and dt Ns / dx_k of the current step (set once per step)
   // limiter scratch, sized for one chunk of `chunk` troubled cells
   double* patch;         // [chunk][nv][L^d]
   double* sweep[3];      // [chunk][nv][...] after the x, y, z reconstructions

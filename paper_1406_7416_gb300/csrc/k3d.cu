@@ -57,6 +57,13 @@ __global__ void k_step_begin(StepLaunch sl) {
     }
     *p.b.dt = dt;
     *p.b.tstart = t;
+    // the step's dt / dx_k and dt Ns / dx_k, evaluated once here instead of in
+    // every thread of every kernel (FP64 divisions)
+    const int Ns = 2 * p.N + 1;
+    for (int k = 0; k < p.dim; ++k) {
+      p.b.coef[k] = dt / p.geo.dx[k];
+      p.b.coef[3 + k] = dt * Ns / p.geo.dx[k];
+    }
     if (dt > 0.0) {
       p.b.counters[CNT_TROUBLED0 + (1 - p.cur)] = 0;
       p.b.counters[CNT_FIX] = 0;

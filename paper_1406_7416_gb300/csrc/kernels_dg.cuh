@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
     if (!(dt > 0.0)) continue;          // state idle this step (block-uniform)
     double c[3];
 #pragma unroll
-    for (int k = 0; k < D; ++k) c[k] = dt / p.geo.dx[k];
+    for (int k = 0; k < D; ++k) c[k] = p.b.coef[k];
     const double gm1 = p.gamma - 1.0;
     const double* Uc = p.b.U[p.cur] + cell * (NV * ND);
     for (int i = tid; i < NV * ND; i += nth) u[i] = Uc[i];
@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(128) k_correct_detect(Batch bt) {
     if (!(dt > 0.0)) continue;
     double c[3];
 #pragma unroll
-    for (int k = 0; k < D; ++k) c[k] = dt / p.geo.dx[k];
+    for (int k = 0; k < D; ++k) c[k] = p.b.coef[k];
     const int nxt = 1 - p.cur;
     int ijk[3];
     cell_coords<D>(cell, p.geo, ijk);

@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass, int n32
       const double dt = *p.b.dt;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        c[k] = dt * Ns / p.geo.dx[k];
+        c[k] = p.b.coef[3 + k];
         cf[k] = (float)c[k];
       }
     }
@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(128) k_lim_update(Batch bt, int pass) {
     {
       const double dt = *p.b.dt;
 #pragma unroll
-      for (int k = 0; k < D; ++k) c[k] = dt * Ns / p.geo.dx[k];
+      for (int k = 0; k < D; ++k) c[k] = p.b.coef[3 + k];
     }
     const int t = pass * p.chunk + j;
     const long long cell = p.b.list[nxt][t];
@@ -724,7 +724,7 @@ __global__ void __launch_bounds__(128) k_lim_fix(Batch bt) {
     __syncthreads();
     for (int e = tid; e < NV * ND; e += nth) U[e] = Uo[e];
     for (int k = 0; k < D; ++k) {
-      const double ck = dt / p.geo.dx[k];
+      const double ck = p.b.coef[k];
       for (int side = -1; side <= 1; side += 2) {
         int nb[3];
         if (!face_neighbour<D>(p.geo, ijk, k, side, nb)) continue;
@@ -847,7 +847,7 @@ __global__ void __launch_bounds__(128) k_lim_fallback(Batch bt) {
       A[e] = blk[v * NB + bi];
     }
     for (int k = 0; k < D; ++k) {
-      const double ck = dt * Ns / g.dx[k];
+      const double ck = p.b.coef[3 + k];
       __syncthreads();
       // faces c_k = 0..Ns between local subcells c_k - 1 and c_k
       for (int e = tid; e < NFK; e += nth) {
@@ -994,7 +994,7 @@ __global__ void __launch_bounds__(128) k_lim_refix(Batch bt) {
       double val = st[e];
 #pragma unroll
       for (int k = 0; k < D; ++k) {
-        const double ck = dt * Ns / g.dx[k];
+        const double ck = p.b.coef[3 + k];
         int ts = 0, mul = 1;
 #pragma unroll
         for (int a = 0; a < D; ++a)

@@ -41,6 +41,12 @@ __global__ void k_noalloc_begin(int* counters, double* dt, Params** pps, long lo
     dt[1] = 0.0;
     dt[2] = 0.0;
     dt[3] = 0.0;
+    // dt / dx_k and dt Ns / dx_k as the step kernels read them (dt + 6)
+    const int Ns = 2 * params->N + 1;
+    for (int k = 0; k < params->dim; ++k) {
+      dt[6 + k] = dtv / params->geo.dx[k];
+      dt[9 + k] = dtv * Ns / params->geo.dx[k];
+    }
     pps[0] = params;
     pre[0] = 0;
     pre[1] = count;
@@ -212,6 +218,7 @@ int run_noalloc(unsigned char* base, double gamma, const double* h, double dt, c
   p.b.dt = reinterpret_cast<double*>(base + 64);
   p.b.lamred = p.b.dt + 1;
   p.b.clock = p.b.dt + 2;
+  p.b.coef = p.b.dt + 6;
   p.b.patch = const_cast<double*>(patches);
   NA::carve(base, count, p);
   e = cudaMemcpyAsync(params_dev, &p, sizeof(Params), cudaMemcpyHostToDevice, s);
