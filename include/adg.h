@@ -114,18 +114,21 @@ extern "C" {
                                      path integral), used for the vortex table of
                                      Sec. 5.2; the first-order layer keeps Rusanov */
 
-#define ADG_OPT_HOST_PASSES 13    /* 1 (default): adg_step / adg_step_cfl wait once per
-                                     step, after the DG phase, for the step's troubled
-                                     count and launch only the limiter passes it needs;
-                                     0: fully asynchronous steps that launch every pass
-                                     the slot capacity allows (empty ones return at
-                                     once).  Batched steps are always asynchronous.  */
+#define ADG_OPT_HOST_PASSES 13    /* 0 (default): each adg_step / adg_step_cfl is one
+                                     CUDA graph launch with no host wait; the limiter
+                                     passes run in a conditional loop of the graph
+                                     whose trip count the device takes from the
+                                     step's troubled count.  1: the host waits once
+                                     per step, after the DG phase, for that count and
+                                     launches the passes itself.  Batched steps are
+                                     always graphs.                                   */
 
 #define ADG_OPT_SUBCELL_FP64_SWEEPS 14  /* mixed precision: how many of the three
                                      Picard sweeps of the degree-2 subcell predictor
                                      run in FP64 after the FP32 ones (0..3, default
-                                     0: all FP32; the sub-face fluxes and the finite
-                                     volume update stay FP64).  States batched
+                                     0: all FP32; the finite volume update stays
+                                     FP64, the sub-face fluxes follow
+                                     ADG_OPT_SUBCELL_FP32).  States batched
                                      together share one launch per value.          */
 
 #define ADG_OPT_SUBCELL_FP32 15   /* mixed precision: the subcell scheme's WENO3
@@ -216,8 +219,8 @@ int adg_read_full(adg_state* st, double* dofs, uint8_t* beta, double* subcells);
  * subcell ADER-WENO3 recomputation of troubled cells (Eq. aderweno with the
  * data of Eq. ader.icbc), reconstruction R, the flux correction of their
  * unlimited face neighbours, and with ADG_OPT_CASCADE the first-order layer.
- * Waits once for the step's troubled count after the DG phase unless
- * ADG_OPT_HOST_PASSES is 0 (then fully asynchronous).  Errors: ADG_ERR_ARG (dt <= 0,
+ * Asynchronous (one CUDA graph launch) unless ADG_OPT_HOST_PASSES is 1 (then
+ * one wait for the step's troubled count after the DG phase).  Errors: ADG_ERR_ARG (dt <= 0,
  * nothing loaded), ADG_ERR_CUDA.  Device-side conditions (capacity overflow,
  * inadmissible subcells) surface on the next synchronizing call. */
 int adg_step(adg_state* st, double dt);
@@ -240,8 +243,9 @@ int adg_time(adg_state* st, double* t, int64_t* steps);
  *   adg_batch_step with dts (host [count]) takes those steps; with dts = NULL
  *   every state takes the CFL step of Eq. (cfl) with the number `cfl`, or
  *   with its own ADG_OPT_CFL when cfl <= 0, cut at its end time
- *   (ADG_OPT_END_TIME); states past their end time idle.  From the
- *   second CFL step on, the whole batched step replays as one CUDA graph.
+ *   (ADG_OPT_END_TIME); states past their end time idle.  CFL steps run as
+ *   one CUDA graph, captured on the first and replayed while cfl is
+ *   unchanged; each group's limiter passes loop on the device.
  * Asynchronous; errors of device-side conditions surface in adg_status of
  * the states. */
 typedef struct adg_batch adg_batch;

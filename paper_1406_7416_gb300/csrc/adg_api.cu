@@ -19,7 +19,9 @@ struct adg_state {
   int force = 0, iters = 0, fp64_sweeps = 1;
   int cascade = 1;          // first-order layer after WENO3
   int flux = ADG_FLUX_RUSANOV;
-  bool host_passes = true;  // single-state steps launch only the limiter passes needed
+  bool host_passes = false; // true: the host waits for the troubled count and launches
+                            // the passes; false: one CUDA graph per step, passes sized
+                            // on the device by a conditional loop
   int sub_fp64 = 0;         // mixed precision: FP64 sweeps of the degree-2 subcell predictor
   int sub_f32 = 1;          // mixed precision: FP32 subcell reconstruction and sub-face fluxes
   int bstate_set = 0;       // bit f: inflow face f has a state
@@ -54,7 +56,7 @@ struct adg_state {
   // device copy of the Params: during steps the device owns cur and stamp
   Params* dparams = nullptr;
   Params** d_pps1 = nullptr;        // [1] = dparams
-  long long* d_pre1 = nullptr;      // cells[2], faces[3][2], lim[2], fix[2], fb[2], refix[2]
+  long long* d_pre1 = nullptr;      // cells[2], faces[3][2], fix[2], fb[2], refix[2], lim[2 + 2]
   double* d_dts1 = nullptr;         // [1]
   bool params_dirty = true;         // host fields changed since the last upload
   bool cur_known = true;            // host cur / stamp equal the device's
@@ -62,10 +64,22 @@ struct adg_state {
   double cfl = 0.0;                 // CFL number of batched CFL steps with cfl <= 0
   size_t scratch_budget = 0;        // bytes of limiter scratch (0: from free memory at allocation)
   Params hparams;                   // source of the last upload
-  cudaEvent_t ev[PHASE_COUNT] = {};
+  // phase events of profiled steps: a ring of kEventSets sets used in turn, so
+  // that the host runs up to kEventSets - 1 steps ahead of the device; a set
+  // is read when it comes round again (or by adg_phase_times)
+  static constexpr int kEventSets = 3;
+  cudaEvent_t ev[kEventSets][PHASE_COUNT] = {};
+  bool pending[kEventSets] = {};
+  int ev_next = 0;
   double phase_ms[PHASE_COUNT] = {};
   int timed_steps = 0;
-  bool pending = false;     // events of the last step not yet read
+  // the step graph (host_passes off): captured on cap_stream (the limiter
+  // pass body on body_stream), replayed on `stream` while `gsl` is unchanged
+  // one graph per event set when profiling (the event nodes differ), else slot 0
+  cudaGraph_t graph[kEventSets] = {};
+  cudaGraphExec_t gexec[kEventSets] = {};
+  StepLaunch gsl[kEventSets];
+  cudaStream_t cap_stream = nullptr, body_stream = nullptr;
 };
 
 namespace {
@@ -104,9 +118,17 @@ void dev_free(adg_state* st, void* p) {
   else cudaFree(p);
 }
 
+void drop_graph(adg_state* st, int slot) {
+  if (st->gexec[slot]) cudaGraphExecDestroy(st->gexec[slot]);
+  if (st->graph[slot]) cudaGraphDestroy(st->graph[slot]);
+  st->gexec[slot] = nullptr;
+  st->graph[slot] = nullptr;
+}
+
 void free_all(adg_state* st) {
   if (st->stream) cudaStreamSynchronize(st->stream);
   else cudaDeviceSynchronize();
+  for (int k = 0; k < adg_state::kEventSets; ++k) drop_graph(st, k);
   if (st->probe) cudaFreeHost(st->probe);
   st->probe = nullptr;
   for (void* p : st->owned) dev_free(st, p);
@@ -258,7 +280,7 @@ int ensure_allocated(adg_state* st) {
   b.coef = b.dt + 6;
   ALLOC(st->dparams, Params, 1);
   ALLOC(st->d_pps1, Params*, 1);
-  ALLOC(st->d_pre1, long long, 16);
+  ALLOC(st->d_pre1, long long, 20);
   ALLOC(st->d_dts1, double, 1);
   ALLOC(b.patch, double, chunk * parts[0]);
   ALLOC(b.sweep[0], double, chunk * parts[1]);
@@ -274,7 +296,7 @@ int ensure_allocated(adg_state* st) {
   CUDA_TRY(st, cudaMemsetAsync(b.fbflag, 0xff, sizeof(int) * cap, st->stream));
   CUDA_TRY(st, cudaMemsetAsync(b.dt, 0, sizeof(double) * 12, st->stream));
   {
-    long long pre[16] = {0, cells, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    long long pre[20] = {0, cells, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int k = 0; k < st->dim; ++k) {
       long long faces = 1;
       for (int j = 0; j < st->dim; ++j) faces *= (j == k) ? st->geo.n[j] + 1 : st->geo.n[j];
@@ -335,7 +357,8 @@ int begin_load(adg_state* st) {
   if (rc) return rc;
   st->cur = 0;
   st->params_dirty = true;
-  CUDA_TRY(st, cudaMemsetAsync(st->b.counters, 0, sizeof(int) * CNT_COUNT, st->stream));
+  // every counter but the cumulative pass count (adg_info's launch count)
+  CUDA_TRY(st, cudaMemsetAsync(st->b.counters, 0, sizeof(int) * CNT_PASSES, st->stream));
   const double clk[3] = {0.0, st->t_end, 0.0};
   CUDA_TRY(st, cudaMemcpyAsync(st->b.clock, clk, sizeof(clk), cudaMemcpyHostToDevice, st->stream));
   CUDA_TRY(st, cudaStreamSynchronize(st->stream));
@@ -394,17 +417,17 @@ int load_detect(adg_state* st, const double* exact_dev) {
   return ADG_OK;
 }
 
-// Fold the events of the previous profiled step into the sums.
-int collect_phases(adg_state* st) {
-  if (!st->pending) return ADG_OK;
-  CUDA_TRY(st, cudaEventSynchronize(st->ev[PHASE_END]));
+// Fold the events of the profiled step recorded in set k into the sums.
+int collect_phases(adg_state* st, int k) {
+  if (!st->pending[k]) return ADG_OK;
+  CUDA_TRY(st, cudaEventSynchronize(st->ev[k][PHASE_END]));
   for (int i = 0; i < PHASE_END; ++i) {
     float ms = 0.f;
-    CUDA_TRY(st, cudaEventElapsedTime(&ms, st->ev[i], st->ev[i + 1]));
+    CUDA_TRY(st, cudaEventElapsedTime(&ms, st->ev[k][i], st->ev[k][i + 1]));
     st->phase_ms[i] += ms;
   }
   st->timed_steps += 1;
-  st->pending = false;
+  st->pending[k] = false;
   return ADG_OK;
 }
 
@@ -415,10 +438,10 @@ StepLaunch single_launch(adg_state* st) {
   sl.n = 1;
   sl.pre_cells = st->d_pre1;
   for (int k = 0; k < 3; ++k) sl.pre_faces[k] = st->d_pre1 + 2 + 2 * k;
-  sl.pre_lim = st->d_pre1 + 8;
-  sl.pre_fix = st->d_pre1 + 10;
-  sl.pre_fb = st->d_pre1 + 12;
-  sl.pre_refix = st->d_pre1 + 14;
+  sl.pre_fix = st->d_pre1 + 8;
+  sl.pre_fb = st->d_pre1 + 10;
+  sl.pre_refix = st->d_pre1 + 12;
+  sl.pre_lim = st->d_pre1 + 14;
   sl.cascade = st->cascade;
   sl.sub32 = 3 - st->sub_fp64;
   sl.sub_f32 = st->sub_f32;
@@ -434,7 +457,7 @@ StepLaunch single_launch(adg_state* st) {
   sl.sum_chunk = st->chunk;
   sl.max_passes = (st->cap + st->chunk - 1) / st->chunk;
   sl.prec = st->prec;
-  sl.ev = st->profile ? st->ev : nullptr;
+  sl.ev = st->profile ? st->ev[st->ev_next] : nullptr;
   return sl;
 }
 
@@ -447,8 +470,9 @@ long long kernels_per_step(int dim, int passes, int cascade) {
 }
 
 // Enqueue one step of the states described by `sl` (all of one dimension,
-// degree and precision; `st` selects the kernel instantiation).
-int run_step(adg_state* st, const StepLaunch& sl, cudaStream_t stream) {
+// degree and precision; `st` selects the kernel instantiation) without
+// counting its launches.
+int enqueue_step(adg_state* st, const StepLaunch& sl, cudaStream_t stream) {
   CUDA_TRY(st, launch_step_begin(sl, stream));
   LaunchArgs a{};
   a.step = &sl;
@@ -461,7 +485,84 @@ int run_step(adg_state* st, const StepLaunch& sl, cudaStream_t stream) {
   if (e != cudaSuccess)
     return fail(st, ADG_ERR_CUDA, std::string("subcell limiter: ") + cudaGetErrorString(e));
   CUDA_TRY(st, launch_step_end(sl, stream));
+  return ADG_OK;
+}
+
+int run_step(adg_state* st, const StepLaunch& sl, cudaStream_t stream) {
+  const int rc = enqueue_step(st, sl, stream);
+  if (rc) return rc;
   st->launch_count += kernels_per_step(st->dim, sl.max_passes, sl.cascade);
+  return ADG_OK;
+}
+
+// Kernels of a step whose passes loop on the device, besides the passes
+// themselves (each pass adds 2d + 5, counted on the device in CNT_PASSES).
+long long kernels_per_loop_step(int dim, int cascade) {
+  return kernels_per_step(dim, 0, cascade) + 1;
+}
+
+// Capture the steps `sl` describes into a new graph `*out` (captured on
+// `cap`, the pass body on `body`): one conditional handle per launch group.
+int capture_step_graph(adg_state* st, StepLaunch* sls, adg_state* const* reps, int count,
+                       cudaStream_t cap, cudaStream_t body, cudaGraph_t* out) {
+  *out = nullptr;
+  cudaGraph_t g = nullptr;
+  CUDA_TRY(st, cudaGraphCreate(&g, 0));
+  for (int i = 0; i < count; ++i) {
+    sls[i].loop = 1;
+    sls[i].body = body;
+    const cudaError_t e = cudaGraphConditionalHandleCreate(&sls[i].cond, g, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return fail(st, ADG_ERR_CUDA, std::string("conditional handle: ") + cudaGetErrorString(e));
+    }
+  }
+  cudaError_t e = cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    return fail(st, ADG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+  }
+  int rc = ADG_OK;
+  for (int i = 0; i < count && rc == ADG_OK; ++i) rc = enqueue_step(reps[i], sls[i], cap);
+  cudaGraph_t captured = nullptr;
+  e = cudaStreamEndCapture(cap, &captured);
+  if (rc || e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    if (rc) return rc;
+    return fail(st, ADG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+  }
+  *out = g;
+  return ADG_OK;
+}
+
+// One step as one graph launch: the DG phase, the limiter passes in a
+// conditional loop sized on the device from the troubled count, the
+// first-order layer, the fix and the level swap, with no host wait.  The
+// graph is captured on the first step and replayed while the launch
+// description (grid, options, dt source, CFL number, phase events) stays the
+// same.
+int run_step_graph(adg_state* st, const StepLaunch& sl) {
+  const int k = st->profile ? st->ev_next : 0;
+  if (!(st->gexec[k] && std::memcmp(&st->gsl[k], &sl, sizeof(sl)) == 0)) {
+    drop_graph(st, k);
+    if (!st->cap_stream) CUDA_TRY(st, cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking));
+    if (!st->body_stream) CUDA_TRY(st, cudaStreamCreateWithFlags(&st->body_stream, cudaStreamNonBlocking));
+    StepLaunch cl = sl;
+    adg_state* rep = st;
+    cudaGraph_t g = nullptr;
+    int rc = capture_step_graph(st, &cl, &rep, 1, st->cap_stream, st->body_stream, &g);
+    if (rc) return rc;
+    const cudaError_t e = cudaGraphInstantiate(&st->gexec[k], g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      st->gexec[k] = nullptr;
+      return fail(st, ADG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    st->graph[k] = g;
+    st->gsl[k] = sl;
+  }
+  CUDA_TRY(st, cudaGraphLaunch(st->gexec[k], st->stream));
+  st->launch_count += kernels_per_loop_step(st->dim, sl.cascade);
   return ADG_OK;
 }
 
@@ -507,7 +608,7 @@ int run_step_host_passes(adg_state* st, StepLaunch& sl) {
 
 int common_step(adg_state* st, const double* dts_dev, double cfl, double dt_max) {
   if (st->profile) {
-    int rc = collect_phases(st);
+    int rc = collect_phases(st, st->ev_next);     // the set this step records into
     if (rc) return rc;
   }
   if (st->params_dirty) {
@@ -522,14 +623,15 @@ int common_step(adg_state* st, const double* dts_dev, double cfl, double dt_max)
     int rc = run_step_host_passes(st, sl);
     if (rc) return rc;
     st->cur_known = true;
-    st->pending = st->profile;
-    st->lam_valid = st->lam_mode;
-    return ADG_OK;
+  } else {
+    int rc = run_step_graph(st, sl);
+    if (rc) return rc;
+    st->cur_known = false;          // the device swapped levels (unless the state idled)
   }
-  int rc = run_step(st, sl, st->stream);
-  if (rc) return rc;
-  st->cur_known = false;            // the device swapped levels (unless the state idled)
-  st->pending = st->profile;
+  if (st->profile) {
+    st->pending[st->ev_next] = true;
+    st->ev_next = (st->ev_next + 1) % adg_state::kEventSets;
+  }
   st->lam_valid = st->lam_mode;
   return ADG_OK;
 }
@@ -570,6 +672,7 @@ struct adg_batch {
   cudaGraphExec_t exec = nullptr;
   double graph_cfl = -1.0;
   int cfl_steps = 0;
+  cudaStream_t cap = nullptr, body = nullptr;   // capture streams of the step graph
 };
 
 namespace {
@@ -578,6 +681,8 @@ void batch_free(adg_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->body) cudaStreamDestroy(b->body);
   for (void* p : b->mem) cudaFree(p);
   if (b->own_stream) {
     for (adg_state* st : b->states) st->stream = nullptr;
@@ -667,7 +772,7 @@ int adg_batch_create(adg_state* const* states, int count, void* stream, adg_batc
       if (passes > max_passes) max_passes = passes;
     }
     void* d = nullptr;
-    const size_t bytes = sizeof(Params*) * n + sizeof(long long) * (size_t)(n + 1) * 8;
+    const size_t bytes = sizeof(Params*) * n + sizeof(long long) * ((size_t)(n + 1) * 8 + 2);
     if (cudaMalloc(&d, bytes) != cudaSuccess) {
       batch_free(b);
       return ADG_ERR_OOM;
@@ -684,10 +789,10 @@ int adg_batch_create(adg_state* const* states, int count, void* stream, adg_batc
     sl.n = n;
     sl.pre_cells = dpre;
     for (int k = 0; k < 3; ++k) sl.pre_faces[k] = dpre + (size_t)(k + 1) * (n + 1);
-    sl.pre_lim = dpre + (size_t)4 * (n + 1);
-    sl.pre_fix = dpre + (size_t)5 * (n + 1);
-    sl.pre_fb = dpre + (size_t)6 * (n + 1);
-    sl.pre_refix = dpre + (size_t)7 * (n + 1);
+    sl.pre_fix = dpre + (size_t)4 * (n + 1);
+    sl.pre_fb = dpre + (size_t)5 * (n + 1);
+    sl.pre_refix = dpre + (size_t)6 * (n + 1);
+    sl.pre_lim = dpre + (size_t)7 * (n + 1);          // n + 3 entries
     sl.total_cells = pc[n];
     for (int k = 0; k < 3; ++k) sl.total_faces[k] = pf[k][n];
     sl.sum_chunk = sum_chunk;
@@ -741,32 +846,39 @@ int adg_batch_step(adg_batch* b, const double* dts, double cfl) {
       if (!rc && st->params_dirty) rc = upload_params(st);
       if (rc) return rc;
     }
-    if (b->exec && b->graph_cfl == cfl) {
-      CUDA_TRY(st0, cudaGraphLaunch(b->exec, b->stream));
-      for (auto& g : b->groups)
-        g.rep->launch_count += kernels_per_step(g.rep->dim, g.sl.max_passes, g.sl.cascade);
-    } else if (b->cfl_steps == 0) {
-      int rc = batch_run(b, false, cfl);         // first step: plain launches
-      if (rc) return rc;
-    } else {
+    if (!(b->exec && b->graph_cfl == cfl)) {
+      // one graph for the step of every group; each group's limiter passes
+      // loop on the device (conditional node), sized by its troubled counts
       if (b->exec) cudaGraphExecDestroy(b->exec);
       if (b->graph) cudaGraphDestroy(b->graph);
       b->exec = nullptr;
       b->graph = nullptr;
-      CUDA_TRY(st0, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-      const int rc = batch_run(b, false, cfl);
-      cudaGraph_t g = nullptr;
-      const cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
-      if (rc) {
-        if (g) cudaGraphDestroy(g);
-        return rc;
+      if (!b->cap) CUDA_TRY(st0, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+      if (!b->body) CUDA_TRY(st0, cudaStreamCreateWithFlags(&b->body, cudaStreamNonBlocking));
+      std::vector<StepLaunch> sls;
+      std::vector<adg_state*> reps;
+      for (auto& g : b->groups) {
+        StepLaunch sl = g.sl;
+        sl.dts = nullptr;
+        sl.cfl = cfl;
+        sl.dt_max = 0.0;
+        sls.push_back(sl);
+        reps.push_back(g.rep);
       }
-      if (ec != cudaSuccess) return fail(st0, ADG_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ec));
+      cudaGraph_t g = nullptr;
+      const int rc = capture_step_graph(st0, sls.data(), reps.data(), (int)sls.size(), b->cap, b->body, &g);
+      if (rc) return rc;
+      const cudaError_t e = cudaGraphInstantiate(&b->exec, g, 0);
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        b->exec = nullptr;
+        return fail(st0, ADG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      }
       b->graph = g;
-      CUDA_TRY(st0, cudaGraphInstantiate(&b->exec, b->graph, 0));
       b->graph_cfl = cfl;
-      CUDA_TRY(st0, cudaGraphLaunch(b->exec, b->stream));
     }
+    CUDA_TRY(st0, cudaGraphLaunch(b->exec, b->stream));
+    for (auto& g : b->groups) g.rep->launch_count += kernels_per_loop_step(g.rep->dim, g.sl.cascade);
     b->cfl_steps += 1;
   }
   for (adg_state* st : b->states) {
@@ -928,8 +1040,9 @@ int adg_set_option(adg_state* st, int key, double value) {
       st->cfl = value;
       return ADG_OK;
     case ADG_OPT_PROFILE:
-      if (value != 0.0 && !st->ev[0])
-        for (int i = 0; i < PHASE_COUNT; ++i) CUDA_TRY(st, cudaEventCreate(&st->ev[i]));
+      if (value != 0.0 && !st->ev[0][0])
+        for (int k = 0; k < adg_state::kEventSets; ++k)
+          for (int i = 0; i < PHASE_COUNT; ++i) CUDA_TRY(st, cudaEventCreate(&st->ev[k][i]));
       st->profile = value != 0.0;
       return ADG_OK;
     case ADG_OPT_SLOT_CAPACITY:
@@ -1040,6 +1153,7 @@ int adg_step(adg_state* st, double dt) {
   if (!st->loaded) return fail(st, ADG_ERR_ARG, "nothing loaded");
   if (!(dt > 0.0) || std::isinf(dt)) return fail(st, ADG_ERR_ARG, "dt must be positive and finite");
   CUDA_TRY(st, launch_set_scalar(st->d_dts1, dt, st->stream));
+  st->launch_count += 1;
   return common_step(st, st->d_dts1, 0.0, 0.0);
 }
 
@@ -1215,8 +1329,10 @@ int adg_sizes(const adg_state* st, int64_t* cells, int* nvar, int* nodes, int* s
 int adg_phase_times(adg_state* st, double* ms, int cap) {
   if (!st || !ms || cap < PHASE_END + 1) return ADG_ERR_ARG;
   if (!st->profile) return fail(st, ADG_ERR_ARG, "profiling is off");
-  int rc = collect_phases(st);
-  if (rc) return rc;
+  for (int k = 0; k < adg_state::kEventSets; ++k) {
+    int rc = collect_phases(st, k);
+    if (rc) return rc;
+  }
   for (int i = 0; i < PHASE_END; ++i) {
     ms[i] = st->phase_ms[i];
     st->phase_ms[i] = 0.0;
@@ -1233,9 +1349,18 @@ int adg_info(const adg_state* st, int64_t* out, int cap) {
   const int nchunks = (st->cap + st->chunk - 1) / st->chunk;
   out[0] = st->cap;
   out[1] = st->chunk;
-  out[2] = kernels_per_step(D, nchunks, st->cascade);
+  out[2] = st->host_passes ? kernels_per_step(D, nchunks, st->cascade)
+                           : kernels_per_loop_step(D, st->cascade) + (int64_t)nchunks * (2 * D + 5);
   out[3] = (int64_t)st->bytes_held;
-  if (cap >= 5) out[4] = st->launch_count;
+  if (cap >= 5) {
+    // host-counted kernels plus the passes that device-sized loops ran
+    int passes = 0;
+    if (cudaMemcpyAsync(&passes, st->b.counters + CNT_PASSES, sizeof(int), cudaMemcpyDeviceToHost,
+                        st->stream) != cudaSuccess ||
+        cudaStreamSynchronize(st->stream) != cudaSuccess)
+      return ADG_ERR_CUDA;
+    out[4] = st->launch_count + (int64_t)passes * (2 * D + 5);
+  }
   if (cap >= 7) {
     out[5] = st->iters;
     out[6] = st->prec == ADG_PREC_MIXED_FP32 ? (st->fp64_sweeps < st->iters ? st->fp64_sweeps : st->iters)
@@ -1252,8 +1377,11 @@ const char* adg_last_error(const adg_state* st) {
 void adg_destroy(adg_state* st) {
   if (!st) return;
   free_all(st);
-  for (int i = 0; i < PHASE_COUNT; ++i)
-    if (st->ev[i]) cudaEventDestroy(st->ev[i]);
+  for (int k = 0; k < adg_state::kEventSets; ++k)
+    for (int i = 0; i < PHASE_COUNT; ++i)
+      if (st->ev[k][i]) cudaEventDestroy(st->ev[k][i]);
+  if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
+  if (st->body_stream) cudaStreamDestroy(st->body_stream);
   delete st;
 }
 

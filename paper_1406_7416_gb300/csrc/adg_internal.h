@@ -105,7 +105,8 @@ enum {
   CNT_FB = 5,            // first-order fallback cells of the current step
   CNT_REFIX = 6,         // WENO3 cells rebalanced against a fallback neighbour
   CNT_FB_TOTAL = 7,      // fallback cells since the last load
-  CNT_COUNT = 8
+  CNT_PASSES = 8,        // limiter passes run by device-sized pass loops (cumulative)
+  CNT_COUNT = 9
 };
 
 struct Params {
@@ -149,7 +150,8 @@ struct StepLaunch {
   int n;
   const long long* pre_cells;  // [n+1]
   const long long* pre_faces[3];  // [n+1] faces x tangential nodes, per axis
-  long long* pre_lim;          // [n+1] troubled cells of one limiter pass (device-computed)
+  long long* pre_lim;          // [n+3] troubled cells of one limiter pass (device-computed);
+                               // [n+1] the pass, [n+2] passes needed (device-sized loops)
   long long* pre_fix;          // [n+1] neighbour-fix entries (device-computed)
   long long* pre_fb;           // [n+1] first-order fallback cells (device-computed)
   long long* pre_refix;        // [n+1] rebalanced WENO3 neighbours (device-computed)
@@ -166,6 +168,11 @@ struct StepLaunch {
   const double* dts;           // [n] fixed steps, or null for CFL steps
   double cfl;                  // CFL number when dts is null
   double dt_max;               // cap of CFL steps (<= 0: none)
+  // device-sized limiter passes (stream capture only): the pass body is the
+  // child graph of a conditional WHILE node on `cond`, captured on `body`
+  int loop;
+  cudaGraphConditionalHandle cond;
+  cudaStream_t body;
 };
 
 // Kernel launch interface: one dispatcher per translation unit (2D low N,
@@ -214,6 +221,13 @@ cudaError_t launch_step_end(const StepLaunch& sl, cudaStream_t s);
 cudaError_t launch_lim_prefix(const StepLaunch& sl, int pass, cudaStream_t s);
 cudaError_t launch_fix_prefix(const StepLaunch& sl, cudaStream_t s);
 cudaError_t launch_count_prefix(const StepLaunch& sl, long long* pre, int counter, cudaStream_t s);
+// Device-sized limiter passes in a captured graph: `begin` sizes the loop from
+// the troubled counts and opens it, then `add_loop_node` appends the WHILE node
+// to the capture on `s` and returns its (empty) body graph; the body ends with
+// `next`, which advances the pass and closes the loop after the last one.
+cudaError_t launch_lim_loop_begin(const StepLaunch& sl, cudaStream_t s);
+cudaError_t launch_lim_loop_next(const StepLaunch& sl, cudaStream_t s);
+cudaError_t add_loop_node(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body);
 
 // Scratch doubles per troubled cell of the limiter chunk buffers.
 size_t limiter_scratch_doubles(int dim, int N, size_t* patch, size_t* sw0, size_t* sw1,
@@ -257,10 +271,13 @@ __device__ __forceinline__ double euler_pressure(const double* Q, double gm1) {
   return gm1 * (Q[D + 1] - 0.5 * kin / Q[0]);
 }
 
-// Rusanov flux through a face with normal +e_k, pointwise (Sec. 2.3).
+// Rusanov flux through a face with normal +e_k, pointwise (Sec. 2.3).  With
+// f32speed (mixed precision) the sound speeds take an FP32 square root: the
+// speed only scales the dissipation term s (QR - QL), so its FP32 rounding
+// is relative to the jump, and the flux stays single-valued.
 template <int D>
 __device__ __forceinline__ void rusanov(const double* QL, const double* QR, int k, double gamma,
-                                        double* G) {
+                                        double* G, bool f32speed = false) {
   const double gm1 = gamma - 1.0;
   double sL, sR, FL[D + 2], FR[D + 2];
   {
@@ -270,7 +287,7 @@ __device__ __forceinline__ void rusanov(const double* QL, const double* QR, int 
     for (int j = 0; j < D; ++j) kin += QL[1 + j] * QL[1 + j];
     const double p = gm1 * (QL[D + 1] - 0.5 * kin * r);
     const double vk = QL[1 + k] * r;
-    sL = fabs(vk) + sqrt(gamma * p * r);
+    sL = fabs(vk) + (f32speed ? (double)sqrtf((float)(gamma * p * r)) : sqrt(gamma * p * r));
     FL[0] = QL[1 + k];
 #pragma unroll
     for (int j = 0; j < D; ++j) FL[1 + j] = QL[1 + j] * vk;
@@ -284,7 +301,7 @@ __device__ __forceinline__ void rusanov(const double* QL, const double* QR, int 
     for (int j = 0; j < D; ++j) kin += QR[1 + j] * QR[1 + j];
     const double p = gm1 * (QR[D + 1] - 0.5 * kin * r);
     const double vk = QR[1 + k] * r;
-    sR = fabs(vk) + sqrt(gamma * p * r);
+    sR = fabs(vk) + (f32speed ? (double)sqrtf((float)(gamma * p * r)) : sqrt(gamma * p * r));
     FR[0] = QR[1 + k];
 #pragma unroll
     for (int j = 0; j < D; ++j) FR[1 + j] = QR[1 + j] * vk;
@@ -426,9 +443,9 @@ __device__ __forceinline__ void rusanov_f(const float* QL, const float* QR, int 
 // The numerical flux selected by the state's option (0 Rusanov, 1 Osher-type).
 template <int D>
 __device__ __forceinline__ void face_flux(int which, const double* QL, const double* QR, int k,
-                                          double gamma, double* G) {
+                                          double gamma, double* G, bool f32speed = false) {
   if (which == 1) osher<D>(QL, QR, k, gamma, G);
-  else rusanov<D>(QL, QR, k, gamma, G);
+  else rusanov<D>(QL, QR, k, gamma, G, f32speed);
 }
 
 // max_k |v_k| + c of one state (wave speed for Eq. cfl)
@@ -443,6 +460,26 @@ __device__ __forceinline__ double wave_speed(const double* Q, double gamma) {
   }
   const double p = (gamma - 1.0) * (Q[D + 1] - 0.5 * kin * r);
   return vm + sqrt(gamma * p * r);
+}
+
+// The same speed for mixed precision (it only sets the CFL step): rho p =
+// (gamma - 1)(E rho - |m|^2 / 2) in FP64, free of the cancellation FP32 would
+// suffer at high Mach numbers, then c = sqrt(gamma rho p) / rho and the
+// velocities in FP32.  Inadmissible states give NaN as in wave_speed.
+template <int D>
+__device__ __forceinline__ double wave_speed_f(const double* Q, double gamma) {
+  double kin = 0.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) kin += Q[1 + k] * Q[1 + k];
+  const double rp = (gamma - 1.0) * (Q[D + 1] * Q[0] - 0.5 * kin);
+  const float r = 1.0f / (float)Q[0];
+  float vm = 0.0f;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const float a = fabsf((float)Q[1 + k]) * r;
+    vm = (a > vm || a != a) ? a : vm;
+  }
+  return (double)(vm + sqrtf((float)(gamma * rp)) * r);
 }
 
 // ---------------------------------------------------------------------------

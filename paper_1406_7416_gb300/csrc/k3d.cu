@@ -84,14 +84,43 @@ __global__ void k_step_end(StepLaunch sl) {
   if (*p.b.dt > 0.0) p.cur = 1 - p.cur;
 }
 
-// Prefix of the troubled cells each state handles in limiter pass `pass`.
+// Prefix of the troubled cells each state handles in limiter pass `pass`
+// (pass < 0: the pass of a device-sized loop, pre_lim[n + 1]).
 __global__ void k_lim_prefix(StepLaunch sl, int pass) {
+  if (pass < 0) pass = (int)sl.pre_lim[sl.n + 1];
   long long acc = 0;
   for (int s = 0; s < sl.n; ++s) {
     sl.pre_lim[s] = acc;
     acc += pass_len(*sl.pps[s], pass);
   }
   sl.pre_lim[sl.n] = acc;
+}
+
+// Opens the device-sized pass loop: the passes this step needs are the most
+// any state of the launch needs, ceil(min(n_T, capacity) / chunk), at most
+// sl.max_passes, so the loop ends after a bounded number of iterations.
+__global__ void k_lim_loop_begin(StepLaunch sl) {
+  int need = 0;
+  for (int s = 0; s < sl.n; ++s) {
+    const Params& p = *sl.pps[s];
+    if (!(*p.b.dt > 0.0)) continue;
+    int nT = p.b.counters[CNT_TROUBLED0 + (1 - p.cur)];
+    if (nT > p.cap) nT = p.cap;
+    const int k = (nT + p.chunk - 1) / p.chunk;
+    if (k > need) need = k;
+  }
+  if (need > sl.max_passes) need = sl.max_passes;
+  sl.pre_lim[sl.n + 1] = 0;
+  sl.pre_lim[sl.n + 2] = need;
+  sl.pps[0]->b.counters[CNT_PASSES] += need;
+  cudaGraphSetConditional(sl.cond, need > 0 ? 1u : 0u);
+}
+
+// Last node of the loop body: the next pass, or the end of the loop.
+__global__ void k_lim_loop_next(StepLaunch sl) {
+  const long long pass = sl.pre_lim[sl.n + 1] + 1;
+  sl.pre_lim[sl.n + 1] = pass;
+  cudaGraphSetConditional(sl.cond, pass < sl.pre_lim[sl.n + 2] ? 1u : 0u);
 }
 
 // Prefix of the entries of one per-step list counter (states idle this step
@@ -150,6 +179,36 @@ cudaError_t launch_step_end(const StepLaunch& sl, cudaStream_t s) {
 cudaError_t launch_lim_prefix(const StepLaunch& sl, int pass, cudaStream_t s) {
   k_lim_prefix<<<1, 1, 0, s>>>(sl, pass);
   return cudaGetLastError();
+}
+
+cudaError_t launch_lim_loop_begin(const StepLaunch& sl, cudaStream_t s) {
+  k_lim_loop_begin<<<1, 1, 0, s>>>(sl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lim_loop_next(const StepLaunch& sl, cudaStream_t s) {
+  k_lim_loop_next<<<1, 1, 0, s>>>(sl);
+  return cudaGetLastError();
+}
+
+cudaError_t add_loop_node(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraph_t* body) {
+  cudaStreamCaptureStatus status;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &status, nullptr, &graph, &deps, nullptr, &ndeps);
+  if (e != cudaSuccess) return e;
+  if (status != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureUnmatched;
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node = nullptr;
+  e = cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &np);
+  if (e != cudaSuccess) return e;
+  *body = np.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
 }
 
 cudaError_t launch_fix_prefix(const StepLaunch& sl, cudaStream_t s) {

@@ -111,12 +111,14 @@ __device__ __forceinline__ void picard_time(T* __restrict__ q, const UT* __restr
 // The time phase of the last FP32 Picard sweep when no FP64 sweep follows:
 // the space-time correction Ktau S is formed in FP32 from the FP32 sweep's
 // S = sum_k c_k D x_k f_k(q) and subtracted from the FP64 u, so q carries no
-// FP32 rounding of u itself (the dominant error of a plain FP32 sweep).
+// FP32 rounding of u itself (the dominant error of a plain FP32 sweep).  The
+// correction itself, dq = q - u, is kept in FP32 for the face traces.
 template <int D, int n>
 __device__ __forceinline__ void picard_time_to64(const float* __restrict__ S,
                                                  const double* __restrict__ u,
                                                  const float* __restrict__ Kt,
-                                                 double* __restrict__ q, int tid, int nth) {
+                                                 double* __restrict__ q, float* __restrict__ dq,
+                                                 int tid, int nth) {
   constexpr int NV = D + 2, ND = ipow(n, D), NST = ipow(n, D + 1);
   for (int e = tid; e < NV * ND; e += nth) {
     const int v = e / ND, i = e - v * ND;
@@ -130,6 +132,7 @@ __device__ __forceinline__ void picard_time_to64(const float* __restrict__ S,
 #pragma unroll
       for (int j = 0; j < n; ++j) acc += Kt[m * n + j] * Sl[j];
       q[v * NST + i + m * ND] = u0 - (double)acc;
+      dq[v * NST + i + m * ND] = -acc;
     }
   }
 }
@@ -250,6 +253,36 @@ __device__ __forceinline__ double block_reduce_min(double v, double* red) {
   return -block_reduce_max(-v, red);
 }
 
+// Trace element e of a cell, laid out [k][side][v][ts + NF * m] (face axis k,
+// side s, variable v, tangential node ts, time node m): returns v and sets the
+// space-time node offset `base` of the line of n nodes across axis k, its
+// stride `stk` and the side s.
+template <int D, int n>
+__device__ __forceinline__ int trace_index(int e, int& base, int& stk, int& s) {
+  constexpr int NV = D + 2, ND = ipow(n, D), NF = ipow(n, D - 1), NT = NF * n;
+  const int k = e / (2 * NV * NT);
+  int r = e - k * (2 * NV * NT);
+  s = r / (NV * NT);
+  r -= s * (NV * NT);
+  const int v = r / NT, tt = r - v * NT;
+  const int m = tt / NF;
+  int ts = tt - m * NF;
+  int st = 1;
+  base = m * ND;
+  stk = 1;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    if (j == k) {
+      stk = st;
+    } else {
+      base += (ts % n) * st;
+      ts /= n;
+    }
+    st *= n;
+  }
+  return v;
+}
+
 // ---------------------------------------------------------------------------
 // K1 predictor: one cell per block.  Writes the candidate's volume part
 // u + sum_k c_k Mvol x_k fbar_k into Unext and the space-time face traces.
@@ -261,7 +294,7 @@ __host__ __device__ constexpr size_t predictor_smem_bytes() {
              (size_t)D * DM::NV * DM::ND + 3 * DM::n * DM::n + 3 * DM::n;
   // the FP32 sweep arrays qf, Ff live inside the FP64 flux array F (unused
   // until the FP32 sweeps are over); only the FP32 operators and u stay apart
-  size_t f = MIXED ? (2 * DM::n * DM::n + (size_t)DM::NV * DM::ND) : 0;
+  size_t f = MIXED ? (2 * DM::n * DM::n + (size_t)DM::NV * DM::ND + 2 * DM::n) : 0;
   return d * sizeof(double) + f * sizeof(float);
 }
 
@@ -287,6 +320,8 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
   float* Dmf = reinterpret_cast<float*>(ph1 + n);
   float* Ktf = Dmf + n * n;
   float* uf = Ktf + n * n;
+  float* ph0f = uf + NV * ND;
+  float* ph1f = ph0f + n;
 
   const int tid = threadIdx.x, nth = blockDim.x;
   const Ops* o = bt.pps[0]->ops;      // every state of a batch has degree N
@@ -303,6 +338,10 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
     w[i] = o->w[i];
     ph0[i] = o->phi0[i];
     ph1[i] = o->phi1[i];
+    if (MIXED) {
+      ph0f[i] = (float)o->phi0[i];
+      ph1f[i] = (float)o->phi1[i];
+    }
   }
   for (long long g = blockIdx.x; g < bt.pre[bt.n]; g += gridDim.x) {
     const int sidx = batch_state(bt, g);
@@ -319,6 +358,11 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
     __syncthreads();
     int it0 = 0;
     const int n32 = p.iters - p.fp64_sweeps;    // sweeps in FP32
+    // with no FP64 sweep the traces split into trace(u) (FP64, once per face
+    // node) + trace(q - u) (FP32, per space-time node): the same sum, with
+    // FP32 rounding only on the small correction
+    const bool split = MIXED && n32 > 0 && p.fp64_sweeps == 0;
+    double* tr = p.b.trace + cell * (size_t)(D * 2 * NV * NT);
     if (MIXED && n32 > 0) {
       float cf[3];
 #pragma unroll
@@ -336,7 +380,7 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
         __syncthreads();
         picard_deriv<D, n, float>(Ff, qf, Dmf, cf, tid, nth);
         __syncthreads();
-        if (last64 && it == n32 - 1) picard_time_to64<D, n>(qf, u, Ktf, q, tid, nth);
+        if (last64 && it == n32 - 1) picard_time_to64<D, n>(qf, u, Ktf, q, Ff, tid, nth);
         else picard_time<D, n, float>(qf, uf, Ktf, tid, nth);
         __syncthreads();
       }
@@ -356,6 +400,32 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
       picard_deriv<D, n, double>(F, q, Dm, c, tid, nth);
       __syncthreads();
       picard_time<D, n, double>(q, u, Kt, tid, nth);
+      __syncthreads();
+    }
+    if (split) {
+      // trace(u) on every face node into fbar (free until the time average)
+      for (int e = tid; e < D * 2 * NV * NF; e += nth) {
+        int base, stk, s;
+        const int v = trace_index<D, n>((e / NF) * NT + e % NF, base, stk, s);   // time node 0
+        const double* ph = s ? ph1 : ph0;
+        double acc = 0.0;
+#pragma unroll
+        for (int a = 0; a < n; ++a) acc += ph[a] * u[v * ND + base + a * stk];
+        fbar[e] = acc;
+      }
+      __syncthreads();
+      const float* dq = Ff;
+      for (int e = tid; e < D * 2 * NV * NT; e += nth) {
+        int base, stk, s;
+        const int v = trace_index<D, n>(e, base, stk, s);
+        const float* ph = s ? ph1f : ph0f;
+        const float* d = dq + v * NST + base;
+        float acc = 0.0f;
+#pragma unroll
+        for (int a = 0; a < n; ++a) acc += ph[a] * d[a * stk];
+        const int tt = e % NT;
+        tr[e] = fbar[(e / NT) * NF + tt % NF] + (double)acc;
+      }
       __syncthreads();
     }
     // corrector volume term from the time-averaged nodal fluxes
@@ -386,33 +456,17 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
       Uo[e] = acc;
     }
     // space-time traces on the 2D faces: trace[cell][k][side][v][ts + NF * m]
-    double* tr = p.b.trace + cell * (size_t)(D * 2 * NV * NT);
-    for (int e = tid; e < D * 2 * NV * NT; e += nth) {
-      const int k = e / (2 * NV * NT);
-      int r = e - k * (2 * NV * NT);
-      const int s = r / (NV * NT);
-      r -= s * (NV * NT);
-      const int v = r / NT, tt = r - v * NT;
-      const int m = tt / NF;
-      int ts = tt - m * NF;
-      int base = m * ND, st = 1, stk = 1;
+    if (!split)
+      for (int e = tid; e < D * 2 * NV * NT; e += nth) {
+        int base, stk, s;
+        const int v = trace_index<D, n>(e, base, stk, s);
+        const double* ph = s ? ph1 : ph0;
+        const double* qq = q + v * NST + base;
+        double acc = 0.0;
 #pragma unroll
-      for (int j = 0; j < D; ++j) {
-        if (j == k) {
-          stk = st;
-        } else {
-          base += (ts % n) * st;
-          ts /= n;
-        }
-        st *= n;
+        for (int a = 0; a < n; ++a) acc += ph[a] * qq[a * stk];
+        tr[e] = acc;
       }
-      const double* ph = s ? ph1 : ph0;
-      const double* qq = q + v * NST + base;
-      double acc = 0.0;
-#pragma unroll
-      for (int a = 0; a < n; ++a) acc += ph[a] * qq[a * stk];
-      tr[e] = acc;
-    }
     __syncthreads();
   }
 }
@@ -494,7 +548,7 @@ __global__ void __launch_bounds__(256) k_faceflux(Batch bt, int k) {
         if (!hasL) boundary_ghost<D>(g, face, QR, QL, pos, t);
         else boundary_ghost<D>(g, face, QL, QR, pos, t);
       }
-      face_flux<D>(p.flux, QL, QR, k, p.gamma, Gm);
+      face_flux<D>(p.flux, QL, QR, k, p.gamma, Gm, p.prec == ADG_PREC_MIXED_FP32);
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] += w[m] * Gm[v];
     }
@@ -604,12 +658,12 @@ __device__ __forceinline__ const long long* block_max_keys(long long* r, long lo
 //   DMP (lohi != null): every subcell inside [lo_v, hi_v], tested exactly on
 //        the per-variable extremes (min >= lo and max <= hi).
 // Writes the per-variable min / max to mm[2v], mm[2v+1] and, when lam != null,
-// the largest wave speed max_k |v_k| + c.  Returns (block-uniform) whether
-// any check failed.  `red` needs (blockDim/32 + 1) * (2 nvar + 1) doubles.
+// the largest wave speed max_k |v_k| + c (FP32 speeds with f32speed).  Returns
+// (block-uniform) whether any check failed.  `red` needs (blockDim/32 + 1) * (2 nvar + 1) doubles.
 template <int D>
 __device__ __forceinline__ bool check_subcells(const double* __restrict__ vs, int nsub,
                                                const double* lohi, double gamma, double* mm,
-                                               double* lam, double* red) {
+                                               double* lam, double* red, bool f32speed = false) {
   constexpr int NV = D + 2, K = 2 * NV + 1;
   bool bad = false;
   long long r[K];
@@ -628,7 +682,8 @@ __device__ __forceinline__ bool check_subcells(const double* __restrict__ vs, in
 #pragma unroll
     for (int k = 0; k < D; ++k) kin += Q[1 + k] * Q[1 + k];
     bad = bad || !((Q[0] > 0.0) && (Q[D + 1] * Q[0] - 0.5 * kin > 0.0));
-    if (lam) r[2 * NV] = max(r[2 * NV], ord_key(wave_speed<D>(Q, gamma)));
+    if (lam)
+      r[2 * NV] = max(r[2 * NV], ord_key(f32speed ? wave_speed_f<D>(Q, gamma) : wave_speed<D>(Q, gamma)));
   }
   bad = __syncthreads_or(bad);
   const long long* res = block_max_keys<K>(r, reinterpret_cast<long long*>(red));
@@ -716,7 +771,8 @@ __global__ void __launch_bounds__(128) k_correct_detect(Batch bt) {
     dmp_interval<D>(p, p.b.cmm[p.cur], ijk, lohi);
     __syncthreads();
     double lam = 0.0;
-    const bool bad = check_subcells<D>(vs, NSD, lohi, p.gamma, mm, p.lam_mode ? &lam : nullptr, red);
+    const bool bad = check_subcells<D>(vs, NSD, lohi, p.gamma, mm, p.lam_mode ? &lam : nullptr, red,
+                                       p.prec == ADG_PREC_MIXED_FP32);
     if (tid == 0) {
       int slot = -1;
       if (bad || p.force) {

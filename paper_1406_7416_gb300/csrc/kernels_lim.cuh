@@ -23,6 +23,12 @@ __device__ __forceinline__ int pass_len(const Params& p, int pass) {
   return len < 0 ? 0 : (len > p.chunk ? p.chunk : len);
 }
 
+// The pass a limiter kernel works on: its argument, or for the pass loop
+// sized on the device (argument < 0) the pass stored after the prefix.
+__device__ __forceinline__ int lim_pass(const Batch& bt, int pass) {
+  return pass >= 0 ? pass : (int)bt.pre[bt.n + 1];
+}
+
 // Item t (a troubled cell of the current pass, counted over the batch) ->
 // state index and the cell's position j within its state's pass.
 struct LimItem {
@@ -138,6 +144,7 @@ __device__ __forceinline__ void patch_value(const Params& p, const int* ijk, con
 // list[chunk0 + j], ghosts by patch_value.
 template <int D, int N>
 __global__ void __launch_bounds__(256) k_lim_patch(Batch bt, int pass) {
+  pass = lim_pass(bt, pass);
   using DM = Dims<D, N>;
   constexpr int n = DM::n, NV = DM::NV, Ns = DM::Ns, L = DM::L, LD = DM::LD;
   __shared__ double P1[DM::Ns * DM::n];
@@ -375,7 +382,6 @@ __global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass, int n32
     double c[3];
     float cf[3];
     {
-      const double dt = *p.b.dt;
 #pragma unroll
       for (int k = 0; k < D; ++k) {
         c[k] = p.b.coef[3 + k];
@@ -471,6 +477,7 @@ __global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass, int n32
 // wholly in FP32, see k_lim_predict).
 template <int D, int N, int k, typename T, typename QT>
 __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
+  pass = lim_pass(bt, pass);
   using DM = Dims<D, N>;
   constexpr int NV = DM::NV, NST3 = DM::NST3, ND3 = DM::ND3, NE = DM::NE, NED = DM::NED,
                 Ns = DM::Ns;
@@ -573,6 +580,7 @@ __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
 // unlimited face neighbours for the flux correction.  One block per cell.
 template <int D, int N>
 __global__ void __launch_bounds__(128) k_lim_update(Batch bt, int pass) {
+  pass = lim_pass(bt, pass);
   using DM = Dims<D, N>;
   constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, Ns = DM::Ns, NSD = DM::NSD, L = DM::L,
                 LD = DM::LD, NSF = DM::NSF;
@@ -592,7 +600,6 @@ __global__ void __launch_bounds__(128) k_lim_update(Batch bt, int pass) {
     const int nxt = 1 - p.cur;
     double c[3];
     {
-      const double dt = *p.b.dt;
 #pragma unroll
       for (int k = 0; k < D; ++k) c[k] = p.b.coef[3 + k];
     }
@@ -634,7 +641,8 @@ __global__ void __launch_bounds__(128) k_lim_update(Batch bt, int pass) {
     }
     __syncthreads();
     double lam = 0.0;
-    const bool bad = check_subcells<D>(A, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red);
+    const bool bad = check_subcells<D>(A, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red,
+                                       p.prec == ADG_PREC_MIXED_FP32);
     if (tid == 0) {
       if (p.lam_mode) p.b.lam[cell] = lam;
       if (bad && p.cascade) {
@@ -716,7 +724,6 @@ __global__ void __launch_bounds__(128) k_lim_fix(Batch bt) {
     const Params& p = *bt.pps[sidx];
     const long long f = fg - bt.pre[sidx];
     const int nxt = 1 - p.cur;
-    const double dt = *p.b.dt;
     const long long cell = p.b.fixlist[f];
     int ijk[3];
     cell_coords<D>(cell, p.geo, ijk);
@@ -774,7 +781,8 @@ __global__ void __launch_bounds__(128) k_lim_fix(Batch bt) {
     __syncthreads();
     double* vs = apply_ct<D, NV, n, Ns>(A, B, P1, tid, nth);
     double lam = 0.0;
-    check_subcells<D>(vs, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red);
+    check_subcells<D>(vs, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red,
+                      p.prec == ADG_PREC_MIXED_FP32);
     if (tid == 0 && p.lam_mode) p.b.lam[cell] = lam;
     if (tid < 2 * NV) p.b.cmm[nxt][cell * 2 * NV + tid] = mm[tid];
   }
@@ -817,7 +825,6 @@ __global__ void __launch_bounds__(128) k_lim_fallback(Batch bt) {
     const Geo& g = p.geo;
     const int t = p.b.fblist[f];
     const long long cell = p.b.list[nxt][t];
-    const double dt = *p.b.dt;
     int ijk[3];
     cell_coords<D>(cell, g, ijk);
     __syncthreads();
@@ -904,7 +911,8 @@ __global__ void __launch_bounds__(128) k_lim_fallback(Batch bt) {
     double* st = p.b.store[nxt] + (size_t)t * NV * NSD;
     for (int e = tid; e < NV * NSD; e += nth) st[e] = A[e];
     double lam = 0.0;
-    const bool bad = check_subcells<D>(A, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red);
+    const bool bad = check_subcells<D>(A, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red,
+                                       p.prec == ADG_PREC_MIXED_FP32);
     if (tid == 0) {
       if (p.lam_mode) p.b.lam[cell] = lam;
       if (bad) atomicAdd(&p.b.counters[CNT_INADM], 1);
@@ -963,7 +971,6 @@ __global__ void __launch_bounds__(128) k_lim_refix(Batch bt) {
     const Geo& g = p.geo;
     const long long cell = p.b.refixlist[f];
     const int t = p.b.slot[nxt][cell];
-    const double dt = *p.b.dt;
     int ijk[3];
     cell_coords<D>(cell, g, ijk);
     __syncthreads();
@@ -1018,7 +1025,8 @@ __global__ void __launch_bounds__(128) k_lim_refix(Batch bt) {
     }
     __syncthreads();
     double lam = 0.0;
-    const bool bad = check_subcells<D>(A, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red);
+    const bool bad = check_subcells<D>(A, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red,
+                                       p.prec == ADG_PREC_MIXED_FP32);
     if (tid == 0) {
       if (p.lam_mode) p.b.lam[cell] = lam;
       if (bad) atomicAdd(&p.b.counters[CNT_INADM], 1);

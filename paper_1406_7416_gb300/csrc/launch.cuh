@@ -45,8 +45,14 @@ struct Launch {
     return (size_t)(NV * ND + 2 * NV * NSD + 2 * Ns * n + 4 * NV + 128) * sizeof(double);
   }
 
+  // (an event node when the stream is being captured into a graph)
   static void mark(cudaEvent_t* ev, int phase, cudaStream_t s) {
-    if (ev) cudaEventRecord(ev[phase], s);
+    if (!ev) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags(ev[phase], s, cudaEventRecordExternal);
+    else
+      cudaEventRecord(ev[phase], s);
   }
 
   static cudaError_t step_dg(const StepLaunch& sl, cudaStream_t s) {
@@ -77,61 +83,89 @@ struct Launch {
     return cudaGetLastError();
   }
 
+  // One limiter pass (pass < 0: the pass of the device-sized loop).
+  static cudaError_t lim_pass(const StepLaunch& sl, int pass, cudaStream_t s) {
+    cudaError_t e;
+    constexpr int SPB = (D == 2) ? SUBS_PER_BLOCK_2D : SUBS_PER_BLOCK_3D;
+    const Batch lim{sl.pps, sl.n, sl.pre_lim};
+    const long long ch = sl.sum_chunk;    // upper bound of the troubled cells of one pass
+    if ((e = launch_lim_prefix(sl, pass, s)) != cudaSuccess) return e;
+    k_lim_patch<D, N><<<grid_for(ch * DM::LD, 256), 256, 0, s>>>(lim, pass);
+    const long long ncross = ch * (DM::NSD + 2 * D * DM::NSF);
+    const int gs = grid_for(ch * NV * DM::LD, 256), gp = grid_for(ncross, SPB, kNumSM * 16);
+    // the subcell predictor stored in FP32 when it runs wholly in FP32
+    const bool qf = sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32 && sl.sub32 == 3;
+    if (sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32) {
+      // mixed precision: FP32 reconstruction feeding the FP32 subcell predictor
+      k_lim_sweep<D, N, 0, float><<<gs, 256, 0, s>>>(lim, pass);
+      k_lim_sweep<D, N, 1, float><<<gs, 256, 0, s>>>(lim, pass);
+      if (D == 3) k_lim_sweep<D, N, (D == 3 ? 2 : 1), float><<<gs, 256, 0, s>>>(lim, pass);
+      if (qf)
+        k_lim_predict<D, N, true, float, true><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, 3);
+      else
+        k_lim_predict<D, N, true, float, false><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, sl.sub32);
+    } else {
+      k_lim_sweep<D, N, 0, double><<<gs, 256, 0, s>>>(lim, pass);
+      k_lim_sweep<D, N, 1, double><<<gs, 256, 0, s>>>(lim, pass);
+      if (D == 3) k_lim_sweep<D, N, (D == 3 ? 2 : 1), double><<<gs, 256, 0, s>>>(lim, pass);
+      if (sl.prec == ADG_PREC_MIXED_FP32)
+        k_lim_predict<D, N, true, double, false><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, sl.sub32);
+      else
+        k_lim_predict<D, N, false, double, false><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, 0);
+    }
+    const int gf = grid_for(ch * (Ns + 1) * DM::NSF, 256);
+    if (sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32 && sl.flux == ADG_FLUX_RUSANOV) {
+      if (qf) {
+        k_lim_flux<D, N, 0, float, float><<<gf, 256, 0, s>>>(lim, pass);
+        k_lim_flux<D, N, 1, float, float><<<gf, 256, 0, s>>>(lim, pass);
+        if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), float, float><<<gf, 256, 0, s>>>(lim, pass);
+      } else {
+        k_lim_flux<D, N, 0, float, double><<<gf, 256, 0, s>>>(lim, pass);
+        k_lim_flux<D, N, 1, float, double><<<gf, 256, 0, s>>>(lim, pass);
+        if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), float, double><<<gf, 256, 0, s>>>(lim, pass);
+      }
+    } else if (qf) {
+      k_lim_flux<D, N, 0, double, float><<<gf, 256, 0, s>>>(lim, pass);
+      k_lim_flux<D, N, 1, double, float><<<gf, 256, 0, s>>>(lim, pass);
+      if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), double, float><<<gf, 256, 0, s>>>(lim, pass);
+    } else {
+      k_lim_flux<D, N, 0, double, double><<<gf, 256, 0, s>>>(lim, pass);
+      k_lim_flux<D, N, 1, double, double><<<gf, 256, 0, s>>>(lim, pass);
+      if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), double, double><<<gf, 256, 0, s>>>(lim, pass);
+    }
+    k_lim_update<D, N><<<(int)(ch < kNumSM * 8 ? ch : kNumSM * 8), 128, cell_smem(), s>>>(lim, pass);
+    return cudaGetLastError();
+  }
+
+  // The limiter passes as a conditional WHILE node of the graph being
+  // captured on `s`: the body (one pass on the device-stored pass index, then
+  // k_lim_loop_next) is captured into the node's child graph on sl.body.
+  static cudaError_t lim_loop(const StepLaunch& sl, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = launch_lim_loop_begin(sl, s)) != cudaSuccess) return e;
+    cudaGraph_t body = nullptr;
+    if ((e = add_loop_node(s, sl.cond, &body)) != cudaSuccess) return e;
+    if ((e = cudaStreamBeginCaptureToGraph(sl.body, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return e;
+    e = lim_pass(sl, -1, sl.body);
+    if (e == cudaSuccess) e = launch_lim_loop_next(sl, sl.body);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(sl.body, &captured);
+    return e != cudaSuccess ? e : ee;
+  }
+
   static cudaError_t step_limiter(const StepLaunch& sl, cudaStream_t s) {
     cudaError_t e;
     cudaEvent_t* ev = sl.ev;
     mark(ev, PHASE_LIMITER, s);
     const size_t su = cell_smem();
     if ((e = set_smem(k_lim_update<D, N>, su)) != cudaSuccess) return e;
-    constexpr int SPB = (D == 2) ? SUBS_PER_BLOCK_2D : SUBS_PER_BLOCK_3D;
-    const Batch lim{sl.pps, sl.n, sl.pre_lim};
-    const long long ch = sl.sum_chunk;    // upper bound of the troubled cells of one pass
-    for (int pass = 0; pass < sl.max_passes; ++pass) {
-      if ((e = launch_lim_prefix(sl, pass, s)) != cudaSuccess) return e;
-      k_lim_patch<D, N><<<grid_for(ch * DM::LD, 256), 256, 0, s>>>(lim, pass);
-      const long long ncross = ch * (DM::NSD + 2 * D * DM::NSF);
-      const int gs = grid_for(ch * NV * DM::LD, 256), gp = grid_for(ncross, SPB, kNumSM * 16);
-      // the subcell predictor stored in FP32 when it runs wholly in FP32
-      const bool qf = sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32 && sl.sub32 == 3;
-      if (sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32) {
-        // mixed precision: FP32 reconstruction feeding the FP32 subcell predictor
-        k_lim_sweep<D, N, 0, float><<<gs, 256, 0, s>>>(lim, pass);
-        k_lim_sweep<D, N, 1, float><<<gs, 256, 0, s>>>(lim, pass);
-        if (D == 3) k_lim_sweep<D, N, (D == 3 ? 2 : 1), float><<<gs, 256, 0, s>>>(lim, pass);
-        if (qf)
-          k_lim_predict<D, N, true, float, true><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, 3);
-        else
-          k_lim_predict<D, N, true, float, false><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, sl.sub32);
-      } else {
-        k_lim_sweep<D, N, 0, double><<<gs, 256, 0, s>>>(lim, pass);
-        k_lim_sweep<D, N, 1, double><<<gs, 256, 0, s>>>(lim, pass);
-        if (D == 3) k_lim_sweep<D, N, (D == 3 ? 2 : 1), double><<<gs, 256, 0, s>>>(lim, pass);
-        if (sl.prec == ADG_PREC_MIXED_FP32)
-          k_lim_predict<D, N, true, double, false><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, sl.sub32);
-        else
-          k_lim_predict<D, N, false, double, false><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, 0);
-      }
-      const int gf = grid_for(ch * (Ns + 1) * DM::NSF, 256);
-      if (sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32 && sl.flux == ADG_FLUX_RUSANOV) {
-        if (qf) {
-          k_lim_flux<D, N, 0, float, float><<<gf, 256, 0, s>>>(lim, pass);
-          k_lim_flux<D, N, 1, float, float><<<gf, 256, 0, s>>>(lim, pass);
-          if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), float, float><<<gf, 256, 0, s>>>(lim, pass);
-        } else {
-          k_lim_flux<D, N, 0, float, double><<<gf, 256, 0, s>>>(lim, pass);
-          k_lim_flux<D, N, 1, float, double><<<gf, 256, 0, s>>>(lim, pass);
-          if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), float, double><<<gf, 256, 0, s>>>(lim, pass);
-        }
-      } else if (qf) {
-        k_lim_flux<D, N, 0, double, float><<<gf, 256, 0, s>>>(lim, pass);
-        k_lim_flux<D, N, 1, double, float><<<gf, 256, 0, s>>>(lim, pass);
-        if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), double, float><<<gf, 256, 0, s>>>(lim, pass);
-      } else {
-        k_lim_flux<D, N, 0, double, double><<<gf, 256, 0, s>>>(lim, pass);
-        k_lim_flux<D, N, 1, double, double><<<gf, 256, 0, s>>>(lim, pass);
-        if (D == 3) k_lim_flux<D, N, (D == 3 ? 2 : 1), double, double><<<gf, 256, 0, s>>>(lim, pass);
-      }
-      k_lim_update<D, N><<<(int)(ch < kNumSM * 8 ? ch : kNumSM * 8), 128, su, s>>>(lim, pass);
+    if (sl.loop) {
+      if ((e = lim_loop(sl, s)) != cudaSuccess) return e;
+    } else {
+      for (int pass = 0; pass < sl.max_passes; ++pass)
+        if ((e = lim_pass(sl, pass, s)) != cudaSuccess) return e;
     }
     if (sl.cascade) {
       // first-order layer after WENO3 (Sec. 6, Fig. algo2); both lists are

@@ -2,6 +2,8 @@
 state alone.  Per-state work is the same arithmetic in both cases, so in FP64
 (and in mixed precision) every state's DOFs, flags and subcell data after the
 steps are bitwise equal alone and in the mix."""
+import time
+
 import numpy as np
 import pytest
 
@@ -79,7 +81,7 @@ def test_cfl_steps_with_graph_replay_equal_alone():
         for _ in range(4):
             s.step_cfl(cfl)
     batch = adg.Batch(mixed)
-    for _ in range(4):                            # step 1 plain, step 2 captured, 3-4 replays
+    for _ in range(4):                            # step 1 captured, 2-4 replays
         batch.step(cfl=cfl)
     batch.close()
     for a, m in zip(alone, mixed):
@@ -108,11 +110,13 @@ def test_end_times_stop_each_state():
 
 
 @pytest.mark.parametrize("prec", [adg.PREC_FP64, adg.PREC_MIXED_FP32])
-def test_host_sized_passes_equal_async_passes(prec):
-    """adg_step with ADG_OPT_HOST_PASSES (the host reads the troubled count
-    after the DG phase and launches only the passes it needs) leaves the same
-    state, bit for bit, as the fully asynchronous step that launches every
-    pass the capacity allows; a small scratch budget forces several passes."""
+def test_host_sized_passes_equal_device_sized_passes(prec):
+    """adg_step with ADG_OPT_HOST_PASSES = 1 (the host reads the troubled count
+    after the DG phase and launches the passes it needs) leaves the same
+    state, bit for bit, as the default graph step whose conditional loop sizes
+    the passes on the device; a small scratch budget forces several passes,
+    and both run the same number of passes (the graph adds its loop kernels:
+    one per step and one per pass)."""
     w = inputs.quadrants_2d(n=24, N=3)
     out = []
     for host in (1, 0):
@@ -127,10 +131,76 @@ def test_host_sized_passes_equal_async_passes(prec):
             s.step_cfl(w["cfl"])
         launched = s.info()["launches"] - l0
         assert s.troubled_count() > 2 * info["chunk"]
-        out.append((_state(s), s.time(), launched, info["launches_per_step"]))
+        out.append((_state(s), s.time(), launched))
         assert s.status() == adg.OK
         s.close()
     _assert_same(out[0][0], out[1][0])
     assert out[0][1] == out[1][1]
-    assert out[1][2] == 6 * out[1][3]                # asynchronous: every pass launched
-    assert out[0][2] < out[1][2]
+    D, steps = 2, 6
+    fixed = 1 + (D + 2) + 4 + 2 + 1                 # begin, DG, first-order layer, fix, end
+    passes, rem = divmod(out[0][2] - steps * fixed, 2 * D + 4)
+    assert rem == 0 and passes > 2 * steps
+    assert out[1][2] == steps * (fixed + 1) + passes * (2 * D + 5)
+
+
+@pytest.mark.parametrize("prec", [adg.PREC_FP64, adg.PREC_MIXED_FP32])
+def test_batch_graph_loops_several_passes(prec):
+    """Batched CFL steps (one graph, a device-sized pass loop per group) with a
+    scratch budget small enough for several passes per step: every state
+    bitwise equal to stepping it alone with host-sized passes."""
+    ws = [inputs.quadrants_2d(n=24, N=3), inputs.quadrants_vortex_2d(n=18, N=3),
+          inputs.explosion_2d(n=16, N=2)]
+    states = []
+    for host in (1, 0):
+        row = []
+        for w in ws:
+            s = adg.Solver.from_workload(w, prec)
+            s.set_option(adg.OPT_SCRATCH_BYTES, 4 * 2 ** 20)
+            s.set_option(adg.OPT_HOST_PASSES, host)
+            s.init_problem(w["problem"])
+            row.append(s)
+        states.append(row)
+    cfl = 0.05
+    for s in states[0]:
+        for _ in range(5):
+            s.step_cfl(cfl)
+    batch = adg.Batch(states[1])
+    for _ in range(5):                            # step 1 captured, 2-5 replays
+        batch.step(cfl=cfl)
+    batch.close()
+    assert max(s.troubled_count() for s in states[0]) > 2 * states[0][0].info()["chunk"]
+    for a, m in zip(*states):
+        _assert_same(_state(a), _state(m))
+        assert a.time() == m.time()
+        assert a.status() == adg.OK and m.status() == adg.OK
+    for s in states[0] + states[1]:
+        s.close()
+
+
+@pytest.mark.parametrize("host", [0, 1])
+def test_profiled_steps_time_every_phase(host):
+    """ADG_OPT_PROFILE on graph steps (event nodes inside the step graph, a
+    ring of event sets so that the host may run ahead) and on host-sized
+    steps (plain event records): every step timed, every phase positive, the
+    phases together within the wall time of the steps; profiling changes no
+    result."""
+    w = inputs.quadrants_2d(n=32, N=3)
+    res = []
+    for prof in (0, 1):
+        s = adg.Solver.from_workload(w, adg.PREC_FP64)
+        s.set_option(adg.OPT_HOST_PASSES, host)
+        s.init_problem(w["problem"])
+        s.set_option(adg.OPT_PROFILE, prof)
+        t0 = time.perf_counter()
+        for _ in range(7):
+            s.step_cfl(w["cfl"])
+        res.append(_state(s))
+        wall_ms = (time.perf_counter() - t0) * 1e3
+        if prof:
+            ph, n = s.phase_times()
+            assert n == 7
+            assert all(v > 0.0 for v in ph.values()), ph
+            assert sum(ph.values()) <= wall_ms
+        assert s.status() == adg.OK
+        s.close()
+    _assert_same(res[0], res[1])

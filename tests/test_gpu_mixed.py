@@ -205,6 +205,7 @@ def test_subcell_predictor_sweep_precision():
     density, and conserves to FP64 round-off."""
     w = inputs.quadrants_2d(n=16, N=3)
     out = {}
+    dt = None
     for key, prec, sub in (("fp64", adg.PREC_FP64, None), ("sub3", adg.PREC_MIXED_FP32, 3),
                            ("sub0", adg.PREC_MIXED_FP32, None)):
         s = adg.Solver.from_workload(w, prec)
@@ -214,8 +215,10 @@ def test_subcell_predictor_sweep_precision():
             s.set_option(adg.OPT_SUBCELL_FP32, 0)
         s.init_problem(w["problem"])
         out[key + "_0"] = s.read()
+        if dt is None:
+            dt = 0.5 * s.max_dt(w["cfl"])   # fixed steps: the mixed CFL speed is FP32
         for _ in range(5):
-            s.step_cfl(w["cfl"])
+            s.step(dt)
         out[key] = s.read_full()
         assert s.status() == adg.OK
         s.close()
