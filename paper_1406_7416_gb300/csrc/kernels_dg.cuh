@@ -109,31 +109,61 @@ __device__ __forceinline__ void picard_time(T* __restrict__ q, const UT* __restr
 }
 
 // The time phase of the last FP32 Picard sweep when no FP64 sweep follows:
-// the space-time correction Ktau S is formed in FP32 from the FP32 sweep's
-// S = sum_k c_k D x_k f_k(q) and subtracted from the FP64 u, so q carries no
-// FP32 rounding of u itself (the dominant error of a plain FP32 sweep).  The
-// correction itself, dq = q - u, is kept in FP32 for the face traces.
+// only the space-time correction dq = q - u = -Ktau S is formed (FP32, from
+// the sweep's S = sum_k c_k D x_k f_k(q)); the final stage adds it to the
+// FP64 u term by term (face traces, fluxes), so q carries no FP32 rounding of
+// u itself (the dominant error of a plain FP32 sweep).
 template <int D, int n>
-__device__ __forceinline__ void picard_time_to64(const float* __restrict__ S,
-                                                 const double* __restrict__ u,
-                                                 const float* __restrict__ Kt,
-                                                 double* __restrict__ q, float* __restrict__ dq,
-                                                 int tid, int nth) {
+__device__ __forceinline__ void picard_time_dq(const float* __restrict__ S,
+                                               const float* __restrict__ Kt,
+                                               float* __restrict__ dq, int tid, int nth) {
   constexpr int NV = D + 2, ND = ipow(n, D), NST = ipow(n, D + 1);
   for (int e = tid; e < NV * ND; e += nth) {
     const int v = e / ND, i = e - v * ND;
     float Sl[n];
 #pragma unroll
     for (int m = 0; m < n; ++m) Sl[m] = S[v * NST + i + m * ND];
-    const double u0 = u[v * ND + i];
 #pragma unroll
     for (int m = 0; m < n; ++m) {
       float acc = 0.0f;
 #pragma unroll
       for (int j = 0; j < n; ++j) acc += Kt[m * n + j] * Sl[j];
-      q[v * NST + i + m * ND] = u0 - (double)acc;
       dq[v * NST + i + m * ND] = -acc;
     }
+  }
+}
+
+// Euler flux difference F_k(U + dQ) - F_k(U), k = 0..D-1, in FP32 and in a
+// form where every term carries a factor of dQ (velocity change
+// dv = (dm - v drho) / (rho + drho), pressure change
+// dp = (gamma - 1)(dE - d(m.v)/2) with d(m.v) = sum_j dm_j (v_j + dv_j) + m_j dv_j),
+// so its rounding error is relative to the change, not to the flux: with
+// F(U) in FP64 the sum equals F(U + dQ) to FP32 rounding of the correction.
+template <int D>
+__device__ __forceinline__ void euler_flux_delta(const float* U, const float* dQ, float gm1,
+                                                 float (*G)[D + 2]) {
+  const float r = 1.0f / U[0];
+  const float r1 = 1.0f / (U[0] + dQ[0]);
+  float v[D], dv[D];
+  float mv = 0.0f, dmv = 0.0f;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    v[j] = U[1 + j] * r;
+    mv += U[1 + j] * v[j];
+    dv[j] = (dQ[1 + j] - v[j] * dQ[0]) * r1;
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) dmv += dQ[1 + j] * (v[j] + dv[j]) + U[1 + j] * dv[j];
+  const float Ep = U[D + 1] + gm1 * (U[D + 1] - 0.5f * mv);
+  const float dp = gm1 * (dQ[D + 1] - 0.5f * dmv);
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const float vk1 = v[k] + dv[k];
+    G[k][0] = dQ[1 + k];
+#pragma unroll
+    for (int j = 0; j < D; ++j) G[k][1 + j] = dQ[1 + j] * vk1 + U[1 + j] * dv[k];
+    G[k][1 + k] += dp;
+    G[k][D + 1] = (dQ[D + 1] + dp) * vk1 + Ep * dv[k];
   }
 }
 
@@ -380,7 +410,7 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
         __syncthreads();
         picard_deriv<D, n, float>(Ff, qf, Dmf, cf, tid, nth);
         __syncthreads();
-        if (last64 && it == n32 - 1) picard_time_to64<D, n>(qf, u, Ktf, q, Ff, tid, nth);
+        if (last64 && it == n32 - 1) picard_time_dq<D, n>(qf, Ktf, Ff, tid, nth);
         else picard_time<D, n, float>(qf, uf, Ktf, tid, nth);
         __syncthreads();
       }
@@ -403,7 +433,23 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
       __syncthreads();
     }
     if (split) {
-      // trace(u) on every face node into fbar (free until the time average)
+      // final stage on u (FP64) + dq (FP32): fbar_k = F_k(u) + sum_m w_m
+      // (F_k(u + dq_m) - F_k(u)) and traces trace(u) + trace(dq)
+      const float* dq = Ff;
+      float* dF = qf + 2 * NV * NST;      // [D][NV][NST] weighted flux differences
+      double* uT = q;                     // [D][2][NV][NF] trace(u)
+      // (at 3D N = 1 uT runs on into qf, the FP32 sweep array after q, dead by now)
+      static_assert(2 * D * NV * NF <= NV * NST + NV * NST / 2, "trace(u) scratch");
+      for (int i = tid; i < ND; i += nth) {
+        double Q[NV], Fl[D][D + 2];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Q[v] = u[v * ND + i];
+        euler_fluxes<D, double>(Q, gm1, Fl);
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) fbar[(k * NV + v) * ND + i] = Fl[k][v];
+      }
       for (int e = tid; e < D * 2 * NV * NF; e += nth) {
         int base, stk, s;
         const int v = trace_index<D, n>((e / NF) * NT + e % NF, base, stk, s);   // time node 0
@@ -411,10 +457,24 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
         double acc = 0.0;
 #pragma unroll
         for (int a = 0; a < n; ++a) acc += ph[a] * u[v * ND + base + a * stk];
-        fbar[e] = acc;
+        uT[e] = acc;
+      }
+      for (int l = tid; l < NST; l += nth) {
+        const int i = l % ND, m = l / ND;
+        float U[NV], dQ[NV], G[D][D + 2];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          U[v] = uf[v * ND + i];
+          dQ[v] = dq[v * NST + l];
+        }
+        euler_flux_delta<D>(U, dQ, (float)gm1, G);
+        const float wm = (float)w[m];
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) dF[(k * NV + v) * NST + l] = wm * G[k][v];
       }
       __syncthreads();
-      const float* dq = Ff;
       for (int e = tid; e < D * 2 * NV * NT; e += nth) {
         int base, stk, s;
         const int v = trace_index<D, n>(e, base, stk, s);
@@ -424,19 +484,26 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
 #pragma unroll
         for (int a = 0; a < n; ++a) acc += ph[a] * d[a * stk];
         const int tt = e % NT;
-        tr[e] = fbar[(e / NT) * NF + tt % NF] + (double)acc;
+        tr[e] = uT[(e / NT) * NF + tt % NF] + (double)acc;
       }
-      __syncthreads();
-    }
-    // corrector volume term from the time-averaged nodal fluxes
-    picard_flux<D, n, double>(q, F, gm1, tid, nth);
-    __syncthreads();
-    for (int e = tid; e < D * NV * ND; e += nth) {
-      const int kv = e / ND, i = e - kv * ND;
-      double acc = 0.0;
+      for (int e = tid; e < D * NV * ND; e += nth) {
+        const int kv = e / ND, i = e - kv * ND;
+        float acc = 0.0f;
 #pragma unroll
-      for (int m = 0; m < n; ++m) acc += w[m] * F[kv * NST + i + m * ND];
-      fbar[e] = acc;
+        for (int m = 0; m < n; ++m) acc += dF[kv * NST + i + m * ND];
+        fbar[e] += (double)acc;
+      }
+    } else {
+      // corrector volume term from the time-averaged nodal fluxes
+      picard_flux<D, n, double>(q, F, gm1, tid, nth);
+      __syncthreads();
+      for (int e = tid; e < D * NV * ND; e += nth) {
+        const int kv = e / ND, i = e - kv * ND;
+        double acc = 0.0;
+#pragma unroll
+        for (int m = 0; m < n; ++m) acc += w[m] * F[kv * NST + i + m * ND];
+        fbar[e] = acc;
+      }
     }
     __syncthreads();
     double* Uo = p.b.U[1 - p.cur] + cell * (NV * ND);
