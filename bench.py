@@ -52,6 +52,12 @@ def workload(n=None, N=N_ORDER):
     return inputs.quadrants_vortex_2d(n=n or GRID, N=N, steps=None)
 
 
+def launch_mode(args):
+    return ("plain kernel launches, limiter passes sized by the host after the DG phase"
+            if args.host_passes else
+            "one CUDA graph per step, limiter passes in a device-sized conditional loop")
+
+
 def config_dict(w, extra=None):
     import numpy as np
     cells = int(np.prod(w["ncell"]))
@@ -237,6 +243,8 @@ def run_gpu(args):
     def make(prec):
         s = adg.Solver.from_workload(w, prec)
         s.set_stream(stream.cuda_stream)
+        if args.host_passes:
+            s.set_option(adg.OPT_HOST_PASSES, 1)
         s.init_problem(w["problem"])
         return s
 
@@ -282,7 +290,7 @@ def run_gpu(args):
             r = results[args.only]
             print(json.dumps({"profile_run": args.only, "ms_per_step": r["ms"],
                               "phases_ms": r["phases"], "troubled_cells": r["troubled"],
-                              "config": config_dict(w)}), flush=True)
+                              "config": config_dict(w, {"launch": launch_mode(args)})}), flush=True)
         for r in results.values():
             r["solver"].close()
         rep.close()
@@ -357,11 +365,13 @@ def emit_line(args, w, results, stdofs, world, cells, cfl, l1, l1ref, e2e, D, N,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
         "config": config_dict(w, {"precision": ("mixed: FP32 Picard sweeps (%d of %d in FP64; with "
-                                                "none the last closes on the FP64 u), FP64 "
-                                                "corrector/detector; subcell scheme: FP32 "
-                                                "reconstruction, predictor and sub-face fluxes, "
-                                                "FP64 update" % (int(mx["info"]["fp64_sweeps"]),
-                                                                 int(mx["info"]["picard_iters"]))),
+                                                "none the final stage takes the FP64 u plus FP32 "
+                                                "corrections), FP64 corrector/detector; subcell "
+                                                "scheme: FP32 reconstruction, predictor and "
+                                                "sub-face fluxes, FP64 update"
+                                                % (int(mx["info"]["fp64_sweeps"]),
+                                                   int(mx["info"]["picard_iters"]))),
+                                  "launch": launch_mode(args),
                                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                                   "time_step": f"CFL {cfl:.6g} of Eq. (cfl), dt from the "
                                                "current subcell data every step"}),
@@ -463,6 +473,10 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer timing")
+    ap.add_argument("--host-passes", action="store_true",
+                    help="plain kernel launches with host-sized limiter passes instead of one "
+                         "CUDA graph per step (profilers skip kernels of graphs with "
+                         "conditional nodes)")
     ap.add_argument("--grid", type=int, default=None,
                     help="cells per axis (profiling runs; default: the workload's own)")
     ap.add_argument("--only", default="both", choices=["both", "mixed", "fp64"])

@@ -141,6 +141,15 @@ extern "C" {
                                      scheme stays conservative.  0: FP64.  With the
                                      Osher-type flux the sub-faces stay FP64.        */
 
+#define ADG_OPT_PROJECT_DELTA 16  /* mixed precision: the detector forms the subcell
+                                     averages of the candidate, P(u*), as the P(u^n)
+                                     kept from the previous step plus an FP32
+                                     projection of the step's change u* - u^n, where
+                                     P(u^n) is known (cells not limited, fixed or
+                                     loaded since); FP64 P everywhere every 16th
+                                     step.  1 (default) or 0; before the first load.
+                                     Needs nv Ns^d doubles per cell.                 */
+
 #define ADG_FLUX_RUSANOV 0
 #define ADG_FLUX_OSHER 1
 

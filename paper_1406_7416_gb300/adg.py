@@ -33,6 +33,7 @@ OPT_FLUX = 12
 OPT_HOST_PASSES = 13
 OPT_SUBCELL_FP64_SWEEPS = 14
 OPT_SUBCELL_FP32 = 15
+OPT_PROJECT_DELTA = 16
 FLUX_RUSANOV, FLUX_OSHER = 0, 1
 PHASES = ("predictor", "faceflux", "correct_detect", "limiter", "fix")
 IC_RADIAL, IC_QUADRANT, IC_PLANAR = 0, 1, 2

@@ -24,6 +24,7 @@ struct adg_state {
                             // on the device by a conditional loop
   int sub_fp64 = 0;         // mixed precision: FP64 sweeps of the degree-2 subcell predictor
   int sub_f32 = 1;          // mixed precision: FP32 subcell reconstruction and sub-face fluxes
+  int project_delta = 1;    // mixed precision: detector projection from the kept P(u^n)
   int bstate_set = 0;       // bit f: inflow face f has a state
   int front_set = 0;        // bit f: front face f has its front
   // pinned host mirror of the device Params, counters and dt, read once per
@@ -260,6 +261,10 @@ int ensure_allocated(adg_state* st) {
     ALLOC(b.store[i], double, cap * nv * nsd);
   }
   ALLOC(b.trace, double, cells * st->dim * 2 * nv * nf * n);
+  if (st->prec == ADG_PREC_MIXED_FP32 && st->project_delta) {
+    ALLOC(b.vstar, double, cells * nv * nsd);
+    ALLOC(b.vok, uint8_t, cells);
+  }
   for (int k = 0; k < st->dim; ++k) {
     long long faces = 1;
     for (int j = 0; j < st->dim; ++j) faces *= (j == k) ? st->geo.n[j] + 1 : st->geo.n[j];
@@ -359,6 +364,7 @@ int begin_load(adg_state* st) {
   st->params_dirty = true;
   // every counter but the cumulative pass count (adg_info's launch count)
   CUDA_TRY(st, cudaMemsetAsync(st->b.counters, 0, sizeof(int) * CNT_PASSES, st->stream));
+  if (st->b.vok) CUDA_TRY(st, cudaMemsetAsync(st->b.vok, 0, st->geo.cells, st->stream));
   const double clk[3] = {0.0, st->t_end, 0.0};
   CUDA_TRY(st, cudaMemcpyAsync(st->b.clock, clk, sizeof(clk), cudaMemcpyHostToDevice, st->stream));
   CUDA_TRY(st, cudaStreamSynchronize(st->stream));
@@ -1029,6 +1035,10 @@ int adg_set_option(adg_state* st, int key, double value) {
       return ADG_OK;
     case ADG_OPT_HOST_PASSES:
       st->host_passes = value != 0.0;
+      return ADG_OK;
+    case ADG_OPT_PROJECT_DELTA:
+      if (st->allocated) return fail(st, ADG_ERR_ARG, "set ADG_OPT_PROJECT_DELTA before the first load");
+      st->project_delta = value != 0.0;
       return ADG_OK;
     case ADG_OPT_FLUX:
       if (value != ADG_FLUX_RUSANOV && value != ADG_FLUX_OSHER)

@@ -88,6 +88,10 @@ struct Bufs {
   double* clock;         // [3] simulated time t, end time t_end (0: none), steps taken
   double* tstart;        // [1] simulated time at the start of the current step
   double* coef;          // [6] dt / dx_k and dt Ns / dx_k of the current step (set once per step)
+  // mixed precision, ADG_OPT_PROJECT_DELTA: the subcell averages P(u) of each
+  // cell's current DOFs, kept from the detector of the step that made them
+  double* vstar;         // [cells][nv][Ns^d] (null when off)
+  uint8_t* vok;          // [cells] 1 where vstar is P of the cell's current DOFs
   // limiter scratch, sized for one chunk of `chunk` troubled cells
   double* patch;         // [chunk][nv][L^d]
   double* sweep[3];      // [chunk][nv][...] after the x, y, z reconstructions

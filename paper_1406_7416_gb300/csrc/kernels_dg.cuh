@@ -226,9 +226,9 @@ __device__ __forceinline__ double* apply_all_axes(double* a, double* b, const do
 
 // Compile-time variant of apply_all_axes: NV variables, NI -> NO points per
 // axis, matrix M[NO][NI]; every index division is by a constant.
-template <int D, int NV, int NI, int NO, int K>
-__device__ __forceinline__ void apply_pass_ct(const double* __restrict__ in, double* __restrict__ out,
-                                              const double* __restrict__ M, int tid, int nth) {
+template <int D, int NV, int NI, int NO, int K, typename T = double>
+__device__ __forceinline__ void apply_pass_ct(const T* __restrict__ in, T* __restrict__ out,
+                                              const T* __restrict__ M, int tid, int nth) {
   constexpr int I0 = (0 < K) ? NO : NI, I1 = (1 < K) ? NO : NI, I2 = (2 < K) ? NO : NI;
   constexpr int O0 = (0 <= K) ? NO : NI, O1 = (1 <= K) ? NO : NI, O2 = (2 <= K) ? NO : NI;
   constexpr int E1 = (D > 1) ? 1 : 0, E2 = (D > 2) ? 1 : 0;
@@ -244,24 +244,24 @@ __device__ __forceinline__ void apply_pass_ct(const double* __restrict__ in, dou
     const int x2 = E2 ? r / O1 : 0;
     const int xk = (K == 0) ? x0 : (K == 1 ? x1 : x2);
     const int off = (K == 0 ? 0 : x0) + I0 * ((K == 1 ? 0 : x1) + I1 * (K == 2 ? 0 : x2));
-    const double* src = in + v * ISZ + off;
-    const double* mr = M + xk * NI;
-    double acc = 0.0;
+    const T* src = in + v * ISZ + off;
+    const T* mr = M + xk * NI;
+    T acc = T(0);
 #pragma unroll
     for (int c = 0; c < NI; ++c) acc += mr[c] * src[c * STRIDE];
     out[e] = acc;
   }
 }
 
-template <int D, int NV, int NI, int NO>
-__device__ __forceinline__ double* apply_ct(double* a, double* b, const double* M, int tid, int nth) {
-  apply_pass_ct<D, NV, NI, NO, 0>(a, b, M, tid, nth);
+template <int D, int NV, int NI, int NO, typename T = double>
+__device__ __forceinline__ T* apply_ct(T* a, T* b, const T* M, int tid, int nth) {
+  apply_pass_ct<D, NV, NI, NO, 0, T>(a, b, M, tid, nth);
   __syncthreads();
   if (D == 1) return b;
-  apply_pass_ct<D, NV, NI, NO, 1>(b, a, M, tid, nth);
+  apply_pass_ct<D, NV, NI, NO, 1, T>(b, a, M, tid, nth);
   __syncthreads();
   if (D == 2) return a;
-  apply_pass_ct<D, NV, NI, NO, 2>(a, b, M, tid, nth);
+  apply_pass_ct<D, NV, NI, NO, 2, T>(a, b, M, tid, nth);
   __syncthreads();
   return b;
 }
@@ -434,12 +434,10 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
     }
     if (split) {
       // final stage on u (FP64) + dq (FP32): fbar_k = F_k(u) + sum_m w_m
-      // (F_k(u + dq_m) - F_k(u)) and traces trace(u) + trace(dq)
+      // (F_k(u + dq_m) - F_k(u)); the face traces stay split, trace(u) in FP64
+      // and trace(dq) in FP32 (split trace layout, see k_faceflux)
       const float* dq = Ff;
       float* dF = qf + 2 * NV * NST;      // [D][NV][NST] weighted flux differences
-      double* uT = q;                     // [D][2][NV][NF] trace(u)
-      // (at 3D N = 1 uT runs on into qf, the FP32 sweep array after q, dead by now)
-      static_assert(2 * D * NV * NF <= NV * NST + NV * NST / 2, "trace(u) scratch");
       for (int i = tid; i < ND; i += nth) {
         double Q[NV], Fl[D][D + 2];
 #pragma unroll
@@ -457,7 +455,7 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
         double acc = 0.0;
 #pragma unroll
         for (int a = 0; a < n; ++a) acc += ph[a] * u[v * ND + base + a * stk];
-        uT[e] = acc;
+        tr[(e / (NV * NF)) * (NV * NT) + e % (NV * NF)] = acc;
       }
       for (int l = tid; l < NST; l += nth) {
         const int i = l % ND, m = l / ND;
@@ -483,8 +481,8 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
         float acc = 0.0f;
 #pragma unroll
         for (int a = 0; a < n; ++a) acc += ph[a] * d[a * stk];
-        const int tt = e % NT;
-        tr[e] = uT[(e / NT) * NF + tt % NF] + (double)acc;
+        const int blk = e / (NV * NT);
+        reinterpret_cast<float*>(tr + blk * (NV * NT) + NV * NF)[e - blk * (NV * NT)] = acc;
       }
       for (int e = tid; e < D * NV * ND; e += nth) {
         const int kv = e / ND, i = e - kv * ND;
@@ -543,8 +541,149 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
 // face normal to axis k.  Transmissive boundary: the missing side copies the
 // interior trace (G = F(q^-)).
 // ---------------------------------------------------------------------------
+// Whether a state's predictor leaves its face traces split: per (cell, axis,
+// side) block of NV x NT doubles, trace(u) [NV][NF] in FP64 followed by
+// trace(dq) [NV][NT] in FP32 (mixed precision with no FP64 Picard sweep).
+__device__ __forceinline__ bool split_traces(const Params& p) {
+  return p.prec == ADG_PREC_MIXED_FP32 && p.fp64_sweeps == 0 && p.iters > 0;
+}
+
+// Space-time trace value at tangential node ts, time node m of one block.
+template <int D, int n>
+__device__ __forceinline__ void load_trace(const double* blk, int ts, int m, bool split, double* Q) {
+  constexpr int NV = D + 2, NF = ipow(n, D - 1), NT = NF * n;
+  if (split) {
+    const float* d = reinterpret_cast<const float*>(blk + NV * NF);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Q[v] = blk[v * NF + ts] + (double)d[v * NT + ts + NF * m];
+  } else {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Q[v] = blk[v * NT + ts + NF * m];
+  }
+}
+
+// Euler flux along axis k (FP64).
+template <int D>
+__device__ __forceinline__ void euler_flux_k(const double* Q, double gm1, int k, double* F) {
+  const double r = 1.0 / Q[0];
+  double kin = 0.0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) kin += Q[1 + j] * Q[1 + j];
+  const double p = gm1 * (Q[D + 1] - 0.5 * kin * r);
+  const double vk = Q[1 + k] * r;
+  F[0] = Q[1 + k];
+#pragma unroll
+  for (int j = 0; j < D; ++j) F[1 + j] = Q[1 + j] * vk;
+  F[1 + k] += p;
+  F[D + 1] = vk * (Q[D + 1] + p);
+}
+
+// F_k(U + dQ) - F_k(U) in FP32, every term carrying a factor of dQ (the
+// along-axis-k part of euler_flux_delta).
+template <int D>
+__device__ __forceinline__ void euler_flux_delta_k(const float* U, const float* dQ, float gm1, int k,
+                                                   float* G) {
+  const float r = 1.0f / U[0];
+  const float r1 = 1.0f / (U[0] + dQ[0]);
+  float v[D], dv[D];
+  float mv = 0.0f, dmv = 0.0f;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    v[j] = U[1 + j] * r;
+    mv += U[1 + j] * v[j];
+    dv[j] = (dQ[1 + j] - v[j] * dQ[0]) * r1;
+  }
+#pragma unroll
+  for (int j = 0; j < D; ++j) dmv += dQ[1 + j] * (v[j] + dv[j]) + U[1 + j] * dv[j];
+  const float Ep = U[D + 1] + gm1 * (U[D + 1] - 0.5f * mv);
+  const float dp = gm1 * (dQ[D + 1] - 0.5f * dmv);
+  const float vk1 = v[k] + dv[k];
+  G[0] = dQ[1 + k];
+#pragma unroll
+  for (int j = 0; j < D; ++j) G[1 + j] = dQ[1 + j] * vk1 + U[1 + j] * dv[k];
+  G[1 + k] += dp;
+  G[D + 1] = (dQ[D + 1] + dp) * vk1 + Ep * dv[k];
+}
+
+// |v_k| + c of U + dQ in FP32, with rho p = (gamma - 1)(E rho - |m|^2 / 2)
+// taken as the FP64 value rpU of U plus its change, which carries a factor of
+// dQ; NaN for an inadmissible state.
+template <int D>
+__device__ __forceinline__ float speed_split(const float* U, const float* dQ, float rpU, float gamma,
+                                             float gm1, int k) {
+  float drp = U[D + 1] * dQ[0] + (U[0] + dQ[0]) * dQ[D + 1];
+#pragma unroll
+  for (int j = 0; j < D; ++j) drp -= (U[1 + j] + 0.5f * dQ[1 + j]) * dQ[1 + j];
+  const float r = 1.0f / (U[0] + dQ[0]);
+  return fabsf(U[1 + k] + dQ[1 + k]) * r + sqrtf(gamma * (rpU + gm1 * drp)) * r;
+}
+
+// Time-averaged Rusanov flux of an interior face from split traces:
+//   G = (F_k(uL) + F_k(uR)) / 2 + sum_m w_m (dF_L,m + dF_R,m) / 2
+//       - (uR - uL) sum_m w_m s_m / 2 - sum_m w_m s_m (dqR_m - dqL_m) / 2,
+// F_k(u) in FP64 once per face node, the per-time-node parts in FP32.
+template <int D, int n>
+__device__ __forceinline__ void face_split_rusanov(const double* bL, const double* bR, int ts, int k,
+                                                   double gamma, const double* w, double* G) {
+  constexpr int NV = D + 2, NF = ipow(n, D - 1), NT = NF * n;
+  const float* dL = reinterpret_cast<const float*>(bL + NV * NF);
+  const float* dR = reinterpret_cast<const float*>(bR + NV * NF);
+  const double gm1 = gamma - 1.0;
+  double uL[NV], uR[NV], FL[NV], FR[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    uL[v] = bL[v * NF + ts];
+    uR[v] = bR[v * NF + ts];
+  }
+  euler_flux_k<D>(uL, gm1, k, FL);
+  euler_flux_k<D>(uR, gm1, k, FR);
+  double kinL = 0.0, kinR = 0.0;
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    kinL += uL[1 + j] * uL[1 + j];
+    kinR += uR[1 + j] * uR[1 + j];
+  }
+  const float rpL = (float)(gm1 * (uL[D + 1] * uL[0] - 0.5 * kinL));
+  const float rpR = (float)(gm1 * (uR[D + 1] * uR[0] - 0.5 * kinR));
+  float ULf[NV], URf[NV], sumD[NV], sumJ[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    ULf[v] = (float)uL[v];
+    URf[v] = (float)uR[v];
+    sumD[v] = 0.0f;
+    sumJ[v] = 0.0f;
+  }
+  float S = 0.0f;
+  const float gf = (float)gamma, gm1f = (float)gm1;
+#pragma unroll 1
+  for (int m = 0; m < n; ++m) {
+    float qL[NV], qR[NV], GL[NV], GR[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      qL[v] = dL[v * NT + ts + NF * m];
+      qR[v] = dR[v * NT + ts + NF * m];
+    }
+    euler_flux_delta_k<D>(ULf, qL, gm1f, k, GL);
+    euler_flux_delta_k<D>(URf, qR, gm1f, k, GR);
+    const float sL = speed_split<D>(ULf, qL, rpL, gf, gm1f, k);
+    const float sR = speed_split<D>(URf, qR, rpR, gf, gm1f, k);
+    const float s = (sL > sR || sL != sL) ? sL : sR;     // NaN propagates
+    const float wm = (float)w[m];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      sumD[v] += wm * (GL[v] + GR[v]);
+      sumJ[v] += wm * s * (qR[v] - qL[v]);
+    }
+    S += wm * s;
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    G[v] = 0.5 * (FL[v] + FR[v]) + 0.5 * (double)sumD[v] -
+           0.5 * ((uR[v] - uL[v]) * (double)S + (double)sumJ[v]);
+}
+
 template <int D, int N>
-__global__ void __launch_bounds__(256) k_faceflux(Batch bt, int k) {
+__global__ void __launch_bounds__(256, 2) k_faceflux(Batch bt, int k) {
   using DM = Dims<D, N>;
   constexpr int n = DM::n, NV = DM::NV, NF = DM::NF, NT = DM::NT;
   for (long long eg = blockIdx.x * (long long)blockDim.x + threadIdx.x; eg < bt.pre[bt.n];
@@ -586,16 +725,20 @@ __global__ void __launch_bounds__(256) k_faceflux(Batch bt, int k) {
                              : nullptr;
     if (!hasL) trL = trR;
     if (!hasR) trR = trL;
+    const bool split = split_traces(p);
     double acc[NV];
+    if (split && hasL && hasR && p.flux == ADG_FLUX_RUSANOV) {
+      face_split_rusanov<D, n>(trL, trR, ts, k, p.gamma, w, acc);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) G[(face * NV + v) * NF + ts] = acc[v];
+      continue;
+    }
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = 0.0;
     for (int m = 0; m < n; ++m) {
       double QL[NV], QR[NV], Gm[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        QL[v] = trL[v * NT + ts + NF * m];
-        QR[v] = trR[v * NT + ts + NF * m];
-      }
+      load_trace<D, n>(trL, ts, m, split, QL);
+      load_trace<D, n>(trR, ts, m, split, QR);
       if (!hasL || !hasR) {
         const int face = 2 * k + (hasL ? 1 : 0);
         double pos = 0.0, t = 0.0;
@@ -783,7 +926,9 @@ template <int D, int N>
 __host__ __device__ constexpr size_t correct_smem_bytes() {
   using DM = Dims<D, N>;
   const int big = DM::NSD > DM::ND * 4 ? DM::NSD : DM::ND * 4;
-  return (size_t)(2 * DM::NV * (DM::NSD > big ? DM::NSD : big) + DM::Ns * DM::n + 4 * DM::NV + 128) *
+  // + the FP32 copy of P1 (Ns n floats) for the projection of the step's change
+  return (size_t)(2 * DM::NV * (DM::NSD > big ? DM::NSD : big) + DM::Ns * DM::n + 4 * DM::NV + 128 +
+                  (DM::Ns * DM::n + 1) / 2) *
          sizeof(double);
 }
 
@@ -799,9 +944,13 @@ __global__ void __launch_bounds__(128) k_correct_detect(Batch bt) {
   double* lohi = P1 + Ns * n;         // 2 NV
   double* mm = lohi + 2 * NV;         // 2 NV
   double* red = mm + 2 * NV;          // 128
+  float* P1f = reinterpret_cast<float*>(red + 128);   // Ns * n
   const int tid = threadIdx.x, nth = blockDim.x;
   const Ops* o = bt.pps[0]->ops;
-  for (int i = tid; i < Ns * n; i += nth) P1[i] = o->P1[i];
+  for (int i = tid; i < Ns * n; i += nth) {
+    P1[i] = o->P1[i];
+    P1f[i] = (float)o->P1[i];
+  }
   __syncthreads();
   for (long long g = blockIdx.x; g < bt.pre[bt.n]; g += gridDim.x) {
     const int sidx = batch_state(bt, g);
@@ -816,6 +965,13 @@ __global__ void __launch_bounds__(128) k_correct_detect(Batch bt) {
     int ijk[3];
     cell_coords<D>(cell, p.geo, ijk);
     double* Uo = p.b.U[nxt] + cell * (NV * ND);
+    // mixed precision: P(u*) = P(u^n) (kept) + P(u* - u^n) in FP32 where P(u^n)
+    // is known, except every 16th step (bounds the drift of the kept values)
+    double* vkeep = p.b.vstar ? p.b.vstar + cell * (size_t)(NV * NSD) : nullptr;
+    const bool delta = vkeep && p.b.vok[cell] && (p.stamp & 15) != 0;
+    const double* Un = p.b.U[p.cur] + cell * (NV * ND);
+    float* dA = reinterpret_cast<float*>(B);          // FP32 change, then its projection
+    float* dB = dA + NV * BUF;
     for (int e = tid; e < NV * ND; e += nth) {
       const int v = e / ND, i = e - v * ND;
       double acc = Uo[e];
@@ -832,9 +988,23 @@ __global__ void __launch_bounds__(128) k_correct_detect(Batch bt) {
       }
       A[e] = acc;
       Uo[e] = acc;
+      if (delta) dA[e] = (float)(acc - Un[e]);
     }
     __syncthreads();
-    double* vs = apply_ct<D, NV, n, Ns>(A, B, P1, tid, nth);
+    double* vs;
+    if (delta) {
+      const float* dv = apply_ct<D, NV, n, Ns, float>(dA, dB, P1f, tid, nth);
+      for (int e = tid; e < NV * NSD; e += nth) {
+        const double x = vkeep[e] + (double)dv[e];
+        A[e] = x;
+        vkeep[e] = x;
+      }
+      vs = A;
+    } else {
+      vs = apply_ct<D, NV, n, Ns>(A, B, P1, tid, nth);
+      if (vkeep)
+        for (int e = tid; e < NV * NSD; e += nth) vkeep[e] = vs[e];
+    }
     dmp_interval<D>(p, p.b.cmm[p.cur], ijk, lohi);
     __syncthreads();
     double lam = 0.0;
@@ -856,6 +1026,7 @@ __global__ void __launch_bounds__(128) k_correct_detect(Batch bt) {
       p.b.beta[nxt][cell] = (uint8_t)(slot >= 0);
       p.b.slot[nxt][cell] = slot;
       if (p.lam_mode) p.b.lam[cell] = lam;
+      if (vkeep) p.b.vok[cell] = 1;       // reset by any later change of the cell's DOFs
     }
     if (tid < 2 * NV) p.b.cmm[nxt][cell * 2 * NV + tid] = mm[tid];
     __syncthreads();

@@ -678,6 +678,7 @@ __global__ void __launch_bounds__(128) k_lim_update(Batch bt, int pass) {
     double* u = apply_ct<D, NV, Ns, n>(A, B, R1, tid, nth);
     double* Uo = p.b.U[nxt] + cell * (NV * ND);
     for (int e = tid; e < NV * ND; e += nth) Uo[e] = u[e];
+    if (tid == 0 && p.b.vok) p.b.vok[cell] = 0;     // P(R(v)) is not v: recompute next step
     // unlimited face neighbours get the flux correction
     if (tid < 2 * D) {
       const int k = tid >> 1, side = (tid & 1) ? 1 : -1;
@@ -780,6 +781,11 @@ __global__ void __launch_bounds__(128) k_lim_fix(Batch bt) {
     }
     __syncthreads();
     double* vs = apply_ct<D, NV, n, Ns>(A, B, P1, tid, nth);
+    if (p.b.vstar) {
+      // the corrected DOFs' projection, kept for the next step's detector
+      double* vk = p.b.vstar + cell * (size_t)(NV * NSD);
+      for (int e = tid; e < NV * NSD; e += nth) vk[e] = vs[e];
+    }
     double lam = 0.0;
     check_subcells<D>(vs, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red,
                       p.prec == ADG_PREC_MIXED_FP32);
@@ -922,6 +928,7 @@ __global__ void __launch_bounds__(128) k_lim_fallback(Batch bt) {
     double* u = apply_ct<D, NV, Ns, n>(A, B, R1, tid, nth);
     double* Uo = p.b.U[nxt] + cell * (NV * ND);
     for (int e = tid; e < NV * ND; e += nth) Uo[e] = u[e];
+    if (tid == 0 && p.b.vok) p.b.vok[cell] = 0;     // P(R(v)) is not v: recompute next step
     if (tid < 2 * D) {
       const int k = tid >> 1, side = (tid & 1) ? 1 : -1;
       int nb[3];
@@ -1036,6 +1043,7 @@ __global__ void __launch_bounds__(128) k_lim_refix(Batch bt) {
     double* u = apply_ct<D, NV, Ns, n>(A, B, R1, tid, nth);
     double* Uo = p.b.U[nxt] + cell * (NV * ND);
     for (int e = tid; e < NV * ND; e += nth) Uo[e] = u[e];
+    if (tid == 0 && p.b.vok) p.b.vok[cell] = 0;     // P(R(v)) is not v: recompute next step
   }
 }
 

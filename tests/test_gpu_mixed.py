@@ -233,3 +233,36 @@ def test_subcell_predictor_sweep_precision():
     tot0 = np.einsum("cvl,l->v", out["sub0_0"], Wd)
     tot = np.einsum("cvl,l->v", out["sub0"][0], Wd)
     np.testing.assert_allclose(tot, tot0, rtol=0, atol=1e-13 * np.abs(tot0).max() * 256)
+
+
+@pytest.mark.parametrize("make", [lambda: inputs.quadrants_2d(n=48, N=5),
+                                  lambda: inputs.explosion_3d(n=12, N=2)])
+def test_projection_from_kept_averages_flags_like_fp64_projection(make):
+    """ADG_OPT_PROJECT_DELTA (the detector's P(u*) as the kept P(u^n) plus an
+    FP32 projection of the step's change) against the FP64 projection of every
+    candidate, both mixed, 20 fixed steps on data that keeps the limiter busy:
+    the projection only feeds the detector, so equal flags at every step leave
+    the states bitwise equal."""
+    w = make()
+    if w["dim"] == 3:
+        w["problem"]["cell_rho_factor"] = None
+    runs = []
+    dt = None
+    for delta in (0, 1):
+        s = adg.Solver.from_workload(w, adg.PREC_MIXED_FP32)
+        s.set_option(adg.OPT_PROJECT_DELTA, delta)
+        s.init_problem(w["problem"])
+        if dt is None:
+            dt = 0.5 * s.max_dt(w["cfl"])
+        flags, troubled = [], 0
+        for _ in range(20):
+            s.step(dt)
+            flags.append(s.flags())
+            troubled += int(flags[-1].sum())
+        runs.append((flags, s.read(), troubled))
+        assert s.status() == adg.OK
+        s.close()
+    assert runs[0][2] > 0
+    for a, b in zip(runs[0][0], runs[1][0]):
+        np.testing.assert_array_equal(a, b)
+    np.testing.assert_array_equal(runs[0][1], runs[1][1])
