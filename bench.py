@@ -34,6 +34,7 @@ WORKLOAD = "quadvortex512"
 METRIC = "space-time DOF updates/s"
 UNIT = "ST-DOF/s"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
 
 
 def workload(n=None, N=N_ORDER):
@@ -84,19 +85,33 @@ def flux_flops(D):
     return D * D + 5 * D + 5
 
 
+def flux_delta_flops(D):
+    """F_k(U + dQ) - F_k(U) in all D directions at one node, in the form whose
+    terms carry a factor of dQ: 2 divisions, velocities and their changes,
+    m.v and its change, E + p and the pressure change, D (3D + 6) for the
+    flux changes."""
+    return 3 * D * D + 17 * D + 9
+
+
 def predictor_flops(D, N, iters, fp64_sweeps):
     """(fp64, fp32) flops of the predictor kernel for one cell: `iters` Picard
-    sweeps of which `fp64_sweeps` in FP64 (the others in FP32; with none the
-    last FP32 sweep's correction is subtracted from the FP64 u, one FP64
-    operation per space-time value), then the FP64 time average, volume term
-    and traces."""
+    sweeps, `fp64_sweeps` of them in FP64 and the others in FP32, then the
+    final stage.  After an FP64 sweep (and in the FP64 path) the final stage
+    is FP64: fluxes at the space-time nodes, their time average, the volume
+    term and the face traces.  With no FP64 sweep it splits: F(u) at the
+    spatial nodes, the volume term and trace(u) in FP64; the flux changes at
+    the space-time nodes, their weighted time sum and trace(q - u) in FP32."""
     n, nv = N + 1, D + 2
-    nst, nd = n ** (D + 1), n ** D
+    nst, nd, nf = n ** (D + 1), n ** D, n ** (D - 1)
     it = nst * flux_flops(D) + nv * nst * D * (2 * n + 2) + nv * nd * n * (2 * n + 1)
-    final = (nst * flux_flops(D) + D * nv * nd * 2 * n + nv * nd * D * (2 * n + 2)
-             + 2 * D * nv * n ** (D - 1) * n * 2 * n)
-    close = nv * nst if fp64_sweeps == 0 else 0
-    return fp64_sweeps * it + final + close, (iters - fp64_sweeps) * it
+    vol = nv * nd * D * (2 * n + 2)
+    if fp64_sweeps > 0:
+        final = nst * flux_flops(D) + D * nv * nd * 2 * n + vol + 2 * D * nv * nf * n * 2 * n
+        return fp64_sweeps * it + final, (iters - fp64_sweeps) * it
+    final64 = nd * flux_flops(D) + D * nv * nd + vol + 2 * D * nv * nf * 2 * n
+    final32 = (nst * flux_delta_flops(D) + D * nv * nst * 2 + 2 * D * nv * nf * n * 2 * n
+               + nv * nst * n * 2)
+    return final64, iters * it + final32
 
 
 def clocks_sampler():
@@ -355,7 +370,13 @@ def emit_line(args, w, results, stdofs, world, cells, cfl, l1, l1ref, e2e, D, N,
     iters = int(mx["info"]["picard_iters"])
     fl64, fl32 = predictor_flops(D, N, iters, int(mx["info"]["fp64_sweeps"]))
     pred_ms = mx["phases"]["predictor"]
-    achieved = fl64 * cells / (pred_ms / 1e3) / 1e12
+    # the predictor's bound: the pipe whose algorithmic flops take longer at its
+    # derived peak (the FP64 and FP32 pipes run side by side)
+    t64 = fl64 * cells / (FP64_PEAK_TFLOPS * 1e12)
+    t32 = fl32 * cells / (FP32_PEAK_TFLOPS * 1e12)
+    pipe, fl_dom, peak = (("fp64", fl64, FP64_PEAK_TFLOPS) if t64 >= t32 else
+                          ("fp32", fl32, FP32_PEAK_TFLOPS))
+    achieved = fl_dom * cells / (pred_ms / 1e3) / 1e12
     fl64f, _ = predictor_flops(D, N, iters, iters)
     achieved_f64 = fl64f * cells / (f64["phases"]["predictor"] / 1e3) / 1e12
     traffic = traffic_record() if (WORKLOAD == "quadvortex512" and GRID == 512) else None
@@ -384,12 +405,15 @@ def emit_line(args, w, results, stdofs, world, cells, cfl, l1, l1ref, e2e, D, N,
                           "steps": args.warmup + args.steps},
         "phases_ms": mx["phases"],
         "troubled_cells": mx["troubled"], "status": mx["status"],
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                     "kernel": "k_predictor (FP64 pipe: FP64 sweeps, closing subtraction and "
-                               "corrector terms; its FP32 sweeps in fp32_flops_per_launch)",
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "pipe": pipe,
+                     "kernel": "k_predictor; bound by the %s pipe: its algorithmic flops take "
+                               "the longer time at the derived peaks (FP64 %.3f, FP32 %.1f "
+                               "TFLOP/s: 2 and 128 FMA per clock per SM at 2.07 GHz)"
+                               % (pipe.upper(), FP64_PEAK_TFLOPS, FP32_PEAK_TFLOPS),
                      "fp32_flops_per_launch": fl32 * cells,
                      "fp64_flops_per_launch": fl64 * cells,
+                     "pipe_time_ms": {"fp64": t64 * 1e3, "fp32": t32 * 1e3},
                      "traffic": traffic["bytes_per_launch"] if traffic else None},
         "e2e": e2e,
         "gpu_launches": int(mx["launches"]),

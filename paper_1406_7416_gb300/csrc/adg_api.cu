@@ -205,6 +205,13 @@ int launch(adg_state* st, LaunchArgs& a, const char* what) {
 
 int ensure_allocated(adg_state* st) {
   if (st->allocated) return ADG_OK;
+  {
+    // the FP32 Picard operators of this degree, in the launching unit's constant memory
+    const cudaError_t e = st->dim == 3 ? upload_constants_3d(st->N, st->ops_host)
+                          : st->N <= 5 ? upload_constants_2d_lo(st->N, st->ops_host)
+                                       : upload_constants_2d_hi(st->N, st->ops_host);
+    if (e != cudaSuccess) return fail(st, ADG_ERR_CUDA, std::string("operator upload: ") + cudaGetErrorString(e));
+  }
   const long long cells = st->geo.cells;
   const int nv = st->nv, nd = nodes_per_cell(st), nsd = subcells_per_cell(st);
   const int n = st->N + 1, Ns = 2 * st->N + 1;

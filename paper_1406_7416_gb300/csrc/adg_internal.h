@@ -217,6 +217,11 @@ enum { PHASE_PREDICTOR = 0, PHASE_FACEFLUX, PHASE_CORRECT, PHASE_LIMITER, PHASE_
 cudaError_t dispatch_2d_lo(int N, const LaunchArgs& a);   // N = 1..5
 cudaError_t dispatch_2d_hi(int N, const LaunchArgs& a);   // N = 6..9
 cudaError_t dispatch_3d(int N, const LaunchArgs& a);      // N = 1..3
+// FP32 Picard operators of degree N into the constant memory of the unit
+// that launches that (dimension, degree)
+cudaError_t upload_constants_2d_lo(int N, const Ops& o);
+cudaError_t upload_constants_2d_hi(int N, const Ops& o);
+cudaError_t upload_constants_3d(int N, const Ops& o);
 cudaError_t launch_dt(const Params& p, double cfl, double dt_max, cudaStream_t s);
 cudaError_t launch_set_scalar(double* dst, double v, cudaStream_t s);
 // dimension-independent batch kernels (k3d.cu)

@@ -3,6 +3,8 @@
 
 namespace adg {
 
+cudaError_t upload_constants_2d_hi(int N, const Ops& o) { return upload_picard_constants_here(N, o); }
+
 cudaError_t dispatch_2d_hi(int N, const LaunchArgs& a) {
   switch (N) {
     case 6: return Launch<2, 6>::run(a);

@@ -3,6 +3,8 @@
 
 namespace adg {
 
+cudaError_t upload_constants_2d_lo(int N, const Ops& o) { return upload_picard_constants_here(N, o); }
+
 cudaError_t dispatch_2d_lo(int N, const LaunchArgs& a) {
   switch (N) {
     case 1: return Launch<2, 1>::run(a);

@@ -31,16 +31,20 @@ struct Dims {
 // Predictor block shape.  The mixed kernel at high 2D degrees is latency
 // bound with one 128-thread block per SM (measured: 4 warps per SM, FP64 pipe
 // 41% busy at N = 9); 256 threads capped at 128 registers, two blocks per SM,
-// hide the FP32 and FP64 latencies.  The FP64 kernel keeps the FP64 pipe busy
-// as it is and runs faster without the register cap.
+// hide the FP32 and FP64 latencies.  Below N = 6 the mixed kernel runs 128
+// threads capped at 102 registers, five blocks per SM (measured against four
+// blocks at 2D N = 4 and 5: 8% and 4% faster; 256 threads: 40% slower).  The
+// FP64 kernel keeps the FP64 pipe busy as it is and runs faster without the
+// register cap.
 template <int D, int N, bool MIXED>
 struct PredShape {
   static constexpr bool wide = MIXED && D == 2 && N >= 6;
   static constexpr int threads = wide ? 256 : 128;      // launched per block
-  static constexpr int bound = 256;                      // __launch_bounds__ maximum
-  // <= 128 registers (two 256-thread or four 128-thread blocks per SM), except
+  static constexpr int bound = (MIXED && !wide) ? 128 : 256;   // __launch_bounds__ maximum
+  // registers: <= 102 for the narrow mixed kernel (five 128-thread blocks per
+  // SM), <= 128 otherwise (two 256-thread or four 128-thread blocks), except
   // the FP64 kernel at 2D N >= 6, which would spill under that cap
-  static constexpr int min_blocks = (!MIXED && D == 2 && N >= 6) ? 1 : 2;
+  static constexpr int min_blocks = (MIXED && !wide) ? 5 : ((!MIXED && D == 2 && N >= 6) ? 1 : 2);
 };
 
 // ---------------------------------------------------------------------------
@@ -108,16 +112,133 @@ __device__ __forceinline__ void picard_time(T* __restrict__ q, const UT* __restr
   }
 }
 
+// FP32 Picard operators D and Ktau of every degree N (index N) in constant
+// memory, one copy per translation unit (filled by upload_picard_constants):
+// with the loops unrolled every operator entry is a constant-bank operand of
+// its FMA, so the FP32 sweeps load only their data from shared memory.
+static __constant__ float c_Dmf[MAXN][MAXN * MAXN];
+static __constant__ float c_Ktf[MAXN][MAXN * MAXN];
+// the degree-2 subcell predictor's operators (3 nodes), likewise
+static __constant__ float c_D3f[9];
+static __constant__ float c_K3f[9];
+
+// Derivative and time phases of an FP32 sweep of the subcell predictor with
+// its operators from constant memory; one output per work item and no
+// barrier inside (the caller's thread groups run them under a condition).
+// Operation order as in picard_deriv / picard_time.
+template <int D>
+__device__ __forceinline__ void picard_deriv_sub(const float* __restrict__ F, float* __restrict__ S,
+                                                 const float* c, int tid, int nth) {
+  constexpr int n = 3, NV = D + 2, NST = ipow(n, D + 1);
+  for (int e = tid; e < NV * NST; e += nth) {
+    const int v = e / NST, l = e - v * NST;
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const int st = (k == 0) ? 1 : (k == 1 ? n : n * n);
+      const int ak = (l / st) % n;
+      const float* f = F + (k * NV + v) * NST + (l - ak * st);
+      float x[n];
+#pragma unroll
+      for (int j = 0; j < n; ++j) x[j] = f[j * st];
+      // row ak of D3 from constant memory (ak is 0, 1 or 2)
+      const float d0 = ak == 0 ? c_D3f[0] : (ak == 1 ? c_D3f[3] : c_D3f[6]);
+      const float d1 = ak == 0 ? c_D3f[1] : (ak == 1 ? c_D3f[4] : c_D3f[7]);
+      const float d2 = ak == 0 ? c_D3f[2] : (ak == 1 ? c_D3f[5] : c_D3f[8]);
+      float acc = 0.0f;
+      acc += d0 * x[0];
+      acc += d1 * x[1];
+      acc += d2 * x[2];
+      s += c[k] * acc;
+    }
+    S[e] = s;
+  }
+}
+
+template <int D>
+__device__ __forceinline__ void picard_time_sub(float* __restrict__ q, const float* __restrict__ u,
+                                                int tid, int nth) {
+  constexpr int n = 3, NV = D + 2, ND = ipow(n, D), NST = ipow(n, D + 1);
+  for (int e = tid; e < NV * ND; e += nth) {
+    const int v = e / ND, i = e - v * ND;
+    float Sl[n];
+#pragma unroll
+    for (int m = 0; m < n; ++m) Sl[m] = q[v * NST + i + m * ND];
+    const float u0 = u[v * ND + i];
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int j = 0; j < n; ++j) acc += c_K3f[m * n + j] * Sl[j];
+      q[v * NST + i + m * ND] = u0 - acc;
+    }
+  }
+}
+
+// Derivative phase of an FP32 sweep, S = sum_k c_k D x_k F_k, one thread per
+// line of n nodes along axis k: the line's n fluxes are loaded once and give
+// n outputs (n independent FMA chains).  The axes run one after the other
+// (S is written for k = 0 and accumulated after), with the same operation
+// order per output as picard_deriv.
+template <int D, int N>
+__device__ __forceinline__ void picard_deriv_lines(const float* __restrict__ F, float* __restrict__ S,
+                                                   const float* c, int tid, int nth) {
+  constexpr int n = N + 1, NV = D + 2, NST = ipow(n, D + 1), NL = NST / n;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const int st = (k == 0) ? 1 : (k == 1 ? n : n * n);
+    const float ck = c[k];
+    for (int e = tid; e < NV * NL; e += nth) {
+      const int v = e / NL, r = e - v * NL;
+      const int base = r % st + (r / st) * (st * n);
+      const float* f = F + (k * NV + v) * NST + base;
+      float x[n];
+#pragma unroll
+      for (int j = 0; j < n; ++j) x[j] = f[j * st];
+      float* sl = S + v * NST + base;
+#pragma unroll
+      for (int a = 0; a < n; ++a) {
+        float acc = 0.0f;
+#pragma unroll
+        for (int j = 0; j < n; ++j) acc += c_Dmf[N][a * n + j] * x[j];
+        if (k == 0) sl[a * st] = ck * acc;
+        else sl[a * st] += ck * acc;
+      }
+    }
+    if (k + 1 < D) __syncthreads();
+  }
+}
+
+// Time phase of an FP32 sweep, q <- u - Ktau S, with Ktau from constant memory.
+template <int D, int N>
+__device__ __forceinline__ void picard_time_cf(float* __restrict__ q, const float* __restrict__ u,
+                                               int tid, int nth) {
+  constexpr int n = N + 1, NV = D + 2, ND = ipow(n, D), NST = ipow(n, D + 1);
+  for (int e = tid; e < NV * ND; e += nth) {
+    const int v = e / ND, i = e - v * ND;
+    float Sl[n];
+#pragma unroll
+    for (int m = 0; m < n; ++m) Sl[m] = q[v * NST + i + m * ND];
+    const float u0 = u[v * ND + i];
+#pragma unroll
+    for (int m = 0; m < n; ++m) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int j = 0; j < n; ++j) acc += c_Ktf[N][m * n + j] * Sl[j];
+      q[v * NST + i + m * ND] = u0 - acc;
+    }
+  }
+}
+
 // The time phase of the last FP32 Picard sweep when no FP64 sweep follows:
 // only the space-time correction dq = q - u = -Ktau S is formed (FP32, from
 // the sweep's S = sum_k c_k D x_k f_k(q)); the final stage adds it to the
 // FP64 u term by term (face traces, fluxes), so q carries no FP32 rounding of
 // u itself (the dominant error of a plain FP32 sweep).
-template <int D, int n>
+template <int D, int N>
 __device__ __forceinline__ void picard_time_dq(const float* __restrict__ S,
-                                               const float* __restrict__ Kt,
                                                float* __restrict__ dq, int tid, int nth) {
-  constexpr int NV = D + 2, ND = ipow(n, D), NST = ipow(n, D + 1);
+  constexpr int n = N + 1, NV = D + 2, ND = ipow(n, D), NST = ipow(n, D + 1);
   for (int e = tid; e < NV * ND; e += nth) {
     const int v = e / ND, i = e - v * ND;
     float Sl[n];
@@ -127,7 +248,7 @@ __device__ __forceinline__ void picard_time_dq(const float* __restrict__ S,
     for (int m = 0; m < n; ++m) {
       float acc = 0.0f;
 #pragma unroll
-      for (int j = 0; j < n; ++j) acc += Kt[m * n + j] * Sl[j];
+      for (int j = 0; j < n; ++j) acc += c_Ktf[N][m * n + j] * Sl[j];
       dq[v * NST + i + m * ND] = -acc;
     }
   }
@@ -408,10 +529,10 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
       for (int it = 0; it < n32; ++it) {
         picard_flux<D, n, float>(qf, Ff, (float)gm1, tid, nth);
         __syncthreads();
-        picard_deriv<D, n, float>(Ff, qf, Dmf, cf, tid, nth);
+        picard_deriv_lines<D, N>(Ff, qf, cf, tid, nth);
         __syncthreads();
-        if (last64 && it == n32 - 1) picard_time_dq<D, n>(qf, Ktf, Ff, tid, nth);
-        else picard_time<D, n, float>(qf, uf, Ktf, tid, nth);
+        if (last64 && it == n32 - 1) picard_time_dq<D, N>(qf, Ff, tid, nth);
+        else picard_time_cf<D, N>(qf, uf, tid, nth);
         __syncthreads();
       }
       if (!last64)

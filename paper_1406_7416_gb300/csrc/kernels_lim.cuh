@@ -407,9 +407,9 @@ __global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass, int n32
       for (int it = 0; it < 3; ++it) {
         if (live) picard_flux<D, 3, float>(sqf[grp], sFf[grp], (float)gm1, lt, NST3);
         __syncthreads();
-        if (live) picard_deriv<D, 3, float>(sFf[grp], sqf[grp], D3f, cf, lt, NST3);
+        if (live) picard_deriv_sub<D>(sFf[grp], sqf[grp], cf, lt, NST3);
         __syncthreads();
-        if (live) picard_time<D, 3, float>(sqf[grp], suf[grp], K3f, lt, NST3);
+        if (live) picard_time_sub<D>(sqf[grp], suf[grp], lt, NST3);
         __syncthreads();
       }
       if (live) {

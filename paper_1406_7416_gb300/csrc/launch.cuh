@@ -25,6 +25,25 @@ cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Copy the FP32 Picard operators of degree N into this translation unit's
+// constant memory (static: every unit that launches the predictor has its own).
+static inline cudaError_t upload_picard_constants_here(int N, const Ops& o) {
+  const int n = N + 1;
+  cudaError_t e = cudaMemcpyToSymbol(c_Dmf, o.Df, sizeof(float) * n * n,
+                                     sizeof(float) * (size_t)N * MAXN * MAXN);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_Ktf, o.Ktf, sizeof(float) * n * n, sizeof(float) * (size_t)N * MAXN * MAXN);
+  if (e != cudaSuccess) return e;
+  float d3[9], k3[9];
+  for (int i = 0; i < 9; ++i) {
+    d3[i] = (float)o.D3[i];
+    k3[i] = (float)o.Kt3[i];
+  }
+  e = cudaMemcpyToSymbol(c_D3f, d3, sizeof(d3));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_K3f, k3, sizeof(k3));
+}
+
 template <int D, int N>
 struct Launch {
   using DM = Dims<D, N>;
