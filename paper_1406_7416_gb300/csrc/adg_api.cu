@@ -286,6 +286,7 @@ int ensure_allocated(adg_state* st) {
   b.fbflag = b.fblist + cap;
   b.refixlist = b.fblist + 2 * cap;
   ALLOC(b.dt, double, 12);
+  ALLOC(b.lamkey, long long, 1);
   b.lamred = b.dt + 1;
   b.clock = b.dt + 2;
   b.tstart = b.dt + 5;
@@ -307,6 +308,7 @@ int ensure_allocated(adg_state* st) {
   CUDA_TRY(st, cudaMemsetAsync(b.fixstamp, 0xff, sizeof(int) * cells, st->stream));
   CUDA_TRY(st, cudaMemsetAsync(b.fbflag, 0xff, sizeof(int) * cap, st->stream));
   CUDA_TRY(st, cudaMemsetAsync(b.dt, 0, sizeof(double) * 12, st->stream));
+  CUDA_TRY(st, cudaMemsetAsync(b.lamkey, 0, sizeof(long long), st->stream));
   {
     long long pre[20] = {0, cells, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int k = 0; k < st->dim; ++k) {
@@ -474,12 +476,13 @@ StepLaunch single_launch(adg_state* st) {
   return sl;
 }
 
-// Kernels of one step: step begin; predictor, d face-flux kernels, corrector;
+// Kernels of one step: the wave-speed maximum and the step begin; predictor,
+// d face-flux kernels, corrector;
 // per limiter pass a prefix, the patch, d sweeps, the subcell predictor, d
 // flux kernels and the update; the first-order layer (two prefixes, two
 // kernels); the fix prefix and the fix; step end.
 long long kernels_per_step(int dim, int passes, int cascade) {
-  return 1 + (1 + dim + 1) + (long long)passes * (2 * dim + 4) + (cascade ? 4 : 0) + 2 + 1;
+  return 2 + (1 + dim + 1) + (long long)passes * (2 * dim + 4) + (cascade ? 4 : 0) + 2 + 1;
 }
 
 // Enqueue one step of the states described by `sl` (all of one dimension,

@@ -85,6 +85,7 @@ struct Bufs {
   int* refixlist;        // [cap] WENO3 cells sharing a face with a fallback cell
   double* dt;            // [1] time step of the current step (0: state idle this step)
   double* lamred;        // [1] reduced lambda
+  long long* lamkey;     // [1] bits of the largest per-cell wave speed (CFL steps; 0 between steps)
   double* clock;         // [3] simulated time t, end time t_end (0: none), steps taken
   double* tstart;        // [1] simulated time at the start of the current step
   double* coef;          // [6] dt / dx_k and dt Ns / dx_k of the current step (set once per step)

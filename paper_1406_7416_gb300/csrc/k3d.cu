@@ -25,34 +25,49 @@ __global__ void k_dt(Params p, double cfl, double dt_max) {
 
 __global__ void k_set_scalar(double* dst, double v) { *dst = v; }
 
+// Largest per-cell wave speed of each state for a CFL step: blockIdx.y is the
+// state, 64 blocks share its cells and combine their block maxima with an
+// atomic max on the bits of the (non-negative) double; NaN is kept as the
+// largest key.  k_step_begin reads the key and clears it.  Fixed steps skip.
+__global__ void k_lam_max(StepLaunch sl) {
+  __shared__ double red[32];
+  if (sl.dts) return;
+  Params& p = *sl.pps[blockIdx.y];
+  double l = 0.0, l1 = 0.0;
+  const long long nc = p.geo.cells;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long c0 = 0;
+  if ((reinterpret_cast<uintptr_t>(p.b.lam) & 15) == 0) {
+    const double2* L2 = reinterpret_cast<const double2*>(p.b.lam);
+    const long long n2 = nc / 2;
+    for (long long c = t; c < n2; c += stride) {
+      const double2 x = L2[c];
+      l = nanmax(l, x.x);
+      l1 = nanmax(l1, x.y);
+    }
+    c0 = 2 * n2;
+  }
+  for (long long c = c0 + t; c < nc; c += stride) l = nanmax(l, p.b.lam[c]);
+  l = block_reduce_max(nanmax(l, l1), red);
+  if (threadIdx.x == 0) atomicMax(p.b.lamkey, l != l ? LLONG_MAX : __double_as_longlong(l));
+}
+
 // Start of a batched step, one block per state: the state's dt (fixed from
-// sl.dts, or Eq. (cfl) from its per-cell wave speeds, capped by sl.dt_max and
+// sl.dts, or Eq. (cfl) from its largest wave speed, capped by sl.dt_max and
 // by its end time), a new step stamp and cleared counters.  A state with
 // dt = 0 idles through the step.
 __global__ void k_step_begin(StepLaunch sl) {
-  __shared__ double red[32];
   Params& p = *sl.pps[blockIdx.x];
   double dt = 0.0;
   if (sl.dts) {
     dt = sl.dts[blockIdx.x];
   } else {
-    // max over the cells in 16-byte loads, two in flight per thread (the max
-    // is exact, so the grouping does not change it)
-    double l = 0.0, l1 = 0.0;
-    const long long nc = p.geo.cells;
-    long long c0 = 0;
-    if ((reinterpret_cast<uintptr_t>(p.b.lam) & 15) == 0) {
-      const double2* L2 = reinterpret_cast<const double2*>(p.b.lam);
-      const long long n2 = nc / 2;
-      for (long long c = threadIdx.x; c < n2; c += blockDim.x) {
-        const double2 x = L2[c];
-        l = nanmax(l, x.x);
-        l1 = nanmax(l1, x.y);
-      }
-      c0 = 2 * n2;
-    }
-    for (long long c = c0 + threadIdx.x; c < nc; c += blockDim.x) l = nanmax(l, p.b.lam[c]);
-    l = block_reduce_max(nanmax(l, l1), red);
+    // the maximum k_lam_max left (the max is exact: any grouping gives it)
+    const long long key = *p.b.lamkey;
+    const double l = key == LLONG_MAX ? __longlong_as_double(0x7ff8000000000000LL) : __longlong_as_double(key);
+    __syncthreads();
+    if (threadIdx.x == 0) *p.b.lamkey = 0;
     double h = p.geo.dx[0];
     for (int k = 1; k < p.dim; ++k) h = fmin(h, p.geo.dx[k]);
     dt = (sl.cfl > 0.0 ? sl.cfl : p.cfl) * h / l;
@@ -183,7 +198,8 @@ cudaError_t launch_set_scalar(double* dst, double v, cudaStream_t s) {
 }
 
 cudaError_t launch_step_begin(const StepLaunch& sl, cudaStream_t s) {
-  k_step_begin<<<sl.n, sl.dts ? 32 : 1024, 0, s>>>(sl);
+  k_lam_max<<<dim3(64, sl.n), 256, 0, s>>>(sl);
+  k_step_begin<<<sl.n, 32, 0, s>>>(sl);
   return cudaGetLastError();
 }
 

@@ -137,7 +137,7 @@ def test_host_sized_passes_equal_device_sized_passes(prec):
     _assert_same(out[0][0], out[1][0])
     assert out[0][1] == out[1][1]
     D, steps = 2, 6
-    fixed = 1 + (D + 2) + 4 + 2 + 1                 # begin, DG, first-order layer, fix, end
+    fixed = 2 + (D + 2) + 4 + 2 + 1                 # speed max + begin, DG, first-order layer, fix, end
     passes, rem = divmod(out[0][2] - steps * fixed, 2 * D + 4)
     assert rem == 0 and passes > 2 * steps
     assert out[1][2] == steps * (fixed + 1) + passes * (2 * D + 5)
