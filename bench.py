@@ -351,15 +351,20 @@ def end_to_end(s, args, stdofs, world, cfl, barrier, max_over_ranks):
     barrier()
     t0 = time.perf_counter()
     s.load_full(hd, hb, hs)
+    t1 = time.perf_counter()
     for _ in range(args.steps):
         s.step_cfl(cfl)
         s.lib.adg_flags(s.h, adg._u8ptr(flags))
+    t2 = time.perf_counter()
     s.read(out)
-    el = max_over_ranks(time.perf_counter() - t0)
+    t3 = time.perf_counter()
+    el = max_over_ranks(t3 - t0)
     h2d = (hd.nbytes + hb.nbytes + hs.nbytes) / args.steps + 8
     d2h = flags.nbytes + out.nbytes / args.steps
     return {"value": stdofs * args.steps * world / el, "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "breakdown_ms": {"load": (t1 - t0) * 1e3, "steps": (t2 - t1) * 1e3,
+                             "read": (t3 - t2) * 1e3},
             "timed": "adg_load_full from pinned host, then per step adg_step_cfl + adg_flags to "
                      "pinned host, then adg_read of the DOFs"}
 
