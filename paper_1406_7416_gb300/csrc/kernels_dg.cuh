@@ -31,20 +31,24 @@ struct Dims {
 // Predictor block shape.  The mixed kernel at high 2D degrees is latency
 // bound with one 128-thread block per SM (measured: 4 warps per SM, FP64 pipe
 // 41% busy at N = 9); 256 threads capped at 128 registers, two blocks per SM,
-// hide the FP32 and FP64 latencies.  Below N = 6 the mixed kernel runs 128
+// hide the FP32 and FP64 latencies.  Below N = 6 the 2D mixed kernel runs 128
 // threads capped at 102 registers, five blocks per SM (measured against four
-// blocks at 2D N = 4 and 5: 8% and 4% faster; 256 threads: 40% slower).  The
-// FP64 kernel keeps the FP64 pipe busy as it is and runs faster without the
-// register cap.
+// blocks at N = 4 and 5: 8% and 4% faster; 160 threads: 17% slower at N = 4;
+// 256 threads: 40% slower), the 3D mixed kernel 160 threads, four blocks per
+// SM (9% faster than 128 at N = 3).  The FP64 kernel keeps the FP64 pipe busy
+// as it is and runs faster without the register cap.
 template <int D, int N, bool MIXED>
 struct PredShape {
   static constexpr bool wide = MIXED && D == 2 && N >= 6;
-  static constexpr int threads = wide ? 256 : 128;      // launched per block
-  static constexpr int bound = (MIXED && !wide) ? 128 : 256;   // __launch_bounds__ maximum
-  // registers: <= 102 for the narrow mixed kernel (five 128-thread blocks per
-  // SM), <= 128 otherwise (two 256-thread or four 128-thread blocks), except
-  // the FP64 kernel at 2D N >= 6, which would spill under that cap
-  static constexpr int min_blocks = (MIXED && !wide) ? 5 : ((!MIXED && D == 2 && N >= 6) ? 1 : 2);
+  static constexpr bool narrow3 = MIXED && D == 3;
+  static constexpr int threads = wide ? 256 : (narrow3 ? 160 : 128);   // launched per block
+  static constexpr int bound = (MIXED && !wide) ? threads : 256;       // __launch_bounds__ maximum
+  // registers: <= 102 for the narrow mixed kernels (five 128- or four
+  // 160-thread blocks per SM), <= 128 otherwise (two 256-thread or four
+  // 128-thread blocks), except the FP64 kernel at 2D N >= 6, which would spill
+  // under that cap
+  static constexpr int min_blocks =
+      narrow3 ? 4 : ((MIXED && !wide) ? 5 : ((!MIXED && D == 2 && N >= 6) ? 1 : 2));
 };
 
 // ---------------------------------------------------------------------------
@@ -1053,8 +1057,10 @@ __host__ __device__ constexpr size_t correct_smem_bytes() {
          sizeof(double);
 }
 
+// (at most 64 registers, eight blocks per SM: 5-12% faster than the 72 the
+// compiler takes unbounded)
 template <int D, int N>
-__global__ void __launch_bounds__(128) k_correct_detect(Batch bt) {
+__global__ void __launch_bounds__(128, 8) k_correct_detect(Batch bt) {
   using DM = Dims<D, N>;
   constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, NF = DM::NF, Ns = DM::Ns, NSD = DM::NSD;
   constexpr int BUF = (DM::NSD > DM::ND * 4 ? DM::NSD : DM::ND * 4);
