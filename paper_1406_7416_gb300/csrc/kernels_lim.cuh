@@ -142,38 +142,168 @@ __device__ __forceinline__ void patch_value(const Params& p, const int* ijk, con
 
 // L0: patch[j][v][L^d], local subcell -3..Ns+2 per axis around troubled cell
 // list[chunk0 + j], ghosts by patch_value.
+// Offset of local subcell loc (-3 .. Ns+2 per axis) in a limiter patch.
+template <int D, int L>
+__device__ __forceinline__ int patch_offset(const int* loc) {
+  int off = 0, m = 1;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    off += (loc[k] + 3) * m;
+    m *= L;
+  }
+  return off;
+}
+
+// Limiter patch of each troubled cell: v^n on L^D subcells (the cell and
+// three layers around it, Eq. ader.icbc), each value as patch_value gives it
+// and in the same operation order, gathered by neighbour boxes.  The patch
+// splits into 3^D boxes, one per neighbour offset o in {-1, 0, 1}^D (per axis
+// the 3 subcell layers below the cell, its Ns subcells, or the 3 layers
+// above).  A box whose owner is one cell reached without a boundary ghost
+// rule (an interior or periodic neighbour) is copied from that cell's stored
+// subcell data when it was troubled at level n, else projected from its DOFs
+// by tensor passes of P, axis by axis over the box (about n FMA per value and
+// axis instead of n^D per value); other boxes take patch_value per subcell.
+// One block per (troubled cell, box).
 template <int D, int N>
-__global__ void __launch_bounds__(256) k_lim_patch(Batch bt, int pass) {
+__global__ void __launch_bounds__(128) k_lim_patch(Batch bt, int pass) {
   pass = lim_pass(bt, pass);
   using DM = Dims<D, N>;
-  constexpr int n = DM::n, NV = DM::NV, Ns = DM::Ns, L = DM::L, LD = DM::LD;
-  __shared__ double P1[DM::Ns * DM::n];
+  constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, Ns = DM::Ns, NSD = DM::NSD, L = DM::L, LD = DM::LD;
+  constexpr int NB = ipow(3, D), NR = ipow(n, D - 1);
+  __shared__ double P1[Ns * n];
+  __shared__ double Us[NV * ND];
+  __shared__ double T1[NV * Ns * NR];                     // after the x pass
+  __shared__ double T2[(D == 3) ? NV * Ns * Ns * n : 1];  // after the y pass (3D)
   for (int i = threadIdx.x; i < Ns * n; i += blockDim.x) P1[i] = bt.pps[0]->ops->P1[i];
-  __syncthreads();
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < bt.pre[bt.n] * LD;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long t = e / LD;
+  for (long long item = blockIdx.x; item < bt.pre[bt.n] * NB; item += gridDim.x) {
+    __syncthreads();
+    const long long t = item / NB;
+    const int b = (int)(item - t * NB);
     const LimItem it = lim_item(bt, t);
     const Params& p = *bt.pps[it.s];
     const Geo& g = p.geo;
     const int j = it.j;
-    int r = (int)(e - t * LD);
     const long long cell = p.b.list[1 - p.cur][pass * p.chunk + j];
     int ijk[3];
     cell_coords<D>(cell, g, ijk);
-    int loc[3] = {0, 0, 0};
+    int o[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, R[3] = {1, 1, 1}, own[3] = {0, 0, 0};
+    bool simple = true;
+    {
+      int bb = b;
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-      loc[k] = r % L - 3;
-      r /= L;
+      for (int k = 0; k < D; ++k) {
+        o[k] = bb % 3 - 1;
+        bb /= 3;
+        lo[k] = o[k] < 0 ? -3 : (o[k] == 0 ? 0 : Ns);
+        R[k] = o[k] == 0 ? Ns : 3;
+        int c = ijk[k] + o[k];
+        if (c < 0 || c >= g.n[k]) {
+          if (g.periodic[k]) c = (c + g.n[k]) % g.n[k];
+          else simple = false;
+        }
+        own[k] = c;
+      }
     }
-    double val[NV];
-    patch_value<D, N>(p, ijk, loc, P1, val);
-    double* dst = p.b.patch + (size_t)j * NV * LD + (e - t * LD);
+    const int nbox = R[0] * R[1] * R[2];
+    double* dst = p.b.patch + (size_t)j * NV * LD;
+    if (!simple) {
+      // a ghost rule applies along some axis: per subcell
+      for (int e = threadIdx.x; e < nbox; e += blockDim.x) {
+        int r = e, loc[3] = {0, 0, 0};
 #pragma unroll
-    for (int v = 0; v < NV; ++v) dst[v * LD] = val[v];
+        for (int k = 0; k < D; ++k) {
+          loc[k] = lo[k] + r % R[k];
+          r /= R[k];
+        }
+        double val[NV];
+        patch_value<D, N>(p, ijk, loc, P1, val);
+        const int off = patch_offset<D, L>(loc);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dst[v * LD + off] = val[v];
+      }
+      continue;
+    }
+    const long long oc = cell_index<D>(own, g);
+    if (p.b.beta[p.cur][oc]) {
+      // the owner's subcell data of level n
+      const double* st = p.b.store[p.cur] + (size_t)p.b.slot[p.cur][oc] * NV * NSD;
+      for (int e = threadIdx.x; e < NV * nbox; e += blockDim.x) {
+        const int v = e / nbox;
+        int r = e - v * nbox, loc[3] = {0, 0, 0}, sidx = 0, m = 1;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+          loc[k] = lo[k] + r % R[k];
+          r /= R[k];
+          sidx += (loc[k] - o[k] * Ns) * m;
+          m *= Ns;
+        }
+        dst[v * LD + patch_offset<D, L>(loc)] = st[v * NSD + sidx];
+      }
+      continue;
+    }
+    // P(u^n) of the owner over the box, by tensor passes (x, y[, z])
+    const double* U = p.b.U[p.cur] + oc * (NV * ND);
+    for (int e = threadIdx.x; e < NV * ND; e += blockDim.x) Us[e] = U[e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < NV * R[0] * NR; e += blockDim.x) {
+      const int v = e / (R[0] * NR);
+      const int r = e - v * (R[0] * NR);
+      const int sx = r % R[0], rest = r / R[0];
+      const double* px = P1 + (lo[0] + sx - o[0] * Ns) * n;
+      const double* u = Us + v * ND + rest * n;
+      double acc = 0.0;
+#pragma unroll
+      for (int a = 0; a < n; ++a) acc += px[a] * u[a];
+      T1[(v * R[0] + sx) * NR + rest] = acc;
+    }
+    __syncthreads();
+    if (D == 2) {
+      for (int e = threadIdx.x; e < NV * R[0] * R[1]; e += blockDim.x) {
+        const int v = e / (R[0] * R[1]);
+        const int r = e - v * (R[0] * R[1]);
+        const int sx = r % R[0], sy = r / R[0];
+        const double* py = P1 + (lo[1] + sy - o[1] * Ns) * n;
+        const double* t1 = T1 + (v * R[0] + sx) * NR;
+        double accb = 0.0;
+#pragma unroll
+        for (int bb = 0; bb < n; ++bb) accb += py[bb] * t1[bb];
+        const int loc[3] = {lo[0] + sx, lo[1] + sy, 0};
+        dst[v * LD + patch_offset<D, L>(loc)] = 0.0 + accb;   // as 0 + 1 * accb in subcell_value
+      }
+    } else {
+      for (int e = threadIdx.x; e < NV * R[0] * R[1] * n; e += blockDim.x) {
+        const int v = e / (R[0] * R[1] * n);
+        int r = e - v * (R[0] * R[1] * n);
+        const int sx = r % R[0];
+        r /= R[0];
+        const int sy = r % R[1], c = r / R[1];
+        const double* py = P1 + (lo[1] + sy - o[1] * Ns) * n;
+        const double* t1 = T1 + (v * R[0] + sx) * NR + c * n;
+        double accb = 0.0;
+#pragma unroll
+        for (int bb = 0; bb < n; ++bb) accb += py[bb] * t1[bb];
+        T2[((v * R[0] + sx) * R[1] + sy) * n + c] = accb;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < NV * nbox; e += blockDim.x) {
+        const int v = e / nbox;
+        int r = e - v * nbox;
+        const int sx = r % R[0];
+        r /= R[0];
+        const int sy = r % R[1], sz = r / R[1];
+        const double* pz = P1 + (lo[2] + sz - o[2] * Ns) * n;
+        const double* t2 = T2 + ((v * R[0] + sx) * R[1] + sy) * n;
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c < n; ++c) acc += pz[c] * t2[c];
+        const int loc[3] = {lo[0] + sx, lo[1] + sy, lo[2] + sz};
+        dst[v * LD + patch_offset<D, L>(loc)] = acc;
+      }
+    }
   }
 }
+
 
 // 1D WENO3 on five consecutive subcell averages u[0..4] (target subcell u[2]):
 // values of the reconstruction at the 3 GL nodes of the target subcell.

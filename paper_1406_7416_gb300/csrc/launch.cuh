@@ -109,7 +109,7 @@ struct Launch {
     const Batch lim{sl.pps, sl.n, sl.pre_lim};
     const long long ch = sl.sum_chunk;    // upper bound of the troubled cells of one pass
     if ((e = launch_lim_prefix(sl, pass, s)) != cudaSuccess) return e;
-    k_lim_patch<D, N><<<grid_for(ch * DM::LD, 256), 256, 0, s>>>(lim, pass);
+    k_lim_patch<D, N><<<grid_for(ch * ipow(3, D), 1, kNumSM * 16), 128, 0, s>>>(lim, pass);
     const long long ncross = ch * (DM::NSD + 2 * D * DM::NSF);
     const int gs = grid_for(ch * NV * DM::LD, 256), gp = grid_for(ncross, SPB, kNumSM * 16);
     // the subcell predictor stored in FP32 when it runs wholly in FP32
