@@ -242,8 +242,8 @@ int adg_step_cfl(adg_state* st, double cfl, double dt_max);
  * the last load (either may be NULL); synchronizes. */
 int adg_time(adg_state* st, double* t, int64_t* steps);
 
-/* Batched stepping of many independent states (spec batching; no
- * counterpart in the paper, which steps one grid): states of the same
+/* Batched stepping of many independent states (no counterpart in the
+ * paper, which steps one grid): states of the same
  * dimension, degree and precision share every kernel launch, each launch
  * covering all their cells, faces or troubled cells.  All states must be
  * loaded; their streams are set to the batch's stream (`stream`, or a stream
