@@ -1,0 +1,179 @@
+"""Host logic of the continuous-batching server (serving.py), on the CPU:
+the device calls are replaced by a fake library whose states advance their
+simulated time by a fixed step per batched step, cut at their end time as
+the device step is, and the clock is simulated.  Checks admission by the
+memory budget, batch rebuilds on membership changes, retirement at the end
+time, retirement of stalled runs as failed, the no-admission wall limit and
+the statistics."""
+import types
+
+import numpy as np
+import pytest
+
+from paper_1406_7416_gb300 import serving
+
+pytestmark = pytest.mark.timeout(60)     # a broken retirement rule would loop forever
+
+
+class FakeSolver:
+    def __init__(self, w, prec):
+        self.w = w
+        self.t = 0.0
+        self.n = 0
+        self.t_end = 0.0
+        self.dt = w["fake_dt"]
+        self.closed = False
+
+    @classmethod
+    def from_workload(cls, w, prec):
+        return cls(w, prec)
+
+    def set_stream(self, s):
+        pass
+
+    def set_option(self, opt, value):
+        if opt == FAKE.OPT_END_TIME:
+            self.t_end = value
+
+    def init_problem(self, problem):
+        pass
+
+    def bytes_held(self):
+        return self.w["fake_bytes"]
+
+    def time(self):
+        return self.t, self.n
+
+    def status(self):
+        return 0
+
+    def read_full(self):
+        return (np.array([self.t]),)
+
+    def close(self):
+        self.closed = True
+
+
+class FakeBatch:
+    built = []
+
+    def __init__(self, solvers, stream=0):
+        self.solvers = list(solvers)
+        FakeBatch.built.append([id(s) for s in solvers])
+
+    def step(self, cfl=0.0):
+        for s in self.solvers:
+            assert not s.closed
+            if serving.reached_end(s.t, s.t_end) or not s.dt > 0.0:
+                continue                      # idle past the end, or no admissible dt
+            s.t = min(s.t + s.dt, s.t_end) if s.t + s.dt < s.t_end else s.t_end
+            s.n += 1
+
+    def close(self):
+        pass
+
+
+FAKE = types.SimpleNamespace(Solver=FakeSolver, Batch=FakeBatch, OPT_CFL=9, OPT_END_TIME=8,
+                             PREC_MIXED_FP32=1)
+
+
+class Clock:
+    """Simulated seconds: every call advances 1 ms."""
+
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        self.t += 1e-3
+        return self.t
+
+
+@pytest.fixture
+def fake_lib(monkeypatch):
+    monkeypatch.setattr(serving, "adg", FAKE)
+    monkeypatch.setattr(serving.time, "sleep", lambda s: None)
+    FakeBatch.built = []
+
+
+def _run(i, dt=0.01, nbytes=100, t_end=0.1, arrival=0.0, shape=None):
+    w = {"dim": 2, "N": 3, "ncell": shape or (8 + i, 8), "cfl": 0.1, "problem": None,
+         "fake_dt": dt, "fake_bytes": nbytes}
+    return serving.RunSpec(w, t_end, arrival, i)
+
+
+class Tracking(serving.Server):
+    """Records the resident memory at each admission."""
+
+    def __init__(self, *a, **k):
+        super().__init__(*a, **k)
+        self.peak = 0
+        self.resident = []
+
+    def _admit(self, r):
+        super()._admit(r)
+        self.resident = [x for x in self.resident if x.finished is None] + [r]
+        self.peak = max(self.peak, sum(x.bytes for x in self.resident))
+
+
+def test_budget_limits_resident_runs_of_one_shape(fake_lib):
+    """Once a run of a shape was admitted its size is known: at most two runs
+    of 100 bytes are resident under a 250-byte budget."""
+    runs = [_run(i, nbytes=100, shape=(16, 16)) for i in range(7)]
+    srv = Tracking(250, steps_per_poll=4)
+    st = srv.serve(runs, clock=Clock())
+    assert st["runs"] == 7 and st["failed"] == 0
+    assert srv.peak == 200
+
+
+def test_budget_limits_resident_runs_and_every_run_finishes(fake_lib):
+    """Shapes never seen before are admitted while the resident bytes are
+    within the budget, so the budget is exceeded by one run at most."""
+    runs = [_run(i, nbytes=100) for i in range(7)]
+    srv = Tracking(250, steps_per_poll=4)
+    st = srv.serve(runs, clock=Clock())
+    assert st["runs"] == 7 and st["failed"] == 0 and st["unserved"] == 0
+    assert 250 < srv.peak <= 250 + 100
+    for r in runs:
+        assert r.finished is not None and r.finished >= r.admitted >= r.arrival
+        assert r.steps == 10                      # t_end / dt steps, the last one cut
+        assert serving.reached_end(r.solver.t if r.solver else r.t_end, r.t_end)
+    assert st["steps"] == 70
+    assert st["stdof_updates"] == sum(r.stdofs_per_step * 10 for r in runs)
+
+
+def test_batch_rebuilt_only_when_membership_changes(fake_lib):
+    runs = [_run(0, dt=0.05), _run(1, dt=0.01)]
+    serving.Server(10 ** 9, steps_per_poll=1).serve(runs, clock=Clock())
+    # both admitted at t = 0 (one batch); run 0 ends after 2 steps (one rebuild to run 1 alone)
+    assert len(FakeBatch.built) == 2
+    assert len(FakeBatch.built[0]) == 2 and len(FakeBatch.built[1]) == 1
+
+
+def test_stalled_run_is_retired_as_failed(fake_lib):
+    runs = [_run(0), _run(1, dt=0.0), _run(2)]
+    st = serving.Server(10 ** 9, steps_per_poll=2).serve(runs, clock=Clock())
+    assert st["failed"] == 1 and st["failed_ids"] == [1] and st["runs"] == 2
+    assert runs[1].failed and runs[1].steps == 0
+    assert not runs[0].failed and not runs[2].failed
+
+
+def test_no_admission_after_the_wall_limit(fake_lib):
+    runs = [_run(0, arrival=0.0), _run(1, arrival=50.0)]
+    st = serving.Server(10 ** 9, steps_per_poll=1).serve(runs, clock=Clock(), max_wall=0.5)
+    assert st["runs"] == 1 and st["unserved"] == 1 and runs[1].finished is None
+
+
+def test_latency_statistics_and_end_test():
+    assert serving.reached_end(1.0, 1.0)
+    assert serving.reached_end(1.0 - 1e-13, 1.0)
+    assert not serving.reached_end(1.0 - 1e-9, 1.0)
+    a = serving.poisson_arrivals(20000, 4.0, seed=3)
+    assert np.all(np.diff(a) > 0)
+    assert abs(np.mean(np.diff(a)) - 0.25) < 0.01
+    np.testing.assert_array_equal(a, serving.poisson_arrivals(20000, 4.0, seed=3))
+
+
+def test_results_kept_on_request(fake_lib):
+    runs = [_run(0, t_end=0.05)]
+    serving.Server(10 ** 9, keep_results=True).serve(runs, clock=Clock())
+    assert runs[0].result[0][0] == pytest.approx(0.05)
