@@ -60,3 +60,36 @@ def test_create_and_destroy_without_device_work(lib):
     with pytest.raises(adg.AdgError):
         s.set_option(99, 1.0)
     s.close()
+
+
+@pytest.mark.parametrize("key,bad,good", [
+    (adg.OPT_DMP_EPS, -1e-3, 1e-3),
+    (adg.OPT_DMP_FLOOR, float("nan"), 1e-4),
+    (adg.OPT_PICARD_ITERS, 0, 6),
+    (adg.OPT_PICARD_ITERS, 65, 64),
+    (adg.OPT_FP64_SWEEPS, -1, 0),
+    (adg.OPT_FP64_SWEEPS, 65, 2),
+    (adg.OPT_SCRATCH_BYTES, 0, 2 ** 30),
+    (adg.OPT_SUBCELL_FP64_SWEEPS, 4, 3),
+    (adg.OPT_FLUX, 2, 1),
+    (adg.OPT_CFL, -0.1, 0.0),
+    (adg.OPT_SLOT_CAPACITY, 0, 16),
+    (adg.OPT_END_TIME, -1.0, 0.2),
+])
+def test_option_ranges_without_device_work(lib, key, bad, good):
+    """Out-of-range option values are refused with ADG_ERR_ARG and a message;
+    in-range values are taken (all before any device allocation)."""
+    h = ctypes.c_void_p()
+    g = adg.AdgGrid()
+    g.dim = 2
+    for k in range(3):
+        g.n[k] = 4
+        g.dx[k] = 0.25
+    bcs = (ctypes.c_int * 6)(0, 0, 0, 0, 0, 0)
+    assert lib.adg_create(ctypes.byref(g), 3, 1.4, bcs, adg.PREC_MIXED_FP32, ctypes.byref(h)) == 0
+    try:
+        assert lib.adg_set_option(h, key, float(bad)) == adg.ERR_ARG
+        assert lib.adg_last_error(h)
+        assert lib.adg_set_option(h, key, float(good)) == 0
+    finally:
+        lib.adg_destroy(h)
