@@ -215,11 +215,11 @@ def oracle_rate(steps, warmup, block=32, budget_s=20.0):
     return dofs * steps / el, el, steps
 
 
-def run_cpu_baseline(steps, warmup, block):
+def run_cpu_baseline(steps, warmup, block, budget_s=20.0):
     """Times the oracle in a child process pinned to one BLAS thread."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-rate",
-                        str(steps), str(warmup), str(block), WORKLOAD], env=env,
+                        str(steps), str(warmup), str(block), WORKLOAD, str(budget_s)], env=env,
                        capture_output=True, text=True, timeout=1800)
     if r.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -473,17 +473,19 @@ def run_reference(args):
     if rank != 0:
         return
     w = workload()
-    block = 32
-    rate, el, _ = oracle_rate(args.steps, args.warmup, block, budget_s=120.0)
+    block = 32 if w["dim"] == 2 else 6
+    cb = run_cpu_baseline(args.steps, args.warmup, block, budget_s=120.0)
+    rate = cb["value"]
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(w, {"sample": f"central {block}x{block} cells per step"}),
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{args.steps} oracle steps on the central {block}x{block} "
-                                       f"cells of the workload (numpy, default threads)"},
+            "config": config_dict(w, {"sample": f"central {block}^d cells per step"}),
+            "cpu_baseline": cb,
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if rate:
+        d = w["dim"]
+        line["ms_per_step"] = block ** d * (w["N"] + 1) ** (d + 1) / rate * 1e3
     print(json.dumps(line), flush=True)
 
 
@@ -492,7 +494,8 @@ def main():
         steps, warmup, block = (int(x) for x in sys.argv[2:5])
         if len(sys.argv) > 5:
             globals()["WORKLOAD"] = sys.argv[5]
-        print(json.dumps(list(oracle_rate(steps, warmup, block))))
+        budget = float(sys.argv[6]) if len(sys.argv) > 6 else 20.0
+        print(json.dumps(list(oracle_rate(steps, warmup, block, budget_s=budget))))
         return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
