@@ -329,28 +329,9 @@ __device__ __forceinline__ void apply_axis(const double* __restrict__ in, double
   }
 }
 
-// Tensor projection / reconstruction of all variables of one cell, in place
-// through two buffers (a, b).  `from` extent per axis -> `to` extent, matrix
-// M[to][from].  Result ends in the buffer returned.
-template <int D>
-__device__ __forceinline__ double* apply_all_axes(double* a, double* b, const double* M, int to,
-                                                  int from, int nv, int tid, int nth) {
-  int ext[3] = {from, from, from};
-  double* src = a;
-  double* dst = b;
-  for (int k = 0; k < D; ++k) {
-    apply_axis<D>(src, dst, M, to, from, k, ext, nv, tid, nth);
-    ext[k] = to;
-    __syncthreads();
-    double* t = src;
-    src = dst;
-    dst = t;
-  }
-  return src;
-}
-
-// Compile-time variant of apply_all_axes: NV variables, NI -> NO points per
-// axis, matrix M[NO][NI]; every index division is by a constant.
+// Tensor projection / reconstruction of all variables of one cell through two
+// buffers: NV variables, NI -> NO points per axis, matrix M[NO][NI]; every
+// index division is by a constant.
 template <int D, int NV, int NI, int NO, int K, typename T = double>
 __device__ __forceinline__ void apply_pass_ct(const T* __restrict__ in, T* __restrict__ out,
                                               const T* __restrict__ M, int tid, int nth) {
@@ -448,8 +429,9 @@ __host__ __device__ constexpr size_t predictor_smem_bytes() {
   size_t d = (size_t)DM::NV * DM::ND + (size_t)DM::NV * DM::NST + (size_t)D * DM::NV * DM::NST +
              (size_t)D * DM::NV * DM::ND + 3 * DM::n * DM::n + 3 * DM::n;
   // the FP32 sweep arrays qf, Ff live inside the FP64 flux array F (unused
-  // until the FP32 sweeps are over); only the FP32 operators and u stay apart
-  size_t f = MIXED ? (2 * DM::n * DM::n + (size_t)DM::NV * DM::ND + 2 * DM::n) : 0;
+  // until the FP32 sweeps are over); u and the trace weights in FP32 stay
+  // apart (the FP32 sweep operators are in constant memory)
+  size_t f = MIXED ? ((size_t)DM::NV * DM::ND + 2 * DM::n) : 0;
   return d * sizeof(double) + f * sizeof(float);
 }
 
@@ -472,9 +454,7 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
   // FP32 sweep arrays inside F: (1 + D) NV NST floats fit in D NV NST doubles
   float* qf = reinterpret_cast<float*>(F);
   float* Ff = qf + NV * NST;
-  float* Dmf = reinterpret_cast<float*>(ph1 + n);
-  float* Ktf = Dmf + n * n;
-  float* uf = Ktf + n * n;
+  float* uf = reinterpret_cast<float*>(ph1 + n);
   float* ph0f = uf + NV * ND;
   float* ph1f = ph0f + n;
 
@@ -484,10 +464,6 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
     Dm[i] = o->D[i];
     Kt[i] = o->Kt[i];
     Mv[i] = o->Mvol[i];
-    if (MIXED) {
-      Dmf[i] = o->Df[i];
-      Ktf[i] = o->Ktf[i];
-    }
   }
   for (int i = tid; i < n; i += nth) {
     w[i] = o->w[i];
@@ -662,9 +638,8 @@ __global__ void __launch_bounds__(PredShape<D, N, MIXED>::bound, PredShape<D, N,
 }
 
 // ---------------------------------------------------------------------------
-// K2 face flux: time-averaged Rusanov flux at every tangential node of every
-// face normal to axis k.  Transmissive boundary: the missing side copies the
-// interior trace (G = F(q^-)).
+// K2 face flux: the time-averaged numerical flux at every tangential node of
+// every face normal to axis k.
 // ---------------------------------------------------------------------------
 // Whether a state's predictor leaves its face traces split: per (cell, axis,
 // side) block of NV x NT doubles, trace(u) [NV][NF] in FP64 followed by
@@ -807,6 +782,9 @@ __device__ __forceinline__ void face_split_rusanov(const double* bL, const doubl
            0.5 * ((uR[v] - uL[v]) * (double)S + (double)sumJ[v]);
 }
 
+// One thread per (face, tangential node): the Rusanov (or Osher-type) flux at
+// each time node, weighted by the time rule.  At a domain boundary the missing
+// side is the ghost state of the face's kind (boundary_ghost).
 template <int D, int N>
 __global__ void __launch_bounds__(256, 2) k_faceflux(Batch bt, int k) {
   using DM = Dims<D, N>;
