@@ -313,10 +313,12 @@ int adg_sizes(const adg_state* st, int64_t* cells, int* nvar, int* nodes, int* s
 
 /* Launch layout after the first load: out[0] = subcell slot capacity,
  * out[1] = troubled cells per limiter chunk, out[2] = kernels launched by one
- * adg_step at most (every limiter pass the capacity allows), out[3] = device
- * bytes held by the state, and with cap >= 5, out[4] = kernels issued by this
- * state's steps so far (batched steps count on the first state of each group
- * of one dimension, degree and precision); with cap >= 7, out[5] = Picard
+ * adg_step at most (every limiter pass the capacity allows, in the state's
+ * launch mode), out[3] = device bytes held by the state, and with cap >= 5,
+ * out[4] = kernels issued by this state's steps so far, the passes of the
+ * device-sized loops counted on the device (batched steps count on the first
+ * state of each group of one dimension, degree and precision; synchronizes
+ * the state's stream); with cap >= 7, out[5] = Picard
  * sweeps of the predictor, out[6] = how many of them run in FP64.  Needs
  * cap >= 4. */
 int adg_info(const adg_state* st, int64_t* out, int cap);
