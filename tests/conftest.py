@@ -11,3 +11,5 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the built libadg.so")
     config.addinivalue_line("markers", "slow: long-running CPU check")
+    # used by pytest-timeout where installed; registered here so that it is known without it
+    config.addinivalue_line("markers", "timeout(seconds): limit on a test's run time")
