@@ -17,12 +17,30 @@ namespace adg {
 namespace {
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;    // 32 MiB
-// control block: counters at 0, dt / clock at 64, the state pointer at 128,
-// the item prefix at 192; then the Params, the operator table and the buffers
-constexpr size_t CTRL_BYTES = 256;
+// Control block, each region in its own 128-byte slot:
+//   [0, 64)     counters (CNT_COUNT ints)
+//   [64, 192)   dt[0], lamred dt[1], clock dt[2..4], dt / dx_k at dt[6..8],
+//               dt Ns / dx_k at dt[9..11] (12 doubles)
+//   [192, 256)  the one-state pointer array of the batch descriptor
+//   [256, 320)  the item prefix pre[0..1]
+// then the Params, the operator table and the buffers.
+constexpr size_t CTRL_COUNTERS = 0, CTRL_DT = 64, CTRL_PPS = 192, CTRL_PRE = 256;
+constexpr size_t CTRL_BYTES = 512;
+constexpr int CTRL_DT_WORDS = 12;
+static_assert(CNT_COUNT * sizeof(int) <= CTRL_DT - CTRL_COUNTERS, "counters overlap dt");
+static_assert(CTRL_DT + CTRL_DT_WORDS * sizeof(double) <= CTRL_PPS, "dt words overlap pps");
+static_assert(CTRL_PPS + sizeof(Params*) <= CTRL_PRE, "pps overlaps pre");
+static_assert(CTRL_PRE + 2 * sizeof(long long) <= CTRL_BYTES, "pre overlaps the Params");
 constexpr size_t PARAMS_BYTES = (sizeof(Params) + 255) / 256 * 256;
 constexpr size_t OPS_BYTES = (sizeof(Ops) + 255) / 256 * 256 + PARAMS_BYTES;
 constexpr int MAX_DEVICES = 64;
+
+// The Params and the operator table of one call, laid out as in the static
+// area (Params at CTRL_BYTES, Ops PARAMS_BYTES after it), so that one copy
+// uploads both.
+struct alignas(256) Upload {
+  unsigned char bytes[PARAMS_BYTES + sizeof(Ops)];
+};
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
@@ -186,16 +204,11 @@ int run_noalloc(unsigned char* base, double gamma, const double* h, double dt, c
                (NOALLOC_SCRATCH_BYTES - CTRL_BYTES - OPS_BYTES) / NA::per_cell_bytes(), D, N);
     return ADG_ERR_CAPACITY;
   }
-  Ops ops_host;
+  Upload up;
+  Ops& ops_host = *reinterpret_cast<Ops*>(up.bytes + PARAMS_BYTES);
   build_ops(N, &ops_host);
   Params* params_dev = reinterpret_cast<Params*>(base + CTRL_BYTES);
   Ops* ops_dev = reinterpret_cast<Ops*>(base + CTRL_BYTES + PARAMS_BYTES);
-  cudaError_t e = cudaMemcpyAsync(ops_dev, &ops_host, sizeof(Ops), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // ops_host lives on this stack frame
-  if (e != cudaSuccess) {
-    if (err && errlen) snprintf(err, errlen, "operator upload failed: %s", cudaGetErrorString(e));
-    return ADG_ERR_CUDA;
-  }
   Params p;
   memset(&p, 0, sizeof(Params));
   p.geo.dim = D;
@@ -214,18 +227,24 @@ int run_noalloc(unsigned char* base, double gamma, const double* h, double dt, c
   p.gamma = gamma;
   p.ops = ops_dev;
   p.cur = 0;
-  p.b.counters = reinterpret_cast<int*>(base);
-  p.b.dt = reinterpret_cast<double*>(base + 64);
+  p.b.counters = reinterpret_cast<int*>(base + CTRL_COUNTERS);
+  p.b.dt = reinterpret_cast<double*>(base + CTRL_DT);
   p.b.lamred = p.b.dt + 1;
   p.b.clock = p.b.dt + 2;
   p.b.coef = p.b.dt + 6;
   p.b.patch = const_cast<double*>(patches);
   NA::carve(base, count, p);
-  e = cudaMemcpyAsync(params_dev, &p, sizeof(Params), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // p lives on this stack frame
-  if (e == cudaSuccess)
-    e = NA::run(p, params_dev, reinterpret_cast<Params**>(base + 128),
-                reinterpret_cast<long long*>(base + 192), count, dt, vnew, faces, s);
+  memcpy(up.bytes, &p, sizeof(Params));
+  // one upload of the Params and the operator table, then one wait: `up`
+  // lives on this stack frame
+  cudaError_t e = cudaMemcpyAsync(params_dev, up.bytes, sizeof(up.bytes), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    if (err && errlen) snprintf(err, errlen, "parameter upload failed: %s", cudaGetErrorString(e));
+    return ADG_ERR_CUDA;
+  }
+  e = NA::run(p, params_dev, reinterpret_cast<Params**>(base + CTRL_PPS),
+              reinterpret_cast<long long*>(base + CTRL_PRE), count, dt, vnew, faces, s);
   if (e != cudaSuccess) {
     if (err && errlen) snprintf(err, errlen, "kernel launch failed: %s", cudaGetErrorString(e));
     return ADG_ERR_CUDA;

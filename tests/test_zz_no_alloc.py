@@ -115,3 +115,54 @@ def test_noalloc_rejects_counts_beyond_its_static_scratch():
     assert "static" in msg and "at most" in msg
     rc, msg = adg.subcell_update_noalloc(4, 5, GAMMA, [0.01, 0.01], 1e-4, 1, 1, 1)
     assert rc == adg.ERR_ARG and "dim" in msg
+
+
+def _advertised_limit(dim, N):
+    """The largest count the static scratch takes, as the capacity error states it."""
+    h = [0.01] * dim
+    rc, msg = adg.subcell_update_noalloc(dim, N, GAMMA, h, 1e-4, 1, 10 ** 7, 1)
+    assert rc == adg.ERR_CAPACITY
+    return int(msg.split("at most ")[1].split()[0])
+
+
+def test_noalloc_at_its_largest_count_without_faces():
+    """The largest advertised count (2D, N = 5) runs and equals adg_step on a
+    one-row periodic grid of that many cells, with the faces output left out
+    (NULL); one patch more is refused with ADG_ERR_CAPACITY."""
+    import torch
+
+    dim, N = 2, 5
+    Ns = 2 * N + 1
+    M = _advertised_limit(dim, N)
+    assert M >= 16
+    ncell = (M, 1)
+    V = _random_subcells(dim, N, ncell, seed=11)
+    dx = (0.1, 0.1)
+    h = [d / Ns for d in dx]
+    dt = 0.05 * min(h)
+    s = adg.Solver(dim, ncell, (0.0, 0.0), dx, (0, 0, 0, 0), N, GAMMA)
+    s.set_option(adg.OPT_FORCE_LIMITER, 1)
+    nv = dim + 2
+    dofs = np.zeros((M, nv, (N + 1) ** dim))
+    dofs[:, 0] = 1.0
+    dofs[:, -1] = 2.5
+    s.load_full(dofs, np.ones(M, dtype=np.uint8), to_abi(V, dim))
+    s.step(dt)
+    _, beta, sub_ref = s.read_full()
+    assert beta.all()
+    s.close()
+    patches = torch.from_numpy(_patches(V, dim, N)).cuda()
+    vnew = torch.full((M, nv, Ns ** dim), float("nan"), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    rc, msg = adg.subcell_update_noalloc(dim, N, GAMMA, h, dt, patches.data_ptr(), M,
+                                         vnew.data_ptr(), 0, stream)
+    assert rc == adg.OK, msg
+    torch.cuda.synchronize()
+    got = vnew.cpu().numpy()
+    scale = np.abs(sub_ref).max(axis=(0, 2))[None, :, None]
+    assert float(np.max(np.abs(got - sub_ref) / scale)) <= RTOL
+    extra = torch.zeros((M + 1, nv, (Ns + 6) ** dim), dtype=torch.float64, device="cuda")
+    out = torch.zeros((M + 1, nv, Ns ** dim), dtype=torch.float64, device="cuda")
+    rc, msg = adg.subcell_update_noalloc(dim, N, GAMMA, h, dt, extra.data_ptr(), M + 1,
+                                         out.data_ptr(), 0, stream)
+    assert rc == adg.ERR_CAPACITY and f"at most {M} " in msg
