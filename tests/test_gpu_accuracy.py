@@ -1,0 +1,150 @@
+"""GPU: the accuracy bar of the mixed-precision path, per workload shape.
+
+The bar: after the same steps (the FP64 path's CFL steps, replayed with the
+same dt in mixed precision), the relative L1 distance between the mixed and
+the FP64 solution, per conserved variable,
+    d_v = sum |U_mixed - U_fp64| W / sum |U_fp64| W    (GL weights, all DOFs),
+is at most 1% of the FP64 scheme's own relative L1 error over the same
+steps.  That error is estimated from r_v, the distance of the FP64 solution to
+the FP64 solution on the grid refined by 2 in every axis (half the step, twice
+the steps; the coarse DG polynomials are evaluated at the fine cells' nodes
+and compared there), by Richardson's rule e_v = r_v / (1 - 2^-p) with the
+convergence order p = 1 of these discontinuous problems (their L1 error is
+that of the captured discontinuities): e_v = 2 r_v, and the bar is
+d_v <= 0.02 r_v.  The FP64 path equals the oracle to 1e-12
+(test_gpu_parity.py); the last test compares the mixed path with the oracle
+itself.
+
+Flag flips at cells whose detector margin is within rounding of a threshold
+are part of the distance: a flipped cell takes the other of two admissible
+updates, whose difference is of the order of the local scheme error, and the
+flips spread to neighbours over later steps.  They dominate d_v at N = 5 and
+N = 9 after about ten steps; the bar holds with them.
+
+The workloads are the benchmark configurations at reduced size (the same
+seeded data, boundary kinds, degree and CFL number)."""
+import numpy as np
+import pytest
+
+from paper_1406_7416_gb300 import adg, build_lib, inputs
+
+from refine import coarse_on_fine, rel_l1, weights
+
+pytestmark = pytest.mark.gpu
+BAR = 0.01
+ORDER = 1          # L1 convergence order of the discontinuous workloads
+RICHARDSON = 1.0 / (1.0 - 2.0 ** -ORDER)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build_lib.build()
+    adg.load_library()
+
+
+def _run(w, prec, steps=None, dts=None, substeps=1, opts=None):
+    s = adg.Solver.from_workload(w, prec)
+    for k, v in (opts or {}).items():
+        s.set_option(k, v)
+    s.init_problem(w["problem"])
+    out, t_prev = [], 0.0
+    if dts is None:
+        for _ in range(steps):
+            s.step_cfl(w["cfl"])
+            t, _ = s.time()
+            out.append(t - t_prev)
+            t_prev = t
+    else:
+        for dt in dts:
+            for _ in range(substeps):
+                s.step(dt / substeps)
+    U = s.read()
+    assert s.status() == adg.OK
+    info = s.info()
+    s.close()
+    return U, out, info
+
+
+def _refined(w):
+    f = dict(w)
+    f["ncell"] = tuple(2 * c for c in w["ncell"])
+    f["dx"] = tuple(0.5 * d for d in w["dx"])
+    fac = w["problem"].get("cell_rho_factor")
+    if fac is not None:
+        f["problem"] = dict(w["problem"])
+        f["problem"]["cell_rho_factor"] = np.repeat(np.repeat(np.repeat(fac, 2, 0), 2, 1), 2, 2)
+    return f
+
+
+def mixed_bar(w, steps, opts=None):
+    """(d, e, info of the mixed run): mixed-vs-FP64 distance and the FP64
+    scheme error (Richardson estimate from the refined run), per variable."""
+    U64, dts, _ = _run(w, adg.PREC_FP64, steps=steps)
+    Umx, _, info = _run(w, adg.PREC_MIXED_FP32, dts=dts, opts=opts)
+    Uf, _, _ = _run(_refined(w), adg.PREC_FP64, dts=dts, substeps=2)
+    dim, N = w["dim"], w["N"]
+    Wd = weights(dim, N + 1)
+    d = rel_l1(Umx, U64, Wd)
+    e = RICHARDSON * rel_l1(coarse_on_fine(U64, w["ncell"], N, dim), Uf, Wd)
+    return d, e, info, dts, Umx
+
+
+CASES = {
+    # config 2 shape: quadrants + vortex, N = 5, periodic
+    "quadvortex_N5_64": (lambda: inputs.quadrants_vortex_2d(n=64, N=5, steps=None), 20),
+    # config 4 shape: quadrants, N = 9, periodic (one FP64 sweep by default)
+    "quadrants_N9_48": (lambda: inputs.quadrants_2d(n=48, N=9), 20),
+    # config 1: the 2D explosion itself (32^2, N = 3, 20 steps, transmissive)
+    "explosion2d_N3_32": (lambda: inputs.explosion_2d(n=32, N=3), 20),
+    # config 3 shape: 3D explosion, N = 3, transmissive, 1% density noise
+    "explosion3d_N3_16": (lambda: inputs.explosion_3d(n=16, N=3), 10),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_mixed_within_one_percent_of_the_scheme_error(name):
+    make, steps = CASES[name]
+    d, e, info, _, _ = mixed_bar(make(), steps)
+    print(f"{name}: predictor shape {info['predictor']}, FP64 sweeps {info['fp64_sweeps']}; "
+          f"d = {np.array2string(d, precision=2)}, e = {np.array2string(e, precision=2)}, "
+          f"d/e = {np.array2string(d / e, precision=3)}")
+    assert np.all(np.isfinite(d)) and np.all(e > 0)
+    assert np.all(d <= BAR * e), (d, e, d / e)
+
+
+@pytest.mark.parametrize("shape", [adg.PRED_BLOCK, adg.PRED_WARP2, adg.PRED_WARP4_TC])
+def test_mixed_bar_holds_for_every_predictor_shape(shape):
+    """The bar of the N = 5 benchmark shape with each predictor shape fixed."""
+    make, steps = CASES["quadvortex_N5_64"]
+    d, e, info, _, _ = mixed_bar(make(), steps, opts={adg.OPT_PREDICTOR: shape})
+    assert info["predictor"] == shape
+    assert np.all(d <= BAR * e), (shape, d, e)
+
+
+def test_mixed_against_the_oracle():
+    """The mixed path against the FP64 oracle directly (quadrants + vortex,
+    N = 5, 12^2 cells, 4 steps of the oracle's CFL dt): its distance to the
+    oracle is its distance to the FP64 path up to the 1e-12 parity of the
+    latter, and within 1% of the scheme error of the FP64 path on the same
+    grid and steps."""
+    from oracle.step import stable_dt, step
+    from helpers import oracle_setup, to_abi
+
+    w = inputs.quadrants_vortex_2d(n=12, N=5, steps=None)
+    sch, st, _, _ = oracle_setup(w)
+    dts = []
+    for _ in range(4):
+        dt = stable_dt(sch, st, w["cfl"])
+        st, _ = step(sch, st, dt)
+        dts.append(dt)
+    Uor = to_abi(st.U, 2)
+    U64, _, _ = _run(w, adg.PREC_FP64, dts=dts)
+    Umx, _, _ = _run(w, adg.PREC_MIXED_FP32, dts=dts)
+    Uf, _, _ = _run(_refined(w), adg.PREC_FP64, dts=dts, substeps=2)
+    Wd = weights(2, 6)
+    d_or = rel_l1(Umx, Uor, Wd)
+    d_64 = rel_l1(Umx, U64, Wd)
+    e = RICHARDSON * rel_l1(coarse_on_fine(U64, w["ncell"], 5, 2), Uf, Wd)
+    assert np.all(rel_l1(U64, Uor, Wd) <= 1e-12)
+    np.testing.assert_allclose(d_or, d_64, rtol=1e-3, atol=1e-13)
+    assert np.all(d_or <= BAR * e), (d_or, e)

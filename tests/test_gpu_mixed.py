@@ -1,5 +1,8 @@
-"""GPU: mixed precision (FP32 Picard sweeps + final FP64 sweep) against the FP64
-path, design order on the smooth vortex, and the paper's vortex error table.
+"""GPU: mixed precision (FP32 Picard sweeps; for N <= 5 the last FP32 sweep's
+space-time correction is added to the FP64 DOFs in the final stage, for N >= 6
+one FP64 sweep follows; FP32 subcell scheme with an FP64 update) against the
+FP64 path, design order on the smooth vortex, and the paper's vortex error
+table.
 
 Mixed-precision budget: after the same steps, the L1 density distance between
 the mixed and the FP64 path is at most 1% of the FP64 path's own L1 density
