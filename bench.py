@@ -9,8 +9,12 @@ of troubled cells, reconstruction and neighbour flux correction.
 
 Metric: space-time DOF updates per second = cells * (N+1)^(d+1) * steps / s
 (per conserved variable, as the paper counts).  `value` is the mixed-precision
-path (FP32 Picard sweeps + one FP64 sweep); the FP64 path is reported beside
-it, with the L1 distance between the two after the same steps.
+path: FP32 Picard sweeps; for N <= 5 no FP64 sweep follows and the final stage
+adds the FP32 space-time correction to the FP64 DOFs term by term, for N >= 6
+one FP64 sweep follows; FP32 subcell scheme with an FP64 update; FP64
+corrector, detector comparisons, projections and flux correction.  The FP64
+path is reported beside it, with the L1 distance between the two after the
+same steps against the stated tolerance of the workload.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU: one independent replica per rank (weak scaling), launched by torchrun.
@@ -234,8 +238,119 @@ def run_cpu_baseline(steps, warmup, block, budget_s=20.0):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def run_gpu(args):
+# Stated accuracy bar of the mixed-precision path per workload: the relative
+# L1 distance to the FP64 path after the run's steps, per conserved variable,
+# may be at most TOL.  Each TOL is at most 1% of the FP64 scheme's own
+# relative L1 error on that workload over the steps the bench runs (3 + 20 for
+# the default workload, 3 + 5 for the others): the error is estimated from
+# the distance r to the FP64 solution on the grid refined by 2 by Richardson's
+# rule with the first-order L1 convergence of discontinuous data, 2 r, so TOL
+# <= 0.02 r, taken over the variables and rounded down (measured on one
+# GB300: quadrants + vortex 512^2 N = 5, 23 steps, 0.02 r >= 8.5e-6; 2D
+# quadrants 200^2 N = 9, 8 steps, >= 7.0e-6; 3D explosion 64^3 N = 3, 8 steps,
+# >= 5.4e-5, finer grids halving it; 2D explosion 32^2 N = 3, 20 steps,
+# >= 1.6e-4).
+TOL = {"quadvortex512": 8e-6, "explosion2d": 1e-5, "explosion3d": 1e-5, "quadrants200": 7e-6,
+       "dmr": None}
+
+
+def measure(args, wname, grid, steps, warmup, stream, rep, clocks=False, keep=False,
+            floor_run=False):
+    """FP64 and mixed runs of one workload: timed CFL steps, phases, the
+    mixed-vs-FP64 distance against the stated bar, troubled counts per step."""
     import numpy as np
+    import torch
+    from paper_1406_7416_gb300 import adg
+    globals()["WORKLOAD"] = wname
+    globals()["GRID_SET"] = grid
+    w = workload()
+    D, N = w["dim"], w["N"]
+    n = N + 1
+    cells = int(np.prod(w["ncell"]))
+    stdofs = cells * n ** (D + 1)
+    rank = rep.rank
+
+    def make(prec, opts=None):
+        s = adg.Solver.from_workload(w, prec)
+        s.set_stream(stream.cuda_stream)
+        if args.host_passes:
+            s.set_option(adg.OPT_HOST_PASSES, 1)
+        for k, v in (opts or {}).items():
+            s.set_option(k, v)
+        s.init_problem(w["problem"])
+        return s
+
+    results = {}
+    precs = [("fp64", adg.PREC_FP64), ("mixed", adg.PREC_MIXED_FP32)]
+    if args.only != "both":
+        precs = [p for p in precs if p[0] == args.only]
+    mixed_opts = {adg.OPT_PREDICTOR: args.predictor} if args.predictor is not None else {}
+    for name, prec in precs:
+        s = make(prec, mixed_opts if name == "mixed" else None)
+        s.set_option(adg.OPT_PROFILE, 1)
+        for _ in range(warmup):
+            s.step_cfl(w["cfl"])
+        s.phase_times()                             # discard warm-up phases
+        torch.cuda.synchronize()
+        rep.barrier()
+        clk = clocks_sampler() if (clocks and name == "mixed" and rank == 0) else None
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = s.info()["launches"]
+        e0.record(stream)
+        for _ in range(steps):
+            s.step_cfl(w["cfl"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        launches = s.info()["launches"] - l0
+        rep.barrier()
+        ms = e0.elapsed_time(e1) / steps
+        r = dict(ms=rep.max_over_ranks(ms), solver=s, status=s.status(),
+                 troubled=s.troubled_count(), info=s.info(), launches=launches,
+                 clocks=clocks_summary(clk, 0) if clk is not None else None,
+                 history=s.troubled_history(warmup + steps).tolist(), time=s.time()[0])
+        phases, nsteps = s.phase_times()
+        r["phases"] = {k: v / max(nsteps, 1) for k, v in phases.items()}
+        results[name] = r
+    out = dict(w=w, D=D, N=N, n=n, cells=cells, stdofs=stdofs, results=results)
+    if args.only == "both":
+        Wd = 0.5 * np.polynomial.legendre.leggauss(n)[1]
+        W1 = Wd
+        for _ in range(D - 1):
+            Wd = np.outer(W1, Wd).ravel()
+        U64 = results["fp64"]["solver"].read()
+        Umx = results["mixed"]["solver"].read()
+        num = np.einsum("cvl,l->v", np.abs(Umx - U64), Wd)
+        den = np.einsum("cvl,l->v", np.abs(U64), Wd)
+        d = (num / den).tolist()
+        tol = TOL.get(wname)
+        out["mixed_vs_fp64"] = {
+            "l1_rel_per_variable": d, "l1_density_rel": d[0], "steps": warmup + steps,
+            "tolerance_rel": tol, "pass": (max(d) <= tol) if tol else None,
+            "bar": "relative L1 distance to the FP64 path per conserved variable after the same "
+                   "number of CFL steps <= tolerance_rel, which is 1% of the FP64 scheme's own "
+                   "relative L1 error on this workload (error against the 2x refined solution)",
+            "final_time": {"fp64": results["fp64"]["time"], "mixed": results["mixed"]["time"]}}
+    if floor_run:
+        # the literal Eq. (relax) (no floor on the DMP relaxation) against the
+        # default floor, same workload and steps, mixed precision (untimed)
+        s = make(adg.PREC_MIXED_FP32, {**mixed_opts, adg.OPT_DMP_FLOOR: 0.0})
+        for _ in range(warmup + steps):
+            s.step_cfl(w["cfl"])
+        h0 = s.troubled_history(warmup + steps).tolist()
+        s.close()
+        h4 = results["mixed"]["history"] if "mixed" in results else None
+        out["dmp_floor"] = {"troubled_per_step_floor_1e-4": h4, "troubled_per_step_floor_0": h0,
+                            "mean_floor_1e-4": float(np.mean(h4)) if h4 else None,
+                            "mean_floor_0": float(np.mean(h0))}
+    if not keep:
+        for r in results.values():
+            r["solver"].close()
+            r["solver"] = None
+    return out
+
+
+def run_gpu(args):
     import torch
     from paper_1406_7416_gb300 import adg, build_lib
     from paper_1406_7416_gb300.replicas import Replicas
@@ -248,90 +363,53 @@ def run_gpu(args):
         build_lib.build()
     rep.barrier()
     adg.load_library()
-    w = workload()
-    D, N = w["dim"], w["N"]
-    n = N + 1
-    cells = int(np.prod(w["ncell"]))
-    stdofs = cells * n ** (D + 1)
     stream = torch.cuda.Stream()
-
-    def make(prec):
-        s = adg.Solver.from_workload(w, prec)
-        s.set_stream(stream.cuda_stream)
-        if args.host_passes:
-            s.set_option(adg.OPT_HOST_PASSES, 1)
-        s.init_problem(w["problem"])
-        return s
-
-    barrier = rep.barrier
-    max_over_ranks = rep.max_over_ranks
-
-    results = {}
-    cfl = w["cfl"]
-    precs = [("fp64", adg.PREC_FP64), ("mixed", adg.PREC_MIXED_FP32)]
-    if args.only != "both":
-        precs = [p for p in precs if p[0] == args.only]
-    for name, prec in precs:
-        s = make(prec)
-        s.set_option(adg.OPT_PROFILE, 1)
-        for _ in range(args.warmup):
-            s.step_cfl(cfl)
-        s.phase_times()                             # discard warm-up phases
-        torch.cuda.synchronize()
-        barrier()
-        clk = clocks_sampler() if (name == "mixed" and rank == 0) else None
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        l0 = s.info()["launches"]
-        e0.record(stream)
-        for _ in range(args.steps):
-            s.step_cfl(cfl)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        launches = s.info()["launches"] - l0
-        barrier()
-        ms = e0.elapsed_time(e1) / args.steps
-        clocks = clocks_summary(clk, local) if clk is not None else None
-        phases, nsteps = s.phase_times()
-        status = s.status()
-        troubled = s.troubled_count()
-        info = s.info()
-        results[name] = dict(ms=max_over_ranks(ms), solver=s, phases={k: v / nsteps for k, v in phases.items()},
-                             status=status, troubled=troubled, info=info, clocks=clocks,
-                             launches=launches)
+    main_wl, main_grid = WORKLOAD, GRID_SET
+    m = measure(args, main_wl, main_grid, args.steps, args.warmup, stream, rep, clocks=True,
+                keep=True, floor_run=(args.only == "both" and not args.no_extras))
+    w, results = m["w"], m["results"]
     if args.only != "both":
         # profiling run of one precision: timings only
         if rank == 0:
             r = results[args.only]
             print(json.dumps({"profile_run": args.only, "ms_per_step": r["ms"],
                               "phases_ms": r["phases"], "troubled_cells": r["troubled"],
+                              "predictor_shape": r["info"]["predictor"],
                               "config": config_dict(w, {"launch": launch_mode(args)})}), flush=True)
         for r in results.values():
             r["solver"].close()
         rep.close()
         return
-    # L1 distance of the density, mixed vs FP64, after warmup + steps equal steps
-    W = 0.5 * np.polynomial.legendre.leggauss(n)[1]
-    Wd = W
-    for _ in range(D - 1):
-        Wd = np.outer(W, Wd).ravel()
-    rho64 = results["fp64"]["solver"].read()[:, 0, :]
-    rhomx = results["mixed"]["solver"].read()[:, 0, :]
-    area = float(np.prod(w["dx"]))
-    l1 = float(np.sum(np.abs(rhomx - rho64) @ Wd) * area)
-    l1ref = float(np.sum(np.abs(rho64) @ Wd) * area)
-
     # end-to-end through the C ABI with host buffers (rank-local)
     e2e = None
     s = results["mixed"]["solver"]
-    if args.no_e2e:
-        s = None
-    if s is not None:
-        e2e = end_to_end(s, args, stdofs, world, cfl, barrier, max_over_ranks)
-    if rank == 0:
-        emit_line(args, w, results, stdofs, world, cells, cfl, l1, l1ref, e2e, D, N, n)
+    tune = None
+    if not args.no_e2e:
+        e2e = end_to_end(s, args, m["stdofs"], world, w["cfl"], rep.barrier, rep.max_over_ranks)
+    tune = s.autotune(3)
     for r in results.values():
         r["solver"].close()
+    # the other configurations (mixed and FP64, 3 warm-up + 5 steps each), on
+    # the default workload only
+    subs = {}
+    if main_wl == "quadvortex512" and main_grid is None and not args.no_extras:
+        for wl in ("explosion2d", "quadrants200", "explosion3d"):
+            sm = measure(args, wl, None, 5, 3, stream, rep)
+            mx, f64 = sm["results"]["mixed"], sm["results"]["fp64"]
+            subs[wl] = {"workload": sm["w"]["name"], "cells": sm["cells"],
+                        "mixed": {"value": sm["stdofs"] * world / (mx["ms"] / 1e3),
+                                  "ms_per_step": mx["ms"], "phases_ms": mx["phases"],
+                                  "predictor_shape": adg.PRED_NAMES[mx["info"]["predictor"]],
+                                  "fp64_sweeps": mx["info"]["fp64_sweeps"]},
+                        "fp64": {"value": sm["stdofs"] * world / (f64["ms"] / 1e3),
+                                 "ms_per_step": f64["ms"]},
+                        "mixed_vs_fp64": sm["mixed_vs_fp64"],
+                        "troubled_per_step": mx["history"],
+                        "troubled_fraction_per_step": [c / sm["cells"] for c in mx["history"]],
+                        "status": mx["status"], "steps": 5, "warmup": 3}
+    globals()["WORKLOAD"], globals()["GRID_SET"] = main_wl, main_grid
+    if rank == 0:
+        emit_line(args, m, e2e, world, tune, subs)
     rep.close()
 
 
@@ -369,7 +447,10 @@ def end_to_end(s, args, stdofs, world, cfl, barrier, max_over_ranks):
                      "pinned host, then adg_read of the DOFs"}
 
 
-def emit_line(args, w, results, stdofs, world, cells, cfl, l1, l1ref, e2e, D, N, n):
+def emit_line(args, m, e2e, world, tune, subs):
+    from paper_1406_7416_gb300 import adg
+    w, results = m["w"], m["results"]
+    D, N, n, cells, stdofs = m["D"], m["N"], m["n"], m["cells"], m["stdofs"]
     mx, f64 = results["mixed"], results["fp64"]
     value = stdofs * world / (mx["ms"] / 1e3)
     iters = int(mx["info"]["picard_iters"])
@@ -385,6 +466,7 @@ def emit_line(args, w, results, stdofs, world, cells, cfl, l1, l1ref, e2e, D, N,
     fl64f, _ = predictor_flops(D, N, iters, iters)
     achieved_f64 = fl64f * cells / (f64["phases"]["predictor"] / 1e3) / 1e12
     traffic = traffic_record() if (WORKLOAD == "quadvortex512" and GRID == 512) else None
+    shape = adg.PRED_NAMES[mx["info"]["predictor"]]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mx["ms"],
@@ -397,33 +479,44 @@ def emit_line(args, w, results, stdofs, world, cells, cfl, l1, l1ref, e2e, D, N,
                                                 "sub-face fluxes, FP64 update"
                                                 % (int(mx["info"]["fp64_sweeps"]),
                                                    int(mx["info"]["picard_iters"]))),
+                                  "predictor_shape": shape,
+                                  "first_order_layer": "on: the extra MOOD layer of Sec. 6 "
+                                                       "(ADG_OPT_CASCADE = 1) recomputes troubled "
+                                                       "cells whose WENO3 result fails PAD",
                                   "launch": launch_mode(args),
                                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                                  "time_step": f"CFL {cfl:.6g} of Eq. (cfl), dt from the "
+                                  "time_step": f"CFL {w['cfl']:.6g} of Eq. (cfl), dt from the "
                                                "current subcell data every step"}),
         "fp64": {"value": stdofs * world / (f64["ms"] / 1e3), "ms_per_step": f64["ms"],
                  "dtype": "f64", "phases_ms": f64["phases"],
+                 "predictor_shape": adg.PRED_NAMES[f64["info"]["predictor"]],
                  "roofline": {"bound": "alu", "achieved": achieved_f64,
                               "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                               "frac": achieved_f64 / FP64_PEAK_TFLOPS}},
-        "mixed_vs_fp64": {"l1_density": l1, "l1_density_rel": l1 / l1ref,
-                          "steps": args.warmup + args.steps},
+        "mixed_vs_fp64": m["mixed_vs_fp64"],
         "phases_ms": mx["phases"],
         "troubled_cells": mx["troubled"], "status": mx["status"],
+        "troubled_per_step": mx["history"],
+        "troubled_fraction_per_step": [c / cells for c in mx["history"]],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "pipe": pipe,
-                     "kernel": "k_predictor; bound by the %s pipe: its algorithmic flops take "
-                               "the longer time at the derived peaks (FP64 %.3f, FP32 %.1f "
+                     "kernel": "predictor (%s shape); bound by the %s pipe: its algorithmic flops "
+                               "take the longer time at the derived peaks (FP64 %.3f, FP32 %.1f "
                                "TFLOP/s: 2 and 128 FMA per clock per SM at 2.07 GHz)"
-                               % (pipe.upper(), FP64_PEAK_TFLOPS, FP32_PEAK_TFLOPS),
+                               % (shape, pipe.upper(), FP64_PEAK_TFLOPS, FP32_PEAK_TFLOPS),
                      "fp32_flops_per_launch": fl32 * cells,
                      "fp64_flops_per_launch": fl64 * cells,
                      "pipe_time_ms": {"fp64": t64 * 1e3, "fp32": t32 * 1e3},
                      "traffic": traffic["bytes_per_launch"] if traffic else None},
+        "autotune_ms_per_launch": tune,
         "e2e": e2e,
         "gpu_launches": int(mx["launches"]),
         "clocks": mx["clocks"],
     }
+    if "dmp_floor" in m:
+        line["dmp_floor"] = m["dmp_floor"]
+    if subs:
+        line["other_configs"] = subs
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = run_cpu_baseline(args.cpu_steps, 1, 32 if D == 2 else 6)
     print(json.dumps(line), flush=True)
@@ -512,6 +605,10 @@ def main():
     ap.add_argument("--grid", type=int, default=None,
                     help="cells per axis (profiling runs; default: the workload's own)")
     ap.add_argument("--only", default="both", choices=["both", "mixed", "fp64"])
+    ap.add_argument("--predictor", type=int, default=None,
+                    help="ADG_OPT_PREDICTOR of the mixed run (-1, -2 autotune; 0..4 a fixed shape)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other configurations and the DMP floor comparison")
     ap.add_argument("--workload", default="quadvortex512",
                     choices=["quadvortex512", "explosion2d", "explosion3d", "quadrants200", "dmr",
                              "serving"])

@@ -27,9 +27,25 @@
  *
  * Precision modes (adg_create `prec`)
  *   ADG_PREC_FP64        every step of the path in FP64.
- *   ADG_PREC_MIXED_FP32  predictor Picard sweeps in FP32 except the last one,
- *                        which runs in FP64; corrector, detector, projections
- *                        and the subcell limiter stay FP64.
+ *   ADG_PREC_MIXED_FP32  the predictor's Picard sweeps (Eq. pde.nc.dg2) run in
+ *                        FP32.  For N <= 5 no FP64 sweep follows: the last
+ *                        FP32 sweep yields only the space-time correction
+ *                        dq = q - u, and the final stage adds it to the FP64 u
+ *                        term by term (face traces as FP64 trace(u) + FP32
+ *                        trace(dq); time-averaged fluxes as FP64 F(u) + FP32
+ *                        flux changes).  For N >= 6 one FP64 sweep follows
+ *                        the FP32 ones and the final stage is FP64
+ *                        (ADG_OPT_FP64_SWEEPS changes either default).  FP64:
+ *                        the corrector accumulation (Eq. pde.nc.gw2), the
+ *                        detector's comparisons, the projection P and the
+ *                        reconstruction R, the finite volume update of the
+ *                        subcells and the neighbour flux correction.  The
+ *                        detector's P(u*) is the kept FP64 P(u^n) plus an FP32
+ *                        projection of the change (ADG_OPT_PROJECT_DELTA).
+ *                        FP32: the subcell scheme's WENO3 reconstruction,
+ *                        degree-2 predictor and sub-face fluxes
+ *                        (ADG_OPT_SUBCELL_FP32), wave-speed square roots.
+ *                        Conservation stays at FP64 round-off.
  */
 #ifndef ADG_H
 #define ADG_H
@@ -149,6 +165,40 @@ extern "C" {
                                      loaded since); FP64 P everywhere every 16th
                                      step.  1 (default) or 0; before the first load.
                                      Needs nv Ns^d doubles per cell.                 */
+
+#define ADG_OPT_PREDICTOR 17       /* launch shape of the space-time predictor
+                                     (Eq. pde.nc.dg2); every shape computes the same
+                                     outputs.  -1 (default): after the state's first
+                                     step the autotuner times the shapes whose
+                                     outputs are bit for bit the default's (FP64:
+                                     both block widths; mixed: WARP2 and WARP4) and
+                                     keeps the fastest (adg_autotune); -2: the same
+                                     over every shape that applies, including those
+                                     that round differently in FP32 (the tensor-pipe
+                                     contractions, the block-per-cell mixed kernel);
+                                     or one of:
+                                       ADG_PRED_BLOCK       one block per cell
+                                       ADG_PRED_BLOCK_WIDE  one 256-thread block per
+                                                            cell (FP64 only)
+                                       ADG_PRED_WARP2 / 4   mixed precision with no
+                                                            FP64 sweep (2D N <= 5,
+                                                            3D): one warp per cell for
+                                                            the FP32 sweeps, 2 or 4
+                                                            cells per block sharing
+                                                            the FP64 terms
+                                       ADG_PRED_WARP4_TC    the same, with the sweeps'
+                                                            contractions on the tensor
+                                                            pipe (TF32 operands split
+                                                            in high and low parts,
+                                                            three products per tile:
+                                                            FP32-accurate)
+                                     A shape that does not apply is refused with
+                                     ADG_ERR_ARG.                                     */
+#define ADG_PRED_BLOCK 0
+#define ADG_PRED_BLOCK_WIDE 1
+#define ADG_PRED_WARP2 2
+#define ADG_PRED_WARP4 3
+#define ADG_PRED_WARP4_TC 4
 
 #define ADG_FLUX_RUSANOV 0
 #define ADG_FLUX_OSHER 1
@@ -280,6 +330,13 @@ int adg_read(adg_state* st, double* dofs);
 /* Number of troubled cells of the last step. */
 int adg_troubled_count(adg_state* st, int64_t* out);
 
+/* Troubled-cell counts (beta^{n+1} = 1, Sec. 4.3) of the last steps since the
+ * last load, oldest first: out[i] (host int64[max]) for the min(max, steps,
+ * 4096) most recent steps; *written receives their number.  The device keeps
+ * the counts as the steps run, so reading them costs the steps nothing.
+ * Synchronizes.  Errors: ADG_ERR_ARG (nothing loaded, bad pointers). */
+int adg_troubled_history(adg_state* st, int64_t* out, int max, int* written);
+
 /* The fixed conserved state q[nvar] of inflow face `face` (2k low, 2k+1 high
  * side of axis k), host memory, copied.  Needed for every ADG_BC_INFLOW face
  * before the first load.  Errors: ADG_ERR_ARG (face out of range or not an
@@ -311,6 +368,20 @@ int adg_status(adg_state* st);
  * subcells per cell (Ns^dim). */
 int adg_sizes(const adg_state* st, int64_t* cells, int* nvar, int* nodes, int* subcells);
 
+/* Autotuner of the predictor's launch shape (no counterpart in the paper):
+ * times the predictor in every shape among which ADG_OPT_PREDICTOR lets it
+ * choose (-1, -2; with a fixed shape every shape that applies, for the
+ * report), `reps` launches each (after one warm-up launch) with CUDA events on
+ * the state's stream, on the current level with the dt of the last step, and
+ * keeps the fastest for the following steps unless ADG_OPT_PREDICTOR fixes a
+ * shape.  The state's data are unchanged (the predictor's outputs are
+ * rewritten by the next step).  ms[k] (host, k < cap) receives the
+ * milliseconds per launch of shape k, NaN for shapes not timed.
+ * Runs automatically after the first step of a state whose ADG_OPT_PREDICTOR
+ * is -1 or -2.  Synchronizes.  Errors: ADG_ERR_ARG (nothing loaded, no step taken
+ * yet, reps < 1), ADG_ERR_CUDA. */
+int adg_autotune(adg_state* st, int reps, double* ms, int cap);
+
 /* Launch layout after the first load: out[0] = subcell slot capacity,
  * out[1] = troubled cells per limiter chunk, out[2] = kernels launched by one
  * adg_step at most (every limiter pass the capacity allows, in the state's
@@ -319,8 +390,9 @@ int adg_sizes(const adg_state* st, int64_t* cells, int* nvar, int* nodes, int* s
  * device-sized loops counted on the device (batched steps count on the first
  * state of each group of one dimension, degree and precision; synchronizes
  * the state's stream); with cap >= 7, out[5] = Picard
- * sweeps of the predictor, out[6] = how many of them run in FP64.  Needs
- * cap >= 4. */
+ * sweeps of the predictor, out[6] = how many of them run in FP64; with
+ * cap >= 8, out[7] = the predictor's launch shape in effect (ADG_PRED_*).
+ * Needs cap >= 4. */
 int adg_info(const adg_state* st, int64_t* out, int cap);
 
 /* Phase timing (ADG_OPT_PROFILE = 1): accumulated milliseconds of the steps
@@ -366,6 +438,40 @@ const char* adg_last_error(const adg_state* st);
 int adg_subcell_update_noalloc(int dim, int N, double gamma, const double* h, double dt,
                                const double* patches, int count, double* vnew, double* faces,
                                void* stream, char* err, size_t errlen);
+
+/* Halo exchange of a domain decomposition (the paper runs its largest tests
+ * on many processes, each owning a block of the grid, Sec. 5.8; the flux
+ * correction of Sec. 4.4 couples cells across a block edge).  A subdomain is a
+ * state whose grid holds its own cells plus halo layers copied from the
+ * states that own them before every step; a step needs the level-n data of
+ * the cells within two cells of the owned ones (face traces and detector
+ * bounds of the face neighbours, and the troubled status and sub-face fluxes
+ * of neighbours that feed the flux correction), so two halo layers make the
+ * owned cells' new level exactly the single-domain one.
+ *
+ * A box is the cells with lo[k] <= index_k < hi[k] along every axis k < dim
+ * (cell coordinates of the state's own grid).  The packed form of `count`
+ * cells, in box order (x fastest), is the byte buffer
+ *   dofs [count][nvar][n^dim] double | sub [count][nvar][Ns^dim] double |
+ *   cmm [count][nvar][2] double | beta [count] uint8
+ * (the DOFs, the stored subcell data of flagged cells -- other rows are
+ * unspecified -- the per-cell min / max of the subcell data, the flags).
+ *
+ * adg_halo_bytes: bytes of the packed form of `count` cells of this state's
+ *   degree and dimension.
+ * adg_pack_cells: the current level of the box into `buf` (device memory of
+ *   at least adg_halo_bytes, 8-byte aligned, owned by the caller).
+ * adg_unpack_cells: the packed cells of `buf` become the current level of the
+ *   box (a box of the same shape in another state of the same dimension and
+ *   degree); the troubled list, subcell slots and kept averages are rebuilt
+ *   and the wave speeds are recomputed at the next CFL query.
+ * Both are enqueued on the state's stream (calls on states with different
+ * streams are ordered by the caller).  Errors: ADG_ERR_ARG (nothing loaded,
+ * box outside the grid or empty, unaligned buffer), ADG_ERR_CUDA; more
+ * flagged cells than subcell slots surfaces in adg_status as ADG_ERR_CAPACITY. */
+int adg_halo_bytes(const adg_state* st, int64_t count, int64_t* bytes);
+int adg_pack_cells(adg_state* st, const int* lo, const int* hi, void* buf);
+int adg_unpack_cells(adg_state* st, const int* lo, const int* hi, const void* buf);
 
 /* Free every device buffer of the state and the state itself. */
 void adg_destroy(adg_state* st);

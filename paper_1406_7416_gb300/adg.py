@@ -34,6 +34,9 @@ OPT_HOST_PASSES = 13
 OPT_SUBCELL_FP64_SWEEPS = 14
 OPT_SUBCELL_FP32 = 15
 OPT_PROJECT_DELTA = 16
+OPT_PREDICTOR = 17
+PRED_BLOCK, PRED_BLOCK_WIDE, PRED_WARP2, PRED_WARP4, PRED_WARP4_TC = 0, 1, 2, 3, 4
+PRED_NAMES = ("block", "block_wide", "warp2", "warp4", "warp4_tc")
 FLUX_RUSANOV, FLUX_OSHER = 0, 1
 PHASES = ("predictor", "faceflux", "correct_detect", "limiter", "fix")
 IC_RADIAL, IC_QUADRANT, IC_PLANAR = 0, 1, 2
@@ -45,7 +48,8 @@ SYMBOLS = ("adg_create", "adg_set_allocator", "adg_set_stream", "adg_set_option"
            "adg_sizes", "adg_info", "adg_phase_times", "adg_last_error", "adg_destroy",
            "adg_subcell_update_noalloc", "adg_time", "adg_batch_create", "adg_batch_step",
            "adg_batch_destroy", "adg_step_batch", "adg_fallback_count", "adg_set_boundary_state",
-           "adg_set_boundary_front", "adg_set_time")
+           "adg_set_boundary_front", "adg_set_time", "adg_autotune", "adg_troubled_history",
+           "adg_halo_bytes", "adg_pack_cells", "adg_unpack_cells")
 
 
 class AdgGrid(ctypes.Structure):
@@ -106,6 +110,13 @@ def load_library(path=None):
                               ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.adg_phase_times.argtypes = [vp, dp, ip]
     lib.adg_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ip]
+    lib.adg_autotune.argtypes = [vp, ip, dp, ip]
+    ipp = ctypes.POINTER(ctypes.c_int)
+    lib.adg_halo_bytes.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    lib.adg_pack_cells.argtypes = [vp, ipp, ipp, vp]
+    lib.adg_unpack_cells.argtypes = [vp, ipp, ipp, vp]
+    lib.adg_troubled_history.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ip,
+                                         ctypes.POINTER(ctypes.c_int)]
     lib.adg_last_error.argtypes = [vp]
     lib.adg_last_error.restype = ctypes.c_char_p
     lib.adg_subcell_update_noalloc.argtypes = [ip, ip, ctypes.c_double, dp, ctypes.c_double, vp, ip,
@@ -332,6 +343,37 @@ class Solver:
         self._check(self.lib.adg_troubled_count(self.h, ctypes.byref(c)), "adg_troubled_count")
         return c.value
 
+    # -- halo exchange of a domain decomposition ----------------------------
+    def halo_bytes(self, count):
+        b = ctypes.c_int64()
+        self._check(self.lib.adg_halo_bytes(self.h, int(count), ctypes.byref(b)), "adg_halo_bytes")
+        return b.value
+
+    @staticmethod
+    def _box(lo, hi):
+        return (ctypes.c_int * 3)(*(list(lo) + [0] * (3 - len(lo)))), \
+               (ctypes.c_int * 3)(*(list(hi) + [1] * (3 - len(hi))))
+
+    def pack_cells(self, lo, hi, buf_ptr):
+        """adg_pack_cells into the device buffer at buf_ptr (raw pointer)."""
+        a, b = self._box(lo, hi)
+        self._check(self.lib.adg_pack_cells(self.h, a, b, ctypes.c_void_p(int(buf_ptr))),
+                    "adg_pack_cells")
+
+    def unpack_cells(self, lo, hi, buf_ptr):
+        a, b = self._box(lo, hi)
+        self._check(self.lib.adg_unpack_cells(self.h, a, b, ctypes.c_void_p(int(buf_ptr))),
+                    "adg_unpack_cells")
+
+    def troubled_history(self, max_steps=4096):
+        """Troubled-cell counts of the last steps since the load, oldest first."""
+        out = np.zeros(max_steps, dtype=np.int64)
+        k = ctypes.c_int()
+        self._check(self.lib.adg_troubled_history(
+            self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(max_steps),
+            ctypes.byref(k)), "adg_troubled_history")
+        return out[:k.value]
+
     def fallback_count(self):
         """(cells recomputed by the first-order layer in the last step, since the load)."""
         a, b = ctypes.c_int64(), ctypes.c_int64()
@@ -357,12 +399,20 @@ class Solver:
 
     def info(self):
         """Slot capacity, limiter chunk, kernels of one adg_step at most, device
-        bytes held, kernels issued by the steps so far, Picard sweeps and how
-        many run in FP64."""
-        out = (ctypes.c_int64 * 7)()
-        self._check(self.lib.adg_info(self.h, out, 7), "adg_info")
+        bytes held, kernels issued by the steps so far, Picard sweeps, how
+        many run in FP64, and the predictor's launch shape in effect."""
+        out = (ctypes.c_int64 * 8)()
+        self._check(self.lib.adg_info(self.h, out, 8), "adg_info")
         return dict(capacity=out[0], chunk=out[1], launches_per_step=out[2], bytes=out[3],
-                    launches=out[4], picard_iters=out[5], fp64_sweeps=out[6])
+                    launches=out[4], picard_iters=out[5], fp64_sweeps=out[6],
+                    predictor=int(out[7]))
+
+    def autotune(self, reps=3):
+        """adg_autotune: {shape name: ms per predictor launch} (NaN: n/a);
+        the state keeps the fastest shape."""
+        ms = np.zeros(len(PRED_NAMES))
+        self._check(self.lib.adg_autotune(self.h, int(reps), _dptr(ms), len(ms)), "adg_autotune")
+        return dict(zip(PRED_NAMES, ms.tolist()))
 
     def time(self):
         """(simulated time, steps taken since the last load)."""

@@ -25,6 +25,10 @@ struct adg_state {
   int sub_fp64 = 0;         // mixed precision: FP64 sweeps of the degree-2 subcell predictor
   int sub_f32 = 1;          // mixed precision: FP32 subcell reconstruction and sub-face fluxes
   int project_delta = 1;    // mixed precision: detector projection from the kept P(u^n)
+  int pred_opt = -1;        // ADG_OPT_PREDICTOR: fixed predictor shape (PRED_*); -1 autotune
+                            // among the shapes of the default arithmetic, -2 among all
+  int pred_tuned = -1;      // the autotuner's choice (-1: not tuned yet)
+  double tune_ms[PRED_COUNT] = {};   // the autotuner's per-shape milliseconds (NaN: n/a)
   int bstate_set = 0;       // bit f: inflow face f has a state
   int front_set = 0;        // bit f: front face f has its front
   // pinned host mirror of the device Params, counters and dt, read once per
@@ -282,6 +286,7 @@ int ensure_allocated(adg_state* st) {
   ALLOC(b.fixlist, int, cells);
   ALLOC(b.fixstamp, int, cells);
   ALLOC(b.edge, double, cap * st->dim * 2 * nv * nsf);
+  ALLOC(b.hist, int, HIST_LEN);
   ALLOC(b.fblist, int, 3 * cap);
   b.fbflag = b.fblist + cap;
   b.refixlist = b.fblist + 2 * cap;
@@ -446,6 +451,48 @@ int collect_phases(adg_state* st, int k) {
   return ADG_OK;
 }
 
+// Whether the state's predictor runs the split final stage (mixed precision
+// with no FP64 sweep) at a degree the warp-per-cell kernel covers.
+bool split_capable(const adg_state* st) {
+  const int f64 = st->fp64_sweeps < st->iters ? st->fp64_sweeps : st->iters;
+  return st->prec == ADG_PREC_MIXED_FP32 && f64 == 0 && st->iters > 0 &&
+         !(st->dim == 2 && st->N >= 6);
+}
+
+// Predictor shapes that apply to the state (PRED_*).
+bool shape_applies(const adg_state* st, int shape) {
+  if (st->prec != ADG_PREC_MIXED_FP32) return shape == PRED_BLOCK || shape == PRED_BLOCK_WIDE;
+  if (shape == PRED_BLOCK) return true;
+  return split_capable(st) &&
+         (shape == PRED_WARP2 || shape == PRED_WARP4 || shape == PRED_WARP4_TC);
+}
+
+// Shapes whose outputs are bit for bit those of the default shape: the
+// block-per-cell FP64 kernel at any width; the warp-per-cell mixed kernel at
+// 2 or 4 cells per block (the same per-output code).
+bool shape_same_arith(const adg_state* st, int shape) {
+  if (!shape_applies(st, shape)) return false;
+  if (st->prec != ADG_PREC_MIXED_FP32) return true;
+  if (!split_capable(st)) return shape == PRED_BLOCK;
+  return shape == PRED_WARP2 || shape == PRED_WARP4;
+}
+
+// Shapes the autotuner times: those of the default arithmetic, or with
+// ADG_OPT_PREDICTOR = -2 every shape that applies (the tensor-pipe
+// contractions and the block-per-cell mixed kernel round differently).
+bool tune_candidate(const adg_state* st, int shape) {
+  return st->pred_opt == -2 ? shape_applies(st, shape) : shape_same_arith(st, shape);
+}
+
+// The shape the state's steps launch: the fixed option, else the tuned
+// choice, else the default (warp-per-cell with 4 cells per block where it
+// applies, the block-per-cell kernel otherwise).
+int effective_pred(const adg_state* st) {
+  if (st->pred_opt >= 0 && shape_applies(st, st->pred_opt)) return st->pred_opt;
+  if (st->pred_tuned >= 0 && shape_applies(st, st->pred_tuned)) return st->pred_tuned;
+  return split_capable(st) ? PRED_WARP4 : PRED_BLOCK;
+}
+
 StepLaunch single_launch(adg_state* st) {
   StepLaunch sl;
   std::memset(&sl, 0, sizeof(sl));
@@ -472,8 +519,72 @@ StepLaunch single_launch(adg_state* st) {
   sl.sum_chunk = st->chunk;
   sl.max_passes = (st->cap + st->chunk - 1) / st->chunk;
   sl.prec = st->prec;
+  sl.pred = effective_pred(st);
   sl.ev = st->profile ? st->ev[st->ev_next] : nullptr;
   return sl;
+}
+
+// Autotuner: times the predictor in every shape that applies to the state on
+// its current level (the dt and coefficients of the last step), `reps`
+// launches each after one warm-up launch, with CUDA events on the state's
+// stream, and keeps the fastest.  The predictor's outputs (the next level's
+// volume part and the face traces) are rewritten by the next step, so the
+// state is unchanged.  Needs a state that has taken a step (dt > 0).
+int autotune_predictor(adg_state* st, int reps, bool* done) {
+  *done = false;
+  for (int k = 0; k < PRED_COUNT; ++k) st->tune_ms[k] = NAN;
+  int rc = refresh(st);
+  if (rc) return rc;
+  if (st->params_dirty && (rc = upload_params(st))) return rc;
+  double dt = 0.0;
+  CUDA_TRY(st, cudaMemcpyAsync(&dt, st->b.dt, sizeof(double), cudaMemcpyDeviceToHost, st->stream));
+  CUDA_TRY(st, cudaStreamSynchronize(st->stream));
+  if (!(dt > 0.0)) return ADG_OK;
+  cudaEvent_t e0, e1;
+  CUDA_TRY(st, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(st, ADG_ERR_CUDA, "event creation failed");
+  }
+  StepLaunch sl = single_launch(st);
+  sl.ev = nullptr;
+  int best = -1;
+  double best_ms = 0.0;
+  cudaError_t e = cudaSuccess;
+  for (int shape = 0; shape < PRED_COUNT && e == cudaSuccess; ++shape) {
+    if (!(st->pred_opt >= 0 ? shape_applies(st, shape) : tune_candidate(st, shape))) continue;
+    sl.pred = shape;
+    LaunchArgs a{};
+    a.op = OP_PREDICTOR;
+    a.step = &sl;
+    a.stream = st->stream;
+    e = dispatch(st, a);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st->stream);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = dispatch(st, a);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) break;
+    st->tune_ms[shape] = ms / reps;
+    if (best < 0 || st->tune_ms[shape] < best_ms) {
+      best = shape;
+      best_ms = st->tune_ms[shape];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(st, ADG_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+  st->pred_tuned = best;
+  *done = true;
+  return ADG_OK;
+}
+
+// Shapes the autotuner chooses among (a choice when > 1).
+int tune_candidates(const adg_state* st) {
+  int c = 0;
+  for (int k = 0; k < PRED_COUNT; ++k) c += tune_candidate(st, k) ? 1 : 0;
+  return c;
 }
 
 // Kernels of one step: the wave-speed maximum and the step begin; predictor,
@@ -649,6 +760,14 @@ int common_step(adg_state* st, const double* dts_dev, double cfl, double dt_max)
     st->ev_next = (st->ev_next + 1) % adg_state::kEventSets;
   }
   st->lam_valid = st->lam_mode;
+  if (st->pred_opt < 0 && st->pred_tuned < 0 && tune_candidates(st) > 1) {
+    // the first step of an untuned state: time the predictor shapes on the
+    // level it left (later steps launch the fastest; the next graph capture
+    // picks it up)
+    bool done = false;
+    int rc = autotune_predictor(st, 3, &done);
+    if (rc) return rc;
+  }
   return ADG_OK;
 }
 
@@ -763,7 +882,8 @@ int adg_batch_create(adg_state* const* states, int count, void* stream, adg_batc
       const adg_state* a = states[i];
       const adg_state* c = states[j];
       if (!done[j] && a->dim == c->dim && a->N == c->N && a->prec == c->prec &&
-          a->sub_fp64 == c->sub_fp64 && a->sub_f32 == c->sub_f32 && a->flux == c->flux) {
+          a->sub_fp64 == c->sub_fp64 && a->sub_f32 == c->sub_f32 && a->flux == c->flux &&
+          effective_pred(a) == effective_pred(c)) {
         g.idx.push_back(j);
         done[j] = 1;
       }
@@ -817,6 +937,7 @@ int adg_batch_create(adg_state* const* states, int count, void* stream, adg_batc
     sl.sub32 = 3 - g.rep->sub_fp64;
     sl.sub_f32 = g.rep->sub_f32;
     sl.flux = g.rep->flux;
+    sl.pred = effective_pred(g.rep);
     sl.ev = nullptr;
     g.sl = sl;
     g.dts_off = off;
@@ -1064,6 +1185,15 @@ int adg_set_option(adg_state* st, int key, double value) {
         for (int k = 0; k < adg_state::kEventSets; ++k)
           for (int i = 0; i < PHASE_COUNT; ++i) CUDA_TRY(st, cudaEventCreate(&st->ev[k][i]));
       st->profile = value != 0.0;
+      return ADG_OK;
+    case ADG_OPT_PREDICTOR:
+      if (!(value == -1.0 || value == -2.0 ||
+            (value >= 0.0 && value < PRED_COUNT && value == (int)value)))
+        return fail(st, ADG_ERR_ARG, "predictor shape must be -1, -2 (autotune) or 0..4");
+      if (value >= 0.0 && !shape_applies(st, (int)value))
+        return fail(st, ADG_ERR_ARG, "that predictor shape does not apply to this state");
+      if ((int)value != st->pred_opt) st->pred_tuned = -1;    // tune again in the new mode
+      st->pred_opt = (int)value;
       return ADG_OK;
     case ADG_OPT_SLOT_CAPACITY:
       if (st->allocated) return fail(st, ADG_ERR_ARG, "capacity must be set before the first load");
@@ -1362,6 +1492,90 @@ int adg_phase_times(adg_state* st, double* ms, int cap) {
   return ADG_OK;
 }
 
+namespace {
+
+// Validates a box [lo, hi) of cells of the state; its cell count.
+int box_count(adg_state* st, const int* lo, const int* hi, long long* count) {
+  if (!lo || !hi) return fail(st, ADG_ERR_ARG, "box bounds are null");
+  long long c = 1;
+  for (int k = 0; k < st->dim; ++k) {
+    if (lo[k] < 0 || hi[k] > st->geo.n[k] || lo[k] >= hi[k])
+      return fail(st, ADG_ERR_ARG, "box outside the grid or empty along axis " + std::to_string(k));
+    c *= hi[k] - lo[k];
+  }
+  *count = c;
+  return ADG_OK;
+}
+
+int pack_unpack(adg_state* st, const int* lo, const int* hi, void* buf, int op) {
+  if (!st || !buf) return ADG_ERR_ARG;
+  if (!st->loaded) return fail(st, ADG_ERR_ARG, "nothing loaded");
+  if ((reinterpret_cast<uintptr_t>(buf) & 7) != 0) return fail(st, ADG_ERR_ARG, "buffer not 8-byte aligned");
+  long long count = 0;
+  int rc = box_count(st, lo, hi, &count);
+  if (rc) return rc;
+  int box[6] = {0, 0, 0, 1, 1, 1};
+  for (int k = 0; k < st->dim; ++k) {
+    box[k] = lo[k];
+    box[3 + k] = hi[k];
+  }
+  LaunchArgs a{};
+  a.op = op;
+  a.box = box;
+  a.buf = buf;
+  rc = launch(st, a, op == OP_PACK ? "pack cells" : "unpack cells");
+  if (rc) return rc;
+  if (op == OP_UNPACK) st->lam_valid = false;      // the box's wave speeds are not known
+  return ADG_OK;
+}
+
+}  // namespace
+
+int adg_halo_bytes(const adg_state* st, int64_t count, int64_t* bytes) {
+  if (!st || !bytes || count < 0) return ADG_ERR_ARG;
+  *bytes = (int64_t)packed_bytes(st->dim, st->N, count);
+  return ADG_OK;
+}
+
+int adg_pack_cells(adg_state* st, const int* lo, const int* hi, void* buf) {
+  return pack_unpack(st, lo, hi, buf, OP_PACK);
+}
+
+int adg_unpack_cells(adg_state* st, const int* lo, const int* hi, const void* buf) {
+  return pack_unpack(st, lo, hi, const_cast<void*>(buf), OP_UNPACK);
+}
+
+int adg_troubled_history(adg_state* st, int64_t* out, int max, int* written) {
+  if (!st || !written || max < 0 || (max > 0 && !out)) return ADG_ERR_ARG;
+  *written = 0;
+  if (!st->loaded) return fail(st, ADG_ERR_ARG, "nothing loaded");
+  double clk[3] = {0.0, 0.0, 0.0};
+  std::vector<int> h(HIST_LEN);
+  CUDA_TRY(st, cudaMemcpyAsync(clk, st->b.clock, sizeof(clk), cudaMemcpyDeviceToHost, st->stream));
+  CUDA_TRY(st, cudaMemcpyAsync(h.data(), st->b.hist, sizeof(int) * HIST_LEN, cudaMemcpyDeviceToHost,
+                               st->stream));
+  int rc = sync(st);
+  if (rc) return rc;
+  const long long steps = (long long)clk[2];
+  long long k = steps < HIST_LEN ? steps : HIST_LEN;
+  if (k > max) k = max;
+  for (long long i = 0; i < k; ++i) out[i] = h[(steps - k + i) % HIST_LEN];
+  *written = (int)k;
+  return ADG_OK;
+}
+
+int adg_autotune(adg_state* st, int reps, double* ms, int cap) {
+  if (!st || reps < 1 || (cap > 0 && !ms)) return ADG_ERR_ARG;
+  if (!st->loaded) return fail(st, ADG_ERR_ARG, "nothing loaded");
+  bool done = false;
+  int rc = autotune_predictor(st, reps, &done);
+  if (rc) return rc;
+  if (!done) return fail(st, ADG_ERR_ARG, "autotune needs a state that has taken a step");
+  for (int k = 0; k < cap && k < PRED_COUNT; ++k) ms[k] = st->tune_ms[k];
+  for (int k = PRED_COUNT; k < cap; ++k) ms[k] = NAN;
+  return ADG_OK;
+}
+
 int adg_info(const adg_state* st, int64_t* out, int cap) {
   if (!st || !out || cap < 4) return ADG_ERR_ARG;
   if (!st->allocated) return ADG_ERR_ARG;
@@ -1381,6 +1595,7 @@ int adg_info(const adg_state* st, int64_t* out, int cap) {
       return ADG_ERR_CUDA;
     out[4] = st->launch_count + (int64_t)passes * (2 * D + 5);
   }
+  if (cap >= 8) out[7] = effective_pred(st);
   if (cap >= 7) {
     out[5] = st->iters;
     out[6] = st->prec == ADG_PREC_MIXED_FP32 ? (st->fp64_sweeps < st->iters ? st->fp64_sweeps : st->iters)

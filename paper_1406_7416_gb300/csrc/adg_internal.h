@@ -80,6 +80,7 @@ struct Bufs {
   int* fixlist;          // [cells]
   int* fixstamp;         // [cells]
   double* edge;          // [cap][d][2][nv][Ns^(d-1)] sub-face fluxes on the cell faces
+  int* hist;             // [HIST_LEN] troubled count of step s at s % HIST_LEN (s from 0)
   int* fblist;           // [cap] slots whose WENO3 result failed PAD this step
   int* fbflag;           // [cap] step stamp of the slots in fblist
   int* refixlist;        // [cap] WENO3 cells sharing a face with a fallback cell
@@ -100,6 +101,8 @@ struct Bufs {
   double* fsub[3];       // [chunk][nv][faces along axis k]
   double* tmp_sub;       // load-time scratch [cells][nv][Ns^d]
 };
+
+constexpr int HIST_LEN = 4096;        // steps of troubled-count history kept per state
 
 enum {
   CNT_TROUBLED0 = 0,     // troubled count of buffer 0
@@ -164,6 +167,7 @@ struct StepLaunch {
   int sub32;                   // mixed precision: FP32 sweeps (of 3) of the subcell predictor
   int sub_f32;                  // mixed precision: WENO3 reconstruction and sub-face fluxes in FP32
   int flux;                    // numerical flux of the launch's states (ADG_FLUX_*)
+  int pred;                    // predictor launch shape (PRED_*)
   long long total_cells;
   long long total_faces[3];
   long long sum_chunk;         // sum over states of the limiter chunk size
@@ -180,6 +184,18 @@ struct StepLaunch {
   cudaStream_t body;
 };
 
+// Launch shapes of the predictor (selected per state by the autotuner or the
+// ADG_OPT_PREDICTOR option; every shape computes the same outputs):
+//   PRED_BLOCK      one block per cell (k_predictor), its default threads;
+//   PRED_BLOCK_WIDE one block per cell with 256 threads (FP64 path);
+//   PRED_WARP2/4    mixed precision with the split final stage: one warp per
+//                   cell for the FP32 sweeps, 2 or 4 cells per block sharing
+//                   the FP64 terms (k_predictor_split);
+//   PRED_WARP4_TC   the same with the sweeps' contractions on the tensor pipe
+//                   (3 x TF32 mma.sync, FP32-accurate).
+enum PredShapeId { PRED_BLOCK = 0, PRED_BLOCK_WIDE = 1, PRED_WARP2 = 2, PRED_WARP4 = 3,
+                   PRED_WARP4_TC = 4, PRED_COUNT = 5 };
+
 // Kernel launch interface: one dispatcher per translation unit (2D low N,
 // 2D high N, 3D), selected by dimension and degree.
 enum LaunchOp {
@@ -192,7 +208,10 @@ enum LaunchOp {
   OP_READ_FULL,        // subcell rows of flagged cells
   OP_PROJECT,          // initial data projection
   OP_SUB_MINMAX,       // per-cell min/max of subcell rows
-  OP_LAMBDA            // per-cell wave speeds of the current level
+  OP_LAMBDA,           // per-cell wave speeds of the current level
+  OP_PREDICTOR,        // the predictor alone (autotuning), shape step->pred
+  OP_PACK,             // halo exchange: a box of cells into a buffer
+  OP_UNPACK            // halo exchange: a buffer into a box of cells, list rebuilt
 };
 
 struct LaunchArgs {
@@ -208,7 +227,12 @@ struct LaunchArgs {
   const double* fac;       // OP_PROJECT per-cell density factor (device) or null
   cudaEvent_t* ev;         // unused (phase events travel in StepLaunch)
   const StepLaunch* step;  // OP_STEP_*: the batched step
+  const int* box;          // OP_PACK / OP_UNPACK: lo[3], hi[3] (host)
+  void* buf;               // OP_PACK / OP_UNPACK: the packed cells (device)
 };
+
+// Bytes of a packed box of `count` cells (halo exchange).
+size_t packed_bytes(int dim, int N, long long count);
 
 // Phase boundaries recorded when profiling is on: ev[PHASE_x] before phase x,
 // ev[PHASE_END] after the last one.

@@ -110,7 +110,12 @@ __global__ void k_step_end(StepLaunch sl) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= sl.n) return;
   Params& p = *sl.pps[s];
-  if (*p.b.dt > 0.0) p.cur = 1 - p.cur;
+  if (*p.b.dt > 0.0) {
+    // the step's troubled count into the history, at the step's index
+    const long long k = (long long)p.b.clock[2] - 1;
+    if (p.b.hist && k >= 0) p.b.hist[k % HIST_LEN] = p.b.counters[CNT_TROUBLED0 + (1 - p.cur)];
+    p.cur = 1 - p.cur;
+  }
 }
 
 // Prefix of the troubled cells each state handles in limiter pass `pass`
@@ -251,6 +256,29 @@ cudaError_t launch_fix_prefix(const StepLaunch& sl, cudaStream_t s) {
 cudaError_t launch_count_prefix(const StepLaunch& sl, long long* pre, int counter, cudaStream_t s) {
   k_count_prefix<<<1, 1, 0, s>>>(sl, pre, counter);
   return cudaGetLastError();
+}
+
+size_t packed_bytes(int dim, int N, long long count) {
+  if (dim == 2) {
+    switch (N) {
+      case 1: return Packed<2, 1>::bytes(count);
+      case 2: return Packed<2, 2>::bytes(count);
+      case 3: return Packed<2, 3>::bytes(count);
+      case 4: return Packed<2, 4>::bytes(count);
+      case 5: return Packed<2, 5>::bytes(count);
+      case 6: return Packed<2, 6>::bytes(count);
+      case 7: return Packed<2, 7>::bytes(count);
+      case 8: return Packed<2, 8>::bytes(count);
+      case 9: return Packed<2, 9>::bytes(count);
+    }
+  } else {
+    switch (N) {
+      case 1: return Packed<3, 1>::bytes(count);
+      case 2: return Packed<3, 2>::bytes(count);
+      case 3: return Packed<3, 3>::bytes(count);
+    }
+  }
+  return 0;
 }
 
 size_t limiter_scratch_doubles(int dim, int N, size_t* a, size_t* b, size_t* c, size_t* d,

@@ -387,3 +387,172 @@ __global__ void __launch_bounds__(128) k_project(Params p, adg_problem pr,
 }
 
 }  // namespace adg
+
+namespace adg {
+
+// ---------------------------------------------------------------------------
+// Halo exchange of a domain decomposition (the paper's MPI runs split the
+// grid among processes and exchange neighbour data every step, Sec. 5.8;
+// the flux correction of Sec. 4.4 couples cells across a partition edge).
+// A box of cells [lo, hi) of one state is packed into a caller buffer with
+// the level-n data another state needs to step cells beyond its own: DOFs,
+// flags, the stored subcell data of flagged cells and the per-cell extrema
+// of the subcell data (the DMP bounds' inputs).  Packed layout, for count
+// cells in box order (x fastest):
+//   dofs [count][nv][n^d] | sub [count][nv][Ns^d] | cmm [count][nv][2] |
+//   beta [count] bytes
+// ---------------------------------------------------------------------------
+struct Box {
+  int lo[3], hi[3];
+  long long count;
+};
+
+template <int D>
+__device__ __forceinline__ long long box_cell(const Box& bx, long long q, const Geo& g) {
+  const int ex = bx.hi[0] - bx.lo[0], ey = bx.hi[1] - bx.lo[1];
+  int ijk[3];
+  ijk[0] = bx.lo[0] + (int)(q % ex);
+  const long long r = q / ex;
+  ijk[1] = bx.lo[1] + (int)(r % ey);
+  ijk[2] = D == 3 ? bx.lo[2] + (int)(r / ey) : 0;
+  return cell_index<D>(ijk, g);
+}
+
+// position of local cell c in the box, or -1
+template <int D>
+__device__ __forceinline__ long long box_index(const Box& bx, long long c, const Geo& g) {
+  int ijk[3];
+  cell_coords<D>(c, g, ijk);
+  long long q = 0, mul = 1;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    if (ijk[k] < bx.lo[k] || ijk[k] >= bx.hi[k]) return -1;
+    q += (ijk[k] - bx.lo[k]) * mul;
+    mul *= bx.hi[k] - bx.lo[k];
+  }
+  return q;
+}
+
+template <int D, int N>
+struct Packed {
+  using DM = Dims<D, N>;
+  static constexpr int NV = DM::NV, ND = DM::ND, NSD = DM::NSD;
+  double* dofs;
+  double* sub;
+  double* cmm;
+  uint8_t* beta;
+  __host__ __device__ Packed(void* buf, long long count) {
+    dofs = static_cast<double*>(buf);
+    sub = dofs + count * NV * ND;
+    cmm = sub + count * NV * NSD;
+    beta = reinterpret_cast<uint8_t*>(cmm + count * 2 * NV);
+  }
+  static size_t bytes(long long count) {
+    return (size_t)count * ((NV * ND + NV * NSD + 2 * NV) * sizeof(double) + 1);
+  }
+};
+
+// One block per box cell: the level-n data of the cell into the buffer.
+template <int D, int N>
+__global__ void __launch_bounds__(128) k_pack(Params p, Box bx, void* buf) {
+  using PK = Packed<D, N>;
+  constexpr int NV = PK::NV, ND = PK::ND, NSD = PK::NSD;
+  PK pk(buf, bx.count);
+  const int cur = p.cur;
+  for (long long q = blockIdx.x; q < bx.count; q += gridDim.x) {
+    const long long c = box_cell<D>(bx, q, p.geo);
+    const double* U = p.b.U[cur] + c * (NV * ND);
+    for (int e = threadIdx.x; e < NV * ND; e += blockDim.x) pk.dofs[q * NV * ND + e] = U[e];
+    for (int e = threadIdx.x; e < 2 * NV; e += blockDim.x)
+      pk.cmm[q * 2 * NV + e] = p.b.cmm[cur][c * 2 * NV + e];
+    const uint8_t b = p.b.beta[cur][c];
+    const int slot = p.b.slot[cur][c];
+    if (threadIdx.x == 0) pk.beta[q] = (b && slot >= 0) ? 1 : 0;
+    if (b && slot >= 0) {
+      const double* src = p.b.store[cur] + (size_t)slot * NV * NSD;
+      for (int e = threadIdx.x; e < NV * NSD; e += blockDim.x) pk.sub[q * NV * NSD + e] = src[e];
+    }
+  }
+}
+
+// One block per box cell: DOFs, flags and extrema of the buffer become the
+// cell's level n; its kept subcell averages (mixed precision) are dropped.
+template <int D, int N>
+__global__ void __launch_bounds__(128) k_unpack(Params p, Box bx, const void* buf) {
+  using PK = Packed<D, N>;
+  constexpr int NV = PK::NV, ND = PK::ND;
+  const PK pk(const_cast<void*>(buf), bx.count);
+  const int cur = p.cur;
+  for (long long q = blockIdx.x; q < bx.count; q += gridDim.x) {
+    const long long c = box_cell<D>(bx, q, p.geo);
+    double* U = p.b.U[cur] + c * (NV * ND);
+    for (int e = threadIdx.x; e < NV * ND; e += blockDim.x) U[e] = pk.dofs[q * NV * ND + e];
+    for (int e = threadIdx.x; e < 2 * NV; e += blockDim.x)
+      p.b.cmm[cur][c * 2 * NV + e] = pk.cmm[q * 2 * NV + e];
+    if (threadIdx.x == 0) {
+      p.b.beta[cur][c] = pk.beta[q];
+      if (p.b.vok) p.b.vok[c] = 0;
+    }
+  }
+}
+
+// One block per cell: the level-n troubled list rebuilt into the other
+// level's (dead) list, slot and store arrays, rows of box cells taken from
+// the buffer and the others from their current slots; the counter of the
+// other level (zeroed by the host, reset again by the next step begin) counts.
+template <int D, int N>
+__global__ void __launch_bounds__(128) k_relist(Params p, Box bx, const void* buf) {
+  using PK = Packed<D, N>;
+  constexpr int NV = PK::NV, NSD = PK::NSD;
+  const PK pk(const_cast<void*>(buf), bx.count);
+  const int cur = p.cur, nxt = 1 - cur;
+  __shared__ int s_slot;
+  for (long long c = blockIdx.x; c < p.geo.cells; c += gridDim.x) {
+    const uint8_t b = p.b.beta[cur][c];
+    if (!b) {
+      if (threadIdx.x == 0) p.b.slot[nxt][c] = -1;
+      continue;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int s = atomicAdd(&p.b.counters[CNT_TROUBLED0 + nxt], 1);
+      if (s < p.cap) {
+        p.b.list[nxt][s] = (int)c;
+      } else {
+        atomicOr(&p.b.counters[CNT_STATUS], 1);
+        s = -1;
+      }
+      p.b.slot[nxt][c] = s;
+      s_slot = s;
+    }
+    __syncthreads();
+    const int s = s_slot;
+    if (s < 0) continue;
+    const long long q = box_index<D>(bx, c, p.geo);
+    const double* src = q >= 0 ? pk.sub + q * NV * NSD
+                               : p.b.store[cur] + (size_t)p.b.slot[cur][c] * NV * NSD;
+    double* dst = p.b.store[nxt] + (size_t)s * NV * NSD;
+    for (int e = threadIdx.x; e < NV * NSD; e += blockDim.x) dst[e] = src[e];
+  }
+}
+
+// The rebuilt list, slots and stored rows copied back to level n.
+template <int D, int N>
+__global__ void k_copyback(Params p) {
+  constexpr int NV = D + 2, NSD = ipow(2 * N + 1, D);
+  const int cur = p.cur, nxt = 1 - cur;
+  int n = p.b.counters[CNT_TROUBLED0 + nxt];
+  if (n > p.cap) n = p.cap;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = t0; e < (long long)n * NV * NSD; e += stride)
+    p.b.store[cur][e] = p.b.store[nxt][e];
+  for (long long e = t0; e < n; e += stride) p.b.list[cur][e] = p.b.list[nxt][e];
+  for (long long c = t0; c < p.geo.cells; c += stride) {
+    p.b.slot[cur][c] = p.b.slot[nxt][c];
+    if (p.b.slot[cur][c] < 0) p.b.beta[cur][c] = 0;      // no slot left: the cell is unflagged
+  }
+  if (t0 == 0) p.b.counters[CNT_TROUBLED0 + cur] = n;
+}
+
+}  // namespace adg

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "kernels_misc.cuh"
+#include "kernels_pred.cuh"
 
 namespace adg {
 
@@ -17,6 +18,36 @@ inline int grid_for(long long work, int threads, int cap_blocks = kNumSM * kBloc
 
 inline int cells_grid(long long cells) {
   return (int)(cells < (1LL << 30) ? cells : (1LL << 30));
+}
+
+// Multiprocessors of the current device (queried once).
+inline int device_sms() {
+  static int sms = [] {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      return kNumSM;
+    }
+    return n;
+  }();
+  return sms;
+}
+
+// Grid of a persistent kernel: the blocks that fit on the device at once (at
+// least one per multiprocessor), at most `work` blocks.
+template <typename K>
+int persistent_grid(K kernel, int threads, size_t smem, long long work) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  if (per_sm < 1) per_sm = 1;
+  long long g = (long long)per_sm * device_sms();
+  if (g > work) g = work;
+  if (g < 1) g = 1;
+  return (int)g;
 }
 
 template <typename K>
@@ -74,6 +105,54 @@ struct Launch {
       cudaEventRecord(ev[phase], s);
   }
 
+  // the warp-per-cell predictor exists for the degrees whose mixed default
+  // is the split final stage (2D N <= 5, 3D)
+  static constexpr bool kSplit = !(D == 2 && N >= 6);
+
+  template <int W, bool TC>
+  static cudaError_t launch_split(const Batch& cells, long long total, cudaStream_t s) {
+    if constexpr (kSplit) {
+      const size_t sm = split_smem_bytes<D, N, W>();
+      cudaError_t e = set_smem(k_predictor_split<D, N, W, TC>, sm);
+      if (e != cudaSuccess) return e;
+      static const int grid_full = persistent_grid(k_predictor_split<D, N, W, TC>, 32 * W, sm, 1LL << 40);
+      const long long groups = (total + W - 1) / W;
+      const int grid = (int)(groups < grid_full ? groups : grid_full);
+      k_predictor_split<D, N, W, TC><<<grid, 32 * W, sm, s>>>(cells);
+      return cudaGetLastError();
+    }
+    return cudaErrorInvalidValue;
+  }
+
+  // The predictor in the launch shape sl.pred (PRED_*); shapes that do not
+  // apply to the launch fall back to the block-per-cell kernel.
+  static cudaError_t launch_predictor(const StepLaunch& sl, cudaStream_t s) {
+    cudaError_t e;
+    const int grid = cells_grid(sl.total_cells);
+    const Batch cells{sl.pps, sl.n, sl.pre_cells};
+    if (sl.prec == ADG_PREC_MIXED_FP32) {
+      if (kSplit && sl.pred == PRED_WARP2) return launch_split<2, false>(cells, sl.total_cells, s);
+      if (kSplit && sl.pred == PRED_WARP4) return launch_split<4, false>(cells, sl.total_cells, s);
+      if (kSplit && sl.pred == PRED_WARP4_TC) return launch_split<4, true>(cells, sl.total_cells, s);
+      const size_t sm = predictor_smem_bytes<D, N, true>();
+      if ((e = set_smem(k_predictor<D, N, true>, sm)) != cudaSuccess) return e;
+      k_predictor<D, N, true><<<grid, pred_threads<true>(), sm, s>>>(cells);
+    } else {
+      const size_t sm = predictor_smem_bytes<D, N, false>();
+      if ((e = set_smem(k_predictor<D, N, false>, sm)) != cudaSuccess) return e;
+      const int th = sl.pred == PRED_BLOCK_WIDE ? wide_threads() : pred_threads<false>();
+      k_predictor<D, N, false><<<grid, th, sm, s>>>(cells);
+    }
+    return cudaGetLastError();
+  }
+
+  // 256 threads (the FP64 kernel's launch bound), fewer when a cell has fewer
+  // work items
+  static int wide_threads() {
+    const int t = ((NV * DM::NST + 31) / 32) * 32;
+    return t > 256 ? 256 : t;
+  }
+
   static cudaError_t step_dg(const StepLaunch& sl, cudaStream_t s) {
     cudaError_t e;
     cudaEvent_t* ev = sl.ev;
@@ -81,15 +160,7 @@ struct Launch {
     const int grid = cells_grid(sl.total_cells);
     const Batch cells{sl.pps, sl.n, sl.pre_cells};
     mark(ev, PHASE_PREDICTOR, s);
-    if (sl.prec == ADG_PREC_MIXED_FP32) {
-      const size_t sm = predictor_smem_bytes<D, N, true>();
-      if ((e = set_smem(k_predictor<D, N, true>, sm)) != cudaSuccess) return e;
-      k_predictor<D, N, true><<<grid, pred_threads<true>(), sm, s>>>(cells);
-    } else {
-      const size_t sm = predictor_smem_bytes<D, N, false>();
-      if ((e = set_smem(k_predictor<D, N, false>, sm)) != cudaSuccess) return e;
-      k_predictor<D, N, false><<<grid, pred_threads<false>(), sm, s>>>(cells);
-    }
+    if ((e = launch_predictor(sl, s)) != cudaSuccess) return e;
     mark(ev, PHASE_FACEFLUX, s);
     for (int k = 0; k < D; ++k) {
       const Batch faces{sl.pps, sl.n, sl.pre_faces[k]};
@@ -212,6 +283,7 @@ struct Launch {
       if (a.op == OP_STEP_DG) return step_dg(*a.step, a.stream);
       return step_limiter(*a.step, a.stream);
     }
+    if (a.op == OP_PREDICTOR) return a.step->total_cells ? launch_predictor(*a.step, a.stream) : cudaSuccess;
     const Params& p = *a.p;
     cudaStream_t s = a.stream;
     cudaError_t e;
@@ -243,6 +315,29 @@ struct Launch {
         const size_t sm = cell_smem();
         if ((e = set_smem(k_lambda<D, N>, sm)) != cudaSuccess) return e;
         k_lambda<D, N><<<grid, 128, sm, s>>>(p);
+        return cudaGetLastError();
+      }
+      case OP_PACK:
+      case OP_UNPACK: {
+        Box bx;
+        bx.count = 1;
+        for (int k = 0; k < 3; ++k) {
+          bx.lo[k] = k < D ? a.box[k] : 0;
+          bx.hi[k] = k < D ? a.box[3 + k] : 1;
+          bx.count *= bx.hi[k] - bx.lo[k];
+        }
+        const int gb = (int)(bx.count < kNumSM * 8 ? bx.count : kNumSM * 8);
+        if (a.op == OP_PACK) {
+          k_pack<D, N><<<gb, 128, 0, s>>>(p, bx, a.buf);
+          return cudaGetLastError();
+        }
+        k_unpack<D, N><<<gb, 128, 0, s>>>(p, bx, a.buf);
+        if ((e = cudaMemsetAsync(p.b.counters + CNT_TROUBLED0 + (1 - p.cur), 0, sizeof(int), s)) !=
+            cudaSuccess)
+          return e;
+        k_relist<D, N><<<cells_grid(p.geo.cells < kNumSM * 64 ? p.geo.cells : kNumSM * 64), 128, 0, s>>>(
+            p, bx, a.buf);
+        k_copyback<D, N><<<kNumSM * 4, 256, 0, s>>>(p);
         return cudaGetLastError();
       }
       case OP_SUB_MINMAX:
