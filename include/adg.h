@@ -46,6 +46,17 @@
  *                        degree-2 predictor and sub-face fluxes
  *                        (ADG_OPT_SUBCELL_FP32), wave-speed square roots.
  *                        Conservation stays at FP64 round-off.
+ *   ADG_PREC_MIXED_TF32  ADG_PREC_MIXED_FP32 with the predictor's Picard
+ *                        contractions on the tensor pipe (ADG_PRED_WARP4_TC:
+ *                        TF32 operands split into high and low parts, three
+ *                        mma products per tile, FP32 accumulation, which keeps
+ *                        them FP32-accurate); 2D N <= 5 and 3D.
+ *   (A BF16 mode is not provided: BF16 operands need three-way splits and six
+ *   products per tile to reach FP32 accuracy, which the mixed scheme's final
+ *   stage needs, and the contractions here are n x n with n <= 10.)
+ * Accuracy bar of the mixed modes (tested on the benchmark workloads): the
+ * relative L1 distance to the FP64 path per conserved variable after the same
+ * steps is at most 1% of the FP64 scheme's own L1 error on that workload.
  */
 #ifndef ADG_H
 #define ADG_H
@@ -94,6 +105,7 @@ extern "C" {
 
 #define ADG_PREC_FP64 0
 #define ADG_PREC_MIXED_FP32 1
+#define ADG_PREC_MIXED_TF32 2
 
 /* adg_set_option keys */
 #define ADG_OPT_DMP_EPS 1         /* eps of Eq. (relax), default 1e-3                 */

@@ -21,7 +21,7 @@ OK = 0
 ERR_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_CAPACITY, ERR_STATE = -1, -2, -3, -4, -5, -6
 WARN_SUBCELL_INADMISSIBLE = 1
 BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_INFLOW, BC_FRONT = 0, 1, 2, 3, 4
-PREC_FP64, PREC_MIXED_FP32 = 0, 1
+PREC_FP64, PREC_MIXED_FP32, PREC_MIXED_TF32 = 0, 1, 2
 OPT_DMP_EPS, OPT_DMP_FLOOR, OPT_FORCE_LIMITER, OPT_PICARD_ITERS, OPT_SLOT_CAPACITY = 1, 2, 3, 4, 5
 OPT_PROFILE = 6
 OPT_FP64_SWEEPS = 7

@@ -1061,7 +1061,10 @@ int adg_create(const adg_grid* grid, int N, double gamma, const int* bc, int pre
   if (grid->dim != 2 && grid->dim != 3) return ADG_ERR_ARG;
   if (N < 1 || N > 9 || (grid->dim == 3 && N > 3)) return ADG_ERR_ARG;
   if (!(gamma > 1.0)) return ADG_ERR_ARG;
-  if (prec != ADG_PREC_FP64 && prec != ADG_PREC_MIXED_FP32) return ADG_ERR_ARG;
+  if (prec != ADG_PREC_FP64 && prec != ADG_PREC_MIXED_FP32 && prec != ADG_PREC_MIXED_TF32)
+    return ADG_ERR_ARG;
+  // the tensor-pipe contractions exist for the split final stage (2D N <= 5, 3D)
+  if (prec == ADG_PREC_MIXED_TF32 && grid->dim == 2 && N >= 6) return ADG_ERR_ARG;
   for (int k = 0; k < grid->dim; ++k) {
     if (grid->n[k] < 1 || !(grid->dx[k] > 0.0)) return ADG_ERR_ARG;
     const int lo = bc[2 * k], hi = bc[2 * k + 1];
@@ -1077,7 +1080,9 @@ int adg_create(const adg_grid* grid, int N, double gamma, const int* bc, int pre
   st->dim = grid->dim;
   st->N = N;
   st->nv = grid->dim + 2;
-  st->prec = prec;
+  // ADG_PREC_MIXED_TF32 is the mixed mode with the tensor-pipe predictor shape
+  st->prec = prec == ADG_PREC_MIXED_TF32 ? ADG_PREC_MIXED_FP32 : prec;
+  if (prec == ADG_PREC_MIXED_TF32) st->pred_opt = PRED_WARP4_TC;
   st->gamma = gamma;
   st->iters = N + 1;
   // mixed precision: up to N = 5 the last FP32 sweep closes on the FP64 u

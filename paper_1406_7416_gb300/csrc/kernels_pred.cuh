@@ -332,18 +332,30 @@ __global__ void __launch_bounds__(32 * W) k_predictor_split(Batch bt) {
         __syncwarp();
       }
       const float* dq = Ff;
-      // trace(dq) in FP32, the split trace layout of k_predictor
+      // trace(dq) in FP32 (the split trace layout of k_predictor: per cell,
+      // axis k and side s a block of NV NT doubles, trace(u) [NV][NF] in FP64
+      // then trace(dq) [NV][NT] in FP32), by lines: the n nodes of each line
+      // along axis k give the traces on both faces normal to k, and the line's
+      // index r within its variable is the trace's index ts + NF m
       double* tr = p.b.trace + cell * (size_t)(D * 2 * NV * NT);
-      for (int e = lane; e < D * 2 * NV * NT; e += 32) {
-        int base, stk, s;
-        const int v = trace_index<D, n>(e, base, stk, s);
-        const float* ph = s ? ph1f : ph0f;
-        const float* d = dq + v * NST + base;
-        float acc = 0.0f;
 #pragma unroll
-        for (int a = 0; a < n; ++a) acc += ph[a] * d[a * stk];
-        const int blk = e / (NV * NT);
-        reinterpret_cast<float*>(tr + blk * (NV * NT) + NV * NF)[e - blk * (NV * NT)] = acc;
+      for (int k = 0; k < D; ++k) {
+        constexpr int NL = NST / n;
+        const int st = (k == 0) ? 1 : (k == 1 ? n : n * n);
+        float* t0 = reinterpret_cast<float*>(tr + (2 * k) * (NV * NT) + NV * NF);
+        float* t1 = reinterpret_cast<float*>(tr + (2 * k + 1) * (NV * NT) + NV * NF);
+        for (int e = lane; e < NV * NL; e += 32) {
+          const int v = e / NL, r = e - v * NL;
+          const float* d = dq + v * NST + r % st + (r / st) * (st * n);
+          float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+          for (int a = 0; a < n; ++a) {
+            a0 += ph0f[a] * d[a * st];
+            a1 += ph1f[a] * d[a * st];
+          }
+          t0[v * NT + r] = a0;
+          t1[v * NT + r] = a1;
+        }
       }
       // time-averaged flux changes per spatial node, into qf: the products
       // w_m G rounded, then summed over m in order (as k_predictor does)
@@ -396,20 +408,28 @@ __global__ void __launch_bounds__(32 * W) k_predictor_split(Batch bt) {
         for (int v = 0; v < NV; ++v)
           fb[(k * NV + v) * ND + i] = Fl[k][v] + (double)dF[(k * NV + v) * ND + i];
     }
-    // trace(u) in FP64 (time node 0 of the split layout)
-    for (int t = tid; t < W * D * 2 * NV * NF; t += 32 * W) {
-      const int ww = t / (D * 2 * NV * NF), e = t - ww * (D * 2 * NV * NF);
+    // trace(u) in FP64 (the split layout's [NV][NF] part), by lines of n
+    // spatial nodes along axis k: both faces normal to k from one line
+    for (int t = tid; t < W * D * NV * NF; t += 32 * W) {
+      const int ww = t / (D * NV * NF);
+      int e = t - ww * (D * NV * NF);
       if (!s_on[ww]) continue;
+      const int k = e / (NV * NF);
+      e -= k * (NV * NF);
+      const int v = e / NF, r = e - v * NF;
+      const int st = (k == 0) ? 1 : (k == 1 ? n : n * n);
       const Params& p = *s_pp[ww];
-      const double* uu = reinterpret_cast<const double*>(cells0 + (size_t)ww * LY::cell_bytes);
-      double* tr = p.b.trace + s_cell[ww] * (size_t)(D * 2 * NV * NT);
-      int base, stk, s;
-      const int v = trace_index<D, n>((e / NF) * NT + e % NF, base, stk, s);
-      const double* ph = s ? ph1 : ph0;
-      double acc = 0.0;
+      const double* uu = reinterpret_cast<const double*>(cells0 + (size_t)ww * LY::cell_bytes) +
+                         v * ND + r % st + (r / st) * (st * n);
+      double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-      for (int a = 0; a < n; ++a) acc += ph[a] * uu[v * ND + base + a * stk];
-      tr[(e / (NV * NF)) * (NV * NT) + e % (NV * NF)] = acc;
+      for (int a = 0; a < n; ++a) {
+        a0 += ph0[a] * uu[a * st];
+        a1 += ph1[a] * uu[a * st];
+      }
+      double* tr = p.b.trace + s_cell[ww] * (size_t)(D * 2 * NV * NT);
+      tr[(2 * k) * (NV * NT) + v * NF + r] = a0;
+      tr[(2 * k + 1) * (NV * NT) + v * NF + r] = a1;
     }
     __syncthreads();
     // B2: the volume part of the candidate, u + sum_k c_k Mvol x_k fbar_k

@@ -136,12 +136,17 @@ struct Launch {
       if (kSplit && sl.pred == PRED_WARP4_TC) return launch_split<4, true>(cells, sl.total_cells, s);
       const size_t sm = predictor_smem_bytes<D, N, true>();
       if ((e = set_smem(k_predictor<D, N, true>, sm)) != cudaSuccess) return e;
-      k_predictor<D, N, true><<<grid, pred_threads<true>(), sm, s>>>(cells);
+      static const int gp = persistent_grid(k_predictor<D, N, true>, pred_threads<true>(), sm, 1LL << 40);
+      k_predictor<D, N, true><<<grid < gp ? grid : gp, pred_threads<true>(), sm, s>>>(cells);
     } else {
       const size_t sm = predictor_smem_bytes<D, N, false>();
       if ((e = set_smem(k_predictor<D, N, false>, sm)) != cudaSuccess) return e;
-      const int th = sl.pred == PRED_BLOCK_WIDE ? wide_threads() : pred_threads<false>();
-      k_predictor<D, N, false><<<grid, th, sm, s>>>(cells);
+      const bool wide = sl.pred == PRED_BLOCK_WIDE;
+      const int th = wide ? wide_threads() : pred_threads<false>();
+      static const int gn = persistent_grid(k_predictor<D, N, false>, pred_threads<false>(), sm, 1LL << 40);
+      static const int gw = persistent_grid(k_predictor<D, N, false>, wide_threads(), sm, 1LL << 40);
+      const int gmax = wide ? gw : gn;
+      k_predictor<D, N, false><<<grid < gmax ? grid : gmax, th, sm, s>>>(cells);
     }
     return cudaGetLastError();
   }
@@ -169,7 +174,9 @@ struct Launch {
     mark(ev, PHASE_CORRECT, s);
     const size_t sc = correct_smem_bytes<D, N>();
     if ((e = set_smem(k_correct_detect<D, N>, sc)) != cudaSuccess) return e;
-    k_correct_detect<D, N><<<grid, 128, sc, s>>>(cells);
+    // persistent: the operator set-up of each block is done once for many cells
+    static const int grid_cd = persistent_grid(k_correct_detect<D, N>, 128, sc, 1LL << 40);
+    k_correct_detect<D, N><<<(int)(sl.total_cells < grid_cd ? sl.total_cells : grid_cd), 128, sc, s>>>(cells);
     return cudaGetLastError();
   }
 

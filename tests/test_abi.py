@@ -118,3 +118,14 @@ def test_predictor_shapes_that_do_not_apply_are_refused(lib):
         mx5.set_option(adg.OPT_PREDICTOR, adg.PRED_WARP4)
     for s in (f64, mx5, mx7):
         s.close()
+
+
+def test_tf32_precision_mode(lib):
+    """ADG_PREC_MIXED_TF32 exists where the tensor-pipe predictor shape does
+    (2D N <= 5, 3D) and is refused elsewhere."""
+    s = adg.Solver(2, (4, 4), (0, 0), (0.1, 0.1), (0, 0, 0, 0), 5, prec=adg.PREC_MIXED_TF32)
+    s.close()
+    s = adg.Solver(3, (2, 2, 2), (0, 0, 0), (0.1,) * 3, (0,) * 6, 3, prec=adg.PREC_MIXED_TF32)
+    s.close()
+    with pytest.raises(adg.AdgError):
+        adg.Solver(2, (4, 4), (0, 0), (0.1, 0.1), (0, 0, 0, 0), 6, prec=adg.PREC_MIXED_TF32)

@@ -76,11 +76,11 @@ def _refined(w):
     return f
 
 
-def mixed_bar(w, steps, opts=None):
+def mixed_bar(w, steps, opts=None, prec=adg.PREC_MIXED_FP32):
     """(d, e, info of the mixed run): mixed-vs-FP64 distance and the FP64
     scheme error (Richardson estimate from the refined run), per variable."""
     U64, dts, _ = _run(w, adg.PREC_FP64, steps=steps)
-    Umx, _, info = _run(w, adg.PREC_MIXED_FP32, dts=dts, opts=opts)
+    Umx, _, info = _run(w, prec, dts=dts, opts=opts)
     Uf, _, _ = _run(_refined(w), adg.PREC_FP64, dts=dts, substeps=2)
     dim, N = w["dim"], w["N"]
     Wd = weights(dim, N + 1)
@@ -119,6 +119,16 @@ def test_mixed_bar_holds_for_every_predictor_shape(shape):
     d, e, info, _, _ = mixed_bar(make(), steps, opts={adg.OPT_PREDICTOR: shape})
     assert info["predictor"] == shape
     assert np.all(d <= BAR * e), (shape, d, e)
+
+
+@pytest.mark.parametrize("name", ["quadvortex_N5_64", "explosion3d_N3_16"])
+def test_tf32_precision_mode_meets_the_bar(name):
+    """ADG_PREC_MIXED_TF32: the mixed mode with the predictor's contractions on
+    the tensor pipe, under the same bar."""
+    make, steps = CASES[name]
+    d, e, info, _, _ = mixed_bar(make(), steps, prec=adg.PREC_MIXED_TF32)
+    assert info["predictor"] == adg.PRED_WARP4_TC
+    assert np.all(d <= BAR * e), (d, e)
 
 
 def test_mixed_against_the_oracle():
