@@ -292,6 +292,47 @@ __device__ __forceinline__ void euler_fluxes(const T* Q, T gm1, T (*F)[D + 2]) {
   }
 }
 
+// Conversions and tests on the integer pipe.  GB300 runs every FP64
+// instruction -- conversions between FP32 and FP64 and FP64 comparisons
+// included -- on its narrow FP64 pipe (about the rate of an FP64 FMA, measured),
+// so the kernels whose FP64 work bounds them use these bit-level forms.
+
+#if defined(__CUDACC__)
+// x > 0, exactly the FP64 comparison (false for NaN, +0 and -0).
+__device__ __forceinline__ bool positive_f64(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b <= 0x7ff0000000000000LL;
+}
+
+__device__ __forceinline__ bool isnan_f64(double x) {
+  return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+}
+
+// FP32 -> FP64 widening: exact for normal numbers, infinities and NaNs; FP32
+// subnormals (|x| < 2^-126) become zeros of their sign.
+__device__ __forceinline__ double widen_f32(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned s = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  if (e == 0) return __hiloint2double((int)s, 0);
+  const unsigned e11 = (e == 0xffu) ? 0x7ffu : e + 896u;   // rebias 127 -> 1023
+  return __hiloint2double((int)(s | (e11 << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// FP64 -> FP32 narrowing toward zero: the top 23 mantissa bits; magnitudes
+// below the FP32 normal range give zeros of their sign, above it the largest
+// finite float; infinities stay, NaNs stay NaN.
+__device__ __forceinline__ float narrow_f64_rz(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned s = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  if (e == 0x7ff) return __uint_as_float(s | ((((hi & 0xfffffu) | lo) != 0u) ? 0x7fc00000u : 0x7f800000u));
+  const int e8 = e - 896;
+  if (e8 <= 0) return __uint_as_float(s);
+  if (e8 >= 255) return __uint_as_float(s | 0x7f7fffffu);
+  return __uint_as_float(s | ((unsigned)e8 << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+#endif
+
 __device__ __forceinline__ double nanmax(double a, double b) {
   // max that propagates NaN from either argument
   return (a > b || a != a) ? a : b;
@@ -498,23 +539,24 @@ __device__ __forceinline__ double wave_speed(const double* Q, double gamma) {
 
 // The same speed for mixed precision (it only sets the CFL step): rho p =
 // (gamma - 1)(E rho - |m|^2 / 2) in FP64, free of the cancellation FP32 would
-// suffer at high Mach numbers, then c = sqrt(gamma rho p) / rho and the
-// velocities in FP32.  Inadmissible states give NaN as in wave_speed.
+// suffer at high Mach numbers (pe = E rho - |m|^2 / 2 from the caller, which
+// tests it for positivity), then c = sqrt(gamma rho p) / rho and the
+// velocities in FP32 from inputs narrowed toward zero on the integer pipe.
+// Inadmissible states give NaN as in wave_speed.
+#if defined(__CUDACC__)
 template <int D>
-__device__ __forceinline__ double wave_speed_f(const double* Q, double gamma) {
-  double kin = 0.0;
-#pragma unroll
-  for (int k = 0; k < D; ++k) kin += Q[1 + k] * Q[1 + k];
-  const double rp = (gamma - 1.0) * (Q[D + 1] * Q[0] - 0.5 * kin);
-  const float r = 1.0f / (float)Q[0];
+__device__ __forceinline__ double wave_speed_f(const double* Q, double pe, double gamma) {
+  const double rp = (gamma - 1.0) * pe;
+  const float r = 1.0f / narrow_f64_rz(Q[0]);
   float vm = 0.0f;
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    const float a = fabsf((float)Q[1 + k]) * r;
+    const float a = fabsf(narrow_f64_rz(Q[1 + k])) * r;
     vm = (a > vm || a != a) ? a : vm;
   }
-  return (double)(vm + sqrtf((float)(gamma * rp)) * r);
+  return widen_f32(vm + sqrtf(narrow_f64_rz(gamma * rp)) * r);
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // Grid helpers

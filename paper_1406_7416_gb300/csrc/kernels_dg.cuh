@@ -886,6 +886,17 @@ __device__ __forceinline__ int tangential(int i, int k) {
   return ts;
 }
 
+// Order-preserving map of a double onto a signed 64-bit key (x < y <=> key(x)
+// < key(y) for non-NaN x, y; +NaN above +inf), so that min / max reductions
+// run on the integer pipe instead of the FP64 pipe.
+__device__ __forceinline__ long long ord_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double ord_val(long long k) {
+  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
+}
+
 // Detector bounds over the Voronoi neighbourhood (3^d block) from per-cell
 // min/max, then the relaxed DMP interval [m - delta, M + delta] (Eq. relax
 // with a relative floor).  Threads v < nvar write lohi[2v], lohi[2v+1].
@@ -896,7 +907,9 @@ __device__ __forceinline__ void dmp_interval(const Params& p, const double* __re
   const int v = threadIdx.x;
   if (v >= NV) return;
   const Geo& g = p.geo;
-  double mn = INFINITY, mx = -INFINITY;
+  // min / max on order-preserving integer keys (the integer pipe), NaNs
+  // skipped as fmin / fmax skip them
+  long long kmn = LLONG_MAX, kmx = LLONG_MIN;
   const int nb3 = ipow(3, D);
   for (int o = 0; o < nb3; ++o) {
     int c[3] = {0, 0, 0}, oo = o;
@@ -923,24 +936,18 @@ __device__ __forceinline__ void dmp_interval(const Params& p, const double* __re
     if (!in) continue;
     const long long nb = cell_index<D>(c, g);
     const double lo = cmm[(nb * NV + v) * 2 + 0], hi = cmm[(nb * NV + v) * 2 + 1];
-    mn = fmin(mn, flip ? -hi : lo);
-    mx = fmax(mx, flip ? -lo : hi);
+    // the mirror image's bounds: negated (sign bit) and swapped
+    const double l2 = flip ? __longlong_as_double(__double_as_longlong(hi) ^ LLONG_MIN) : lo;
+    const double h2 = flip ? __longlong_as_double(__double_as_longlong(lo) ^ LLONG_MIN) : hi;
+    if (!isnan_f64(l2)) kmn = min(kmn, ord_key(l2));
+    if (!isnan_f64(h2)) kmx = max(kmx, ord_key(h2));
   }
+  const double mn = kmn == LLONG_MAX ? INFINITY : ord_val(kmn);
+  const double mx = kmx == LLONG_MIN ? -INFINITY : ord_val(kmx);
   const double scale = fmax(1.0, fmax(fabs(mx), fabs(mn)));
   const double delta = fmax(p.eps * (mx - mn), p.floor * scale);
   lohi[2 * v] = mn - delta;
   lohi[2 * v + 1] = mx + delta;
-}
-
-// Order-preserving map of a double onto a signed 64-bit key (x < y <=> key(x)
-// < key(y) for non-NaN x, y; +NaN above +inf), so that min / max reductions
-// run on the integer pipe instead of the FP64 pipe.
-__device__ __forceinline__ long long ord_key(double x) {
-  const long long b = __double_as_longlong(x);
-  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
-}
-__device__ __forceinline__ double ord_val(long long k) {
-  return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
 }
 
 // Max-reduces K integer keys per thread over the block (blockDim a multiple of
@@ -994,9 +1001,11 @@ __device__ __forceinline__ bool check_subcells(const double* __restrict__ vs, in
     double kin = 0.0;
 #pragma unroll
     for (int k = 0; k < D; ++k) kin += Q[1 + k] * Q[1 + k];
-    bad = bad || !((Q[0] > 0.0) && (Q[D + 1] * Q[0] - 0.5 * kin > 0.0));
+    const double pe = Q[D + 1] * Q[0] - 0.5 * kin;
+    // the two PAD comparisons as exact integer tests
+    bad = bad || !(positive_f64(Q[0]) && positive_f64(pe));
     if (lam)
-      r[2 * NV] = max(r[2 * NV], ord_key(f32speed ? wave_speed_f<D>(Q, gamma) : wave_speed<D>(Q, gamma)));
+      r[2 * NV] = max(r[2 * NV], ord_key(f32speed ? wave_speed_f<D>(Q, pe, gamma) : wave_speed<D>(Q, gamma)));
   }
   bad = __syncthreads_or(bad);
   const long long* res = block_max_keys<K>(r, reinterpret_cast<long long*>(red));
@@ -1007,9 +1016,14 @@ __device__ __forceinline__ bool check_subcells(const double* __restrict__ vs, in
     mx[v] = ord_val(res[2 * v + 1]);
   }
   if (lohi) {
+    // the DMP test on the extremes, by one warp (the others would repeat it)
+    int dmp = 0;
+    if (threadIdx.x < 32) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v)
-      bad = bad || !((mn[v] >= lohi[2 * v]) && (mx[v] <= lohi[2 * v + 1]));
+      for (int v = 0; v < NV; ++v)
+        dmp |= !((mn[v] >= lohi[2 * v]) && (mx[v] <= lohi[2 * v + 1]));
+    }
+    bad = __syncthreads_or(bad || dmp);
   }
   if (threadIdx.x == 0) {
 #pragma unroll
@@ -1100,7 +1114,7 @@ __global__ void __launch_bounds__(128, 8) k_correct_detect(Batch bt) {
     if (delta) {
       const float* dv = apply_ct<D, NV, n, Ns, float>(dA, dB, P1f, tid, nth);
       for (int e = tid; e < NV * NSD; e += nth) {
-        const double x = vkeep[e] + (double)dv[e];
+        const double x = vkeep[e] + widen_f32(dv[e]);
         A[e] = x;
         vkeep[e] = x;
       }

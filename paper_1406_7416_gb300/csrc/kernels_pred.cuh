@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(32 * W) k_predictor_split(Batch bt) {
       for (int k = 0; k < D; ++k)
 #pragma unroll
         for (int v = 0; v < NV; ++v)
-          fb[(k * NV + v) * ND + i] = Fl[k][v] + (double)dF[(k * NV + v) * ND + i];
+          fb[(k * NV + v) * ND + i] = Fl[k][v] + widen_f32(dF[(k * NV + v) * ND + i]);
     }
     // trace(u) in FP64 (the split layout's [NV][NF] part), by lines of n
     // spatial nodes along axis k: both faces normal to k from one line
