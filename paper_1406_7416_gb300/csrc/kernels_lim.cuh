@@ -598,6 +598,66 @@ __global__ void __launch_bounds__(256) k_lim_predict(Batch bt, int pass, int n32
   }
 }
 
+// L4 in mixed precision with the whole subcell predictor in FP32 (the default
+// of the FP32 subcell scheme): one warp per subcell, W subcells per block,
+// each warp synchronised by __syncwarp alone (the per-subcell arithmetic of
+// k_lim_predict's QF path, none of its block barriers, and no thread group
+// straddling two warps).  The blocks loop over the pass's subcells.
+template <int D>
+struct LimWarps {
+  static constexpr int W = (D == 2) ? 8 : 4;     // subcells per block (static shared memory)
+};
+
+template <int D, int N>
+__global__ void __launch_bounds__(32 * LimWarps<D>::W) k_lim_predict_w(Batch bt) {
+  using DM = Dims<D, N>;
+  constexpr int NV = DM::NV, NST3 = DM::NST3, ND3 = DM::ND3, NED = DM::NED, Ns = DM::Ns;
+  constexpr int NCROSS = DM::NSD + 2 * D * DM::NSF;
+  constexpr int W = LimWarps<D>::W;
+  __shared__ float suf[W][NV * ND3];
+  __shared__ float sqf[W][NV * NST3];
+  __shared__ float sFf[W][D * NV * NST3];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float* u = suf[w];
+  float* q = sqf[w];
+  float* F = sFf[w];
+  const long long total = bt.pre[bt.n] * NCROSS;
+  for (long long item = (long long)blockIdx.x * W + w; item < total;
+       item += (long long)gridDim.x * W) {
+    const long long tg = item / NCROSS;
+    const LimItem it = lim_item(bt, tg);
+    const Params& p = *bt.pps[it.s];
+    const long long j = it.j;
+    const int sc = cross_subcell<D, Ns>((int)(item - tg * NCROSS));
+    float cf[3];
+#pragma unroll
+    for (int k = 0; k < D; ++k) cf[k] = (float)p.b.coef[3 + k];
+    const float gm1 = (float)(p.gamma - 1.0);
+    const float* Wr = reinterpret_cast<const float*>(p.b.sweep[D - 1]);   // [j][v][NED][ND3]
+    for (int e = lane; e < NV * ND3; e += 32) {
+      const int v = e / ND3, i = e - v * ND3;
+      u[e] = Wr[((j * NV + v) * NED + sc) * ND3 + i];
+    }
+    __syncwarp();
+    for (int e = lane; e < NV * NST3; e += 32) {
+      const int v = e / NST3, l = e - v * NST3;
+      q[e] = u[v * ND3 + (l % ND3)];
+    }
+    __syncwarp();
+    for (int sweep = 0; sweep < 3; ++sweep) {
+      picard_flux<D, 3, float>(q, F, gm1, lane, 32);
+      __syncwarp();
+      picard_deriv_sub<D>(F, q, cf, lane, 32);
+      __syncwarp();
+      picard_time_sub<D>(q, u, lane, 32);
+      __syncwarp();
+    }
+    float* dst = reinterpret_cast<float*>(p.b.qsub) + ((size_t)j * NED + sc) * (size_t)(NV * NST3);
+    for (int e = lane; e < NV * NST3; e += 32) dst[e] = q[e];
+    __syncwarp();
+  }
+}
+
 // L5: sub-face fluxes normal to axis k: Rusanov at the 3^(d-1) x 3
 // tangential x time GL points, averaged with the GL weights.  Faces f = 0..Ns
 // along k (between local subcells f-1 and f), tangential subcells 0..Ns-1.
