@@ -364,6 +364,7 @@ def run_gpu(args):
     rep.barrier()
     adg.load_library()
     stream = torch.cuda.Stream()
+    rates = adg.pipe_rates()            # measured arithmetic-pipe rates, beside the derived peaks
     main_wl, main_grid = WORKLOAD, GRID_SET
     m = measure(args, main_wl, main_grid, args.steps, args.warmup, stream, rep, clocks=True,
                 keep=True, floor_run=(args.only == "both" and not args.no_extras))
@@ -409,7 +410,7 @@ def run_gpu(args):
                         "status": mx["status"], "steps": 5, "warmup": 3}
     globals()["WORKLOAD"], globals()["GRID_SET"] = main_wl, main_grid
     if rank == 0:
-        emit_line(args, m, e2e, world, tune, subs)
+        emit_line(args, m, e2e, world, tune, subs, rates)
     rep.close()
 
 
@@ -447,7 +448,7 @@ def end_to_end(s, args, stdofs, world, cfl, barrier, max_over_ranks):
                      "pinned host, then adg_read of the DOFs"}
 
 
-def emit_line(args, m, e2e, world, tune, subs):
+def emit_line(args, m, e2e, world, tune, subs, rates=None):
     from paper_1406_7416_gb300 import adg
     w, results = m["w"], m["results"]
     D, N, n, cells, stdofs = m["D"], m["N"], m["n"], m["cells"], m["stdofs"]
@@ -509,10 +510,16 @@ def emit_line(args, m, e2e, world, tune, subs):
                      "pipe_time_ms": {"fp64": t64 * 1e3, "fp32": t32 * 1e3},
                      "traffic": traffic["bytes_per_launch"] if traffic else None},
         "autotune_ms_per_launch": tune,
+        "pipe_rates_measured": ({k: v for k, v in rates.items()} if rates else None),
         "e2e": e2e,
         "gpu_launches": int(mx["launches"]),
         "clocks": mx["clocks"],
     }
+    if rates:
+        # the same kernel against the measured pipe rate (adg_pipe_rates: FMA = 2 flop)
+        meas = 2.0 * rates["dfma" if pipe == "fp64" else "ffma"] / 1e12
+        line["roofline"]["peak_measured"] = meas
+        line["roofline"]["frac_of_measured"] = achieved / meas
     if "dmp_floor" in m:
         line["dmp_floor"] = m["dmp_floor"]
     if subs:
@@ -539,11 +546,30 @@ def run_serving(args):
     specs = inputs.serving_runs(count=args.runs)
     for w in specs:
         w["t_end"] = min(w["t_end"], args.t_end)
-    runs = [RunSpec(w, w["t_end"], 0.0, i) for i, w in enumerate(specs)]
+    # capacity from a closed-loop pass (all runs at t = 0) over the first
+    # --capacity-runs runs (all by default), scaled to the whole stream by work
+    ncap = args.capacity_runs or len(specs)
+    runs = [RunSpec(w, w["t_end"], 0.0, i) for i, w in enumerate(specs[:ncap])]
     closed = Server(budget, adg.PREC_MIXED_FP32).serve(runs, max_wall=args.max_wall)
     print(json.dumps({"closed_loop": closed}), file=sys.stderr, flush=True)
     capacity = closed["runs"] / closed["wall_s"]
     rate = 0.8 * capacity
+    # single-grid reference rates: one 256^2 run alone per degree, 20 CFL steps
+    single = {}
+    for N in (3, 5):
+        w = inputs.riemann_2d(256, N, 3)
+        sv = adg.Solver.from_workload(w, adg.PREC_MIXED_FP32)
+        sv.init_problem(w["problem"])
+        for _ in range(3):
+            sv.step_cfl(w["cfl"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(20):
+            sv.step_cfl(w["cfl"])
+        sv.status()
+        el = time.perf_counter() - t0
+        single[f"256^2 N={N}"] = 256 * 256 * (N + 1) ** 3 * 20 / el
+        sv.close()
     arrivals = poisson_arrivals(len(specs), rate, seed=1406 + 4)
     runs = [RunSpec(w, w["t_end"], a, i) for i, (w, a) in enumerate(zip(specs, arrivals))]
     opened = Server(budget, adg.PREC_MIXED_FP32).serve(runs, max_wall=args.max_wall)
@@ -556,7 +582,8 @@ def run_serving(args):
                                    "Poisson arrivals at 80% of the measured capacity",
                        "hbm_budget_bytes": budget, "mixed precision": True},
             "latency_p50_s": opened["latency_p50_s"], "latency_p99_s": opened["latency_p99_s"],
-            "closed_loop": closed, "open_loop": opened, "arrival_rate_per_s": rate}
+            "single_grid_rate": single, "closed_loop": closed, "open_loop": opened,
+            "arrival_rate_per_s": rate, "capacity_runs": ncap}
     print(json.dumps(line), flush=True)
 
 
@@ -615,6 +642,8 @@ def main():
     ap.add_argument("--runs", type=int, default=32, help="serving: number of runs")
     ap.add_argument("--t-end", type=float, default=0.02,
                     help="serving: end time cap of every run (each stops at min(cap, its final time))")
+    ap.add_argument("--capacity-runs", type=int, default=0,
+                    help="serving: runs of the closed-loop capacity pass (0: all)")
     ap.add_argument("--max-wall", type=float, default=120.0,
                     help="serving: no admissions after this many seconds per pass")
     args = ap.parse_args()

@@ -485,6 +485,17 @@ int adg_halo_bytes(const adg_state* st, int64_t count, int64_t* bytes);
 int adg_pack_cells(adg_state* st, const int* lo, const int* hi, void* buf);
 int adg_unpack_cells(adg_state* st, const int* lo, const int* hi, const void* buf);
 
+/* Arithmetic-pipe rates of the current device (no counterpart in the paper;
+ * the step's kernels are bound by these pipes, and they are the denominators
+ * the roofline figures are checked against): out[0] FP64 FMA, out[1] FP32 FMA,
+ * out[2] FP64 -> FP32 conversion, out[3] FP64 comparison, each in thread
+ * operations per second (an FMA is two flop), from 3 timed runs of a
+ * dependency-chain kernel over 8 blocks of 256 threads per multiprocessor
+ * (best of the last two).  Allocates and frees one scratch buffer;
+ * synchronizes the device.  Needs cap >= 4.  Errors: ADG_ERR_ARG,
+ * ADG_ERR_OOM, ADG_ERR_CUDA. */
+int adg_pipe_rates(double* out, int cap);
+
 /* Free every device buffer of the state and the state itself. */
 void adg_destroy(adg_state* st);
 

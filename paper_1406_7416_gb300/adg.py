@@ -49,7 +49,7 @@ SYMBOLS = ("adg_create", "adg_set_allocator", "adg_set_stream", "adg_set_option"
            "adg_subcell_update_noalloc", "adg_time", "adg_batch_create", "adg_batch_step",
            "adg_batch_destroy", "adg_step_batch", "adg_fallback_count", "adg_set_boundary_state",
            "adg_set_boundary_front", "adg_set_time", "adg_autotune", "adg_troubled_history",
-           "adg_halo_bytes", "adg_pack_cells", "adg_unpack_cells")
+           "adg_halo_bytes", "adg_pack_cells", "adg_unpack_cells", "adg_pipe_rates")
 
 
 class AdgGrid(ctypes.Structure):
@@ -111,6 +111,7 @@ def load_library(path=None):
     lib.adg_phase_times.argtypes = [vp, dp, ip]
     lib.adg_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ip]
     lib.adg_autotune.argtypes = [vp, ip, dp, ip]
+    lib.adg_pipe_rates.argtypes = [dp, ip]
     ipp = ctypes.POINTER(ctypes.c_int)
     lib.adg_halo_bytes.argtypes = [vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     lib.adg_pack_cells.argtypes = [vp, ipp, ipp, vp]
@@ -147,6 +148,16 @@ def _u8ptr(a):
 
 def _contig(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
+
+
+def pipe_rates():
+    """adg_pipe_rates: {pipe: thread operations per second} of the current device."""
+    lib = load_library()
+    out = np.zeros(4)
+    rc = lib.adg_pipe_rates(_dptr(out), 4)
+    if rc != OK:
+        raise AdgError(rc, "adg_pipe_rates failed")
+    return dict(zip(("dfma", "ffma", "f64_to_f32", "f64_compare"), out.tolist()))
 
 
 def subcell_update_noalloc(dim, N, gamma, h, dt, patches_ptr, count, vnew_ptr, faces_ptr=0,

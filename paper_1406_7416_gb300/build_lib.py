@@ -16,7 +16,8 @@ LIB = os.path.join(HERE, "libadg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
                      "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]
-SOURCES = ["adg_api.cu", "k2d_lo.cu", "k2d_hi.cu", "k3d.cu", "noalloc.cu", "ops_host.cpp"]
+SOURCES = ["adg_api.cu", "k2d_lo.cu", "k2d_hi.cu", "k3d.cu", "noalloc.cu", "pipe_probe.cu",
+           "ops_host.cpp"]
 HEADERS = ["adg_internal.h", "kernels_dg.cuh", "kernels_lim.cuh", "kernels_misc.cuh",
            "kernels_pred.cuh",
            "launch.cuh", os.path.join("..", "..", "include", "adg.h")]

@@ -67,13 +67,14 @@ __device__ __forceinline__ void deriv_lines_warp(const float* __restrict__ F, fl
     const int st = (k == 0) ? 1 : (k == 1 ? n : n * n);
     const float ck = c[k];
     for (int e = lane; e < NV * NL; e += 32) {
-      const int v = e / NL, r = e - v * NL;
-      const int base = r % st + (r / st) * (st * n);
-      const float* f = F + (k * NV + v) * NST + base;
+      // line e of variable v = e / NL starts at v NST + (e % st) + ((e % NL) / st) st n,
+      // which is n e - (n - 1)(e % st) (st divides NL and NST = n NL)
+      const int base = n * e - (n - 1) * (e % st);
+      const float* f = F + k * NV * NST + base;
       float x[n];
 #pragma unroll
       for (int j = 0; j < n; ++j) x[j] = f[j * st];
-      float* sl = S + v * NST + base;
+      float* sl = S + base;
 #pragma unroll
       for (int a = 0; a < n; ++a) {
         float acc = 0.0f;
@@ -309,13 +310,64 @@ __global__ void __launch_bounds__(32 * W) k_predictor_split(Batch bt) {
         uf[e] = (float)x;
       }
       __syncwarp();
-      for (int e = lane; e < NV * NST; e += 32) {
-        const int v = e / NST, l = e - v * NST;
-        qf[e] = uf[v * ND + (l % ND)];
+      const int n32 = p.iters;           // all sweeps in FP32 (split final stage)
+      // The first sweep starts from q^0 = u (x) 1, whose fluxes and their
+      // derivatives S are the same at every time node: both phases run on the
+      // n^d spatial nodes only (time slice 0), and q^1_m = u - kappa_m S with
+      // kappa_m = sum_j Ktau[m][j] (dq = -kappa_m S when it is also the last).
+      for (int i = lane; i < ND; i += 32) {
+        float Q[NV], Fl[D][D + 2];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Q[v] = uf[v * ND + i];
+        euler_fluxes<D, float>(Q, gm1f, Fl);
+#pragma unroll
+        for (int k = 0; k < D; ++k)
+#pragma unroll
+          for (int v = 0; v < NV; ++v) Ff[(k * NV + v) * NST + i] = Fl[k][v];
       }
       __syncwarp();
-      const int n32 = p.iters;           // all sweeps in FP32 (split final stage)
-      for (int it = 0; it < n32; ++it) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        constexpr int NLS = ND / n;        // lines of one variable's time slice along an axis
+        const int st = (k == 0) ? 1 : (k == 1 ? n : n * n);
+        const float ck = cf[k];
+        for (int e = lane; e < NV * NLS; e += 32) {
+          const int v = e / NLS, r = e - v * NLS;
+          const int base = v * NST + n * r - (n - 1) * (r % st);
+          float x[n];
+#pragma unroll
+          for (int j = 0; j < n; ++j) x[j] = Ff[k * NV * NST + base + j * st];
+#pragma unroll
+          for (int a = 0; a < n; ++a) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int j = 0; j < n; ++j) acc += c_Dmf[N][a * n + j] * x[j];
+            if (k == 0) qf[base + a * st] = ck * acc;
+            else qf[base + a * st] += ck * acc;
+          }
+        }
+        __syncwarp();
+      }
+      {
+        float kap[n];
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+          float t = 0.0f;
+#pragma unroll
+          for (int j = 0; j < n; ++j) t += c_Ktf[N][m * n + j];
+          kap[m] = t;
+        }
+        float* out = n32 == 1 ? Ff : qf;
+        for (int e = lane; e < NV * ND; e += 32) {
+          const int v = e / ND, i = e - v * ND;
+          const float sv = qf[v * NST + i];
+          const float u0 = n32 == 1 ? 0.0f : uf[e];
+#pragma unroll
+          for (int m = 0; m < n; ++m) out[v * NST + i + m * ND] = u0 - kap[m] * sv;
+        }
+      }
+      __syncwarp();
+      for (int it = 1; it < n32; ++it) {
         picard_flux<D, n, float>(qf, Ff, gm1f, lane, 32);
         __syncwarp();
         if constexpr (TC) tc.deriv(Ff, qf, cf, lane);
@@ -344,17 +396,17 @@ __global__ void __launch_bounds__(32 * W) k_predictor_split(Batch bt) {
         const int st = (k == 0) ? 1 : (k == 1 ? n : n * n);
         float* t0 = reinterpret_cast<float*>(tr + (2 * k) * (NV * NT) + NV * NF);
         float* t1 = reinterpret_cast<float*>(tr + (2 * k + 1) * (NV * NT) + NV * NF);
+        static_assert(NL == NT, "a variable has as many lines along an axis as trace values per side");
         for (int e = lane; e < NV * NL; e += 32) {
-          const int v = e / NL, r = e - v * NL;
-          const float* d = dq + v * NST + r % st + (r / st) * (st * n);
+          const float* d = dq + n * e - (n - 1) * (e % st);
           float a0 = 0.0f, a1 = 0.0f;
 #pragma unroll
           for (int a = 0; a < n; ++a) {
             a0 += ph0f[a] * d[a * st];
             a1 += ph1f[a] * d[a * st];
           }
-          t0[v * NT + r] = a0;
-          t1[v * NT + r] = a1;
+          t0[e] = a0;     // [v][ts + NF m] with v NT + ts + NF m = e
+          t1[e] = a1;
         }
       }
       // time-averaged flux changes per spatial node, into qf: the products

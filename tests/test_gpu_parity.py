@@ -223,3 +223,49 @@ def test_capacity_overflow_is_reported():
         solver.status()
     assert e.value.code == adg.ERR_CAPACITY
     solver.close()
+
+
+def _smooth_rough_state(sch, seed=3):
+    """DOFs of a field that varies in every cell (smooth waves plus a density
+    jump), nodal values at the GL points, no cell flagged."""
+    from oracle import euler
+    from oracle.step import State
+    g = sch.grid
+    n = sch.N + 1
+    xi = 0.5 * (np.polynomial.legendre.leggauss(n)[0] + 1.0)
+    nx, ny = g.ncell
+    X = g.x0[0] + (np.arange(nx)[:, None, None, None] + xi[None, None, :, None]) * g.dx[0]
+    Y = g.x0[1] + (np.arange(ny)[None, :, None, None] + xi[None, None, None, :]) * g.dx[1]
+    X, Y = np.broadcast_arrays(X, Y)                    # (nx, ny, a, b)
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y) + 0.3 * (X > 0.1)
+    vel = [0.3 * np.cos(2 * np.pi * Y), 0.2 * np.sin(2 * np.pi * X)]
+    p = 1.0 + 0.1 * np.cos(2 * np.pi * (X + Y))
+    U = euler.prim_to_cons(rho, vel, p, sch.gamma)
+    nc = tuple(g.ncell)
+    return State(U, np.zeros(nc, dtype=np.int32), np.full((4,) + nc + (sch.Ns,) * 2, np.nan))
+
+
+def test_step_parity_literal_dmp():
+    """The literal Eq. (relax), delta = eps (M - m) with no floor (ADG_OPT_DMP_FLOOR
+    = 0), against the oracle run with floor 0, on a field that varies in every
+    cell: the same bar as the other parity cases.  Without the floor smooth
+    extrema are flagged too, so the step limits many cells."""
+    w = inputs.quadrants_2d(n=4, N=3)
+    w["ncell"], w["x0"], w["dx"] = (10, 8), (0.0, 0.0), (0.1, 0.125)
+    w["bc"] = (0, 0, 0, 0)
+    sch, _, _, _ = oracle_setup(w, floor=0.0)
+    st = _smooth_rough_state(sch)
+    solver = adg.Solver.from_workload(w)
+    solver.set_option(adg.OPT_DMP_FLOOR, 0.0)
+    flagged = 0
+    compared = 0
+    for _ in range(2):
+        dt = stable_dt(sch, st, 0.5 * w["cfl"])
+        ref, info, _ = _compare_step(w, sch, st, dt, solver)
+        near = near_threshold_cells(sch, info)
+        compared += int((~neighbourhood_mask(near, 2, _periodic(w))).sum())
+        flagged += int(ref.beta.sum())
+        st = ref
+    solver.close()
+    assert flagged > 0
+    assert compared >= 80                  # most of the 2 x 80 cells were compared
