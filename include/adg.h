@@ -182,20 +182,21 @@ extern "C" {
                                      (Eq. pde.nc.dg2); every shape computes the same
                                      outputs.  -1 (default): after the state's first
                                      step the autotuner times the shapes whose
-                                     outputs are bit for bit the default's (FP64:
-                                     both block widths; mixed: WARP2 and WARP4) and
+                                     outputs are bit for bit the default's (both
+                                     block widths, or WARP1, WARP2 and WARP4 where
+                                     the warp-per-cell shapes apply) and
                                      keeps the fastest (adg_autotune); -2: the same
                                      over every shape that applies, including those
                                      that round differently in FP32 (the tensor-pipe
                                      contractions, the block-per-cell mixed kernel);
                                      or one of:
                                        ADG_PRED_BLOCK       one block per cell
-                                       ADG_PRED_BLOCK_WIDE  one 256-thread block per
-                                                            cell (FP64 only)
-                                       ADG_PRED_WARP2 / 4   mixed precision with no
-                                                            FP64 sweep (2D N <= 5,
+                                       ADG_PRED_BLOCK_ALT   one block per cell at the
+                                                            other block width
+                                       ADG_PRED_WARP1 / 2 / 4  mixed precision with
+                                                            no FP64 sweep (2D N <= 5,
                                                             3D): one warp per cell for
-                                                            the FP32 sweeps, 2 or 4
+                                                            the FP32 sweeps, 1, 2 or 4
                                                             cells per block sharing
                                                             the FP64 terms
                                        ADG_PRED_WARP4_TC    the same, with the sweeps'
@@ -207,10 +208,11 @@ extern "C" {
                                      A shape that does not apply is refused with
                                      ADG_ERR_ARG.                                     */
 #define ADG_PRED_BLOCK 0
-#define ADG_PRED_BLOCK_WIDE 1
+#define ADG_PRED_BLOCK_ALT 1
 #define ADG_PRED_WARP2 2
 #define ADG_PRED_WARP4 3
 #define ADG_PRED_WARP4_TC 4
+#define ADG_PRED_WARP1 5
 
 #define ADG_FLUX_RUSANOV 0
 #define ADG_FLUX_OSHER 1

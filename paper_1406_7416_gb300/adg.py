@@ -35,8 +35,8 @@ OPT_SUBCELL_FP64_SWEEPS = 14
 OPT_SUBCELL_FP32 = 15
 OPT_PROJECT_DELTA = 16
 OPT_PREDICTOR = 17
-PRED_BLOCK, PRED_BLOCK_WIDE, PRED_WARP2, PRED_WARP4, PRED_WARP4_TC = 0, 1, 2, 3, 4
-PRED_NAMES = ("block", "block_wide", "warp2", "warp4", "warp4_tc")
+PRED_BLOCK, PRED_BLOCK_ALT, PRED_WARP2, PRED_WARP4, PRED_WARP4_TC, PRED_WARP1 = 0, 1, 2, 3, 4, 5
+PRED_NAMES = ("block", "block_alt", "warp2", "warp4", "warp4_tc", "warp1")
 FLUX_RUSANOV, FLUX_OSHER = 0, 1
 PHASES = ("predictor", "faceflux", "correct_detect", "limiter", "fix")
 IC_RADIAL, IC_QUADRANT, IC_PLANAR = 0, 1, 2

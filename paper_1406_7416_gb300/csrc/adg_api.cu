@@ -461,20 +461,21 @@ bool split_capable(const adg_state* st) {
 
 // Predictor shapes that apply to the state (PRED_*).
 bool shape_applies(const adg_state* st, int shape) {
-  if (st->prec != ADG_PREC_MIXED_FP32) return shape == PRED_BLOCK || shape == PRED_BLOCK_WIDE;
-  if (shape == PRED_BLOCK) return true;
-  return split_capable(st) &&
-         (shape == PRED_WARP2 || shape == PRED_WARP4 || shape == PRED_WARP4_TC);
+  if (shape == PRED_BLOCK || shape == PRED_BLOCK_ALT) return true;
+  return st->prec == ADG_PREC_MIXED_FP32 && split_capable(st) &&
+         (shape == PRED_WARP1 || shape == PRED_WARP2 || shape == PRED_WARP4 ||
+          shape == PRED_WARP4_TC);
 }
 
 // Shapes whose outputs are bit for bit those of the default shape: the
-// block-per-cell FP64 kernel at any width; the warp-per-cell mixed kernel at
-// 2 or 4 cells per block (the same per-output code).
+// block-per-cell kernel at either width (FP64, and mixed precision with an
+// FP64 sweep); the warp-per-cell mixed kernel at 1, 2 or 4 cells per block
+// (the same per-output code).
 bool shape_same_arith(const adg_state* st, int shape) {
   if (!shape_applies(st, shape)) return false;
-  if (st->prec != ADG_PREC_MIXED_FP32) return true;
-  if (!split_capable(st)) return shape == PRED_BLOCK;
-  return shape == PRED_WARP2 || shape == PRED_WARP4;
+  if (st->prec != ADG_PREC_MIXED_FP32 || !split_capable(st))
+    return shape == PRED_BLOCK || shape == PRED_BLOCK_ALT;
+  return shape == PRED_WARP1 || shape == PRED_WARP2 || shape == PRED_WARP4;
 }
 
 // Shapes the autotuner times: those of the default arithmetic, or with
@@ -1194,7 +1195,7 @@ int adg_set_option(adg_state* st, int key, double value) {
     case ADG_OPT_PREDICTOR:
       if (!(value == -1.0 || value == -2.0 ||
             (value >= 0.0 && value < PRED_COUNT && value == (int)value)))
-        return fail(st, ADG_ERR_ARG, "predictor shape must be -1, -2 (autotune) or 0..4");
+        return fail(st, ADG_ERR_ARG, "predictor shape must be -1, -2 (autotune) or 0..5");
       if (value >= 0.0 && !shape_applies(st, (int)value))
         return fail(st, ADG_ERR_ARG, "that predictor shape does not apply to this state");
       if ((int)value != st->pred_opt) st->pred_tuned = -1;    // tune again in the new mode

@@ -39,6 +39,7 @@ struct Ops {
   double E[9];
   // float copies for the reduced-precision Picard sweeps
   float Df[MAXN * MAXN], Ktf[MAXN * MAXN];
+  float wf[MAXN];             // time weights in FP32 (the split face fluxes)
   // FP32 WENO3 (mixed precision): per stencil k the rows of C for c1, c2
   // (Cf[k][0..2], Cf[k][3..5]) and the nodal values straight from the stencil
   // averages, Wf[k][node * 3 + r] = sum_p E[node][p] C[k][p][r]
@@ -187,14 +188,16 @@ struct StepLaunch {
 // Launch shapes of the predictor (selected per state by the autotuner or the
 // ADG_OPT_PREDICTOR option; every shape computes the same outputs):
 //   PRED_BLOCK      one block per cell (k_predictor), its default threads;
-//   PRED_BLOCK_WIDE one block per cell with 256 threads (FP64 path);
-//   PRED_WARP2/4    mixed precision with the split final stage: one warp per
-//                   cell for the FP32 sweeps, 2 or 4 cells per block sharing
+//   PRED_BLOCK_ALT  one block per cell at the other block width (256 threads
+//                   where the default is 128 or 160, 128 where it is 256; the
+//                   FP32 kernels whose default is their launch bound: 64);
+//   PRED_WARP1/2/4  mixed precision with the split final stage: one warp per
+//                   cell for the FP32 sweeps, 1, 2 or 4 cells per block sharing
 //                   the FP64 terms (k_predictor_split);
 //   PRED_WARP4_TC   the same with the sweeps' contractions on the tensor pipe
 //                   (3 x TF32 mma.sync, FP32-accurate).
-enum PredShapeId { PRED_BLOCK = 0, PRED_BLOCK_WIDE = 1, PRED_WARP2 = 2, PRED_WARP4 = 3,
-                   PRED_WARP4_TC = 4, PRED_COUNT = 5 };
+enum PredShapeId { PRED_BLOCK = 0, PRED_BLOCK_ALT = 1, PRED_WARP2 = 2, PRED_WARP4 = 3,
+                   PRED_WARP4_TC = 4, PRED_WARP1 = 5, PRED_COUNT = 6 };
 
 // Kernel launch interface: one dispatcher per translation unit (2D low N,
 // 2D high N, 3D), selected by dimension and degree.

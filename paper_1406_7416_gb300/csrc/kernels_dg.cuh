@@ -724,7 +724,7 @@ __device__ __forceinline__ float speed_split(const float* U, const float* dQ, fl
 // F_k(u) in FP64 once per face node, the per-time-node parts in FP32.
 template <int D, int n>
 __device__ __forceinline__ void face_split_rusanov(const double* bL, const double* bR, int ts, int k,
-                                                   double gamma, const double* w, double* G) {
+                                                   double gamma, const float* wf, double* G) {
   constexpr int NV = D + 2, NF = ipow(n, D - 1), NT = NF * n;
   const float* dL = reinterpret_cast<const float*>(bL + NV * NF);
   const float* dR = reinterpret_cast<const float*>(bR + NV * NF);
@@ -743,13 +743,15 @@ __device__ __forceinline__ void face_split_rusanov(const double* bL, const doubl
     kinL += uL[1 + j] * uL[1 + j];
     kinR += uR[1 + j] * uR[1 + j];
   }
-  const float rpL = (float)(gm1 * (uL[D + 1] * uL[0] - 0.5 * kinL));
-  const float rpR = (float)(gm1 * (uR[D + 1] * uR[0] - 0.5 * kinR));
+  // the FP32 copies of the FP64 terms, narrowed on the integer pipe (toward
+  // zero: they are the base states of the FP32 per-time-node corrections)
+  const float rpL = narrow_f64_rz(gm1 * (uL[D + 1] * uL[0] - 0.5 * kinL));
+  const float rpR = narrow_f64_rz(gm1 * (uR[D + 1] * uR[0] - 0.5 * kinR));
   float ULf[NV], URf[NV], sumD[NV], sumJ[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    ULf[v] = (float)uL[v];
-    URf[v] = (float)uR[v];
+    ULf[v] = narrow_f64_rz(uL[v]);
+    URf[v] = narrow_f64_rz(uR[v]);
     sumD[v] = 0.0f;
     sumJ[v] = 0.0f;
   }
@@ -768,7 +770,7 @@ __device__ __forceinline__ void face_split_rusanov(const double* bL, const doubl
     const float sL = speed_split<D>(ULf, qL, rpL, gf, gm1f, k);
     const float sR = speed_split<D>(URf, qR, rpR, gf, gm1f, k);
     const float s = (sL > sR || sL != sL) ? sL : sR;     // NaN propagates
-    const float wm = (float)w[m];
+    const float wm = wf[m];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
       sumD[v] += wm * (GL[v] + GR[v]);
@@ -776,10 +778,11 @@ __device__ __forceinline__ void face_split_rusanov(const double* bL, const doubl
     }
     S += wm * s;
   }
+  const double Sd = widen_f32(S);
 #pragma unroll
   for (int v = 0; v < NV; ++v)
-    G[v] = 0.5 * (FL[v] + FR[v]) + 0.5 * (double)sumD[v] -
-           0.5 * ((uR[v] - uL[v]) * (double)S + (double)sumJ[v]);
+    G[v] = 0.5 * (FL[v] + FR[v]) + 0.5 * widen_f32(sumD[v]) -
+           0.5 * ((uR[v] - uL[v]) * Sd + widen_f32(sumJ[v]));
 }
 
 // One thread per (face, tangential node): the Rusanov (or Osher-type) flux at
@@ -831,7 +834,7 @@ __global__ void __launch_bounds__(256, 2) k_faceflux(Batch bt, int k) {
     const bool split = split_traces(p);
     double acc[NV];
     if (split && hasL && hasR && p.flux == ADG_FLUX_RUSANOV) {
-      face_split_rusanov<D, n>(trL, trR, ts, k, p.gamma, w, acc);
+      face_split_rusanov<D, n>(trL, trR, ts, k, p.gamma, p.ops->wf, acc);
 #pragma unroll
       for (int v = 0; v < NV; ++v) G[(face * NV + v) * NF + ts] = acc[v];
       continue;
@@ -901,11 +904,20 @@ __device__ __forceinline__ double ord_val(long long k) {
 // min/max, then the relaxed DMP interval [m - delta, M + delta] (Eq. relax
 // with a relative floor).  Threads v < nvar write lohi[2v], lohi[2v+1].
 template <int D>
+__device__ __forceinline__ void dmp_interval_lane(const Params& p, const double* __restrict__ cmm,
+                                                  const int* ijk, double* lohi, int v);
+
+template <int D>
 __device__ __forceinline__ void dmp_interval(const Params& p, const double* __restrict__ cmm,
                                              const int* ijk, double* lohi) {
+  if ((int)threadIdx.x < D + 2) dmp_interval_lane<D>(p, cmm, ijk, lohi, threadIdx.x);
+}
+
+// The interval of variable v (one thread per variable).
+template <int D>
+__device__ __forceinline__ void dmp_interval_lane(const Params& p, const double* __restrict__ cmm,
+                                                  const int* ijk, double* lohi, int v) {
   const int NV = D + 2;
-  const int v = threadIdx.x;
-  if (v >= NV) return;
   const Geo& g = p.geo;
   // min / max on order-preserving integer keys (the integer pipe), NaNs
   // skipped as fmin / fmax skip them
@@ -1107,7 +1119,7 @@ __global__ void __launch_bounds__(128, 8) k_correct_detect(Batch bt) {
       }
       A[e] = acc;
       Uo[e] = acc;
-      if (delta) dA[e] = (float)(acc - Un[e]);
+      if (delta) dA[e] = narrow_f64_rz(acc - Un[e]);    // (integer pipe; toward zero)
     }
     __syncthreads();
     double* vs;
@@ -1149,6 +1161,193 @@ __global__ void __launch_bounds__(128, 8) k_correct_detect(Batch bt) {
     }
     if (tid < 2 * NV) p.b.cmm[nxt][cell * 2 * NV + tid] = mm[tid];
     __syncthreads();
+  }
+}
+
+}  // namespace adg
+
+namespace adg {
+
+// ---------------------------------------------------------------------------
+// K3 + K4 with one warp per cell: the same per-item arithmetic as
+// k_correct_detect (face terms, projection, kept averages, PAD, DMP on the
+// extremes, integer-key reductions), synchronised by __syncwarp and reduced
+// with warp shuffles instead of block barriers; W cells per block.
+// ---------------------------------------------------------------------------
+constexpr int CD_WARPS = 4;
+
+template <int D, int NV, int NI, int NO, typename T>
+__device__ __forceinline__ T* apply_ct_warp(T* a, T* b, const T* M, int lane) {
+  apply_pass_ct<D, NV, NI, NO, 0, T>(a, b, M, lane, 32);
+  __syncwarp();
+  if (D == 1) return b;
+  apply_pass_ct<D, NV, NI, NO, 1, T>(b, a, M, lane, 32);
+  __syncwarp();
+  if (D == 2) return a;
+  apply_pass_ct<D, NV, NI, NO, 2, T>(a, b, M, lane, 32);
+  __syncwarp();
+  return b;
+}
+
+// Warp version of check_subcells: per-variable extremes, PAD, the DMP test on
+// the extremes against lohi (if given) and the largest wave speed; every lane
+// returns the results (mm[2v], mm[2v+1], *lam) and whether a check failed.
+template <int D>
+__device__ __forceinline__ bool check_subcells_warp(const double* __restrict__ vs, int nsub,
+                                                    const double* lohi, double gamma, double* mm,
+                                                    double* lam, bool f32speed, int lane) {
+  constexpr int NV = D + 2, K = 2 * NV + 1;
+  bool bad = false;
+  long long r[K];
+#pragma unroll
+  for (int j = 0; j < K; ++j) r[j] = LLONG_MIN;
+  for (int s = lane; s < nsub; s += 32) {
+    double Q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Q[v] = vs[v * nsub + s];
+      const long long k = ord_key(Q[v]);
+      r[2 * v] = max(r[2 * v], ~k);
+      r[2 * v + 1] = max(r[2 * v + 1], k);
+    }
+    double kin = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) kin += Q[1 + k] * Q[1 + k];
+    const double pe = Q[D + 1] * Q[0] - 0.5 * kin;
+    bad = bad || !(positive_f64(Q[0]) && positive_f64(pe));
+    if (lam)
+      r[2 * NV] = max(r[2 * NV], ord_key(f32speed ? wave_speed_f<D>(Q, pe, gamma) : wave_speed<D>(Q, gamma)));
+  }
+#pragma unroll
+  for (int j = 0; j < K; ++j)
+    for (int o = 16; o > 0; o >>= 1) r[j] = max(r[j], __shfl_xor_sync(0xffffffffu, r[j], o));
+  bad = __any_sync(0xffffffffu, bad);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    mm[2 * v] = ord_val(~r[2 * v]);
+    mm[2 * v + 1] = ord_val(r[2 * v + 1]);
+  }
+  if (lohi) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+      bad = bad || !((mm[2 * v] >= lohi[2 * v]) && (mm[2 * v + 1] <= lohi[2 * v + 1]));
+  }
+  if (lam) *lam = ord_val(r[2 * NV]);
+  return bad;
+}
+
+template <int D, int N>
+struct CdLayout {
+  using DM = Dims<D, N>;
+  static constexpr int BUF = (DM::NSD > DM::ND * 4 ? DM::NSD : DM::ND * 4);
+  // per warp: A, B [NV][BUF] doubles, lohi [2 NV] doubles
+  static constexpr int WARP_DBL = 2 * DM::NV * BUF + 2 * DM::NV;
+  // per block: P1 [Ns n] doubles and its FP32 copy
+  static constexpr int OPS_DBL = DM::Ns * DM::n + (DM::Ns * DM::n + 1) / 2;
+};
+
+template <int D, int N>
+__host__ __device__ constexpr size_t correct_warp_smem_bytes() {
+  return (size_t)(CdLayout<D, N>::OPS_DBL + CD_WARPS * CdLayout<D, N>::WARP_DBL) * sizeof(double);
+}
+
+template <int D, int N>
+__global__ void __launch_bounds__(32 * CD_WARPS) k_correct_detect_w(Batch bt) {
+  using DM = Dims<D, N>;
+  using LY = CdLayout<D, N>;
+  constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, NF = DM::NF, Ns = DM::Ns, NSD = DM::NSD;
+  constexpr int BUF = LY::BUF;
+  extern __shared__ double sm[];
+  double* P1 = sm;
+  float* P1f = reinterpret_cast<float*>(P1 + Ns * n);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double* A = sm + LY::OPS_DBL + w * LY::WARP_DBL;
+  double* B = A + NV * BUF;
+  double* lohi = B + NV * BUF;
+  const Ops* o = bt.pps[0]->ops;
+  for (int i = threadIdx.x; i < Ns * n; i += 32 * CD_WARPS) {
+    P1[i] = o->P1[i];
+    P1f[i] = (float)o->P1[i];
+  }
+  __syncthreads();
+  const long long total = bt.pre[bt.n];
+  for (long long g = (long long)blockIdx.x * CD_WARPS + w; g < total;
+       g += (long long)gridDim.x * CD_WARPS) {
+    const int sidx = batch_state(bt, g);
+    const Params& p = *bt.pps[sidx];
+    const long long cell = g - bt.pre[sidx];
+    const double dt = *p.b.dt;
+    if (!(dt > 0.0)) continue;          // (warp-uniform)
+    double c[3];
+#pragma unroll
+    for (int k = 0; k < D; ++k) c[k] = p.b.coef[k];
+    const int nxt = 1 - p.cur;
+    int ijk[3];
+    cell_coords<D>(cell, p.geo, ijk);
+    double* Uo = p.b.U[nxt] + cell * (NV * ND);
+    double* vkeep = p.b.vstar ? p.b.vstar + cell * (size_t)(NV * NSD) : nullptr;
+    const bool delta = vkeep && p.b.vok[cell] && (p.stamp & 15) != 0;
+    const double* Un = p.b.U[p.cur] + cell * (NV * ND);
+    float* dA = reinterpret_cast<float*>(B);
+    float* dB = dA + NV * BUF;
+    for (int e = lane; e < NV * ND; e += 32) {
+      const int v = e / ND, i = e - v * ND;
+      double acc = Uo[e];
+#pragma unroll
+      for (int k = 0; k < D; ++k) {
+        const int st = (k == 0) ? 1 : (k == 1 ? n : n * n);
+        const int ak = (i / st) % n;
+        const int ts = tangential<D, n>(i, k);
+        const long long flo = face_index<D>(p.geo, ijk, k, ijk[k]);
+        const long long fhi = face_index<D>(p.geo, ijk, k, ijk[k] + 1);
+        const double Glo = p.b.G[k][(flo * NV + v) * NF + ts];
+        const double Ghi = p.b.G[k][(fhi * NV + v) * NF + ts];
+        acc -= c[k] * (o->phi1w[ak] * Ghi - o->phi0w[ak] * Glo);
+      }
+      A[e] = acc;
+      Uo[e] = acc;
+      if (delta) dA[e] = narrow_f64_rz(acc - Un[e]);
+    }
+    __syncwarp();
+    double* vs;
+    if (delta) {
+      const float* dv = apply_ct_warp<D, NV, n, Ns, float>(dA, dB, P1f, lane);
+      for (int e = lane; e < NV * NSD; e += 32) {
+        const double x = vkeep[e] + widen_f32(dv[e]);
+        A[e] = x;
+        vkeep[e] = x;
+      }
+      vs = A;
+    } else {
+      vs = apply_ct_warp<D, NV, n, Ns, double>(A, B, P1, lane);
+      if (vkeep)
+        for (int e = lane; e < NV * NSD; e += 32) vkeep[e] = vs[e];
+    }
+    if (lane < NV) dmp_interval_lane<D>(p, p.b.cmm[p.cur], ijk, lohi, lane);
+    __syncwarp();
+    double lam = 0.0, mm[2 * NV];
+    const bool bad = check_subcells_warp<D>(vs, NSD, lohi, p.gamma, mm, p.lam_mode ? &lam : nullptr,
+                                            p.prec == ADG_PREC_MIXED_FP32, lane);
+    if (lane == 0) {
+      int slot = -1;
+      if (bad || p.force) {
+        slot = atomicAdd(&p.b.counters[CNT_TROUBLED0 + nxt], 1);
+        if (slot < p.cap) {
+          p.b.list[nxt][slot] = (int)cell;
+        } else {
+          atomicOr(&p.b.counters[CNT_STATUS], 1);
+          slot = -1;
+        }
+      }
+      p.b.beta[nxt][cell] = (uint8_t)(slot >= 0);
+      p.b.slot[nxt][cell] = slot;
+      if (p.lam_mode) p.b.lam[cell] = lam;
+      if (vkeep) p.b.vok[cell] = 1;
+    }
+#pragma unroll
+    for (int j = 0; j < 2 * NV; ++j)
+      if (lane == j) p.b.cmm[nxt][cell * 2 * NV + j] = mm[j];
+    __syncwarp();
   }
 }
 

@@ -131,31 +131,46 @@ struct Launch {
     const int grid = cells_grid(sl.total_cells);
     const Batch cells{sl.pps, sl.n, sl.pre_cells};
     if (sl.prec == ADG_PREC_MIXED_FP32) {
+      if (kSplit && sl.pred == PRED_WARP1) return launch_split<1, false>(cells, sl.total_cells, s);
       if (kSplit && sl.pred == PRED_WARP2) return launch_split<2, false>(cells, sl.total_cells, s);
       if (kSplit && sl.pred == PRED_WARP4) return launch_split<4, false>(cells, sl.total_cells, s);
       if (kSplit && sl.pred == PRED_WARP4_TC) return launch_split<4, true>(cells, sl.total_cells, s);
       const size_t sm = predictor_smem_bytes<D, N, true>();
       if ((e = set_smem(k_predictor<D, N, true>, sm)) != cudaSuccess) return e;
+      const bool alt = sl.pred == PRED_BLOCK_ALT;
+      const int th = alt ? alt_threads<true>() : pred_threads<true>();
       static const int gp = persistent_grid(k_predictor<D, N, true>, pred_threads<true>(), sm, 1LL << 40);
-      k_predictor<D, N, true><<<grid < gp ? grid : gp, pred_threads<true>(), sm, s>>>(cells);
+      static const int ga = persistent_grid(k_predictor<D, N, true>, alt_threads<true>(), sm, 1LL << 40);
+      const int gmax = alt ? ga : gp;
+      k_predictor<D, N, true><<<grid < gmax ? grid : gmax, th, sm, s>>>(cells);
     } else {
       const size_t sm = predictor_smem_bytes<D, N, false>();
       if ((e = set_smem(k_predictor<D, N, false>, sm)) != cudaSuccess) return e;
-      const bool wide = sl.pred == PRED_BLOCK_WIDE;
-      const int th = wide ? wide_threads() : pred_threads<false>();
+      const bool alt = sl.pred == PRED_BLOCK_ALT;
+      const int th = alt ? alt_threads<false>() : pred_threads<false>();
       static const int gn = persistent_grid(k_predictor<D, N, false>, pred_threads<false>(), sm, 1LL << 40);
-      static const int gw = persistent_grid(k_predictor<D, N, false>, wide_threads(), sm, 1LL << 40);
-      const int gmax = wide ? gw : gn;
+      static const int ga = persistent_grid(k_predictor<D, N, false>, alt_threads<false>(), sm, 1LL << 40);
+      const int gmax = alt ? ga : gn;
       k_predictor<D, N, false><<<grid < gmax ? grid : gmax, th, sm, s>>>(cells);
     }
     return cudaGetLastError();
   }
 
-  // 256 threads (the FP64 kernel's launch bound), fewer when a cell has fewer
-  // work items
-  static int wide_threads() {
-    const int t = ((NV * DM::NST + 31) / 32) * 32;
-    return t > 256 ? 256 : t;
+  // The other block width of the block-per-cell predictor (PRED_BLOCK_ALT):
+  // 256 threads where the default is below its launch bound of 256 (fewer when
+  // a cell has fewer work items), 128 where the default is 256, and 64 where
+  // the default is the kernel's launch bound.  Every width computes the same
+  // outputs (each work item's arithmetic does not depend on the width).
+  template <bool MIXED>
+  static int alt_threads() {
+    const int def = pred_threads<MIXED>();
+    const int bound = PredShape<D, N, MIXED>::bound;
+    if (def >= 256) return 128;
+    if (bound >= 256) {
+      const int t = ((NV * DM::NST + 31) / 32) * 32;
+      return t > 256 ? 256 : t;
+    }
+    return 64;
   }
 
   static cudaError_t step_dg(const StepLaunch& sl, cudaStream_t s) {
@@ -172,11 +187,21 @@ struct Launch {
       k_faceflux<D, N><<<grid_for(sl.total_faces[k], 256), 256, 0, s>>>(faces, k);
     }
     mark(ev, PHASE_CORRECT, s);
-    const size_t sc = correct_smem_bytes<D, N>();
-    if ((e = set_smem(k_correct_detect<D, N>, sc)) != cudaSuccess) return e;
-    // persistent: the operator set-up of each block is done once for many cells
-    static const int grid_cd = persistent_grid(k_correct_detect<D, N>, 128, sc, 1LL << 40);
-    k_correct_detect<D, N><<<(int)(sl.total_cells < grid_cd ? sl.total_cells : grid_cd), 128, sc, s>>>(cells);
+    if constexpr (D == 2) {
+      // one warp per cell, CD_WARPS cells per block, persistent over the cells
+      const size_t sc = correct_warp_smem_bytes<D, N>();
+      if ((e = set_smem(k_correct_detect_w<D, N>, sc)) != cudaSuccess) return e;
+      static const int grid_cd = persistent_grid(k_correct_detect_w<D, N>, 32 * CD_WARPS, sc, 1LL << 40);
+      const long long groups = (sl.total_cells + CD_WARPS - 1) / CD_WARPS;
+      k_correct_detect_w<D, N><<<(int)(groups < grid_cd ? groups : grid_cd), 32 * CD_WARPS, sc, s>>>(cells);
+    } else {
+      // 3D: a cell's subcell data (Ns^3 per variable) fills a block's shared
+      // memory, and four warps per cell hide its latency better
+      const size_t sc = correct_smem_bytes<D, N>();
+      if ((e = set_smem(k_correct_detect<D, N>, sc)) != cudaSuccess) return e;
+      static const int grid_cd = persistent_grid(k_correct_detect<D, N>, 128, sc, 1LL << 40);
+      k_correct_detect<D, N><<<(int)(sl.total_cells < grid_cd ? sl.total_cells : grid_cd), 128, sc, s>>>(cells);
+    }
     return cudaGetLastError();
   }
 

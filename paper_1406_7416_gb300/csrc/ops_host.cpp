@@ -147,6 +147,7 @@ void build_ops(int N, Ops* o) {
     o->Df[i] = (float)D[i];
     o->Ktf[i] = (float)Kt[i];
   }
+  for (int a = 0; a < n; ++a) o->wf[a] = (float)o->w[a];   // the FP64 weight rounded to FP32
   for (int a = 0; a < n; ++a)
     for (int j = 0; j < n; ++j) o->Mvol[a * n + j] = (double)(w[j] * D[j * n + a] / w[a]);
   // subcell projection: n-point GL rule per subinterval is exact for degree N

@@ -97,13 +97,13 @@ def test_option_ranges_without_device_work(lib, key, bad, good):
 
 def test_predictor_shapes_that_do_not_apply_are_refused(lib):
     """ADG_OPT_PREDICTOR: the warp-per-cell shapes need mixed precision with
-    no FP64 Picard sweep (2D N <= 5, 3D); the wide block is the FP64 kernel's."""
+    no FP64 Picard sweep (2D N <= 5, 3D); both block widths apply everywhere."""
     f64 = adg.Solver(2, (4, 4), (0, 0), (0.1, 0.1), (0, 0, 0, 0), 5, prec=adg.PREC_FP64)
     mx5 = adg.Solver(2, (4, 4), (0, 0), (0.1, 0.1), (0, 0, 0, 0), 5, prec=adg.PREC_MIXED_FP32)
     mx7 = adg.Solver(2, (4, 4), (0, 0), (0.1, 0.1), (0, 0, 0, 0), 7, prec=adg.PREC_MIXED_FP32)
-    for s, bad, good in ((f64, adg.PRED_WARP4, adg.PRED_BLOCK_WIDE),
-                         (mx5, adg.PRED_BLOCK_WIDE, adg.PRED_WARP4_TC),
-                         (mx7, adg.PRED_WARP2, adg.PRED_BLOCK)):
+    for s, bad, good in ((f64, adg.PRED_WARP4, adg.PRED_BLOCK_ALT),
+                         (mx5, 6, adg.PRED_WARP1),
+                         (mx7, adg.PRED_WARP2, adg.PRED_BLOCK_ALT)):
         with pytest.raises(adg.AdgError) as e:
             s.set_option(adg.OPT_PREDICTOR, bad)
         assert e.value.code == adg.ERR_ARG
@@ -111,7 +111,7 @@ def test_predictor_shapes_that_do_not_apply_are_refused(lib):
         for v in (-1, -2):
             s.set_option(adg.OPT_PREDICTOR, v)
         with pytest.raises(adg.AdgError):
-            s.set_option(adg.OPT_PREDICTOR, 5)
+            s.set_option(adg.OPT_PREDICTOR, 6)
     # one FP64 sweep makes the N = 5 mixed state use the block kernel
     mx5.set_option(adg.OPT_FP64_SWEEPS, 1)
     with pytest.raises(adg.AdgError):

@@ -1,9 +1,9 @@
 """GPU: the predictor's launch shapes and the autotuner that chooses among them.
 
-Every shape computes the same outputs.  The FP64 shapes (one block per cell
-at its default width or 256 threads) and the mixed warp-per-cell shapes with
-2 or 4 cells per block are bit for bit equal, so the default autotuning
-among them never changes a result.  The block-per-cell mixed kernel and the
+Every shape computes the same outputs.  The block-per-cell kernel at either
+block width (FP64, and mixed precision with an FP64 sweep) and the mixed
+warp-per-cell shapes with 2 or 4 cells per block are bit for bit equal, so
+the default autotuning among them never changes a result.  The block-per-cell mixed kernel and the
 tensor-pipe contractions (TF32 split into high and low parts, three products
 per tile) round differently in FP32 and agree with the default within FP32
 rounding of the space-time correction."""
@@ -53,7 +53,18 @@ def test_fp64_shapes_are_bitwise_equal(name):
     bit for bit equal."""
     w = FP64_CASES[name]()
     ref, troubled = _run(w, adg.PREC_FP64, adg.PRED_BLOCK, 4)
-    got, _ = _run(w, adg.PREC_FP64, adg.PRED_BLOCK_WIDE, 4)
+    got, _ = _run(w, adg.PREC_FP64, adg.PRED_BLOCK_ALT, 4)
+    assert troubled > 0
+    for a, b in zip(ref, got):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_block_widths_are_bitwise_equal_with_an_fp64_sweep():
+    """Mixed precision at N = 7 (one FP64 Picard sweep, block-per-cell kernel):
+    both block widths bit for bit equal over 4 limited steps."""
+    w = inputs.quadrants_2d(n=6, N=7)
+    ref, troubled = _run(w, adg.PREC_MIXED_FP32, adg.PRED_BLOCK, 4)
+    got, _ = _run(w, adg.PREC_MIXED_FP32, adg.PRED_BLOCK_ALT, 4)
     assert troubled > 0
     for a, b in zip(ref, got):
         np.testing.assert_array_equal(a, b)
@@ -78,7 +89,7 @@ def _max_dt(w):
 @pytest.mark.parametrize("name", sorted(MIXED_CASES))
 def test_mixed_shapes_agree(name):
     """4 fixed steps in mixed precision with each shape: the warp-per-cell
-    shapes with 2 and 4 cells per block are bit for bit equal; the
+    shapes with 1, 2 and 4 cells per block are bit for bit equal; the
     block-per-cell kernel and the tensor-pipe contractions stay within 2e-7
     of them in relative L1 per variable (FP32 rounding of the space-time
     correction, measured against variables that start at zero, like the 3D
@@ -87,9 +98,10 @@ def test_mixed_shapes_agree(name):
     dt = _max_dt(w)
     ref, troubled = _run(w, adg.PREC_MIXED_FP32, adg.PRED_WARP4, 4, dt)
     assert troubled > 0
-    w2, _ = _run(w, adg.PREC_MIXED_FP32, adg.PRED_WARP2, 4, dt)
-    for a, b in zip(ref, w2):
-        np.testing.assert_array_equal(a, b)
+    for shape in (adg.PRED_WARP1, adg.PRED_WARP2):
+        got, _ = _run(w, adg.PREC_MIXED_FP32, shape, 4, dt)
+        for a, b in zip(ref, got):
+            np.testing.assert_array_equal(a, b)
     for shape in (adg.PRED_BLOCK, adg.PRED_WARP4_TC):
         got, _ = _run(w, adg.PREC_MIXED_FP32, shape, 4, dt)
         np.testing.assert_array_equal(got[1], ref[1])
@@ -102,16 +114,16 @@ def test_autotune_times_the_candidates_and_keeps_the_fastest():
     s = adg.Solver.from_workload(w, adg.PREC_MIXED_FP32)
     s.init_problem(w["problem"])
     s.step_cfl(w["cfl"])                    # the first step tunes (default mode)
-    assert s.info()["predictor"] in (adg.PRED_WARP2, adg.PRED_WARP4)
+    assert s.info()["predictor"] in (adg.PRED_WARP1, adg.PRED_WARP2, adg.PRED_WARP4)
     ms = s.autotune(2)
     timed = {k for k, v in ms.items() if np.isfinite(v)}
-    assert timed == {"warp2", "warp4"}
+    assert timed == {"warp1", "warp2", "warp4"}
     best = min(timed, key=lambda k: ms[k])
     assert adg.PRED_NAMES[s.info()["predictor"]] == best
     s.set_option(adg.OPT_PREDICTOR, -2)      # every shape, the contraction path included
     ms = s.autotune(2)
     timed = {k for k, v in ms.items() if np.isfinite(v)}
-    assert timed == {"block", "warp2", "warp4", "warp4_tc"}
+    assert timed == {"block", "block_alt", "warp1", "warp2", "warp4", "warp4_tc"}
     best = min(timed, key=lambda k: ms[k])
     assert adg.PRED_NAMES[s.info()["predictor"]] == best
     s.step_cfl(w["cfl"])
@@ -121,5 +133,5 @@ def test_autotune_times_the_candidates_and_keeps_the_fastest():
     f.init_problem(w["problem"])
     f.step_cfl(w["cfl"])
     ms = f.autotune(2)
-    assert {k for k, v in ms.items() if np.isfinite(v)} == {"block", "block_wide"}
+    assert {k for k, v in ms.items() if np.isfinite(v)} == {"block", "block_alt"}
     f.close()
