@@ -161,11 +161,11 @@ def traffic_record():
     taken on the current kernel source (else null)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "predictor_traffic.json")
-    src = os.path.join(ROOT, "paper_1406_7416_gb300", "csrc", "kernels_dg.cuh")
+    src = os.path.join(ROOT, "paper_1406_7416_gb300", "csrc", "kernels_pred.cuh")
     try:
         rec = json.load(open(path))
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if rec.get("kernels_dg_sha256") == h:
+        if rec.get("kernels_pred_sha256") == h:
             return rec
     except (OSError, ValueError):
         pass

@@ -658,6 +658,97 @@ __global__ void __launch_bounds__(32 * LimWarps<D>::W) k_lim_predict_w(Batch bt)
   }
 }
 
+// The same subcell predictor in 2D with the 27 space-time nodes of a subcell
+// held one per lane in registers: the derivative and time contractions take
+// their three operands from the neighbouring lanes by warp shuffles, so a
+// sweep needs no shared memory and no synchronisation.  Lane l < 27 holds node
+// (a, b, m) = (l % 3, (l / 3) % 3, l / 9); the operation order of every output
+// is that of picard_flux / picard_deriv_sub / picard_time_sub.
+template <int N>
+__global__ void __launch_bounds__(256) k_lim_predict_s2(Batch bt) {
+  using DM = Dims<2, N>;
+  constexpr int NV = 4, NST3 = 27, ND3 = 9, NED = DM::NED, Ns = DM::Ns;
+  constexpr int NCROSS = DM::NSD + 4 * DM::NSF;
+  const int lane = threadIdx.x & 31;
+  const int l = lane < NST3 ? lane : NST3 - 1;          // idle lanes mirror node 26
+  const int a = l % 3, b = (l / 3) % 3, m = l / 9;
+  // this lane's rows of the operators
+  float da[3], db[3], km[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    da[j] = c_D3f[a * 3 + j];
+    db[j] = c_D3f[b * 3 + j];
+    km[j] = c_K3f[m * 3 + j];
+  }
+  const int sx = l - a, sy = l - 3 * b, st = l - 9 * m;   // first lanes of this node's lines
+  const int wpb = blockDim.x >> 5;
+  const long long total = bt.pre[bt.n] * NCROSS;
+  for (long long item = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); item < total;
+       item += (long long)gridDim.x * wpb) {
+    const long long tg = item / NCROSS;
+    const LimItem it = lim_item(bt, tg);
+    const Params& p = *bt.pps[it.s];
+    const long long j0 = it.j;
+    const int sc = cross_subcell<2, Ns>((int)(item - tg * NCROSS));
+    const float cx = (float)p.b.coef[3], cy = (float)p.b.coef[4];
+    const float gm1 = (float)(p.gamma - 1.0);
+    const float* Wr = reinterpret_cast<const float*>(p.b.sweep[1]);   // [j][v][NED][ND3]
+    float u[NV], q[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      u[v] = Wr[((j0 * NV + v) * NED + sc) * ND3 + (l % ND3)];
+      q[v] = u[v];
+    }
+#pragma unroll 1
+    for (int sweep = 0; sweep < 3; ++sweep) {
+      float F[2][4];
+      euler_fluxes<2, float>(q, gm1, F);
+      float S[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        float s = 0.0f;
+        {
+          const float x0 = __shfl_sync(0xffffffffu, F[0][v], sx);
+          const float x1 = __shfl_sync(0xffffffffu, F[0][v], sx + 1);
+          const float x2 = __shfl_sync(0xffffffffu, F[0][v], sx + 2);
+          float acc = 0.0f;
+          acc += da[0] * x0;
+          acc += da[1] * x1;
+          acc += da[2] * x2;
+          s += cx * acc;
+        }
+        {
+          const float x0 = __shfl_sync(0xffffffffu, F[1][v], sy);
+          const float x1 = __shfl_sync(0xffffffffu, F[1][v], sy + 3);
+          const float x2 = __shfl_sync(0xffffffffu, F[1][v], sy + 6);
+          float acc = 0.0f;
+          acc += db[0] * x0;
+          acc += db[1] * x1;
+          acc += db[2] * x2;
+          s += cy * acc;
+        }
+        S[v] = s;
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const float y0 = __shfl_sync(0xffffffffu, S[v], st);
+        const float y1 = __shfl_sync(0xffffffffu, S[v], st + 9);
+        const float y2 = __shfl_sync(0xffffffffu, S[v], st + 18);
+        float acc = 0.0f;
+        acc += km[0] * y0;
+        acc += km[1] * y1;
+        acc += km[2] * y2;
+        q[v] = u[v] - acc;
+      }
+    }
+    if (lane < NST3) {
+      float* dst = reinterpret_cast<float*>(p.b.qsub) + ((size_t)j0 * NED + sc) * (size_t)(NV * NST3);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) dst[v * NST3 + l] = q[v];
+    }
+  }
+}
+
 // L5: sub-face fluxes normal to axis k: Rusanov at the 3^(d-1) x 3
 // tangential x time GL points, averaged with the GL weights.  Faces f = 0..Ns
 // along k (between local subcells f-1 and f), tangential subcells 0..Ns-1.

@@ -40,6 +40,12 @@ struct SplitLayout {
   static constexpr int QF = ((NV * NST > D * NV * ND) ? NV * NST : D * NV * ND) / 2 * 2 + 2;
   static constexpr int FF = D * NV * NST;
   static constexpr int FB_OFF = (NV * NST + 1) / 2 * 2;          // float offset of fbar in Ff
+  // groups of time nodes of the flux-change sums (see k_predictor_split):
+  // 3 or 2 when n divides evenly, the groups' partial sums fit in qf and the
+  // ND nodes alone would leave most lanes of a round idle
+  static constexpr int TSPLIT =
+      (ND % 32 != 0 && ND < 64 && DM::n % 3 == 0 && 3 * D * NV * ND <= QF) ? 3
+      : (ND % 32 != 0 && ND < 64 && DM::n % 2 == 0 && 2 * D * NV * ND <= QF) ? 2 : 1;
   static constexpr bool FB_IN_F = FB_OFF + 2 * D * NV * ND <= FF;
   // per cell: doubles (u, and fbar when it does not fit in Ff), then floats
   static constexpr int DBL = NV * ND + (FB_IN_F ? 0 : D * NV * ND);
@@ -241,6 +247,12 @@ struct TcSweep {
   }
 };
 
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2 by the
+// TMA unit (cp.async.bulk.prefetch): no shared memory, nothing to wait for.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 template <int D, int N, int W, bool TC>
 __global__ void __launch_bounds__(32 * W) k_predictor_split(Batch bt) {
   using DM = Dims<D, N>;
@@ -296,6 +308,14 @@ __global__ void __launch_bounds__(32 * W) k_predictor_split(Batch bt) {
       s_pp[w] = pp;
       s_cell[w] = cell;
       s_on[w] = on ? 1 : 0;
+      // the DOF block of the cell this warp takes next, into L2 while this one runs
+      constexpr unsigned UBYTES = NV * ND * sizeof(double);
+      const long long gn = g + (long long)gridDim.x * W;
+      if (UBYTES % 16 == 0 && gn < total) {
+        const int sn = batch_state(bt, gn);
+        const Params* pn = bt.pps[sn];
+        bulk_prefetch_l2(pn->b.U[pn->cur] + (gn - bt.pre[sn]) * (NV * ND), UBYTES);
+      }
     }
     if (on) {
       const Params& p = *pp;
@@ -410,9 +430,14 @@ __global__ void __launch_bounds__(32 * W) k_predictor_split(Batch bt) {
         }
       }
       // time-averaged flux changes per spatial node, into qf: the products
-      // w_m G rounded, then summed over m in order (as k_predictor does)
+      // w_m G rounded and summed over the time nodes in order.  When a warp
+      // has few nodes (ND not much larger than 32 or far below it) the time
+      // nodes are split in TS groups, each lane summing one group of one node,
+      // and the groups' partial sums are added in group order afterwards.
+      constexpr int TS = LY::TSPLIT, MG = n / TS;
       float* dFb = qf;
-      for (int i = lane; i < ND; i += 32) {
+      for (int t = lane; t < ND * TS; t += 32) {
+        const int i = t % ND, grp = t / ND;
         float U[NV], acc[D][D + 2];
 #pragma unroll
         for (int v = 0; v < NV; ++v) U[v] = uf[v * ND + i];
@@ -420,7 +445,8 @@ __global__ void __launch_bounds__(32 * W) k_predictor_split(Batch bt) {
         for (int k = 0; k < D; ++k)
 #pragma unroll
           for (int v = 0; v < NV; ++v) acc[k][v] = 0.0f;
-        for (int m = 0; m < n; ++m) {
+        for (int mm = 0; mm < MG; ++mm) {
+          const int m = grp * MG + mm;
           float dQ[NV], G[D][D + 2];
 #pragma unroll
           for (int v = 0; v < NV; ++v) dQ[v] = dq[v * NST + i + m * ND];
@@ -434,7 +460,16 @@ __global__ void __launch_bounds__(32 * W) k_predictor_split(Batch bt) {
 #pragma unroll
         for (int k = 0; k < D; ++k)
 #pragma unroll
-          for (int v = 0; v < NV; ++v) dFb[(k * NV + v) * ND + i] = acc[k][v];
+          for (int v = 0; v < NV; ++v) dFb[(grp * D * NV + k * NV + v) * ND + i] = acc[k][v];
+      }
+      if constexpr (TS > 1) {
+        __syncwarp();
+        for (int e = lane; e < D * NV * ND; e += 32) {
+          float x = dFb[e];
+#pragma unroll
+          for (int grp = 1; grp < TS; ++grp) x = __fadd_rn(x, dFb[grp * D * NV * ND + e]);
+          dFb[e] = x;
+        }
       }
     }
     __syncthreads();

@@ -223,11 +223,18 @@ struct Launch {
       k_lim_sweep<D, N, 1, float><<<gs, 256, 0, s>>>(lim, pass);
       if (D == 3) k_lim_sweep<D, N, (D == 3 ? 2 : 1), float><<<gs, 256, 0, s>>>(lim, pass);
       if (qf) {
-        // one warp per subcell, blocks looping over the pass's subcells
-        constexpr int W = LimWarps<D>::W;
-        static const int gw = persistent_grid(k_lim_predict_w<D, N>, 32 * W, 0, 1LL << 40);
-        const long long want = (ncross + W - 1) / W;
-        k_lim_predict_w<D, N><<<(int)(want < gw ? want : gw), 32 * W, 0, s>>>(lim);
+        // one warp per subcell, blocks looping over the pass's subcells; in 2D
+        // the subcell's 27 nodes live in the warp's registers
+        if constexpr (D == 2) {
+          static const int gw = persistent_grid(k_lim_predict_s2<N>, 256, 0, 1LL << 40);
+          const long long want = (ncross + 7) / 8;
+          k_lim_predict_s2<N><<<(int)(want < gw ? want : gw), 256, 0, s>>>(lim);
+        } else {
+          constexpr int W = LimWarps<D>::W;
+          static const int gw = persistent_grid(k_lim_predict_w<D, N>, 32 * W, 0, 1LL << 40);
+          const long long want = (ncross + W - 1) / W;
+          k_lim_predict_w<D, N><<<(int)(want < gw ? want : gw), 32 * W, 0, s>>>(lim);
+        }
       } else
         k_lim_predict<D, N, true, float, false><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, sl.sub32);
     } else {
