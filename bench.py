@@ -546,6 +546,10 @@ def run_serving(args):
     specs = inputs.serving_runs(count=args.runs)
     for w in specs:
         w["t_end"] = min(w["t_end"], args.t_end)
+        # runs of hundreds to thousands of steps take half the factor of
+        # Eq. (cfl), as the paper's own long runs did (at the full factor the
+        # one-step scheme's error grows over such runs)
+        w["cfl"] *= args.serving_cfl_factor
     # capacity from a closed-loop pass (all runs at t = 0) over the first
     # --capacity-runs runs (all by default), scaled to the whole stream by work
     ncap = args.capacity_runs or len(specs)
@@ -579,6 +583,7 @@ def run_serving(args):
             "config": {"workload": f"serving: {len(specs)} independent 2D Riemann-problem runs "
                                    f"(Sec. 5.6 RP1-RP5, 2% jitter), grids from "
                                    f"{{32,64,128,256}}^2, N in {{3,5}}, t_end={args.t_end}, "
+                                   f"CFL {args.serving_cfl_factor} x 0.9/(d(2N+1)), "
                                    "Poisson arrivals at 80% of the measured capacity",
                        "hbm_budget_bytes": budget, "mixed precision": True},
             "latency_p50_s": opened["latency_p50_s"], "latency_p99_s": opened["latency_p99_s"],
@@ -642,6 +647,8 @@ def main():
     ap.add_argument("--runs", type=int, default=32, help="serving: number of runs")
     ap.add_argument("--t-end", type=float, default=0.02,
                     help="serving: end time cap of every run (each stops at min(cap, its final time))")
+    ap.add_argument("--serving-cfl-factor", type=float, default=0.5,
+                    help="serving: fraction of the CFL number of Eq. (cfl) the runs take")
     ap.add_argument("--capacity-runs", type=int, default=0,
                     help="serving: runs of the closed-loop capacity pass (0: all)")
     ap.add_argument("--max-wall", type=float, default=120.0,

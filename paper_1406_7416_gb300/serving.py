@@ -120,7 +120,10 @@ class Server:
                 r.steps = n
                 if done or stalled:
                     r.finished = clock() - t0
-                    r.status = r.solver.status()
+                    try:
+                        r.status = r.solver.status()
+                    except adg.AdgError as e:   # e.g. no admissible wave speed left
+                        r.status = e.code
                     r.failed = stalled or r.status < 0
                     if self.keep:
                         r.result = r.solver.read_full()

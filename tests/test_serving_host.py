@@ -15,6 +15,12 @@ from paper_1406_7416_gb300 import serving
 pytestmark = pytest.mark.timeout(60)     # a broken retirement rule would loop forever
 
 
+class FakeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(msg)
+        self.code = code
+
+
 class FakeSolver:
     def __init__(self, w, prec):
         self.w = w
@@ -45,6 +51,10 @@ class FakeSolver:
         return self.t, self.n
 
     def status(self):
+        # a state that stopped stepping has no admissible wave speed: the real
+        # library's status call raises then
+        if self.dt == 0.0:
+            raise FakeError(-6, "no admissible wave speed")
         return 0
 
     def read_full(self):
@@ -74,7 +84,7 @@ class FakeBatch:
 
 
 FAKE = types.SimpleNamespace(Solver=FakeSolver, Batch=FakeBatch, OPT_CFL=9, OPT_END_TIME=8,
-                             PREC_MIXED_FP32=1)
+                             PREC_MIXED_FP32=1, AdgError=FakeError)
 
 
 class Clock:
@@ -153,7 +163,7 @@ def test_stalled_run_is_retired_as_failed(fake_lib):
     runs = [_run(0), _run(1, dt=0.0), _run(2)]
     st = serving.Server(10 ** 9, steps_per_poll=2).serve(runs, clock=Clock())
     assert st["failed"] == 1 and st["failed_ids"] == [1] and st["runs"] == 2
-    assert runs[1].failed and runs[1].steps == 0
+    assert runs[1].failed and runs[1].steps == 0 and runs[1].status == -6
     assert not runs[0].failed and not runs[2].failed
 
 
