@@ -104,7 +104,9 @@ def predictor_flops(D, N, iters, fp64_sweeps):
     is FP64: fluxes at the space-time nodes, their time average, the volume
     term and the face traces.  With no FP64 sweep it splits: F(u) at the
     spatial nodes, the volume term and trace(u) in FP64; the flux changes at
-    the space-time nodes, their weighted time sum and trace(q - u) in FP32."""
+    the space-time nodes, their weighted time sum and trace(q - u) in FP32;
+    and the first sweep, from the time-constant u (x) 1, runs on the spatial
+    nodes only."""
     n, nv = N + 1, D + 2
     nst, nd, nf = n ** (D + 1), n ** D, n ** (D - 1)
     it = nst * flux_flops(D) + nv * nst * D * (2 * n + 2) + nv * nd * n * (2 * n + 1)
@@ -115,7 +117,10 @@ def predictor_flops(D, N, iters, fp64_sweeps):
     final64 = nd * flux_flops(D) + D * nv * nd + vol + 2 * D * nv * nf * 2 * n
     final32 = (nst * flux_delta_flops(D) + D * nv * nst * 2 + 2 * D * nv * nf * n * 2 * n
                + nv * nst * n * 2)
-    return final64, iters * it + final32
+    # the first sweep from u (x) 1: fluxes and derivatives on the n^d spatial
+    # nodes, then one FMA per space-time node (q1_m = u - kappa_m S)
+    first = nd * flux_flops(D) + nv * nd * D * (2 * n + 2) + nv * nd * n * 2
+    return final64, (iters - 1) * it + first + final32
 
 
 def clocks_sampler():
