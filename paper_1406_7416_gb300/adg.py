@@ -35,6 +35,7 @@ OPT_SUBCELL_FP64_SWEEPS = 14
 OPT_SUBCELL_FP32 = 15
 OPT_PROJECT_DELTA = 16
 OPT_PREDICTOR = 17
+OPT_SUBCELL_REGISTERS = 18
 PRED_BLOCK, PRED_BLOCK_ALT, PRED_WARP2, PRED_WARP4, PRED_WARP4_TC, PRED_WARP1 = 0, 1, 2, 3, 4, 5
 PRED_NAMES = ("block", "block_alt", "warp2", "warp4", "warp4_tc", "warp1")
 FLUX_RUSANOV, FLUX_OSHER = 0, 1

@@ -24,6 +24,7 @@ struct adg_state {
                             // on the device by a conditional loop
   int sub_fp64 = 0;         // mixed precision: FP64 sweeps of the degree-2 subcell predictor
   int sub_f32 = 1;          // mixed precision: FP32 subcell reconstruction and sub-face fluxes
+  int sub_reg = 1;          // FP32 subcell predictor: register form (1) or shared-memory form (0)
   int project_delta = 1;    // mixed precision: detector projection from the kept P(u^n)
   int pred_opt = -1;        // ADG_OPT_PREDICTOR: fixed predictor shape (PRED_*); -1 autotune
                             // among the shapes of the default arithmetic, -2 among all
@@ -508,6 +509,7 @@ StepLaunch single_launch(adg_state* st) {
   sl.cascade = st->cascade;
   sl.sub32 = 3 - st->sub_fp64;
   sl.sub_f32 = st->sub_f32;
+  sl.sub_reg = st->sub_reg;
   sl.flux = st->flux;
   sl.total_cells = st->geo.cells;
   for (int k = 0; k < st->dim; ++k) {
@@ -883,7 +885,8 @@ int adg_batch_create(adg_state* const* states, int count, void* stream, adg_batc
       const adg_state* a = states[i];
       const adg_state* c = states[j];
       if (!done[j] && a->dim == c->dim && a->N == c->N && a->prec == c->prec &&
-          a->sub_fp64 == c->sub_fp64 && a->sub_f32 == c->sub_f32 && a->flux == c->flux &&
+          a->sub_fp64 == c->sub_fp64 && a->sub_f32 == c->sub_f32 && a->sub_reg == c->sub_reg &&
+          a->flux == c->flux &&
           effective_pred(a) == effective_pred(c)) {
         g.idx.push_back(j);
         done[j] = 1;
@@ -937,6 +940,7 @@ int adg_batch_create(adg_state* const* states, int count, void* stream, adg_batc
     sl.prec = g.rep->prec;
     sl.sub32 = 3 - g.rep->sub_fp64;
     sl.sub_f32 = g.rep->sub_f32;
+    sl.sub_reg = g.rep->sub_reg;
     sl.flux = g.rep->flux;
     sl.pred = effective_pred(g.rep);
     sl.ev = nullptr;
@@ -1169,6 +1173,9 @@ int adg_set_option(adg_state* st, int key, double value) {
       return ADG_OK;
     case ADG_OPT_SUBCELL_FP32:
       st->sub_f32 = value != 0.0;
+      return ADG_OK;
+    case ADG_OPT_SUBCELL_REGISTERS:
+      st->sub_reg = value != 0.0;
       return ADG_OK;
     case ADG_OPT_HOST_PASSES:
       st->host_passes = value != 0.0;

@@ -167,6 +167,7 @@ struct StepLaunch {
   int cascade;                 // any state of the launch runs the first-order layer
   int sub32;                   // mixed precision: FP32 sweeps (of 3) of the subcell predictor
   int sub_f32;                  // mixed precision: WENO3 reconstruction and sub-face fluxes in FP32
+  int sub_reg;                 // the FP32 subcell predictor with a subcell in one warp's registers
   int flux;                    // numerical flux of the launch's states (ADG_FLUX_*)
   int pred;                    // predictor launch shape (PRED_*)
   long long total_cells;

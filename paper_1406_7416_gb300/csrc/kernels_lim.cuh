@@ -749,6 +749,95 @@ __global__ void __launch_bounds__(256) k_lim_predict_s2(Batch bt) {
   }
 }
 
+// The 3D subcell predictor in registers: lane l < 27 holds spatial node
+// (a, b, c) = (l % 3, (l / 3) % 3, l / 9) of the subcell and its three time
+// nodes.  The space derivatives take their three operands per axis from the
+// lanes on the node's line by warp shuffles; the time contraction (Ktau) runs
+// on the lane's own three time nodes, so it needs no exchange at all.  A
+// sweep uses no shared memory and no synchronisation.  The operation order of
+// every output is that of picard_flux / picard_deriv_sub / picard_time_sub.
+template <int N>
+__global__ void __launch_bounds__(256) k_lim_predict_s3(Batch bt) {
+  using DM = Dims<3, N>;
+  constexpr int NV = 5, NST3 = 81, ND3 = 27, NED = DM::NED, Ns = DM::Ns;
+  constexpr int NCROSS = DM::NSD + 6 * DM::NSF;
+  const int lane = threadIdx.x & 31;
+  const int l = lane < ND3 ? lane : ND3 - 1;            // idle lanes mirror node 26
+  const int a = l % 3, b = (l / 3) % 3, c = l / 9;
+  float da[3], db[3], dc[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    da[j] = c_D3f[a * 3 + j];
+    db[j] = c_D3f[b * 3 + j];
+    dc[j] = c_D3f[c * 3 + j];
+  }
+  const int sx = l - a, sy = l - 3 * b, sz = l - 9 * c;   // first lanes of this node's lines
+  const int wpb = blockDim.x >> 5;
+  const long long total = bt.pre[bt.n] * NCROSS;
+  for (long long item = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); item < total;
+       item += (long long)gridDim.x * wpb) {
+    const long long tg = item / NCROSS;
+    const LimItem it = lim_item(bt, tg);
+    const Params& p = *bt.pps[it.s];
+    const long long j0 = it.j;
+    const int sc = cross_subcell<3, Ns>((int)(item - tg * NCROSS));
+    const float cf[3] = {(float)p.b.coef[3], (float)p.b.coef[4], (float)p.b.coef[5]};
+    const float gm1 = (float)(p.gamma - 1.0);
+    const float* Wr = reinterpret_cast<const float*>(p.b.sweep[2]);   // [j][v][NED][ND3]
+    float u[NV], q[3][NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      u[v] = Wr[((j0 * NV + v) * NED + sc) * ND3 + l];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) q[m][v] = u[v];
+    }
+#pragma unroll 1
+    for (int sweep = 0; sweep < 3; ++sweep) {
+      float S[3][NV];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        float F[3][5];
+        euler_fluxes<3, float>(q[m], gm1, F);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          float s = 0.0f;
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const int base = k == 0 ? sx : (k == 1 ? sy : sz);
+            const int st = k == 0 ? 1 : (k == 1 ? 3 : 9);
+            const float* dr = k == 0 ? da : (k == 1 ? db : dc);
+            const float x0 = __shfl_sync(0xffffffffu, F[k][v], base);
+            const float x1 = __shfl_sync(0xffffffffu, F[k][v], base + st);
+            const float x2 = __shfl_sync(0xffffffffu, F[k][v], base + 2 * st);
+            float acc = 0.0f;
+            acc += dr[0] * x0;
+            acc += dr[1] * x1;
+            acc += dr[2] * x2;
+            s += cf[k] * acc;
+          }
+          S[m][v] = s;
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int j = 0; j < 3; ++j) acc += c_K3f[m * 3 + j] * S[j][v];
+          q[m][v] = u[v] - acc;
+        }
+    }
+    if (lane < ND3) {
+      float* dst = reinterpret_cast<float*>(p.b.qsub) + ((size_t)j0 * NED + sc) * (size_t)(NV * NST3);
+#pragma unroll
+      for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) dst[v * NST3 + m * ND3 + l] = q[m][v];
+    }
+  }
+}
+
 // L5: sub-face fluxes normal to axis k: Rusanov at the 3^(d-1) x 3
 // tangential x time GL points, averaged with the GL weights.  Faces f = 0..Ns
 // along k (between local subcells f-1 and f), tangential subcells 0..Ns-1.

@@ -223,12 +223,16 @@ struct Launch {
       k_lim_sweep<D, N, 1, float><<<gs, 256, 0, s>>>(lim, pass);
       if (D == 3) k_lim_sweep<D, N, (D == 3 ? 2 : 1), float><<<gs, 256, 0, s>>>(lim, pass);
       if (qf) {
-        // one warp per subcell, blocks looping over the pass's subcells; in 2D
-        // the subcell's 27 nodes live in the warp's registers
-        if constexpr (D == 2) {
+        // one warp per subcell, blocks looping over the pass's subcells; by
+        // default the subcell's space-time nodes live in the warp's registers
+        if (sl.sub_reg && D == 2) {
           static const int gw = persistent_grid(k_lim_predict_s2<N>, 256, 0, 1LL << 40);
           const long long want = (ncross + 7) / 8;
           k_lim_predict_s2<N><<<(int)(want < gw ? want : gw), 256, 0, s>>>(lim);
+        } else if (sl.sub_reg && D == 3) {
+          static const int gw = persistent_grid(k_lim_predict_s3<N>, 256, 0, 1LL << 40);
+          const long long want = (ncross + 7) / 8;
+          k_lim_predict_s3<N><<<(int)(want < gw ? want : gw), 256, 0, s>>>(lim);
         } else {
           constexpr int W = LimWarps<D>::W;
           static const int gw = persistent_grid(k_lim_predict_w<D, N>, 32 * W, 0, 1LL << 40);

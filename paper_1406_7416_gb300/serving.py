@@ -8,9 +8,12 @@ steps (adg_batch_step, one CUDA graph per membership), then reads each run's
 simulated time; finished runs are retired, which frees memory for waiting
 runs, and the batch is rebuilt whenever its membership changes.  A run that
 takes no step over a whole poll before its end time (no finite positive CFL
-time step, e.g. after a loss of positivity) is retired as failed.  Reports the
-latency of every run (arrival to completion) and the aggregate space-time DOF
-update rate.
+time step, e.g. after a loss of positivity) has failed: with retries left it is
+started again from its initial data at a smaller CFL number (the time step of
+Eq. (cfl) is an upper bound; any smaller step is admissible), else it is
+retired as failed.  Reports the latency of every run (arrival to completion,
+retries included) and the aggregate space-time DOF update rate (the steps of
+failed attempts are not counted as work done).
 """
 import collections
 import time
@@ -36,6 +39,9 @@ class RunSpec:
         self.result = None
         self.status = 0
         self.failed = False
+        self.attempts = 0          # retries taken
+        self.cfl_scale = 1.0       # factor on the workload's CFL number
+        self.wasted_steps = 0      # steps of failed attempts
 
     @property
     def stdofs_per_step(self):
@@ -47,8 +53,10 @@ class Server:
     """hbm_budget: bytes of device memory the resident runs may hold."""
 
     def __init__(self, hbm_budget, prec=adg.PREC_MIXED_FP32, steps_per_poll=8, keep_results=False,
-                 stream=0):
+                 stream=0, retries=0, retry_cfl_factor=0.5):
         self.budget = int(hbm_budget)
+        self.retries = int(retries)
+        self.retry_cfl_factor = float(retry_cfl_factor)
         self.prec = prec
         self.steps_per_poll = steps_per_poll
         self.keep = keep_results
@@ -63,7 +71,7 @@ class Server:
         s = adg.Solver.from_workload(w, self.prec)
         if self.stream:
             s.set_stream(self.stream)
-        s.set_option(adg.OPT_CFL, w["cfl"])
+        s.set_option(adg.OPT_CFL, w["cfl"] * r.cfl_scale)
         s.set_option(adg.OPT_END_TIME, r.t_end)
         s.init_problem(w["problem"])
         r.solver = s
@@ -109,7 +117,7 @@ class Server:
             for _ in range(self.steps_per_poll):
                 batch.step(cfl=0.0)
             polls += 1
-            still = []
+            still, retry = [], []
             for r in active:
                 t, n = r.solver.time()
                 done = reached_end(t, r.t_end)
@@ -119,14 +127,19 @@ class Server:
                 stalled = not done and n == r.steps
                 r.steps = n
                 if done or stalled:
-                    r.finished = clock() - t0
                     try:
-                        r.status = r.solver.status()
+                        status = r.solver.status()
                     except adg.AdgError as e:   # e.g. no admissible wave speed left
-                        r.status = e.code
-                    r.failed = stalled or r.status < 0
-                    if self.keep:
-                        r.result = r.solver.read_full()
+                        status = e.code
+                    failed = stalled or status < 0
+                    if failed and r.attempts < self.retries:
+                        retry.append(r)
+                    else:
+                        r.finished = clock() - t0
+                        r.status = status
+                        r.failed = failed
+                        if self.keep:
+                            r.result = r.solver.read_full()
                     used -= r.bytes
                     rebuild = True
                 else:
@@ -136,9 +149,17 @@ class Server:
                     batch.close()
                     batch = None
                 for r in active:
-                    if r.finished is not None and r.solver is not None:
+                    if (r.finished is not None or r in retry) and r.solver is not None:
                         r.solver.close()
                         r.solver = None
+            # failed runs with retries left go back to the head of the queue
+            # (their arrival is earlier than every waiting run's)
+            for r in reversed(retry):
+                r.attempts += 1
+                r.cfl_scale *= self.retry_cfl_factor
+                r.wasted_steps += r.steps
+                r.steps = 0
+                waiting.appendleft(r)
             active = still
         wall = clock() - t0
         if batch is not None:
@@ -155,7 +176,11 @@ class Server:
                 "latency_p99_s": float(np.percentile(lat, 99)),
                 "latency_max_s": float(lat.max()),
                 "stdof_updates": int(stdofs), "stdof_per_s": stdofs / wall,
-                "steps": int(sum(r.steps for r in served))}
+                "steps": int(sum(r.steps for r in served)),
+                "retried": sum(1 for r in runs if r.attempts > 0),
+                "retried_served": sum(1 for r in served if r.attempts > 0),
+                "retried_ids": [r.rid for r in runs if r.attempts > 0],
+                "wasted_steps": int(sum(r.wasted_steps for r in runs) + sum(r.steps for r in failed))}
 
 
 def reached_end(t, t_end):

@@ -31,6 +31,22 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(names) == set(adg.SYMBOLS)
 
 
+def test_binding_constants_match_the_header():
+    """Every #define of include/adg.h that the binding names (ADG_X as adg.X)
+    has the header's value."""
+    txt = open(os.path.join(ROOT, "include", "adg.h")).read()
+    defs = dict(re.findall(r"#define ADG_([A-Z0-9_]+)\s+(-?\d+)\b", txt))
+    assert len(defs) > 30
+    checked = 0
+    for name, val in defs.items():
+        if hasattr(adg, name):
+            assert getattr(adg, name) == int(val), name
+            checked += 1
+    assert checked >= 25
+    for opt in ("OPT_PREDICTOR", "OPT_SUBCELL_REGISTERS", "PREC_MIXED_TF32"):
+        assert opt in defs and hasattr(adg, opt), opt
+
+
 @pytest.mark.parametrize("dim,N,gamma,bc,prec", [
     (1, 3, 1.4, [0, 0], 0),            # bad dimension
     (2, 0, 1.4, [0, 0, 0, 0], 0),      # N out of range

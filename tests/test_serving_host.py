@@ -3,8 +3,8 @@ the device calls are replaced by a fake library whose states advance their
 simulated time by a fixed step per batched step, cut at their end time as
 the device step is, and the clock is simulated.  Checks admission by the
 memory budget, batch rebuilds on membership changes, retirement at the end
-time, retirement of stalled runs as failed, the no-admission wall limit and
-the statistics."""
+time, retirement of stalled runs as failed, their retry at a smaller CFL number,
+the no-admission wall limit and the statistics."""
 import types
 
 import numpy as np
@@ -27,8 +27,17 @@ class FakeSolver:
         self.t = 0.0
         self.n = 0
         self.t_end = 0.0
-        self.dt = w["fake_dt"]
+        self._dt = w["fake_dt"]
+        self.cfl = None
         self.closed = False
+
+    @property
+    def dt(self):
+        # a state whose CFL number is at least w["fake_fail_cfl"] loses
+        # admissibility after three steps
+        if self.cfl is not None and self.cfl >= self.w.get("fake_fail_cfl", np.inf) and self.n >= 3:
+            return 0.0
+        return self._dt
 
     @classmethod
     def from_workload(cls, w, prec):
@@ -40,6 +49,8 @@ class FakeSolver:
     def set_option(self, opt, value):
         if opt == FAKE.OPT_END_TIME:
             self.t_end = value
+        if opt == FAKE.OPT_CFL:
+            self.cfl = value
 
     def init_problem(self, problem):
         pass
@@ -105,9 +116,9 @@ def fake_lib(monkeypatch):
     FakeBatch.built = []
 
 
-def _run(i, dt=0.01, nbytes=100, t_end=0.1, arrival=0.0, shape=None):
+def _run(i, dt=0.01, nbytes=100, t_end=0.1, arrival=0.0, shape=None, fail_cfl=np.inf):
     w = {"dim": 2, "N": 3, "ncell": shape or (8 + i, 8), "cfl": 0.1, "problem": None,
-         "fake_dt": dt, "fake_bytes": nbytes}
+         "fake_dt": dt, "fake_bytes": nbytes, "fake_fail_cfl": fail_cfl}
     return serving.RunSpec(w, t_end, arrival, i)
 
 
@@ -187,3 +198,33 @@ def test_results_kept_on_request(fake_lib):
     runs = [_run(0, t_end=0.05)]
     serving.Server(10 ** 9, keep_results=True).serve(runs, clock=Clock())
     assert runs[0].result[0][0] == pytest.approx(0.05)
+
+
+def test_failed_run_is_retried_at_a_smaller_cfl(fake_lib):
+    """Run 1 loses admissibility after three steps at the workload's CFL
+    number: with one retry it starts again from its initial data at half the
+    CFL number and finishes; its failed attempt's steps are not counted as
+    work, and its latency runs from its arrival."""
+    runs = [_run(0), _run(1, fail_cfl=0.1), _run(2)]
+    st = serving.Server(10 ** 9, steps_per_poll=2, retries=1).serve(runs, clock=Clock())
+    assert st["runs"] == 3 and st["failed"] == 0
+    assert st["retried"] == 1 and st["retried_served"] == 1 and st["retried_ids"] == [1]
+    r = runs[1]
+    assert r.attempts == 1 and r.cfl_scale == 0.5 and not r.failed and r.status == 0
+    assert r.wasted_steps == 3 and r.steps == 10 and st["wasted_steps"] == 3
+    assert st["steps"] == 30
+    assert st["stdof_updates"] == sum(x.stdofs_per_step * 10 for x in runs)
+    assert r.finished > r.admitted > r.arrival
+
+
+def test_run_failing_every_attempt_is_retired_as_failed(fake_lib):
+    """A run that fails at every CFL number is retired as failed once its
+    retries are spent; without retries it is retired at the first failure."""
+    runs = [_run(0, fail_cfl=0.0), _run(1)]
+    st = serving.Server(10 ** 9, steps_per_poll=2, retries=2).serve(runs, clock=Clock())
+    assert st["failed"] == 1 and st["runs"] == 1 and st["failed_ids"] == [0]
+    assert runs[0].attempts == 2 and runs[0].cfl_scale == 0.25 and runs[0].status == -6
+    assert st["wasted_steps"] == 9 and runs[0].steps == 3
+    runs = [_run(0, fail_cfl=0.0)]
+    st = serving.Server(10 ** 9, steps_per_poll=2).serve(runs, clock=Clock())
+    assert st["failed"] == 1 and runs[0].attempts == 0 and st["retried"] == 0
