@@ -291,12 +291,13 @@ int ensure_allocated(adg_state* st) {
   ALLOC(b.fblist, int, 3 * cap);
   b.fbflag = b.fblist + cap;
   b.refixlist = b.fblist + 2 * cap;
-  ALLOC(b.dt, double, 12);
+  ALLOC(b.dt, double, 16);
   ALLOC(b.lamkey, long long, 1);
   b.lamred = b.dt + 1;
   b.clock = b.dt + 2;
   b.tstart = b.dt + 5;
   b.coef = b.dt + 6;
+  b.coef_f = reinterpret_cast<float*>(b.dt + 12);
   ALLOC(st->dparams, Params, 1);
   ALLOC(st->d_pps1, Params*, 1);
   ALLOC(st->d_pre1, long long, 20);

@@ -91,6 +91,8 @@ struct Bufs {
   double* clock;         // [3] simulated time t, end time t_end (0: none), steps taken
   double* tstart;        // [1] simulated time at the start of the current step
   double* coef;          // [6] dt / dx_k and dt Ns / dx_k of the current step (set once per step)
+  float* coef_f;         // [8] FP32 copies for the FP32 subcell kernels: coef[0..5], gamma - 1,
+                         // gamma (conversions from FP64 run on the narrow FP64 pipe)
   // mixed precision, ADG_OPT_PROJECT_DELTA: the subcell averages P(u) of each
   // cell's current DOFs, kept from the detector of the step that made them
   double* vstar;         // [cells][nv][Ns^d] (null when off)

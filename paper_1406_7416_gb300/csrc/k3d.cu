@@ -93,6 +93,14 @@ __global__ void k_step_begin(StepLaunch sl) {
       p.b.coef[k] = dt / p.geo.dx[k];
       p.b.coef[3 + k] = dt * Ns / p.geo.dx[k];
     }
+    if (p.b.coef_f) {
+      for (int k = 0; k < p.dim; ++k) {
+        p.b.coef_f[k] = (float)p.b.coef[k];
+        p.b.coef_f[3 + k] = (float)p.b.coef[3 + k];
+      }
+      p.b.coef_f[6] = (float)(p.gamma - 1.0);
+      p.b.coef_f[7] = (float)p.gamma;
+    }
     if (dt > 0.0) {
       p.b.counters[CNT_TROUBLED0 + (1 - p.cur)] = 0;
       p.b.counters[CNT_FIX] = 0;

@@ -899,6 +899,13 @@ __device__ __forceinline__ long long ord_key(double x) {
 __device__ __forceinline__ double ord_val(long long k) {
   return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
 }
+// Key of a wave speed for a max-reduction: a NaN of either sign (an
+// inadmissible state) is the largest key, so the cell's speed is NaN and the
+// CFL step reports the state (ord_key alone would order a NaN with its sign
+// bit set below every speed).
+__device__ __forceinline__ long long speed_key(double s) {
+  return isnan_f64(s) ? LLONG_MAX : ord_key(s);
+}
 
 // Detector bounds over the Voronoi neighbourhood (3^d block) from per-cell
 // min/max, then the relaxed DMP interval [m - delta, M + delta] (Eq. relax
@@ -1017,7 +1024,7 @@ __device__ __forceinline__ bool check_subcells(const double* __restrict__ vs, in
     // the two PAD comparisons as exact integer tests
     bad = bad || !(positive_f64(Q[0]) && positive_f64(pe));
     if (lam)
-      r[2 * NV] = max(r[2 * NV], ord_key(f32speed ? wave_speed_f<D>(Q, pe, gamma) : wave_speed<D>(Q, gamma)));
+      r[2 * NV] = max(r[2 * NV], speed_key(f32speed ? wave_speed_f<D>(Q, pe, gamma) : wave_speed<D>(Q, gamma)));
   }
   bad = __syncthreads_or(bad);
   const long long* res = block_max_keys<K>(r, reinterpret_cast<long long*>(red));
@@ -1216,7 +1223,7 @@ __device__ __forceinline__ bool check_subcells_warp(const double* __restrict__ v
     const double pe = Q[D + 1] * Q[0] - 0.5 * kin;
     bad = bad || !(positive_f64(Q[0]) && positive_f64(pe));
     if (lam)
-      r[2 * NV] = max(r[2 * NV], ord_key(f32speed ? wave_speed_f<D>(Q, pe, gamma) : wave_speed<D>(Q, gamma)));
+      r[2 * NV] = max(r[2 * NV], speed_key(f32speed ? wave_speed_f<D>(Q, pe, gamma) : wave_speed<D>(Q, gamma)));
   }
 #pragma unroll
   for (int j = 0; j < K; ++j)

@@ -631,8 +631,8 @@ __global__ void __launch_bounds__(32 * LimWarps<D>::W) k_lim_predict_w(Batch bt)
     const int sc = cross_subcell<D, Ns>((int)(item - tg * NCROSS));
     float cf[3];
 #pragma unroll
-    for (int k = 0; k < D; ++k) cf[k] = (float)p.b.coef[3 + k];
-    const float gm1 = (float)(p.gamma - 1.0);
+    for (int k = 0; k < D; ++k) cf[k] = p.b.coef_f[3 + k];
+    const float gm1 = p.b.coef_f[6];
     const float* Wr = reinterpret_cast<const float*>(p.b.sweep[D - 1]);   // [j][v][NED][ND3]
     for (int e = lane; e < NV * ND3; e += 32) {
       const int v = e / ND3, i = e - v * ND3;
@@ -690,8 +690,8 @@ __global__ void __launch_bounds__(256) k_lim_predict_s2(Batch bt) {
     const Params& p = *bt.pps[it.s];
     const long long j0 = it.j;
     const int sc = cross_subcell<2, Ns>((int)(item - tg * NCROSS));
-    const float cx = (float)p.b.coef[3], cy = (float)p.b.coef[4];
-    const float gm1 = (float)(p.gamma - 1.0);
+    const float cx = p.b.coef_f[3], cy = p.b.coef_f[4];
+    const float gm1 = p.b.coef_f[6];
     const float* Wr = reinterpret_cast<const float*>(p.b.sweep[1]);   // [j][v][NED][ND3]
     float u[NV], q[NV];
 #pragma unroll
@@ -749,6 +749,22 @@ __global__ void __launch_bounds__(256) k_lim_predict_s2(Batch bt) {
   }
 }
 
+// Face traces of the 3D subcell predictor, the input of k_lim_flux_t: for
+// each troubled cell j, axis k, sub-face e normal to k (the enumeration of
+// k_lim_flux: digits over the axes, Ns + 1 values along k and Ns along the
+// others) and side (0: the trace of the left subcell at its high end, 1: of
+// the right subcell at its low end), 27 points times NV variables, where the
+// point t enumerates the node digits of the two tangential axes (lower axis
+// fastest) and then the time node.
+template <int N>
+struct SubTraces {
+  static constexpr int Ns = 2 * N + 1, NSF = Ns * Ns, NFK = (Ns + 1) * NSF, NP = 27;
+  static constexpr long long per_cell = 3LL * NFK * 2 * 5 * NP;     // floats
+  __host__ __device__ static constexpr long long offset(int k, int e, int side) {
+    return ((long long)(k * NFK + e) * 2 + side) * 5 * NP;
+  }
+};
+
 // The 3D subcell predictor in registers: lane l < 27 holds spatial node
 // (a, b, c) = (l % 3, (l / 3) % 3, l / 9) of the subcell and its three time
 // nodes.  The space derivatives take their three operands per axis from the
@@ -756,6 +772,9 @@ __global__ void __launch_bounds__(256) k_lim_predict_s2(Batch bt) {
 // on the lane's own three time nodes, so it needs no exchange at all.  A
 // sweep uses no shared memory and no synchronisation.  The operation order of
 // every output is that of picard_flux / picard_deriv_sub / picard_time_sub.
+// The subcell's traces on the sub-faces the flux kernels use are written in
+// place of its nodal values (SubTraces), each evaluated as k_lim_flux
+// evaluates it from the nodal values.
 template <int N>
 __global__ void __launch_bounds__(256) k_lim_predict_s3(Batch bt) {
   using DM = Dims<3, N>;
@@ -772,6 +791,17 @@ __global__ void __launch_bounds__(256) k_lim_predict_s3(Batch bt) {
     dc[j] = c_D3f[c * 3 + j];
   }
   const int sx = l - a, sy = l - 3 * b, sz = l - 9 * c;   // first lanes of this node's lines
+  // the trace weights in FP32, converted once per thread (FP64 -> FP32
+  // conversions run on the narrow FP64 pipe)
+  float ph0[3], ph1[3];
+  {
+    const Ops* o = bt.pps[0]->ops;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      ph0[j] = (float)o->phi03[j];
+      ph1[j] = (float)o->phi13[j];
+    }
+  }
   const int wpb = blockDim.x >> 5;
   const long long total = bt.pre[bt.n] * NCROSS;
   for (long long item = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); item < total;
@@ -781,8 +811,8 @@ __global__ void __launch_bounds__(256) k_lim_predict_s3(Batch bt) {
     const Params& p = *bt.pps[it.s];
     const long long j0 = it.j;
     const int sc = cross_subcell<3, Ns>((int)(item - tg * NCROSS));
-    const float cf[3] = {(float)p.b.coef[3], (float)p.b.coef[4], (float)p.b.coef[5]};
-    const float gm1 = (float)(p.gamma - 1.0);
+    const float cf[3] = {p.b.coef_f[3], p.b.coef_f[4], p.b.coef_f[5]};
+    const float gm1 = p.b.coef_f[6];
     const float* Wr = reinterpret_cast<const float*>(p.b.sweep[2]);   // [j][v][NED][ND3]
     float u[NV], q[3][NV];
 #pragma unroll
@@ -828,13 +858,134 @@ __global__ void __launch_bounds__(256) k_lim_predict_s3(Batch bt) {
           q[m][v] = u[v] - acc;
         }
     }
-    if (lane < ND3) {
-      float* dst = reinterpret_cast<float*>(p.b.qsub) + ((size_t)j0 * NED + sc) * (size_t)(NV * NST3);
+    // traces: the subcell's block coordinates (local + 1, 0 .. Ns + 1 per axis)
+    using TR = SubTraces<N>;
+    float* trc = reinterpret_cast<float*>(p.b.qsub) + (size_t)j0 * TR::per_cell;
+    const int cc[3] = {sc % (Ns + 2), (sc / (Ns + 2)) % (Ns + 2), sc / ((Ns + 2) * (Ns + 2))};
 #pragma unroll
-      for (int v = 0; v < NV; ++v)
+    for (int k = 0; k < 3; ++k) {
+      // a subcell has faces normal to k in the set when its other coordinates are interior
+      bool inner = true;
 #pragma unroll
-        for (int m = 0; m < 3; ++m) dst[v * NST3 + m * ND3 + l] = q[m][v];
+      for (int x = 0; x < 3; ++x)
+        if (x != k && (cc[x] < 1 || cc[x] > Ns)) inner = false;
+      if (!inner) continue;                                 // uniform over the warp
+      const int ak = k == 0 ? a : (k == 1 ? b : c);
+      const int base = k == 0 ? sx : (k == 1 ? sy : sz);
+      const int st = k == 0 ? 1 : (k == 1 ? 3 : 9);
+      // tangential digits (lower axis first) and the face's tangential index
+      const int d0 = k == 0 ? b : a, d1 = k == 2 ? b : c;
+      int ft = 0, mul = 1;
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        const int ext = (x == k) ? Ns + 1 : Ns;
+        if (x != k) ft += (cc[x] - 1) * mul;
+        mul *= ext;
+      }
+      const int kmul = k == 0 ? 1 : (k == 1 ? Ns : Ns * Ns);   // place of fc[k] in e
+      // left of face cc[k] (high-end trace, lanes with a_k = 2), right of
+      // face cc[k] - 1 (low-end trace, lanes with a_k = 0)
+      const bool wr_hi = ak == 2 && cc[k] <= Ns && lane < ND3;
+      const bool wr_lo = ak == 0 && cc[k] >= 1 && lane < ND3;
+      float* hi = trc + TR::offset(k, ft + cc[k] * kmul, 0);
+      float* lo = trc + TR::offset(k, ft + (cc[k] - 1) * kmul, 1);
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const float x0 = __shfl_sync(0xffffffffu, q[m][v], base);
+          const float x1 = __shfl_sync(0xffffffffu, q[m][v], base + st);
+          const float x2 = __shfl_sync(0xffffffffu, q[m][v], base + 2 * st);
+          const int t = d0 + 3 * d1 + 9 * m;
+          if (wr_hi) hi[v * 27 + t] = ph1[0] * x0 + ph1[1] * x1 + ph1[2] * x2;
+          if (wr_lo) lo[v * 27 + t] = ph0[0] * x0 + ph0[1] * x1 + ph0[2] * x2;
+        }
     }
+  }
+}
+
+// Sub-face fluxes normal to axis k from the face traces of k_lim_predict_s3
+// (3D, FP32 subcell scheme, Rusanov): one warp per sub-face, lane t < 27
+// evaluates the flux at point t of the face (its two traces are contiguous
+// across the lanes), then the GL-weighted sum over the 27 points runs in
+// point order, as k_lim_flux accumulates it.  The result is stored in FP64.
+template <int N, int k>
+__global__ void __launch_bounds__(256) k_lim_flux_t(Batch bt, int pass) {
+  pass = lim_pass(bt, pass);
+  using TR = SubTraces<N>;
+  constexpr int NV = 5, Ns = TR::Ns, NFK = TR::NFK, NP = TR::NP;
+  constexpr int WPB = 8;
+  __shared__ float wts[NP];
+  __shared__ float gsum[WPB][NV][NP + 1];
+  const Ops* o = bt.pps[0]->ops;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x < NP) {
+    // the point's weight, formed in k_lim_flux's order
+    int tt = threadIdx.x;
+    float wt = 1.0f;
+#pragma unroll
+    for (int x = 0; x < 3; ++x)
+      if (x != k) {
+        wt *= (float)o->w3[tt % 3];
+        tt /= 3;
+      }
+    wt *= (float)o->w3[tt];
+    wts[threadIdx.x] = wt;
+  }
+  __syncthreads();
+  const int t = lane < NP ? lane : NP - 1;                 // idle lanes mirror point 26
+  const long long total = bt.pre[bt.n] * NFK;
+  for (long long item = (long long)blockIdx.x * WPB + w; item < total;
+       item += (long long)gridDim.x * WPB) {
+    const long long tg = item / NFK;
+    const LimItem it = lim_item(bt, tg);
+    const Params& p = *bt.pps[it.s];
+    const long long j = it.j;
+    const int e = (int)(item - tg * NFK);
+    // the face's index along k (e = fc0 + ext0 (fc1 + ext1 fc2))
+    const int fck = k == 0 ? e % (Ns + 1) : (k == 1 ? (e / Ns) % (Ns + 1) : e / (Ns * Ns));
+    // reflecting walls: as in k_lim_flux
+    int wall = 0;
+    const bool lo_wall = fck == 0 && p.geo.bc[2 * k] == ADG_BC_REFLECTIVE;
+    const bool hi_wall = fck == Ns && p.geo.bc[2 * k + 1] == ADG_BC_REFLECTIVE;
+    if (lo_wall || hi_wall) {
+      const long long cell = p.b.list[1 - p.cur][pass * p.chunk + j];
+      int ijk[3];
+      cell_coords<3>(cell, p.geo, ijk);
+      if (lo_wall && ijk[k] == 0) wall = -1;
+      if (hi_wall && ijk[k] == p.geo.n[k] - 1) wall = 1;
+    }
+    const float* tr = reinterpret_cast<const float*>(p.b.qsub) + (size_t)j * TR::per_cell;
+    const float* tl = tr + TR::offset(k, e, 0);
+    const float* trr = tr + TR::offset(k, e, 1);
+    float QL[NV], QR[NV], G[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      QL[v] = tl[v * NP + t];
+      QR[v] = trr[v * NP + t];
+    }
+    if (wall < 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) QL[v] = QR[v];
+      QL[1 + k] = -QR[1 + k];
+    } else if (wall > 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) QR[v] = QL[v];
+      QR[1 + k] = -QL[1 + k];
+    }
+    rusanov_f<3>(QL, QR, k, p.b.coef_f[7], G);
+    if (lane < NP) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) gsum[w][v][lane] = G[v];
+    }
+    __syncwarp();
+    if (lane < NV) {
+      float acc = 0.0f;
+#pragma unroll
+      for (int q = 0; q < NP; ++q) acc += wts[q] * gsum[w][lane][q];
+      p.b.fsub[k][((size_t)j * NV + lane) * NFK + e] = (double)acc;
+    }
+    __syncwarp();
   }
 }
 
@@ -854,6 +1005,14 @@ __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
   constexpr int NFK = (Ns + 1) * DM::NSF;
   const Ops* o = bt.pps[0]->ops;
   constexpr int stk = (k == 0) ? 1 : (k == 1 ? 3 : 9);   // node stride of axis k
+  // the GL weights and trace weights in T, converted once per thread
+  T w3t[3], p0t[3], p1t[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    w3t[q] = (T)o->w3[q];
+    p0t[q] = (T)o->phi03[q];
+    p1t[q] = (T)o->phi13[q];
+  }
   for (long long eg = blockIdx.x * (long long)blockDim.x + threadIdx.x; eg < bt.pre[bt.n] * NFK;
        eg += (long long)gridDim.x * blockDim.x) {
     const long long tg = eg / NFK;
@@ -898,6 +1057,7 @@ __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
     T acc[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) acc[v] = T(0);
+    const float gf = p.b.coef_f ? p.b.coef_f[7] : (float)p.gamma;
     // tangential x time nodes: digits over axes != k, then time
     for (int t = 0; t < ND3; ++t) {
       int base = 0, tt = t, wmul = 1;
@@ -909,12 +1069,12 @@ __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
           const int dg = tt % 3;
           tt /= 3;
           base += dg * st;
-          wt *= (T)o->w3[dg];
+          wt *= w3t[dg];
         }
         st *= 3;
       }
       const int m = tt;                 // remaining digit: time node
-      wt *= (T)o->w3[m];
+      wt *= w3t[m];
       base += m * ND3;
       (void)wmul;
       T QL[NV], QR[NV], G[NV];
@@ -922,8 +1082,8 @@ __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
       for (int v = 0; v < NV; ++v) {
         const QT* a = qL + v * NST3 + base;
         const QT* b = qR + v * NST3 + base;
-        QL[v] = (T)o->phi13[0] * (T)a[0] + (T)o->phi13[1] * (T)a[stk] + (T)o->phi13[2] * (T)a[2 * stk];
-        QR[v] = (T)o->phi03[0] * (T)b[0] + (T)o->phi03[1] * (T)b[stk] + (T)o->phi03[2] * (T)b[2 * stk];
+        QL[v] = p1t[0] * (T)a[0] + p1t[1] * (T)a[stk] + p1t[2] * (T)a[2 * stk];
+        QR[v] = p0t[0] * (T)b[0] + p0t[1] * (T)b[stk] + p0t[2] * (T)b[2 * stk];
       }
       if (wall < 0) {
 #pragma unroll
@@ -935,7 +1095,7 @@ __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
         QR[1 + k] = -QL[1 + k];
       }
       if constexpr (sizeof(T) == sizeof(double)) face_flux<D>(p.flux, QL, QR, k, p.gamma, G);
-      else rusanov_f<D>(QL, QR, k, (float)p.gamma, G);
+      else rusanov_f<D>(QL, QR, k, gf, G);
 #pragma unroll
       for (int v = 0; v < NV; ++v) acc[v] += wt * G[v];
     }

@@ -217,6 +217,9 @@ struct Launch {
     const int gs = grid_for(ch * NV * DM::LD, 256), gp = grid_for(ncross, SPB, kNumSM * 16);
     // the subcell predictor stored in FP32 when it runs wholly in FP32
     const bool qf = sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32 && sl.sub32 == 3;
+    // 3D register form with the Rusanov sub-face flux: the predictor leaves
+    // face traces (SubTraces) for k_lim_flux_t instead of nodal values
+    const bool traces = D == 3 && qf && sl.sub_reg && sl.flux == ADG_FLUX_RUSANOV;
     if (sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32) {
       // mixed precision: FP32 reconstruction feeding the FP32 subcell predictor
       k_lim_sweep<D, N, 0, float><<<gs, 256, 0, s>>>(lim, pass);
@@ -229,10 +232,14 @@ struct Launch {
           static const int gw = persistent_grid(k_lim_predict_s2<N>, 256, 0, 1LL << 40);
           const long long want = (ncross + 7) / 8;
           k_lim_predict_s2<N><<<(int)(want < gw ? want : gw), 256, 0, s>>>(lim);
-        } else if (sl.sub_reg && D == 3) {
-          static const int gw = persistent_grid(k_lim_predict_s3<N>, 256, 0, 1LL << 40);
-          const long long want = (ncross + 7) / 8;
-          k_lim_predict_s3<N><<<(int)(want < gw ? want : gw), 256, 0, s>>>(lim);
+        } else if (traces) {
+          if constexpr (D == 3) {
+            static_assert(SubTraces<N>::per_cell <= 2LL * DM::NED * DM::NV * DM::NST3,
+                          "the traces fit the subcell predictor's scratch");
+            static const int gw = persistent_grid(k_lim_predict_s3<N>, 256, 0, 1LL << 40);
+            const long long want = (ncross + 7) / 8;
+            k_lim_predict_s3<N><<<(int)(want < gw ? want : gw), 256, 0, s>>>(lim);
+          }
         } else {
           constexpr int W = LimWarps<D>::W;
           static const int gw = persistent_grid(k_lim_predict_w<D, N>, 32 * W, 0, 1LL << 40);
@@ -251,7 +258,18 @@ struct Launch {
         k_lim_predict<D, N, false, double, false><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, 0);
     }
     const int gf = grid_for(ch * (Ns + 1) * DM::NSF, 256);
-    if (sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32 && sl.flux == ADG_FLUX_RUSANOV) {
+    if (traces) {
+      if constexpr (D == 3) {
+        // one warp per sub-face, persistent
+        const long long want = (ch * (Ns + 1) * DM::NSF + 7) / 8;
+        static const int g0 = persistent_grid(k_lim_flux_t<N, 0>, 256, 0, 1LL << 40);
+        static const int g1 = persistent_grid(k_lim_flux_t<N, 1>, 256, 0, 1LL << 40);
+        static const int g2 = persistent_grid(k_lim_flux_t<N, 2>, 256, 0, 1LL << 40);
+        k_lim_flux_t<N, 0><<<(int)(want < g0 ? want : g0), 256, 0, s>>>(lim, pass);
+        k_lim_flux_t<N, 1><<<(int)(want < g1 ? want : g1), 256, 0, s>>>(lim, pass);
+        k_lim_flux_t<N, 2><<<(int)(want < g2 ? want : g2), 256, 0, s>>>(lim, pass);
+      }
+    } else if (sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32 && sl.flux == ADG_FLUX_RUSANOV) {
       if (qf) {
         k_lim_flux<D, N, 0, float, float><<<gf, 256, 0, s>>>(lim, pass);
         k_lim_flux<D, N, 1, float, float><<<gf, 256, 0, s>>>(lim, pass);
