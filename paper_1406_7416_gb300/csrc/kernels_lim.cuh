@@ -661,7 +661,8 @@ __global__ void __launch_bounds__(32 * LimWarps<D>::W) k_lim_predict_w(Batch bt)
 // The same subcell predictor in 2D with the 27 space-time nodes of a subcell
 // held one per lane in registers: the derivative and time contractions take
 // their three operands from the neighbouring lanes by warp shuffles, so a
-// sweep needs no shared memory and no synchronisation.  Lane l < 27 holds node
+// sweep needs no shared memory and no synchronisation; the first sweep, from
+// the time-constant u (x) 1, takes the time operands from the lane itself.  Lane l < 27 holds node
 // (a, b, m) = (l % 3, (l / 3) % 3, l / 9); the operation order of every output
 // is that of picard_flux / picard_deriv_sub / picard_time_sub.
 template <int N>
@@ -731,9 +732,14 @@ __global__ void __launch_bounds__(256) k_lim_predict_s2(Batch bt) {
       }
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        const float y0 = __shfl_sync(0xffffffffu, S[v], st);
-        const float y1 = __shfl_sync(0xffffffffu, S[v], st + 9);
-        const float y2 = __shfl_sync(0xffffffffu, S[v], st + 18);
+        // the first sweep starts from u (x) 1: the three time nodes of this
+        // lane's spatial node carry the lane's own space term
+        float y0 = S[v], y1 = S[v], y2 = S[v];
+        if (sweep > 0) {
+          y0 = __shfl_sync(0xffffffffu, S[v], st);
+          y1 = __shfl_sync(0xffffffffu, S[v], st + 9);
+          y2 = __shfl_sync(0xffffffffu, S[v], st + 18);
+        }
         float acc = 0.0f;
         acc += km[0] * y0;
         acc += km[1] * y1;
@@ -768,8 +774,10 @@ struct SubTraces {
 // The 3D subcell predictor in registers: lane l < 27 holds spatial node
 // (a, b, c) = (l % 3, (l / 3) % 3, l / 9) of the subcell and its three time
 // nodes.  The space derivatives take their three operands per axis from the
-// lanes on the node's line by warp shuffles; the time contraction (Ktau) runs
-// on the lane's own three time nodes, so it needs no exchange at all.  A
+// lanes on the node's line by warp shuffles; the time contraction
+// (Ktau) runs on the lane's own three time nodes, so it needs no exchange at
+// all, and the first sweep, from the time-constant u (x) 1, forms the space
+// term once for the three time nodes.  A
 // sweep uses no shared memory and no synchronisation.  The operation order of
 // every output is that of picard_flux / picard_deriv_sub / picard_time_sub.
 // The subcell's traces on the sub-faces the flux kernels use are written in
@@ -821,32 +829,42 @@ __global__ void __launch_bounds__(256) k_lim_predict_s3(Batch bt) {
 #pragma unroll
       for (int m = 0; m < 3; ++m) q[m][v] = u[v];
     }
+    // S = sum_k c_k D x_k f_k(Q) at this lane's node, in picard_deriv_sub's order
+    auto space_term = [&](const float* Q, float* Sv) {
+      float F[3][5];
+      euler_fluxes<3, float>(Q, gm1, F);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        float s = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const int base = k == 0 ? sx : (k == 1 ? sy : sz);
+          const int st = k == 0 ? 1 : (k == 1 ? 3 : 9);
+          const float* dr = k == 0 ? da : (k == 1 ? db : dc);
+          const float x0 = __shfl_sync(0xffffffffu, F[k][v], base);
+          const float x1 = __shfl_sync(0xffffffffu, F[k][v], base + st);
+          const float x2 = __shfl_sync(0xffffffffu, F[k][v], base + 2 * st);
+          float acc = 0.0f;
+          acc += dr[0] * x0;
+          acc += dr[1] * x1;
+          acc += dr[2] * x2;
+          s += cf[k] * acc;
+        }
+        Sv[v] = s;
+      }
+    };
 #pragma unroll 1
     for (int sweep = 0; sweep < 3; ++sweep) {
       float S[3][NV];
+      if (sweep == 0) {
+        // the first sweep starts from u (x) 1: its three time nodes carry the
+        // same values, hence the same space term
+        space_term(u, S[0]);
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        float F[3][5];
-        euler_fluxes<3, float>(q[m], gm1, F);
+        for (int v = 0; v < NV; ++v) S[1][v] = S[2][v] = S[0][v];
+      } else {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          float s = 0.0f;
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const int base = k == 0 ? sx : (k == 1 ? sy : sz);
-            const int st = k == 0 ? 1 : (k == 1 ? 3 : 9);
-            const float* dr = k == 0 ? da : (k == 1 ? db : dc);
-            const float x0 = __shfl_sync(0xffffffffu, F[k][v], base);
-            const float x1 = __shfl_sync(0xffffffffu, F[k][v], base + st);
-            const float x2 = __shfl_sync(0xffffffffu, F[k][v], base + 2 * st);
-            float acc = 0.0f;
-            acc += dr[0] * x0;
-            acc += dr[1] * x1;
-            acc += dr[2] * x2;
-            s += cf[k] * acc;
-          }
-          S[m][v] = s;
-        }
+        for (int m = 0; m < 3; ++m) space_term(q[m], S[m]);
       }
 #pragma unroll
       for (int m = 0; m < 3; ++m)
@@ -1069,12 +1087,12 @@ __global__ void __launch_bounds__(256) k_lim_flux(Batch bt, int pass) {
           const int dg = tt % 3;
           tt /= 3;
           base += dg * st;
-          wt *= w3t[dg];
+          wt *= dg == 0 ? w3t[0] : (dg == 1 ? w3t[1] : w3t[2]);   // (registers, not a local array)
         }
         st *= 3;
       }
       const int m = tt;                 // remaining digit: time node
-      wt *= w3t[m];
+      wt *= m == 0 ? w3t[0] : (m == 1 ? w3t[1] : w3t[2]);
       base += m * ND3;
       (void)wmul;
       T QL[NV], QR[NV], G[NV];
