@@ -1246,9 +1246,21 @@ __device__ __forceinline__ bool check_subcells_warp(const double* __restrict__ v
 template <int D, int N>
 struct CdLayout {
   using DM = Dims<D, N>;
-  static constexpr int BUF = (DM::NSD > DM::ND * 4 ? DM::NSD : DM::ND * 4);
-  // per warp: A, B [NV][BUF] doubles, lohi [2 NV] doubles
-  static constexpr int WARP_DBL = 2 * DM::NV * BUF + 2 * DM::NV;
+  // sizes per variable of the projection's stages: u (n^D), after the x pass
+  // (Ns n^(D-1)), after the y pass (Ns^2 n^(D-2)), after the z pass (Ns^3)
+  static constexpr int S0 = DM::ND, S1 = DM::Ns * ipow(DM::n, D - 1);
+  static constexpr int S2 = (D >= 2) ? DM::Ns * DM::Ns * ipow(DM::n, D - 2) : 0;
+  static constexpr int S3 = (D == 3) ? DM::NSD : 0;
+  static constexpr int SA = S0 > S2 ? S0 : S2, SB = S1 > S3 ? S1 : S3;
+  // per warp: A [NV][SA] doubles (u*, then P(u*)), B (the FP64 projection's
+  // other stage, [NV][SB] doubles, or the FP32 projection of the change:
+  // [NV][SA] + [NV][SB] floats), face weights [2 D][n] doubles, lohi [2 NV]
+  static constexpr int A_DBL = DM::NV * SA;
+  static constexpr int B_DBL = (DM::NV * SB > (DM::NV * (SA + SB) + 1) / 2) ? DM::NV * SB
+                                                                            : (DM::NV * (SA + SB) + 1) / 2;
+  static constexpr int DB_FLT = DM::NV * SA;          // offset of the second FP32 stage
+  static constexpr int CW_DBL = 2 * D * DM::n;
+  static constexpr int WARP_DBL = A_DBL + B_DBL + CW_DBL + 2 * DM::NV;
   // per block: P1 [Ns n] doubles and its FP32 copy
   static constexpr int OPS_DBL = DM::Ns * DM::n + (DM::Ns * DM::n + 1) / 2;
 };
@@ -1263,14 +1275,14 @@ __global__ void __launch_bounds__(32 * CD_WARPS) k_correct_detect_w(Batch bt) {
   using DM = Dims<D, N>;
   using LY = CdLayout<D, N>;
   constexpr int n = DM::n, NV = DM::NV, ND = DM::ND, NF = DM::NF, Ns = DM::Ns, NSD = DM::NSD;
-  constexpr int BUF = LY::BUF;
   extern __shared__ double sm[];
   double* P1 = sm;
   float* P1f = reinterpret_cast<float*>(P1 + Ns * n);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   double* A = sm + LY::OPS_DBL + w * LY::WARP_DBL;
-  double* B = A + NV * BUF;
-  double* lohi = B + NV * BUF;
+  double* B = A + LY::A_DBL;
+  double* cw = B + LY::B_DBL;          // [k][side][a]: dt/dx_k phi_side(a) / w_a
+  double* lohi = cw + LY::CW_DBL;
   const Ops* o = bt.pps[0]->ops;
   for (int i = threadIdx.x; i < Ns * n; i += 32 * CD_WARPS) {
     P1[i] = o->P1[i];
@@ -1285,7 +1297,7 @@ __global__ void __launch_bounds__(32 * CD_WARPS) k_correct_detect_w(Batch bt) {
     const long long cell = g - bt.pre[sidx];
     const double dt = *p.b.dt;
     if (!(dt > 0.0)) continue;          // (warp-uniform)
-    double c[3];
+    double c[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < D; ++k) c[k] = p.b.coef[k];
     const int nxt = 1 - p.cur;
@@ -1296,7 +1308,14 @@ __global__ void __launch_bounds__(32 * CD_WARPS) k_correct_detect_w(Batch bt) {
     const bool delta = vkeep && p.b.vok[cell] && (p.stamp & 15) != 0;
     const double* Un = p.b.U[p.cur] + cell * (NV * ND);
     float* dA = reinterpret_cast<float*>(B);
-    float* dB = dA + NV * BUF;
+    float* dB = dA + LY::DB_FLT;
+    // the face terms' weights of this cell's step, one product each
+    for (int q = lane; q < 2 * D * n; q += 32) {
+      const int k = q / (2 * n), r = q - k * 2 * n;
+      const double ck = k == 0 ? c[0] : (k == 1 ? c[1] : c[2]);   // (registers, not a local array)
+      cw[q] = ck * (r < n ? o->phi0w[r] : o->phi1w[r - n]);
+    }
+    __syncwarp();
     for (int e = lane; e < NV * ND; e += 32) {
       const int v = e / ND, i = e - v * ND;
       double acc = Uo[e];
@@ -1309,7 +1328,9 @@ __global__ void __launch_bounds__(32 * CD_WARPS) k_correct_detect_w(Batch bt) {
         const long long fhi = face_index<D>(p.geo, ijk, k, ijk[k] + 1);
         const double Glo = p.b.G[k][(flo * NV + v) * NF + ts];
         const double Ghi = p.b.G[k][(fhi * NV + v) * NF + ts];
-        acc -= c[k] * (o->phi1w[ak] * Ghi - o->phi0w[ak] * Glo);
+        // u* -= dt/dx_k (phi1(a)/w_a Ghi - phi0(a)/w_a Glo), as two FMAs
+        acc = fma(-cw[(2 * k + 1) * n + ak], Ghi, acc);
+        acc = fma(cw[2 * k * n + ak], Glo, acc);
       }
       A[e] = acc;
       Uo[e] = acc;
