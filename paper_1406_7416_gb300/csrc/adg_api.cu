@@ -167,6 +167,7 @@ Params make_params(const adg_state* st) {
   p.cap = st->cap;
   p.chunk = st->chunk;
   p.gamma = st->gamma;
+  p.gam2f = (float)(st->gamma * (st->gamma - 1.0));
   p.eps = st->eps;
   p.floor = st->floor;
   p.ops = st->ops_dev;

@@ -133,6 +133,7 @@ struct Params {
   int cascade;           // 1: first-order layer after WENO3 (Sec. 6, Fig. algo2)
   int flux;              // numerical flux of DG faces and WENO3 sub-faces: 0 Rusanov, 1 Osher
   double cfl;            // the state's CFL number for batched CFL steps (0: none)
+  float gam2f;           // gamma (gamma - 1) in FP32: the mixed-precision wave speed's factor
 };
 
 // A batch of states of one (dimension, degree, precision) stepped by the same
@@ -543,16 +544,15 @@ __device__ __forceinline__ double wave_speed(const double* Q, double gamma) {
   return vm + sqrt(gamma * p * r);
 }
 
-// The same speed for mixed precision (it only sets the CFL step): rho p =
-// (gamma - 1)(E rho - |m|^2 / 2) in FP64, free of the cancellation FP32 would
-// suffer at high Mach numbers (pe = E rho - |m|^2 / 2 from the caller, which
-// tests it for positivity), then c = sqrt(gamma rho p) / rho and the
-// velocities in FP32 from inputs narrowed toward zero on the integer pipe.
-// Inadmissible states give NaN as in wave_speed.
+// The same speed for mixed precision (it only sets the CFL step): pe =
+// E rho - |m|^2 / 2 comes from the caller in FP64 (free of the cancellation
+// FP32 would suffer at high Mach numbers; the caller tests it for
+// positivity), then c = sqrt(gamma (gamma - 1) pe) / rho with g2f =
+// gamma (gamma - 1) and the velocities in FP32, from inputs narrowed toward
+// zero on the integer pipe.  Inadmissible states give NaN as in wave_speed.
 #if defined(__CUDACC__)
 template <int D>
-__device__ __forceinline__ double wave_speed_f(const double* Q, double pe, double gamma) {
-  const double rp = (gamma - 1.0) * pe;
+__device__ __forceinline__ double wave_speed_f(const double* Q, double pe, float g2f) {
   const float r = 1.0f / narrow_f64_rz(Q[0]);
   float vm = 0.0f;
 #pragma unroll
@@ -560,7 +560,7 @@ __device__ __forceinline__ double wave_speed_f(const double* Q, double pe, doubl
     const float a = fabsf(narrow_f64_rz(Q[1 + k])) * r;
     vm = (a > vm || a != a) ? a : vm;
   }
-  return widen_f32(vm + sqrtf(narrow_f64_rz(gamma * rp)) * r);
+  return widen_f32(vm + sqrtf(g2f * narrow_f64_rz(pe)) * r);
 }
 #endif
 

@@ -899,6 +899,11 @@ __device__ __forceinline__ long long ord_key(double x) {
 __device__ __forceinline__ double ord_val(long long k) {
   return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
 }
+// max(a, b) of two doubles that are not negative (+0 included) and not NaN:
+// their bit patterns order as signed integers
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+  return __double_as_longlong(a) >= __double_as_longlong(b) ? a : b;
+}
 // Key of a wave speed for a max-reduction: a NaN of either sign (an
 // inadmissible state) is the largest key, so the cell's speed is NaN and the
 // CFL step reports the state (ord_key alone would order a NaN with its sign
@@ -963,8 +968,10 @@ __device__ __forceinline__ void dmp_interval_lane(const Params& p, const double*
   }
   const double mn = kmn == LLONG_MAX ? INFINITY : ord_val(kmn);
   const double mx = kmx == LLONG_MIN ? -INFINITY : ord_val(kmx);
-  const double scale = fmax(1.0, fmax(fabs(mx), fabs(mn)));
-  const double delta = fmax(p.eps * (mx - mn), p.floor * scale);
+  // fmax of non-negative doubles as integer compares of their bit patterns
+  // (the same result; the FP64 pipe runs fmax)
+  const double scale = max_nonneg(1.0, max_nonneg(fabs(mx), fabs(mn)));
+  const double delta = max_nonneg(p.eps * (mx - mn), p.floor * scale);
   lohi[2 * v] = mn - delta;
   lohi[2 * v + 1] = mx + delta;
 }
@@ -1002,7 +1009,8 @@ __device__ __forceinline__ const long long* block_max_keys(long long* r, long lo
 template <int D>
 __device__ __forceinline__ bool check_subcells(const double* __restrict__ vs, int nsub,
                                                const double* lohi, double gamma, double* mm,
-                                               double* lam, double* red, bool f32speed = false) {
+                                               double* lam, double* red, bool f32speed = false,
+                                               float g2f = 0.0f) {
   constexpr int NV = D + 2, K = 2 * NV + 1;
   bool bad = false;
   long long r[K];
@@ -1024,7 +1032,7 @@ __device__ __forceinline__ bool check_subcells(const double* __restrict__ vs, in
     // the two PAD comparisons as exact integer tests
     bad = bad || !(positive_f64(Q[0]) && positive_f64(pe));
     if (lam)
-      r[2 * NV] = max(r[2 * NV], speed_key(f32speed ? wave_speed_f<D>(Q, pe, gamma) : wave_speed<D>(Q, gamma)));
+      r[2 * NV] = max(r[2 * NV], speed_key(f32speed ? wave_speed_f<D>(Q, pe, g2f) : wave_speed<D>(Q, gamma)));
   }
   bad = __syncthreads_or(bad);
   const long long* res = block_max_keys<K>(r, reinterpret_cast<long long*>(red));
@@ -1147,7 +1155,7 @@ __global__ void __launch_bounds__(128, 8) k_correct_detect(Batch bt) {
     __syncthreads();
     double lam = 0.0;
     const bool bad = check_subcells<D>(vs, NSD, lohi, p.gamma, mm, p.lam_mode ? &lam : nullptr, red,
-                                       p.prec == ADG_PREC_MIXED_FP32);
+                                       p.prec == ADG_PREC_MIXED_FP32, p.gam2f);
     if (tid == 0) {
       int slot = -1;
       if (bad || p.force) {
@@ -1202,7 +1210,8 @@ __device__ __forceinline__ T* apply_ct_warp(T* a, T* b, const T* M, int lane) {
 template <int D>
 __device__ __forceinline__ bool check_subcells_warp(const double* __restrict__ vs, int nsub,
                                                     const double* lohi, double gamma, double* mm,
-                                                    double* lam, bool f32speed, int lane) {
+                                                    double* lam, bool f32speed, int lane,
+                                                    float g2f) {
   constexpr int NV = D + 2, K = 2 * NV + 1;
   bool bad = false;
   long long r[K];
@@ -1223,7 +1232,7 @@ __device__ __forceinline__ bool check_subcells_warp(const double* __restrict__ v
     const double pe = Q[D + 1] * Q[0] - 0.5 * kin;
     bad = bad || !(positive_f64(Q[0]) && positive_f64(pe));
     if (lam)
-      r[2 * NV] = max(r[2 * NV], speed_key(f32speed ? wave_speed_f<D>(Q, pe, gamma) : wave_speed<D>(Q, gamma)));
+      r[2 * NV] = max(r[2 * NV], speed_key(f32speed ? wave_speed_f<D>(Q, pe, g2f) : wave_speed<D>(Q, gamma)));
   }
 #pragma unroll
   for (int j = 0; j < K; ++j)
@@ -1355,7 +1364,7 @@ __global__ void __launch_bounds__(32 * CD_WARPS) k_correct_detect_w(Batch bt) {
     __syncwarp();
     double lam = 0.0, mm[2 * NV];
     const bool bad = check_subcells_warp<D>(vs, NSD, lohi, p.gamma, mm, p.lam_mode ? &lam : nullptr,
-                                            p.prec == ADG_PREC_MIXED_FP32, lane);
+                                            p.prec == ADG_PREC_MIXED_FP32, lane, p.gam2f);
     if (lane == 0) {
       int slot = -1;
       if (bad || p.force) {

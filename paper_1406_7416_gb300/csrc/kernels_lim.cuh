@@ -666,6 +666,15 @@ __global__ void __launch_bounds__(32 * LimWarps<D>::W) k_lim_predict_w(Batch bt)
 // (a, b, m) = (l % 3, (l / 3) % 3, l / 9); the operation order of every output
 // is that of picard_flux / picard_deriv_sub / picard_time_sub.
 template <int N>
+struct SubTraces2 {
+  static constexpr int Ns = 2 * N + 1, NFK = (Ns + 1) * Ns, NP = 9;
+  static constexpr long long per_cell = 2LL * NFK * 2 * 4 * NP;     // floats
+  __host__ __device__ static constexpr long long offset(int k, int e, int side) {
+    return ((long long)(k * NFK + e) * 2 + side) * 4 * NP;
+  }
+};
+
+template <int N, bool TRACES>
 __global__ void __launch_bounds__(256) k_lim_predict_s2(Batch bt) {
   using DM = Dims<2, N>;
   constexpr int NV = 4, NST3 = 27, ND3 = 9, NED = DM::NED, Ns = DM::Ns;
@@ -682,6 +691,16 @@ __global__ void __launch_bounds__(256) k_lim_predict_s2(Batch bt) {
     km[j] = c_K3f[m * 3 + j];
   }
   const int sx = l - a, sy = l - 3 * b, st = l - 9 * m;   // first lanes of this node's lines
+  // the trace weights in FP32, converted once per thread
+  float ph0[3], ph1[3];
+  {
+    const Ops* o = bt.pps[0]->ops;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      ph0[j] = (float)o->phi03[j];
+      ph1[j] = (float)o->phi13[j];
+    }
+  }
   const int wpb = blockDim.x >> 5;
   const long long total = bt.pre[bt.n] * NCROSS;
   for (long long item = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); item < total;
@@ -747,11 +766,133 @@ __global__ void __launch_bounds__(256) k_lim_predict_s2(Batch bt) {
         q[v] = u[v] - acc;
       }
     }
-    if (lane < NST3) {
-      float* dst = reinterpret_cast<float*>(p.b.qsub) + ((size_t)j0 * NED + sc) * (size_t)(NV * NST3);
+    if constexpr (!TRACES) {
+      if (lane < NST3) {
+        float* dst = reinterpret_cast<float*>(p.b.qsub) + ((size_t)j0 * NED + sc) * (size_t)(NV * NST3);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) dst[v * NST3 + l] = q[v];
+        for (int v = 0; v < NV; ++v) dst[v * NST3 + l] = q[v];
+      }
+    } else {
+      // the subcell's traces on the sub-faces of the flux kernels (SubTraces2),
+      // each evaluated as k_lim_flux evaluates it from the nodal values
+      using TR = SubTraces2<N>;
+      float* trc = reinterpret_cast<float*>(p.b.qsub) + (size_t)j0 * TR::per_cell;
+      const int cc[2] = {sc % (Ns + 2), sc / (Ns + 2)};
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int o = 1 - k;                              // the tangential axis
+        if (cc[o] < 1 || cc[o] > Ns) continue;            // (uniform over the warp)
+        const int ak = k == 0 ? a : b;
+        const int base = k == 0 ? sx : sy;
+        const int stk = k == 0 ? 1 : 3;
+        const int t = (k == 0 ? b : a) + 3 * m;           // tangential digit, then time
+        const int ft = (cc[o] - 1) * (k == 0 ? Ns + 1 : 1);
+        const int kmul = k == 0 ? 1 : Ns;
+        const bool wr_hi = ak == 2 && cc[k] <= Ns && lane < NST3;
+        const bool wr_lo = ak == 0 && cc[k] >= 1 && lane < NST3;
+        float* hi = trc + TR::offset(k, ft + cc[k] * kmul, 0);
+        float* lo = trc + TR::offset(k, ft + (cc[k] - 1) * kmul, 1);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          const float x0 = __shfl_sync(0xffffffffu, q[v], base);
+          const float x1 = __shfl_sync(0xffffffffu, q[v], base + stk);
+          const float x2 = __shfl_sync(0xffffffffu, q[v], base + 2 * stk);
+          if (wr_hi) hi[v * 9 + t] = ph1[0] * x0 + ph1[1] * x1 + ph1[2] * x2;
+          if (wr_lo) lo[v * 9 + t] = ph0[0] * x0 + ph0[1] * x1 + ph0[2] * x2;
+        }
+      }
     }
+  }
+}
+
+// Sub-face fluxes normal to axis k from the face traces of k_lim_predict_s2
+// (2D, FP32 subcell scheme, Rusanov): three sub-faces per warp, lane
+// 9 f + t evaluating the flux at point t of sub-face f from two contiguous
+// trace rows, then the GL-weighted sum over each sub-face's 9 points in point
+// order, as k_lim_flux accumulates it.  The result is stored in FP64.
+template <int N, int k>
+__global__ void __launch_bounds__(256) k_lim_flux_t2(Batch bt, int pass) {
+  pass = lim_pass(bt, pass);
+  using TR = SubTraces2<N>;
+  constexpr int NV = 4, Ns = TR::Ns, NFK = TR::NFK, NP = TR::NP;
+  constexpr int WPB = 8;
+  __shared__ float wts[NP];
+  __shared__ float gsum[WPB][3][NV][NP + 1];
+  const Ops* o = bt.pps[0]->ops;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x < NP) {
+    // the point's weight, formed in k_lim_flux's order (tangential digit, then time)
+    const int d = threadIdx.x % 3, mt = threadIdx.x / 3;
+    float wt = 1.0f;
+    wt *= (float)o->w3[d];
+    wt *= (float)o->w3[mt];
+    wts[threadIdx.x] = wt;
+  }
+  __syncthreads();
+  const int fl = lane < 27 ? lane / 9 : 2, t = lane < 27 ? lane % 9 : 8;   // idle lanes mirror lane 26
+  const long long total = bt.pre[bt.n] * NFK;
+  const long long groups = (total + 2) / 3;
+  for (long long grp = (long long)blockIdx.x * WPB + w; grp < groups; grp += (long long)gridDim.x * WPB) {
+    const long long f = grp * 3 + fl;
+    const bool live = f < total;
+    const long long tg = live ? f / NFK : 0;
+    const LimItem it = lim_item(bt, tg);
+    const Params& p = *bt.pps[it.s];
+    const long long j = it.j;
+    const int e = live ? (int)(f - tg * NFK) : 0;
+    const int fck = k == 0 ? e % (Ns + 1) : e / Ns;     // the face's index along k
+    int wall = 0;
+    const bool lo_wall = fck == 0 && p.geo.bc[2 * k] == ADG_BC_REFLECTIVE;
+    const bool hi_wall = fck == Ns && p.geo.bc[2 * k + 1] == ADG_BC_REFLECTIVE;
+    if (live && (lo_wall || hi_wall)) {
+      const long long cell = p.b.list[1 - p.cur][pass * p.chunk + j];
+      int ijk[3];
+      cell_coords<2>(cell, p.geo, ijk);
+      if (lo_wall && ijk[k] == 0) wall = -1;
+      if (hi_wall && ijk[k] == p.geo.n[k] - 1) wall = 1;
+    }
+    float G[NV] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (live) {
+      const float* tr = reinterpret_cast<const float*>(p.b.qsub) + (size_t)j * TR::per_cell;
+      const float* tl = tr + TR::offset(k, e, 0);
+      const float* trr = tr + TR::offset(k, e, 1);
+      float QL[NV], QR[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        QL[v] = tl[v * NP + t];
+        QR[v] = trr[v * NP + t];
+      }
+      if (wall < 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) QL[v] = QR[v];
+        QL[1 + k] = -QR[1 + k];
+      } else if (wall > 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) QR[v] = QL[v];
+        QR[1 + k] = -QL[1 + k];
+      }
+      rusanov_f<2>(QL, QR, k, p.b.coef_f[7], G);
+    }
+    if (lane < 27) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) gsum[w][fl][v][t] = G[v];
+    }
+    __syncwarp();
+    if (lane < 3 * NV) {
+      const int ff = lane / NV, v = lane - ff * NV;
+      const long long fo = grp * 3 + ff;
+      if (fo < total) {
+        const long long tgo = fo / NFK;
+        const LimItem ito = lim_item(bt, tgo);
+        const Params& po = *bt.pps[ito.s];
+        const int eo = (int)(fo - tgo * NFK);
+        float acc = 0.0f;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) acc += wts[q] * gsum[w][ff][v][q];
+        po.b.fsub[k][((size_t)ito.j * NV + v) * NFK + eo] = (double)acc;
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -1190,7 +1331,7 @@ __global__ void __launch_bounds__(128) k_lim_update(Batch bt, int pass) {
     __syncthreads();
     double lam = 0.0;
     const bool bad = check_subcells<D>(A, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red,
-                                       p.prec == ADG_PREC_MIXED_FP32);
+                                       p.prec == ADG_PREC_MIXED_FP32, p.gam2f);
     if (tid == 0) {
       if (p.lam_mode) p.b.lam[cell] = lam;
       if (bad && p.cascade) {
@@ -1336,7 +1477,7 @@ __global__ void __launch_bounds__(128) k_lim_fix(Batch bt) {
     }
     double lam = 0.0;
     check_subcells<D>(vs, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red,
-                      p.prec == ADG_PREC_MIXED_FP32);
+                      p.prec == ADG_PREC_MIXED_FP32, p.gam2f);
     if (tid == 0 && p.lam_mode) p.b.lam[cell] = lam;
     if (tid < 2 * NV) p.b.cmm[nxt][cell * 2 * NV + tid] = mm[tid];
   }
@@ -1466,7 +1607,7 @@ __global__ void __launch_bounds__(128) k_lim_fallback(Batch bt) {
     for (int e = tid; e < NV * NSD; e += nth) st[e] = A[e];
     double lam = 0.0;
     const bool bad = check_subcells<D>(A, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red,
-                                       p.prec == ADG_PREC_MIXED_FP32);
+                                       p.prec == ADG_PREC_MIXED_FP32, p.gam2f);
     if (tid == 0) {
       if (p.lam_mode) p.b.lam[cell] = lam;
       if (bad) atomicAdd(&p.b.counters[CNT_INADM], 1);
@@ -1581,7 +1722,7 @@ __global__ void __launch_bounds__(128) k_lim_refix(Batch bt) {
     __syncthreads();
     double lam = 0.0;
     const bool bad = check_subcells<D>(A, NSD, nullptr, p.gamma, mm, p.lam_mode ? &lam : nullptr, red,
-                                       p.prec == ADG_PREC_MIXED_FP32);
+                                       p.prec == ADG_PREC_MIXED_FP32, p.gam2f);
     if (tid == 0) {
       if (p.lam_mode) p.b.lam[cell] = lam;
       if (bad) atomicAdd(&p.b.counters[CNT_INADM], 1);

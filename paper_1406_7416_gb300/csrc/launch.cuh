@@ -217,9 +217,10 @@ struct Launch {
     const int gs = grid_for(ch * NV * DM::LD, 256), gp = grid_for(ncross, SPB, kNumSM * 16);
     // the subcell predictor stored in FP32 when it runs wholly in FP32
     const bool qf = sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32 && sl.sub32 == 3;
-    // 3D register form with the Rusanov sub-face flux: the predictor leaves
-    // face traces (SubTraces) for k_lim_flux_t instead of nodal values
-    const bool traces = D == 3 && qf && sl.sub_reg && sl.flux == ADG_FLUX_RUSANOV;
+    // register form with the Rusanov sub-face flux: the predictor leaves face
+    // traces (SubTraces2 / SubTraces) for k_lim_flux_t2 / k_lim_flux_t instead
+    // of nodal values
+    const bool traces = qf && sl.sub_reg && sl.flux == ADG_FLUX_RUSANOV;
     if (sl.prec == ADG_PREC_MIXED_FP32 && sl.sub_f32) {
       // mixed precision: FP32 reconstruction feeding the FP32 subcell predictor
       k_lim_sweep<D, N, 0, float><<<gs, 256, 0, s>>>(lim, pass);
@@ -229,9 +230,18 @@ struct Launch {
         // one warp per subcell, blocks looping over the pass's subcells; by
         // default the subcell's space-time nodes live in the warp's registers
         if (sl.sub_reg && D == 2) {
-          static const int gw = persistent_grid(k_lim_predict_s2<N>, 256, 0, 1LL << 40);
-          const long long want = (ncross + 7) / 8;
-          k_lim_predict_s2<N><<<(int)(want < gw ? want : gw), 256, 0, s>>>(lim);
+          if constexpr (D == 2) {
+            static_assert(SubTraces2<N>::per_cell <= 2LL * DM::NED * DM::NV * DM::NST3,
+                          "the traces fit the subcell predictor's scratch");
+            const long long want = (ncross + 7) / 8;
+            if (traces) {
+              static const int gw = persistent_grid(k_lim_predict_s2<N, true>, 256, 0, 1LL << 40);
+              k_lim_predict_s2<N, true><<<(int)(want < gw ? want : gw), 256, 0, s>>>(lim);
+            } else {
+              static const int gw = persistent_grid(k_lim_predict_s2<N, false>, 256, 0, 1LL << 40);
+              k_lim_predict_s2<N, false><<<(int)(want < gw ? want : gw), 256, 0, s>>>(lim);
+            }
+          }
         } else if (traces) {
           if constexpr (D == 3) {
             static_assert(SubTraces<N>::per_cell <= 2LL * DM::NED * DM::NV * DM::NST3,
@@ -258,7 +268,16 @@ struct Launch {
         k_lim_predict<D, N, false, double, false><<<gp, SPB * DM::NST3, 0, s>>>(lim, pass, 0);
     }
     const int gf = grid_for(ch * (Ns + 1) * DM::NSF, 256);
-    if (traces) {
+    if (traces && D == 2) {
+      if constexpr (D == 2) {
+        // three sub-faces per warp, persistent
+        const long long want = ((ch * (Ns + 1) * DM::NSF + 2) / 3 + 7) / 8;
+        static const int g0 = persistent_grid(k_lim_flux_t2<N, 0>, 256, 0, 1LL << 40);
+        static const int g1 = persistent_grid(k_lim_flux_t2<N, 1>, 256, 0, 1LL << 40);
+        k_lim_flux_t2<N, 0><<<(int)(want < g0 ? want : g0), 256, 0, s>>>(lim, pass);
+        k_lim_flux_t2<N, 1><<<(int)(want < g1 ? want : g1), 256, 0, s>>>(lim, pass);
+      }
+    } else if (traces) {
       if constexpr (D == 3) {
         // one warp per sub-face, persistent
         const long long want = (ch * (Ns + 1) * DM::NSF + 7) / 8;

@@ -5,9 +5,13 @@ bit for bit.
 The register form holds one subcell per warp with its 27 spatial nodes one
 per lane (2D: the 27 space-time nodes one per lane; 3D: each lane also holds
 its node's three time nodes) and exchanges line operands by warp shuffles;
-the shared-memory form keeps the subcell's nodes in shared memory.  Both take
-every output through the same operation sequence.  Every cell is forced
-through the limiter, so every subcell of the grid runs the predictor."""
+the shared-memory form keeps the subcell's nodes in shared memory.  With the
+Rusanov sub-face flux the register form writes the subcells' face traces and
+the fluxes are taken per sub-face from them; the shared-memory form stores
+nodal values and the flux kernel forms the traces.  Both take every output
+through the same operation sequence.  Every cell is forced through the
+limiter in one run of each case, so every subcell of the grid runs the
+predictor."""
 import numpy as np
 import pytest
 
@@ -42,6 +46,10 @@ CASES = {
     "explosion3d_N1_5": lambda: inputs.explosion_3d(n=5, N=1),
     "explosion3d_N2_5": lambda: inputs.explosion_3d(n=5, N=2),
     "explosion3d_N3_6": lambda: inputs.explosion_3d(n=6, N=3),
+    # reflecting walls on every face (the sub-face fluxes' wall rule)
+    "closed_box2d_N3_8": lambda: inputs.closed_box(n=8, N=3, dim=2),
+    "closed_box3d_N2_4": lambda: inputs.closed_box(n=4, N=2, dim=3),
+    "double_mach_N5": lambda: inputs.double_mach(nx=14, ny=4, N=5),
 }
 
 
