@@ -12,7 +12,9 @@ Metric: space-time DOF updates per second = cells * (N+1)^(d+1) * steps / s
 path: FP32 Picard sweeps; for N <= 5 no FP64 sweep follows and the final stage
 adds the FP32 space-time correction to the FP64 DOFs term by term, for N >= 6
 one FP64 sweep follows; FP32 subcell scheme with an FP64 update; FP64
-corrector, detector comparisons, projections and flux correction.  The FP64
+corrector, detector tests and flux correction, the detector's subcell
+averages being the kept FP64 averages plus an FP32 projection of the step's
+change (an FP64 projection every 16th step).  The FP64
 path is reported beside it, with the L1 distance between the two after the
 same steps against the stated tolerance of the workload.
 
@@ -534,6 +536,46 @@ def emit_line(args, m, e2e, world, tune, subs, rates=None):
     print(json.dumps(line), flush=True)
 
 
+def run_serving_solo(args):
+    """Serving runs alone (ids from --serving-solo), each to min(--t-end, its
+    final time) at the serving CFL number, in FP64, in mixed precision with
+    the FP64 subcell scheme and in mixed precision: whether each reaches its
+    end time, and how long it takes.  One JSON line per run and mode."""
+    from paper_1406_7416_gb300 import adg, build_lib, inputs
+    build_lib.build()
+    adg.load_library()
+    specs = inputs.serving_runs(count=args.runs)
+    modes = (("fp64", adg.PREC_FP64, {}),
+             ("mixed_fp64_subcells", adg.PREC_MIXED_FP32,
+              {adg.OPT_SUBCELL_FP32: 0, adg.OPT_SUBCELL_FP64_SWEEPS: 3}),
+             ("mixed", adg.PREC_MIXED_FP32, {}))
+    for rid in (int(x) for x in args.serving_solo.split(",")):
+        w = specs[rid]
+        t_end = min(w["t_end"], args.t_end)
+        for name, prec, opts in modes:
+            s = adg.Solver.from_workload(w, prec)
+            for k, v in opts.items():
+                s.set_option(k, v)
+            s.set_option(adg.OPT_END_TIME, t_end)
+            s.init_problem(w["problem"])
+            t0 = time.perf_counter()
+            ok = True
+            try:
+                while True:
+                    for _ in range(64):
+                        s.step_cfl(args.serving_cfl_factor * w["cfl"])
+                    s.status()
+                    if s.time()[0] >= t_end * (1 - 1e-12):
+                        break
+            except adg.AdgError:
+                ok = False
+            t, steps = s.time()
+            print(json.dumps({"run": rid, "name": w["name"], "mode": name, "reached_end": ok,
+                              "t": t, "t_end": t_end, "steps": steps,
+                              "seconds": round(time.perf_counter() - t0, 2)}), flush=True)
+            s.close()
+
+
 def run_serving(args):
     """Serving: independent 2D runs (grids from {32,64,128,256}^2, N in {3,5},
     the 2D Riemann problems of Sec. 5.6 with seeded jitter, each to
@@ -559,8 +601,10 @@ def run_serving(args):
     # --capacity-runs runs (all by default), scaled to the whole stream by work
     ncap = args.capacity_runs or len(specs)
     runs = [RunSpec(w, w["t_end"], 0.0, i) for i, w in enumerate(specs[:ncap])]
-    closed = Server(budget, adg.PREC_MIXED_FP32, retries=args.serving_retries).serve(
-        runs, max_wall=args.max_wall)
+    retry = dict(retries=args.serving_retries,
+                 retry_prec=adg.PREC_FP64 if args.serving_retry_prec == "fp64" else None,
+                 retry_cfl_factor=args.serving_retry_cfl_factor)
+    closed = Server(budget, adg.PREC_MIXED_FP32, **retry).serve(runs, max_wall=args.max_wall)
     print(json.dumps({"closed_loop": closed}), file=sys.stderr, flush=True)
     capacity = closed["runs"] / closed["wall_s"]
     rate = 0.8 * capacity
@@ -582,8 +626,7 @@ def run_serving(args):
         sv.close()
     arrivals = poisson_arrivals(len(specs), rate, seed=1406 + 4)
     runs = [RunSpec(w, w["t_end"], a, i) for i, (w, a) in enumerate(zip(specs, arrivals))]
-    opened = Server(budget, adg.PREC_MIXED_FP32, retries=args.serving_retries).serve(
-        runs, max_wall=args.max_wall)
+    opened = Server(budget, adg.PREC_MIXED_FP32, **retry).serve(runs, max_wall=args.max_wall)
     line = {"metric": METRIC, "value": opened["stdof_per_s"], "unit": UNIT, "n_gpus": 1,
             "steps": opened["steps"], "warmup": 0, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
@@ -592,7 +635,8 @@ def run_serving(args):
                                    f"{{32,64,128,256}}^2, N in {{3,5}}, t_end={args.t_end}, "
                                    f"CFL {args.serving_cfl_factor} x 0.9/(d(2N+1)), "
                                    "Poisson arrivals at 80% of the measured capacity; "
-                                   f"a failed run restarts at half its CFL number, "
+                                   f"a failed run restarts in {args.serving_retry_prec} at "
+                                   f"{args.serving_retry_cfl_factor} x its CFL number, "
                                    f"{args.serving_retries} time(s) at most",
                        "hbm_budget_bytes": budget, "mixed precision": True},
             "latency_p50_s": opened["latency_p50_s"], "latency_p99_s": opened["latency_p99_s"],
@@ -657,11 +701,18 @@ def main():
     ap.add_argument("--t-end", type=float, default=0.02,
                     help="serving: end time cap of every run (each stops at min(cap, its final time))")
     ap.add_argument("--serving-retries", type=int, default=1,
-                    help="serving: restarts of a failed run, each at half its CFL number")
+                    help="serving: restarts of a failed run (see --serving-retry-*)")
+    ap.add_argument("--serving-retry-prec", default="fp64", choices=["fp64", "same"],
+                    help="serving: precision of a restarted run")
+    ap.add_argument("--serving-retry-cfl-factor", type=float, default=1.0,
+                    help="serving: factor on a restarted run's CFL number")
     ap.add_argument("--serving-cfl-factor", type=float, default=0.5,
                     help="serving: fraction of the CFL number of Eq. (cfl) the runs take")
     ap.add_argument("--capacity-runs", type=int, default=0,
                     help="serving: runs of the closed-loop capacity pass (0: all)")
+    ap.add_argument("--serving-solo", default="",
+                    help="serving: comma-separated run ids to run alone in FP64, mixed with FP64 "
+                         "subcells and mixed, each to its end time")
     ap.add_argument("--max-wall", type=float, default=120.0,
                     help="serving: no admissions after this many seconds per pass")
     args = ap.parse_args()
@@ -672,6 +723,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serving" and args.serving_solo:
+        run_serving_solo(args)
     elif args.workload == "serving":
         run_serving(args)
     else:

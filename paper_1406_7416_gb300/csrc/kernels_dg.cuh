@@ -904,6 +904,12 @@ __device__ __forceinline__ double ord_val(long long k) {
 __device__ __forceinline__ double max_nonneg(double a, double b) {
   return __double_as_longlong(a) >= __double_as_longlong(b) ? a : b;
 }
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2 by the
+// TMA unit (cp.async.bulk.prefetch): no shared memory, nothing to wait for.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Key of a wave speed for a max-reduction: a NaN of either sign (an
 // inadmissible state) is the largest key, so the cell's speed is NaN and the
 // CFL step reports the state (ord_key alone would order a NaN with its sign
@@ -1304,6 +1310,22 @@ __global__ void __launch_bounds__(32 * CD_WARPS) k_correct_detect_w(Batch bt) {
     const int sidx = batch_state(bt, g);
     const Params& p = *bt.pps[sidx];
     const long long cell = g - bt.pre[sidx];
+    if (lane == 0) {
+      // the next cell's DOF blocks and kept averages, into L2 while this one runs
+      const long long gn = g + (long long)gridDim.x * CD_WARPS;
+      if (gn < total) {
+        const int sn = batch_state(bt, gn);
+        const Params* pn = bt.pps[sn];
+        const long long cn = gn - bt.pre[sn];
+        constexpr unsigned UB = NV * ND * sizeof(double), VB = NV * NSD * sizeof(double);
+        static_assert(UB % 16 == 0 && VB % 16 == 0, "bulk prefetch sizes are multiples of 16 bytes");
+        bulk_prefetch_l2(pn->b.U[1 - pn->cur] + cn * (NV * ND), UB);
+        if (pn->b.vstar) {
+          bulk_prefetch_l2(pn->b.U[pn->cur] + cn * (NV * ND), UB);
+          bulk_prefetch_l2(pn->b.vstar + cn * (size_t)(NV * NSD), VB);
+        }
+      }
+    }
     const double dt = *p.b.dt;
     if (!(dt > 0.0)) continue;          // (warp-uniform)
     double c[3] = {0.0, 0.0, 0.0};

@@ -247,12 +247,6 @@ struct TcSweep {
   }
 };
 
-// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2 by the
-// TMA unit (cp.async.bulk.prefetch): no shared memory, nothing to wait for.
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
-}
-
 template <int D, int N, int W, bool TC>
 __global__ void __launch_bounds__(32 * W) k_predictor_split(Batch bt) {
   using DM = Dims<D, N>;

@@ -9,9 +9,10 @@ simulated time; finished runs are retired, which frees memory for waiting
 runs, and the batch is rebuilt whenever its membership changes.  A run that
 takes no step over a whole poll before its end time (no finite positive CFL
 time step, e.g. after a loss of positivity) has failed: with retries left it is
-started again from its initial data at a smaller CFL number (the time step of
-Eq. (cfl) is an upper bound; any smaller step is admissible), else it is
-retired as failed.  Reports the latency of every run (arrival to completion,
+started again from its initial data in the retry precision (FP64 by default)
+and at retry_cfl_factor times its CFL number (the time step of Eq. (cfl) is
+an upper bound; any smaller step is admissible), else it is retired as
+failed.  Reports the latency of every run (arrival to completion,
 retries included) and the aggregate space-time DOF update rate (the steps of
 failed attempts are not counted as work done).
 """
@@ -41,6 +42,7 @@ class RunSpec:
         self.failed = False
         self.attempts = 0          # retries taken
         self.cfl_scale = 1.0       # factor on the workload's CFL number
+        self.prec = None           # precision override of a retried run (None: the server's)
         self.wasted_steps = 0      # steps of failed attempts
 
     @property
@@ -53,9 +55,10 @@ class Server:
     """hbm_budget: bytes of device memory the resident runs may hold."""
 
     def __init__(self, hbm_budget, prec=adg.PREC_MIXED_FP32, steps_per_poll=8, keep_results=False,
-                 stream=0, retries=0, retry_cfl_factor=0.5):
+                 stream=0, retries=0, retry_prec=adg.PREC_FP64, retry_cfl_factor=1.0):
         self.budget = int(hbm_budget)
         self.retries = int(retries)
+        self.retry_prec = retry_prec          # None: keep the server's precision
         self.retry_cfl_factor = float(retry_cfl_factor)
         self.prec = prec
         self.steps_per_poll = steps_per_poll
@@ -63,12 +66,12 @@ class Server:
         self.stream = stream
         self.bytes_cache = {}
 
-    def _key(self, w):
-        return (w["dim"], w["N"], tuple(w["ncell"]))
+    def _key(self, w, prec):
+        return (w["dim"], w["N"], tuple(w["ncell"]), prec)
 
     def _admit(self, r):
         w = r.w
-        s = adg.Solver.from_workload(w, self.prec)
+        s = adg.Solver.from_workload(w, self.prec if r.prec is None else r.prec)
         if self.stream:
             s.set_stream(self.stream)
         s.set_option(adg.OPT_CFL, w["cfl"] * r.cfl_scale)
@@ -76,7 +79,7 @@ class Server:
         s.init_problem(w["problem"])
         r.solver = s
         r.bytes = s.bytes_held()
-        self.bytes_cache[self._key(w)] = r.bytes
+        self.bytes_cache[self._key(w, r.prec)] = r.bytes
 
     def serve(self, runs, clock=time.perf_counter, max_wall=None):
         """Serve `runs` (RunSpec, arrival times in seconds from the start);
@@ -96,7 +99,7 @@ class Server:
                 waiting.clear()
             while waiting and waiting[0].arrival <= now:
                 r = waiting[0]
-                need = self.bytes_cache.get(self._key(r.w), 0)
+                need = self.bytes_cache.get(self._key(r.w, r.prec), 0)
                 if active and used + need > self.budget:
                     break
                 waiting.popleft()
@@ -157,6 +160,8 @@ class Server:
             for r in reversed(retry):
                 r.attempts += 1
                 r.cfl_scale *= self.retry_cfl_factor
+                if self.retry_prec is not None:
+                    r.prec = self.retry_prec
                 r.wasted_steps += r.steps
                 r.steps = 0
                 waiting.appendleft(r)

@@ -24,6 +24,7 @@ class FakeError(RuntimeError):
 class FakeSolver:
     def __init__(self, w, prec):
         self.w = w
+        self.prec = prec
         self.t = 0.0
         self.n = 0
         self.t_end = 0.0
@@ -34,8 +35,11 @@ class FakeSolver:
     @property
     def dt(self):
         # a state whose CFL number is at least w["fake_fail_cfl"] loses
-        # admissibility after three steps
-        if self.cfl is not None and self.cfl >= self.w.get("fake_fail_cfl", np.inf) and self.n >= 3:
+        # admissibility after three steps (only in precision w["fake_fail_prec"]
+        # when that is given)
+        fails_here = self.w.get("fake_fail_prec") in (None, self.prec)
+        if (fails_here and self.cfl is not None and self.cfl >= self.w.get("fake_fail_cfl", np.inf)
+                and self.n >= 3):
             return 0.0
         return self._dt
 
@@ -95,7 +99,7 @@ class FakeBatch:
 
 
 FAKE = types.SimpleNamespace(Solver=FakeSolver, Batch=FakeBatch, OPT_CFL=9, OPT_END_TIME=8,
-                             PREC_MIXED_FP32=1, AdgError=FakeError)
+                             PREC_FP64=0, PREC_MIXED_FP32=1, AdgError=FakeError)
 
 
 class Clock:
@@ -116,9 +120,10 @@ def fake_lib(monkeypatch):
     FakeBatch.built = []
 
 
-def _run(i, dt=0.01, nbytes=100, t_end=0.1, arrival=0.0, shape=None, fail_cfl=np.inf):
+def _run(i, dt=0.01, nbytes=100, t_end=0.1, arrival=0.0, shape=None, fail_cfl=np.inf,
+         fail_prec=None):
     w = {"dim": 2, "N": 3, "ncell": shape or (8 + i, 8), "cfl": 0.1, "problem": None,
-         "fake_dt": dt, "fake_bytes": nbytes, "fake_fail_cfl": fail_cfl}
+         "fake_dt": dt, "fake_bytes": nbytes, "fake_fail_cfl": fail_cfl, "fake_fail_prec": fail_prec}
     return serving.RunSpec(w, t_end, arrival, i)
 
 
@@ -206,11 +211,13 @@ def test_failed_run_is_retried_at_a_smaller_cfl(fake_lib):
     CFL number and finishes; its failed attempt's steps are not counted as
     work, and its latency runs from its arrival."""
     runs = [_run(0), _run(1, fail_cfl=0.1), _run(2)]
-    st = serving.Server(10 ** 9, steps_per_poll=2, retries=1).serve(runs, clock=Clock())
+    st = serving.Server(10 ** 9, steps_per_poll=2, retries=1, retry_prec=None,
+                        retry_cfl_factor=0.5).serve(runs, clock=Clock())
     assert st["runs"] == 3 and st["failed"] == 0
     assert st["retried"] == 1 and st["retried_served"] == 1 and st["retried_ids"] == [1]
     r = runs[1]
-    assert r.attempts == 1 and r.cfl_scale == 0.5 and not r.failed and r.status == 0
+    assert r.attempts == 1 and r.cfl_scale == 0.5 and r.prec is None
+    assert not r.failed and r.status == 0
     assert r.wasted_steps == 3 and r.steps == 10 and st["wasted_steps"] == 3
     assert st["steps"] == 30
     assert st["stdof_updates"] == sum(x.stdofs_per_step * 10 for x in runs)
@@ -221,10 +228,22 @@ def test_run_failing_every_attempt_is_retired_as_failed(fake_lib):
     """A run that fails at every CFL number is retired as failed once its
     retries are spent; without retries it is retired at the first failure."""
     runs = [_run(0, fail_cfl=0.0), _run(1)]
-    st = serving.Server(10 ** 9, steps_per_poll=2, retries=2).serve(runs, clock=Clock())
+    st = serving.Server(10 ** 9, steps_per_poll=2, retries=2,
+                        retry_cfl_factor=0.5).serve(runs, clock=Clock())
     assert st["failed"] == 1 and st["runs"] == 1 and st["failed_ids"] == [0]
     assert runs[0].attempts == 2 and runs[0].cfl_scale == 0.25 and runs[0].status == -6
     assert st["wasted_steps"] == 9 and runs[0].steps == 3
     runs = [_run(0, fail_cfl=0.0)]
     st = serving.Server(10 ** 9, steps_per_poll=2).serve(runs, clock=Clock())
     assert st["failed"] == 1 and runs[0].attempts == 0 and st["retried"] == 0
+
+
+def test_default_retry_restarts_in_fp64_at_the_same_cfl(fake_lib):
+    """Run 1 loses admissibility in mixed precision only: the default retry
+    restarts it in FP64 at its own CFL number, and it finishes."""
+    runs = [_run(0), _run(1, fail_cfl=0.1, fail_prec=1), _run(2)]
+    st = serving.Server(10 ** 9, steps_per_poll=2, retries=1).serve(runs, clock=Clock())
+    assert st["runs"] == 3 and st["failed"] == 0 and st["retried_served"] == 1
+    r = runs[1]
+    assert r.attempts == 1 and r.prec == 0 and r.cfl_scale == 1.0 and r.steps == 10
+    assert all(x.prec is None for x in (runs[0], runs[2]))
