@@ -910,6 +910,18 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
+// Bulk prefetch into L2 of the 16-byte-aligned part of [src, src + bytes), in
+// pieces of at most 4 KB (the bytes outside it, at most 15 at each end, are
+// left to the loads).
+__device__ __forceinline__ void prefetch_range_l2(const void* src, size_t bytes) {
+  const uintptr_t a = (reinterpret_cast<uintptr_t>(src) + 15) & ~(uintptr_t)15;
+  const uintptr_t e = (reinterpret_cast<uintptr_t>(src) + bytes) & ~(uintptr_t)15;
+  for (uintptr_t x = a; x < e; x += 4096) {
+    const uintptr_t len = (e - x < 4096) ? (e - x) : 4096;
+    bulk_prefetch_l2(reinterpret_cast<const void*>(x), (unsigned)len);
+  }
+}
+
 // Key of a wave speed for a max-reduction: a NaN of either sign (an
 // inadmissible state) is the largest key, so the cell's speed is NaN and the
 // CFL step reports the state (ord_key alone would order a NaN with its sign
@@ -1108,6 +1120,20 @@ __global__ void __launch_bounds__(128, 8) k_correct_detect(Batch bt) {
     const int sidx = batch_state(bt, g);
     const Params& p = *bt.pps[sidx];
     const long long cell = g - bt.pre[sidx];
+    if (tid == 0) {
+      // the next cell's DOF blocks and kept averages, into L2 while this one runs
+      const long long gn = g + gridDim.x;
+      if (gn < bt.pre[bt.n]) {
+        const int sn = batch_state(bt, gn);
+        const Params* pn = bt.pps[sn];
+        const long long cn = gn - bt.pre[sn];
+        prefetch_range_l2(pn->b.U[1 - pn->cur] + cn * (NV * ND), NV * ND * sizeof(double));
+        if (pn->b.vstar) {
+          prefetch_range_l2(pn->b.U[pn->cur] + cn * (NV * ND), NV * ND * sizeof(double));
+          prefetch_range_l2(pn->b.vstar + cn * (size_t)(NV * NSD), NV * NSD * sizeof(double));
+        }
+      }
+    }
     const double dt = *p.b.dt;
     if (!(dt > 0.0)) continue;
     double c[3];
