@@ -544,12 +544,13 @@ def run_serving_solo(args):
     from paper_1406_7416_gb300 import adg, build_lib, inputs
     build_lib.build()
     adg.load_library()
-    specs = inputs.serving_runs(count=args.runs)
+    ids = [int(x) for x in args.serving_solo.split(",")]
+    specs = inputs.serving_runs(count=max(args.runs, max(ids) + 1))
     modes = (("fp64", adg.PREC_FP64, {}),
              ("mixed_fp64_subcells", adg.PREC_MIXED_FP32,
               {adg.OPT_SUBCELL_FP32: 0, adg.OPT_SUBCELL_FP64_SWEEPS: 3}),
              ("mixed", adg.PREC_MIXED_FP32, {}))
-    for rid in (int(x) for x in args.serving_solo.split(",")):
+    for rid in ids:
         w = specs[rid]
         t_end = min(w["t_end"], args.t_end)
         for name, prec, opts in modes:
