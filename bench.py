@@ -701,7 +701,7 @@ def main():
     ap.add_argument("--runs", type=int, default=32, help="serving: number of runs")
     ap.add_argument("--t-end", type=float, default=0.02,
                     help="serving: end time cap of every run (each stops at min(cap, its final time))")
-    ap.add_argument("--serving-retries", type=int, default=1,
+    ap.add_argument("--serving-retries", type=int, default=0,
                     help="serving: restarts of a failed run (see --serving-retry-*)")
     ap.add_argument("--serving-retry-prec", default="fp64", choices=["fp64", "same"],
                     help="serving: precision of a restarted run")

@@ -658,13 +658,11 @@ __global__ void __launch_bounds__(32 * LimWarps<D>::W) k_lim_predict_w(Batch bt)
   }
 }
 
-// The same subcell predictor in 2D with the 27 space-time nodes of a subcell
-// held one per lane in registers: the derivative and time contractions take
-// their three operands from the neighbouring lanes by warp shuffles, so a
-// sweep needs no shared memory and no synchronisation; the first sweep, from
-// the time-constant u (x) 1, takes the time operands from the lane itself.  Lane l < 27 holds node
-// (a, b, m) = (l % 3, (l / 3) % 3, l / 9); the operation order of every output
-// is that of picard_flux / picard_deriv_sub / picard_time_sub.
+// Face traces of the 2D subcell predictor, the input of k_lim_flux_t2: for
+// each troubled cell j, axis k, sub-face e normal to k (the enumeration of
+// k_lim_flux) and side (0: the left subcell's trace at its high end, 1: the
+// right subcell's at its low end), 9 points times 4 variables, the point
+// t = (tangential node digit) + 3 (time node).
 template <int N>
 struct SubTraces2 {
   static constexpr int Ns = 2 * N + 1, NFK = (Ns + 1) * Ns, NP = 9;
@@ -674,23 +672,32 @@ struct SubTraces2 {
   }
 };
 
+// The same subcell predictor in 2D in registers, three subcells per warp:
+// lane l < 27 works on subcell l / 9 of the warp's three and holds its spatial
+// node (a, b) = (l % 3, (l / 3) % 3) with the three time nodes.  The space
+// derivatives take their three operands from the lanes on the node's line by
+// warp shuffles; the time solve (Ktau) runs on the lane's own time nodes; the
+// first sweep, from u (x) 1, forms the space term once for the three time
+// nodes.  The operation order of every output is that of picard_flux /
+// picard_deriv_sub / picard_time_sub.  TRACES: the subcell's traces on the
+// sub-faces of the flux kernels (SubTraces2), each evaluated as k_lim_flux
+// evaluates it from the nodal values, instead of the nodal values.
 template <int N, bool TRACES>
 __global__ void __launch_bounds__(256) k_lim_predict_s2(Batch bt) {
   using DM = Dims<2, N>;
   constexpr int NV = 4, NST3 = 27, ND3 = 9, NED = DM::NED, Ns = DM::Ns;
   constexpr int NCROSS = DM::NSD + 4 * DM::NSF;
   const int lane = threadIdx.x & 31;
-  const int l = lane < NST3 ? lane : NST3 - 1;          // idle lanes mirror node 26
-  const int a = l % 3, b = (l / 3) % 3, m = l / 9;
-  // this lane's rows of the operators
-  float da[3], db[3], km[3];
+  const int l = lane < 27 ? lane : 26;                  // idle lanes mirror lane 26
+  const int g = l / 9, node = l - 9 * g;                 // subcell slot, spatial node
+  const int a = node % 3, b = node / 3;
+  float da[3], db[3];
 #pragma unroll
   for (int j = 0; j < 3; ++j) {
     da[j] = c_D3f[a * 3 + j];
     db[j] = c_D3f[b * 3 + j];
-    km[j] = c_K3f[m * 3 + j];
   }
-  const int sx = l - a, sy = l - 3 * b, st = l - 9 * m;   // first lanes of this node's lines
+  const int sx = l - a, sy = l - 3 * b;                 // first lanes of this node's lines
   // the trace weights in FP32, converted once per thread
   float ph0[3], ph1[3];
   {
@@ -703,27 +710,26 @@ __global__ void __launch_bounds__(256) k_lim_predict_s2(Batch bt) {
   }
   const int wpb = blockDim.x >> 5;
   const long long total = bt.pre[bt.n] * NCROSS;
-  for (long long item = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); item < total;
-       item += (long long)gridDim.x * wpb) {
-    const long long tg = item / NCROSS;
+  const long long groups = (total + 2) / 3;
+  for (long long grp = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); grp < groups;
+       grp += (long long)gridDim.x * wpb) {
+    const long long item = grp * 3 + g;
+    const bool live = item < total && lane < 27;
+    const long long tg = item < total ? item / NCROSS : 0;
     const LimItem it = lim_item(bt, tg);
     const Params& p = *bt.pps[it.s];
     const long long j0 = it.j;
-    const int sc = cross_subcell<2, Ns>((int)(item - tg * NCROSS));
+    const int sc = item < total ? cross_subcell<2, Ns>((int)(item - tg * NCROSS)) : 0;
     const float cx = p.b.coef_f[3], cy = p.b.coef_f[4];
     const float gm1 = p.b.coef_f[6];
     const float* Wr = reinterpret_cast<const float*>(p.b.sweep[1]);   // [j][v][NED][ND3]
-    float u[NV], q[NV];
+    float u[NV], q[3][NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      u[v] = Wr[((j0 * NV + v) * NED + sc) * ND3 + (l % ND3)];
-      q[v] = u[v];
-    }
-#pragma unroll 1
-    for (int sweep = 0; sweep < 3; ++sweep) {
+    for (int v = 0; v < NV; ++v) u[v] = item < total ? Wr[((j0 * NV + v) * NED + sc) * ND3 + node] : 1.0f;
+    // S = cx D x F_x + cy D y F_y at this lane's node (picard_deriv_sub's order)
+    auto space_term = [&](const float* Q, float* Sv) {
       float F[2][4];
-      euler_fluxes<2, float>(q, gm1, F);
-      float S[NV];
+      euler_fluxes<2, float>(Q, gm1, F);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         float s = 0.0f;
@@ -747,59 +753,69 @@ __global__ void __launch_bounds__(256) k_lim_predict_s2(Batch bt) {
           acc += db[2] * x2;
           s += cy * acc;
         }
-        S[v] = s;
+        Sv[v] = s;
+      }
+    };
+#pragma unroll 1
+    for (int sweep = 0; sweep < 3; ++sweep) {
+      float S[3][NV];
+      if (sweep == 0) {
+        space_term(u, S[0]);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) S[1][v] = S[2][v] = S[0][v];
+      } else {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) space_term(q[m], S[m]);
       }
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        // the first sweep starts from u (x) 1: the three time nodes of this
-        // lane's spatial node carry the lane's own space term
-        float y0 = S[v], y1 = S[v], y2 = S[v];
-        if (sweep > 0) {
-          y0 = __shfl_sync(0xffffffffu, S[v], st);
-          y1 = __shfl_sync(0xffffffffu, S[v], st + 9);
-          y2 = __shfl_sync(0xffffffffu, S[v], st + 18);
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int jj = 0; jj < 3; ++jj) acc += c_K3f[m * 3 + jj] * S[jj][v];
+          q[m][v] = u[v] - acc;
         }
-        float acc = 0.0f;
-        acc += km[0] * y0;
-        acc += km[1] * y1;
-        acc += km[2] * y2;
-        q[v] = u[v] - acc;
-      }
     }
     if constexpr (!TRACES) {
-      if (lane < NST3) {
+      if (live) {
         float* dst = reinterpret_cast<float*>(p.b.qsub) + ((size_t)j0 * NED + sc) * (size_t)(NV * NST3);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) dst[v * NST3 + l] = q[v];
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+          for (int m = 0; m < 3; ++m) dst[v * NST3 + m * ND3 + node] = q[m][v];
       }
     } else {
-      // the subcell's traces on the sub-faces of the flux kernels (SubTraces2),
-      // each evaluated as k_lim_flux evaluates it from the nodal values
       using TR = SubTraces2<N>;
       float* trc = reinterpret_cast<float*>(p.b.qsub) + (size_t)j0 * TR::per_cell;
       const int cc[2] = {sc % (Ns + 2), sc / (Ns + 2)};
 #pragma unroll
       for (int k = 0; k < 2; ++k) {
         const int o = 1 - k;                              // the tangential axis
-        if (cc[o] < 1 || cc[o] > Ns) continue;            // (uniform over the warp)
+        // (lanes of different subcells disagree here: every lane takes part in
+        // the shuffles and only writes when its subcell has these faces)
+        const bool faces = cc[o] >= 1 && cc[o] <= Ns;
         const int ak = k == 0 ? a : b;
         const int base = k == 0 ? sx : sy;
         const int stk = k == 0 ? 1 : 3;
-        const int t = (k == 0 ? b : a) + 3 * m;           // tangential digit, then time
-        const int ft = (cc[o] - 1) * (k == 0 ? Ns + 1 : 1);
+        const int d = k == 0 ? b : a;                     // tangential digit
+        const int ft = (faces ? cc[o] - 1 : 0) * (k == 0 ? Ns + 1 : 1);
         const int kmul = k == 0 ? 1 : Ns;
-        const bool wr_hi = ak == 2 && cc[k] <= Ns && lane < NST3;
-        const bool wr_lo = ak == 0 && cc[k] >= 1 && lane < NST3;
-        float* hi = trc + TR::offset(k, ft + cc[k] * kmul, 0);
-        float* lo = trc + TR::offset(k, ft + (cc[k] - 1) * kmul, 1);
+        const bool wr_hi = live && faces && ak == 2 && cc[k] <= Ns;
+        const bool wr_lo = live && faces && ak == 0 && cc[k] >= 1;
+        // (offsets clamped into the cell's block when the lane does not write)
+        float* hi = trc + TR::offset(k, ft + (cc[k] <= Ns ? cc[k] : Ns) * kmul, 0);
+        float* lo = trc + TR::offset(k, ft + (cc[k] >= 1 ? cc[k] - 1 : 0) * kmul, 1);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          const float x0 = __shfl_sync(0xffffffffu, q[v], base);
-          const float x1 = __shfl_sync(0xffffffffu, q[v], base + stk);
-          const float x2 = __shfl_sync(0xffffffffu, q[v], base + 2 * stk);
-          if (wr_hi) hi[v * 9 + t] = ph1[0] * x0 + ph1[1] * x1 + ph1[2] * x2;
-          if (wr_lo) lo[v * 9 + t] = ph0[0] * x0 + ph0[1] * x1 + ph0[2] * x2;
-        }
+        for (int m = 0; m < 3; ++m)
+#pragma unroll 2
+          for (int v = 0; v < NV; ++v) {
+            const float x0 = __shfl_sync(0xffffffffu, q[m][v], base);
+            const float x1 = __shfl_sync(0xffffffffu, q[m][v], base + stk);
+            const float x2 = __shfl_sync(0xffffffffu, q[m][v], base + 2 * stk);
+            if (wr_hi) hi[v * 9 + d + 3 * m] = ph1[0] * x0 + ph1[1] * x1 + ph1[2] * x2;
+            if (wr_lo) lo[v * 9 + d + 3 * m] = ph0[0] * x0 + ph0[1] * x1 + ph0[2] * x2;
+          }
       }
     }
   }

@@ -233,7 +233,7 @@ struct Launch {
           if constexpr (D == 2) {
             static_assert(SubTraces2<N>::per_cell <= 2LL * DM::NED * DM::NV * DM::NST3,
                           "the traces fit the subcell predictor's scratch");
-            const long long want = (ncross + 7) / 8;
+            const long long want = ((ncross + 2) / 3 + 7) / 8;      // three subcells per warp
             if (traces) {
               static const int gw = persistent_grid(k_lim_predict_s2<N, true>, 256, 0, 1LL << 40);
               k_lim_predict_s2<N, true><<<(int)(want < gw ? want : gw), 256, 0, s>>>(lim);
