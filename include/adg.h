@@ -216,13 +216,16 @@ extern "C" {
 
 #define ADG_OPT_SUBCELL_REGISTERS 18  /* mixed precision with the FP32 subcell
                                      predictor (the default subcell options): 1
-                                     (default) one warp per subcell with the
-                                     subcell's 27 spatial nodes one per lane and,
-                                     in 2D, its time nodes in the other lanes, in
-                                     3D in each lane's registers (warp shuffles,
-                                     no shared memory); 0: one warp per subcell
-                                     with the nodes in shared memory.  Both give
-                                     the same results bit for bit.              */
+                                     (default) the subcell's space-time nodes in
+                                     registers -- each lane holds a spatial node
+                                     and its three time nodes, three subcells per
+                                     warp in 2D, one in 3D (27 spatial nodes);
+                                     warp shuffles, no shared memory -- and, with
+                                     the Rusanov flux, face traces handed to a
+                                     warp-per-sub-face flux kernel; 0: one warp
+                                     per subcell with the nodes in shared memory
+                                     and the thread-per-sub-face flux kernel.
+                                     Both give the same results bit for bit.    */
 
 #define ADG_FLUX_RUSANOV 0
 #define ADG_FLUX_OSHER 1
