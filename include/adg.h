@@ -44,7 +44,8 @@
  *                        projection of the change (ADG_OPT_PROJECT_DELTA).
  *                        FP32: the subcell scheme's WENO3 reconstruction,
  *                        degree-2 predictor and sub-face fluxes
- *                        (ADG_OPT_SUBCELL_FP32), wave-speed square roots.
+ *                        (ADG_OPT_SUBCELL_FP32); the wave speeds of the CFL
+ *                        step, from the FP64 rho E - |m|^2 / 2.
  *                        Conservation stays at FP64 round-off.
  *   ADG_PREC_MIXED_TF32  ADG_PREC_MIXED_FP32 with the predictor's Picard
  *                        contractions on the tensor pipe (ADG_PRED_WARP4_TC:
