@@ -504,12 +504,17 @@ int adg_unpack_cells(adg_state* st, const int* lo, const int* hi, const void* bu
 /* Arithmetic-pipe rates of the current device (no counterpart in the paper;
  * the step's kernels are bound by these pipes, and they are the denominators
  * the roofline figures are checked against): out[0] FP64 FMA, out[1] FP32 FMA,
- * out[2] FP64 -> FP32 conversion, out[3] FP64 comparison, each in thread
- * operations per second (an FMA is two flop), from 3 timed runs of a
- * dependency-chain kernel over 8 blocks of 256 threads per multiprocessor
- * (best of the last two).  Allocates and frees one scratch buffer;
- * synchronizes the device.  Needs cap >= 4.  Errors: ADG_ERR_ARG,
- * ADG_ERR_OOM, ADG_ERR_CUDA. */
+ * out[2] FP64 -> FP32 conversion, out[3] FP64 comparison, and with cap >= 6
+ * out[4] the FP64 reciprocal by division (1.0 / x) and out[5] the same by the
+ * library's Newton-Raphson form (an FP32 seed and two FP64 steps, used on the
+ * mixed-precision path), each in thread operations per second (an FMA is two
+ * flop), from 3 timed runs of a dependency-chain kernel over 8 blocks of 256
+ * threads per multiprocessor (best of the last two).  With cap >= 8 it also
+ * compares the Newton form with 1.0 / x on 2^22 values (mantissas from a
+ * hash, magnitudes 2^-60 .. 2^60, both signs): out[6] the largest difference
+ * in units of the last place, out[7] the fraction of values that differ.
+ * Allocates and frees scratch buffers; synchronizes the device.  Needs
+ * cap >= 4.  Errors: ADG_ERR_ARG, ADG_ERR_OOM, ADG_ERR_CUDA. */
 int adg_pipe_rates(double* out, int cap);
 
 /* Free every device buffer of the state and the state itself. */

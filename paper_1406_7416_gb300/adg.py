@@ -152,13 +152,16 @@ def _contig(a, dtype):
 
 
 def pipe_rates():
-    """adg_pipe_rates: {pipe: thread operations per second} of the current device."""
+    """adg_pipe_rates: {pipe: thread operations per second} of the current device, and the
+    Newton reciprocal's largest difference from 1.0 / x (ulps) with the fraction that differs."""
     lib = load_library()
-    out = np.zeros(4)
-    rc = lib.adg_pipe_rates(_dptr(out), 4)
+    out = np.zeros(8)
+    rc = lib.adg_pipe_rates(_dptr(out), 8)
     if rc != OK:
         raise AdgError(rc, "adg_pipe_rates failed")
-    return dict(zip(("dfma", "ffma", "f64_to_f32", "f64_compare"), out.tolist()))
+    return dict(zip(("dfma", "ffma", "f64_to_f32", "f64_compare", "f64_reciprocal_div",
+                     "f64_reciprocal_newton", "newton_max_ulp", "newton_differ_fraction"),
+                    out.tolist()))
 
 
 def subcell_update_noalloc(dim, N, gamma, h, dt, patches_ptr, count, vnew_ptr, faces_ptr=0,

@@ -662,10 +662,11 @@ __device__ __forceinline__ void load_trace(const double* blk, int ts, int m, boo
   }
 }
 
-// Euler flux along axis k (FP64).
-template <int D>
+// Euler flux along axis k (FP64); RCP: 1 / rho from rcp_newton (the
+// mixed-precision path's split face flux).
+template <int D, bool RCP = false>
 __device__ __forceinline__ void euler_flux_k(const double* Q, double gm1, int k, double* F) {
-  const double r = 1.0 / Q[0];
+  const double r = RCP ? rcp_newton(Q[0]) : 1.0 / Q[0];
   double kin = 0.0;
 #pragma unroll
   for (int j = 0; j < D; ++j) kin += Q[1 + j] * Q[1 + j];
@@ -724,7 +725,8 @@ __device__ __forceinline__ float speed_split(const float* U, const float* dQ, fl
 // F_k(u) in FP64 once per face node, the per-time-node parts in FP32.
 template <int D, int n>
 __device__ __forceinline__ void face_split_rusanov(const double* bL, const double* bR, int ts, int k,
-                                                   double gamma, const float* wf, double* G) {
+                                                   double gamma, const float* wf, float gf,
+                                                   float gm1f, double* G) {
   constexpr int NV = D + 2, NF = ipow(n, D - 1), NT = NF * n;
   const float* dL = reinterpret_cast<const float*>(bL + NV * NF);
   const float* dR = reinterpret_cast<const float*>(bR + NV * NF);
@@ -735,8 +737,8 @@ __device__ __forceinline__ void face_split_rusanov(const double* bL, const doubl
     uL[v] = bL[v * NF + ts];
     uR[v] = bR[v * NF + ts];
   }
-  euler_flux_k<D>(uL, gm1, k, FL);
-  euler_flux_k<D>(uR, gm1, k, FR);
+  euler_flux_k<D, true>(uL, gm1, k, FL);
+  euler_flux_k<D, true>(uR, gm1, k, FR);
   double kinL = 0.0, kinR = 0.0;
 #pragma unroll
   for (int j = 0; j < D; ++j) {
@@ -756,7 +758,6 @@ __device__ __forceinline__ void face_split_rusanov(const double* bL, const doubl
     sumJ[v] = 0.0f;
   }
   float S = 0.0f;
-  const float gf = (float)gamma, gm1f = (float)gm1;
 #pragma unroll 1
   for (int m = 0; m < n; ++m) {
     float qL[NV], qR[NV], GL[NV], GR[NV];
@@ -834,7 +835,7 @@ __global__ void __launch_bounds__(256, 2) k_faceflux(Batch bt, int k) {
     const bool split = split_traces(p);
     double acc[NV];
     if (split && hasL && hasR && p.flux == ADG_FLUX_RUSANOV) {
-      face_split_rusanov<D, n>(trL, trR, ts, k, p.gamma, p.ops->wf, acc);
+      face_split_rusanov<D, n>(trL, trR, ts, k, p.gamma, p.ops->wf, p.b.coef_f[7], p.b.coef_f[6], acc);
 #pragma unroll
       for (int v = 0; v < NV; ++v) G[(face * NV + v) * NF + ts] = acc[v];
       continue;
