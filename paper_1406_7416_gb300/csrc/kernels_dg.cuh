@@ -1089,9 +1089,10 @@ template <int D, int N>
 __host__ __device__ constexpr size_t correct_smem_bytes() {
   using DM = Dims<D, N>;
   const int big = DM::NSD > DM::ND * 4 ? DM::NSD : DM::ND * 4;
-  // + the FP32 copy of P1 (Ns n floats) for the projection of the step's change
+  // + the face terms' weights (2 d n doubles) and the FP32 copy of P1 (Ns n
+  // floats) for the projection of the step's change
   return (size_t)(2 * DM::NV * (DM::NSD > big ? DM::NSD : big) + DM::Ns * DM::n + 4 * DM::NV + 128 +
-                  (DM::Ns * DM::n + 1) / 2) *
+                  2 * D * DM::n + (DM::Ns * DM::n + 1) / 2) *
          sizeof(double);
 }
 
@@ -1109,7 +1110,8 @@ __global__ void __launch_bounds__(128, 8) k_correct_detect(Batch bt) {
   double* lohi = P1 + Ns * n;         // 2 NV
   double* mm = lohi + 2 * NV;         // 2 NV
   double* red = mm + 2 * NV;          // 128
-  float* P1f = reinterpret_cast<float*>(red + 128);   // Ns * n
+  double* cw = red + 128;             // 2 D n: [k][side][a] dt/dx_k phi_side(a) / w_a
+  float* P1f = reinterpret_cast<float*>(cw + 2 * D * n);   // Ns * n
   const int tid = threadIdx.x, nth = blockDim.x;
   const Ops* o = bt.pps[0]->ops;
   for (int i = tid; i < Ns * n; i += nth) {
@@ -1137,7 +1139,7 @@ __global__ void __launch_bounds__(128, 8) k_correct_detect(Batch bt) {
     }
     const double dt = *p.b.dt;
     if (!(dt > 0.0)) continue;
-    double c[3];
+    double c[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int k = 0; k < D; ++k) c[k] = p.b.coef[k];
     const int nxt = 1 - p.cur;
@@ -1151,6 +1153,14 @@ __global__ void __launch_bounds__(128, 8) k_correct_detect(Batch bt) {
     const double* Un = p.b.U[p.cur] + cell * (NV * ND);
     float* dA = reinterpret_cast<float*>(B);          // FP32 change, then its projection
     float* dB = dA + NV * BUF;
+    // the face terms' weights of this cell's step, one product each (the
+    // previous cell's readers passed several barriers since)
+    for (int q = tid; q < 2 * D * n; q += nth) {
+      const int k = q / (2 * n), r = q - k * 2 * n;
+      const double ck = k == 0 ? c[0] : (k == 1 ? c[1] : c[2]);
+      cw[q] = ck * (r < n ? o->phi0w[r] : o->phi1w[r - n]);
+    }
+    __syncthreads();
     for (int e = tid; e < NV * ND; e += nth) {
       const int v = e / ND, i = e - v * ND;
       double acc = Uo[e];
@@ -1163,7 +1173,9 @@ __global__ void __launch_bounds__(128, 8) k_correct_detect(Batch bt) {
         const long long fhi = face_index<D>(p.geo, ijk, k, ijk[k] + 1);
         const double Glo = p.b.G[k][(flo * NV + v) * NF + ts];
         const double Ghi = p.b.G[k][(fhi * NV + v) * NF + ts];
-        acc -= c[k] * (o->phi1w[ak] * Ghi - o->phi0w[ak] * Glo);
+        // u* -= dt/dx_k (phi1(a)/w_a Ghi - phi0(a)/w_a Glo), as two FMAs
+        acc = fma(-cw[(2 * k + 1) * n + ak], Ghi, acc);
+        acc = fma(cw[2 * k * n + ak], Glo, acc);
       }
       A[e] = acc;
       Uo[e] = acc;
